@@ -1,0 +1,178 @@
+/*
+ * rve.h -- C ABI of the GB300 finite-strain FFT homogenisation solver.
+ *
+ * The library solves the mechanical equilibrium of a periodic cell on a
+ * regular voxel grid with the method of de Geus, Vondrejc, Zeman, Peerlings
+ * and Geers, "Finite strain FFT-based non-linear solvers made simple"
+ * (CMAME 318, 2017):
+ *
+ *   G : P(F) = 0,  <F> = F-bar                      (Eq. weak:discr:FFT, Sec. 3.1)
+ *
+ * by Newton iterations (Algorithm 1) whose linear systems
+ *
+ *   G : K_(i) : dF = rhs                             (Eq. iter:system, Eq. bc:lin)
+ *
+ * are solved matrix-free by conjugate gradients.  G is applied in Fourier
+ * space with the closed-form G-hat of Eq. G; the per-voxel stress P and
+ * tangent K come from the constitutive model (Sec. 4 Saint Venant-Kirchhoff).
+ *
+ * Conventions (all calls):
+ *  - Grids are nx x ny x nz voxels, each size odd (Eq. G is stated for odd
+ *    grids); n = nx*ny*nz.  Voxel v = (x*ny + y)*nz + z (z fastest).
+ *  - Second-order tensor fields are [9][n] float64, component 3*i+j holding
+ *    A_ij; F_ij = dx_i/dX_j (Appendix A).  Fourth-order tangents are [81][n]
+ *    with component ((i*3+j)*3+k)*3+l holding K_ijkl in the convention of
+ *    Eq. iter:varP:  dP_ji = K_ijkl dF_kl.
+ *  - Every function returns RVE_OK (0) or a negative RVE_ERR_* code; the
+ *    text of the last error of a handle is returned by rve_last_error().
+ *  - Pointers passed with an "_on_device" flag of 0 are host memory, with 1
+ *    device memory of the current CUDA device.  Inputs are copied during the
+ *    call; the caller keeps ownership of every array it passes.
+ *  - All device work of a handle is enqueued on the stream given in
+ *    rve_options.stream.  Calls that return host data synchronise that stream.
+ *  - The handle owns its device memory: either one block it allocates with
+ *    cudaMalloc, or the caller's block given in rve_options.workspace (which
+ *    must stay valid until rve_destroy).
+ *  - A handle is not thread safe; distinct handles are independent.
+ */
+#ifndef RVE_H
+#define RVE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define RVE_OK 0
+#define RVE_ERR_INVALID (-1)      /* bad argument: grid, model, pointer, option */
+#define RVE_ERR_CUDA (-2)         /* a CUDA runtime call failed */
+#define RVE_ERR_NOMEM (-3)        /* device allocation failed / workspace too small */
+#define RVE_ERR_CG_MAXIT (-4)     /* CG reached max_cg iterations */
+#define RVE_ERR_CG_BREAKDOWN (-5) /* p.Ap <= 0: tangent not positive on compatible fields */
+#define RVE_ERR_NEWTON_MAXIT (-6) /* Newton reached max_newton iterations */
+#define RVE_ERR_NONFINITE (-7)    /* NaN or Inf in a residual, norm or stress */
+#define RVE_ERR_DETF (-8)         /* det F <= 0 in some voxel */
+#define RVE_ERR_TIMEOUT (-9)      /* a bounded device wait gave up */
+#define RVE_ERR_UNSUPPORTED (-10) /* valid request this build does not implement */
+
+/* constitutive models */
+#define RVE_SVK 0 /* Saint Venant-Kirchhoff (Sec. 4); params per phase: K, mu */
+#define RVE_J2 1  /* finite-strain J2 plasticity (Sec. 5); params: K, mu, tau_y0, H */
+
+/* precision of the CG operator */
+#define RVE_FP64 0  /* everything in float64 */
+#define RVE_MIXED 1 /* CG operator and vectors in float32; residual G:P(F), F and all
+                       reductions in float64 (Newton acts as iterative refinement) */
+
+/* storage of the tangent used by the CG operator */
+#define RVE_TAN_AUTO 0      /* library choice (RECOMPUTE for SVK) */
+#define RVE_TAN_FULL81 1    /* K_ijkl stored, 81 reals per voxel */
+#define RVE_TAN_RECOMPUTE 2 /* SVK: dP = dF.S + F.dS recomputed from F (and S) */
+
+typedef struct rve_s* rve_t;
+
+typedef struct {
+  int precision;        /* RVE_FP64 (default) or RVE_MIXED */
+  int tangent;          /* RVE_TAN_* (default AUTO) */
+  int max_newton;       /* default 50 */
+  int max_cg;           /* default 10000 */
+  double cg_tol_floor;  /* MIXED only: CG tolerance used = max(tol_cg, floor); default 1e-5 */
+  double cg_atol;       /* absolute CG floor: stop when ||r|| <= max(tol ||b||, atol); default 0 */
+  void* stream;         /* cudaStream_t; NULL = legacy default stream */
+  void* workspace;      /* optional caller-owned device memory (see rve_workspace_size) */
+  size_t workspace_bytes;
+} rve_options;
+
+#define RVE_MAX_NEWTON_LOG 64
+
+typedef struct {
+  int status;                              /* return code of the increment */
+  int newton_iters;                        /* linear solves (Algorithm 1 iterations) */
+  int cg_iters_total;
+  int cg_iters[RVE_MAX_NEWTON_LOG];        /* per Newton iteration */
+  double rel_update[RVE_MAX_NEWTON_LOG];   /* ||dF|| / ||F|| per Newton iteration */
+  double residual[RVE_MAX_NEWTON_LOG];     /* ||G:P(F)||, float64, after each update */
+  double elapsed_ms;                       /* device time of the increment (CUDA events) */
+} rve_stats;
+
+/* Fills *opt with the defaults listed above. */
+void rve_default_options(rve_options* opt);
+
+/* Device bytes a handle of this grid/model/options needs (for
+ * rve_options.workspace).  Returns RVE_ERR_INVALID for unsupported grids. */
+int rve_workspace_size(int nx, int ny, int nz, int model, const rve_options* opt, size_t* bytes);
+
+/* Creates a solver for an nx x ny x nz periodic cell with F = I everywhere
+ * (Algorithm 1, first line) and evaluates the constitutive model there.
+ *  phase        : [n] uint8 phase index per voxel (host), or NULL
+ *  nphase       : rows of phase_params (1..256)
+ *  phase_params : [nphase][nparam] float64 (host), nparam = 2 (SVK: K, mu)
+ *                 or 4 (J2: K, mu, tau_y0, H); K is the bulk modulus
+ *                 (lambda = K - 2 mu / 3, Eq. elas:C)
+ *  voxel_params : [nparam][n] float64 (host) per-voxel parameters, used
+ *                 when phase is NULL
+ *  opt          : may be NULL (defaults)
+ * Errors: RVE_ERR_INVALID (even or non-positive sizes, bad model, phase index
+ * >= nphase, missing parameters), RVE_ERR_NOMEM, RVE_ERR_CUDA. */
+int rve_create(rve_t* out, int nx, int ny, int nz, int model, int nphase, const uint8_t* phase,
+               const double* phase_params, const double* voxel_params, const rve_options* opt);
+
+/* Releases all device memory of the handle (not a caller workspace). */
+void rve_destroy(rve_t h);
+
+/* Prescribes the macroscopic deformation gradient F-bar (row-major, host).
+ * The next increment applies dF-bar = F-bar - <F> (Sec. 3.1). */
+int rve_set_macro_F(rve_t h, const double Fbar[9]);
+
+/* One load increment (Algorithm 1): tangent of the last converged state,
+ * predictor G:K:dF = -G:K:dF-bar (Eq. bc:lin), then Newton iterations
+ * dF from G:K:dF = -G:P (Eq. iter:system) until ||dF||/||F|| < tol_newton
+ * after at least two linear solves; each CG solve stops at
+ * ||r|| <= max(tol_cg ||b||, cg_atol).  On success the state is committed;
+ * on failure F and the history return to the last committed state and the
+ * error code is returned.  st may be NULL. */
+int rve_solve_increment(rve_t h, double tol_newton, double tol_cg, rve_stats* st);
+
+/* Copies F, P (each [9][n] float64) or the tangent K ([81][n] float64,
+ * evaluated in float64 at the current F) to dst (host or device). */
+int rve_get_F(rve_t h, double* dst, int dst_on_device);
+int rve_get_P(rve_t h, double* dst, int dst_on_device);
+int rve_get_K4(rve_t h, double* dst, int dst_on_device);
+
+/* Homogenised first Piola-Kirchhoff stress P-bar = <P> (voxel average),
+ * row-major, host. */
+int rve_homogenized_P(rve_t h, double Pbar[9]);
+
+/* Replaces the deformation field F ([9][n] float64) and re-evaluates P and
+ * K there.  The new field becomes the committed state. */
+int rve_set_F(rve_t h, const double* F, int src_on_device);
+
+/* out = G : (K : dF) -- one application of the CG operator with the current
+ * tangent, in the handle's CG precision (float32 when MIXED).  dF and out are
+ * [9][n] float64, both on the host or both on the device. */
+int rve_apply_operator(rve_t h, const double* dF, double* out, int on_device);
+
+/* out = G : A in float64 (Eq. weak:discr:FFT-intermediate).  A and out are
+ * [9][n] float64, both on the host or both on the device. */
+int rve_project(rve_t h, const double* A, double* out, int on_device);
+
+/* Text of the last error of h (never NULL); rve_status_string maps a code. */
+const char* rve_last_error(rve_t h);
+const char* rve_status_string(int code);
+
+/* Instrumentation: number of kernels this handle has launched, and optional
+ * CUDA-event timing of every launch of one kernel family
+ * (0 zfwd, 1 fft_y fwd, 2 fft_x+projection, 3 fft_y inv, 4 zinv, 5 cg_update).
+ * rve_kernel_time returns the summed milliseconds and launches since the
+ * timing was enabled (synchronises the stream). */
+int rve_launch_count(rve_t h, long long* count);
+int rve_kernel_timing(rve_t h, int family, int enable);
+int rve_kernel_time(rve_t h, double* total_ms, long long* launches);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RVE_H */

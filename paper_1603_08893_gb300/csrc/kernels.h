@@ -1,0 +1,86 @@
+// Host-side launchers of the device kernels (implemented in the .cu files).
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "common.cuh"
+#include "fft.cuh"
+
+// tangent storage modes
+enum { TAN_FULL81 = 1, TAN_SVK = 2 };
+// sources of the forward pass input
+enum { SRC_FIELD = 0, SRC_CGP = 1, SRC_UNIFORM = 2 };
+// outputs of the inverse z pass
+enum { OUT_PLAIN = 0, OUT_CGAP = 1, OUT_RESID = 2 };
+
+struct GridGeom {
+  int nx, ny, nz;
+  int hz, hzp;        // nz/2+1 and its padded row length
+  size_t n;           // nx*ny*nz
+  size_t sstride;     // nx*ny*hzp (complex elements per spectrum component)
+  AxisPlan px, py, pz;
+  int lz_f, lz_d;     // z lines per CTA (float, double)
+  int ty_f, ty_d, gy_f, gy_d;  // y tile (kz) and groups per CTA
+  int tx_f, tx_d;     // x tile (kz)
+};
+
+template <typename R>
+struct TangentView {
+  int mode;           // TAN_FULL81 / TAN_SVK / 0 (plain copy)
+  const R* K4;        // [81][n]
+  const R* Fop;       // [9][n]
+  const R* Sop;       // [6][n] or null (compute S from F)
+  MatView<R> mat;     // lambda, mu
+};
+
+template <typename R>
+struct Twiddles {
+  const cplx<R>* x;
+  const cplx<R>* y;
+  const cplx<R>* z;
+};
+
+// Forward transform chain front: (optional p-update) -> tangent -> R2C along z.
+template <typename R>
+void launch_zfwd(const GridGeom& g, int src, const TangentView<R>& tan, const R* field, const R* r,
+                 R* p, const double* unif, const SolverState* st, const int* done, cplx<R>* spec,
+                 const Twiddles<R>& tw, cudaStream_t s);
+template <typename R>
+void launch_fft_y(const GridGeom& g, bool inverse, cplx<R>* spec, const int* done,
+                  const Twiddles<R>& tw, cudaStream_t s);
+template <typename R>
+void launch_fft_x_proj(const GridGeom& g, double scale, cplx<R>* spec, const int* done,
+                       const Twiddles<R>& tw, cudaStream_t s);
+// Inverse z transform and output stage.
+template <typename R, typename RC>
+void launch_zinv(const GridGeom& g, int out, const cplx<R>* spec, R* dst, RC* r_out, RC* x_out,
+                 const RC* p_in, SolverState* st, double* partials, const int* done,
+                 const Twiddles<R>& tw, cudaStream_t s);
+
+cudaError_t fft_kernels_init();  // opt-in to large dynamic shared memory
+size_t fft_max_blocks(const GridGeom& g);
+
+// ---- vector / material kernels (kernels_mat.cu) ----
+template <typename R>
+void launch_cg_update(size_t n9, R* x, R* r, const R* p, const R* Ap, SolverState* st,
+                      double* partials, cudaStream_t s);
+template <typename T>
+void launch_mean9(const T* A, size_t n, double* out9, double* partials, unsigned int* counter,
+                  int post, SolverState* st, cudaStream_t s);
+void launch_add_uniform(double* F, size_t n, SolverState* st, double* partials, cudaStream_t s);
+template <typename RC>
+void launch_newton_update(double* F, const RC* x, size_t n, SolverState* st, double* partials,
+                          cudaStream_t s);
+template <typename RO>
+void launch_svk_constitutive(const double* F, size_t n, MatView<double> mat, double* P,
+                             int tan_mode, RO* K4, RO* Fop, RO* Sop, SolverState* st,
+                             cudaStream_t s);
+void launch_svk_k4_full(const double* F, size_t v0, size_t count, size_t n,
+                        MatView<double> mat, double* dst, cudaStream_t s);
+template <typename Ti, typename To>
+void launch_convert(const Ti* in, To* out, size_t count, cudaStream_t s);
+size_t vec_max_blocks();
+
+// mean9 post-processing modes
+enum { MEAN_PLAIN = 0, MEAN_DFBAR = 1, MEAN_X = 2, MEAN_PBAR = 3 };

@@ -1,0 +1,570 @@
+// FFT pass kernels of the projected tangent operator  p -> G : (K : p)
+// (Eq. iter:system; G-hat of Eq. G, applied in the reduced form of
+// Eq. G_red).  Fields are component-major [9][nx][ny][nz] (z fastest); the
+// half spectrum is [9][nx][ny][hzp] complex with kz in [0, nz/2].
+//
+//   zfwd   : per z-line: CG direction update, tangent contraction K : p,
+//            then a real-to-complex DFT along z (two real components are
+//            packed into one complex line and split by Hermitian symmetry).
+//   fft_y  : complex DFT along y on (kz-tile x ny) tiles.
+//   fft_x  : forward DFT along x, projection, inverse DFT along x, on
+//            (kz-tile x nx x 9 components) tiles that stay in shared memory.
+//   zinv   : complex-to-real inverse DFT along z and the output stage
+//            (plain copy, CG product p.Ap, or residual / CG initialisation).
+#include "kernels.h"
+
+#define FFT_THREADS 256
+
+template <typename R>
+RVE_DEV R signed_freq(int k, int n) {
+  return (R)((k <= (n - 1) / 2) ? k : k - n);
+}
+
+// --------------------------------------------------------------------------
+// Input stage: tangent contraction of one voxel.
+//   FULL81: out_(3a+b) = (K : in)_ab = sum_kl K_(b a k l) in_(3k+l)
+//           (delta P_ji = K_ijkl delta F_kl, Eq. iter:varP)
+//   SVK   : linearisation of P = F.S with S = lambda tr(E) I + 2 mu E:
+//           dP = dF.S + F.(lambda tr(dE) I + 2 mu dE), dE = sym(F^T dF)
+// --------------------------------------------------------------------------
+template <typename R>
+RVE_DEV void tangent_voxel(const TangentView<R>& T, size_t v, size_t n, const R (&in)[9],
+                           R (&out)[9]) {
+  if (T.mode == TAN_FULL81) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        R s = 0;
+#pragma unroll
+        for (int kl = 0; kl < 9; ++kl) s = fma(__ldg(T.K4 + (size_t)((b * 3 + a) * 9 + kl) * n + v), in[kl], s);
+        out[3 * a + b] = s;
+      }
+  } else if (T.mode == TAN_SVK) {
+    R F[9];
+#pragma unroll
+    for (int c = 0; c < 9; ++c) F[c] = __ldg(T.Fop + (size_t)c * n + v);
+    const R lam = T.mat.get(v, 0), mu = T.mat.get(v, 1);
+    R S[3][3];
+    if (T.Sop) {
+      const R s0 = __ldg(T.Sop + v), s1 = __ldg(T.Sop + n + v), s2 = __ldg(T.Sop + 2 * n + v);
+      const R s3 = __ldg(T.Sop + 3 * n + v), s4 = __ldg(T.Sop + 4 * n + v), s5 = __ldg(T.Sop + 5 * n + v);
+      S[0][0] = s0; S[1][1] = s1; S[2][2] = s2;
+      S[0][1] = S[1][0] = s3; S[0][2] = S[2][0] = s4; S[1][2] = S[2][1] = s5;
+    } else {
+      R E[3][3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+          R c = F[a] * F[b] + F[3 + a] * F[3 + b] + F[6 + a] * F[6 + b];
+          E[a][b] = R(0.5) * (c - (a == b ? R(1) : R(0)));
+        }
+      const R tr = E[0][0] + E[1][1] + E[2][2];
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) S[a][b] = 2 * mu * E[a][b] + (a == b ? lam * tr : R(0));
+    }
+    // dE = sym(F^T in)
+    R dE[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        const R fa = F[a] * in[b] + F[3 + a] * in[3 + b] + F[6 + a] * in[6 + b];
+        const R fb = F[b] * in[a] + F[3 + b] * in[3 + a] + F[6 + b] * in[6 + a];
+        dE[a][b] = R(0.5) * (fa + fb);
+      }
+    const R trd = dE[0][0] + dE[1][1] + dE[2][2];
+    R dS[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) dS[a][b] = 2 * mu * dE[a][b] + (a == b ? lam * trd : R(0));
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        R s = 0;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) s += in[3 * a + c] * S[c][b] + F[3 * a + c] * dS[c][b];
+        out[3 * a + b] = s;
+      }
+  } else {
+#pragma unroll
+    for (int c = 0; c < 9; ++c) out[c] = in[c];
+  }
+}
+
+template <typename R>
+struct ZfwdParams {
+  GridGeom g;
+  int lz;
+  int src;
+  TangentView<R> tan;
+  const R* field;
+  const R* r;
+  R* p;
+  const double* unif;
+  const SolverState* st;
+  const int* done;
+  cplx<R>* spec;
+  const cplx<R>* tw;
+};
+
+template <typename R, int SRC, int TAN>
+__global__ void __launch_bounds__(FFT_THREADS) k_zfwd(const ZfwdParams<R> P) {
+  if (P.done && *P.done) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int nz = P.g.nz, lz = P.lz;
+  cplx<R>* tw = reinterpret_cast<cplx<R>*>(smem_raw);
+  cplx<R>* buf = tw + nz;  // [5][lz][nz]
+  for (int i = threadIdx.x; i < nz; i += blockDim.x) tw[i] = P.tw[i];
+  const size_t n = P.g.n;
+  const int nlines = P.g.nx * P.g.ny;
+  const int l0 = blockIdx.x * lz;
+  const int nl = min(lz, nlines - l0);
+  const int nvox = nl * nz;
+  const size_t v0 = (size_t)l0 * nz;
+  R beta = 0;
+  bool first = true;
+  if (SRC == SRC_CGP) {
+    first = (P.st->it == 0);
+    beta = (R)P.st->beta;
+  }
+  TangentView<R> T = P.tan;
+  T.mode = TAN;
+  for (int i = threadIdx.x; i < lz * nz; i += blockDim.x) {
+    R in[9], out[9];
+    if (i < nvox) {
+      const size_t v = v0 + i;
+      if (SRC == SRC_FIELD) {
+#pragma unroll
+        for (int c = 0; c < 9; ++c) in[c] = P.field[(size_t)c * n + v];
+      } else if (SRC == SRC_CGP) {
+#pragma unroll
+        for (int c = 0; c < 9; ++c) {
+          const R rr = P.r[(size_t)c * n + v];
+          const R pp = first ? rr : fma(beta, P.p[(size_t)c * n + v], rr);
+          P.p[(size_t)c * n + v] = pp;
+          in[c] = pp;
+        }
+      } else {
+#pragma unroll
+        for (int c = 0; c < 9; ++c) in[c] = (R)P.unif[c];
+      }
+      tangent_voxel<R>(T, v, n, in, out);
+    } else {
+#pragma unroll
+      for (int c = 0; c < 9; ++c) out[c] = 0;
+    }
+#pragma unroll
+    for (int k = 0; k < 5; ++k)
+      buf[k * lz * nz + i] = {out[2 * k], (2 * k + 1 < 9) ? out[2 * k + 1] : R(0)};
+  }
+  __syncthreads();
+  const LineMap lm{1 << 30, 0, nz, 1, 0};
+  fft_lines<R, false>(buf, lm, 5 * lz, P.g.pz, tw);
+  const int hz = P.g.hz, hzp = P.g.hzp;
+  const size_t ss = P.g.sstride;
+  for (int i = threadIdx.x; i < 5 * nl * hz; i += blockDim.x) {
+    const int kz = i % hz;
+    const int rest = i / hz;
+    const int li = rest % nl;
+    const int k = rest / nl;
+    const cplx<R> z1 = buf[(k * lz + li) * nz + kz];
+    cplx<R> z2 = buf[(k * lz + li) * nz + (kz ? nz - kz : 0)];
+    z2.y = -z2.y;
+    const size_t o = (size_t)(l0 + li) * hzp + kz;
+    P.spec[(size_t)(2 * k) * ss + o] = {R(0.5) * (z1.x + z2.x), R(0.5) * (z1.y + z2.y)};
+    if (2 * k + 1 < 9) {
+      // B = (z1 - conj(z_-k)) / (2i)
+      const R dx = R(0.5) * (z1.x - z2.x), dy = R(0.5) * (z1.y - z2.y);
+      P.spec[(size_t)(2 * k + 1) * ss + o] = {dy, -dx};
+    }
+  }
+}
+
+template <typename R>
+struct LineParams {
+  GridGeom g;
+  int t, grp;  // kz tile and groups (y pass)
+  double scale;
+  cplx<R>* spec;
+  const int* done;
+  const cplx<R>* tw;
+};
+
+template <typename R, bool INV>
+__global__ void __launch_bounds__(FFT_THREADS) k_fft_y(const LineParams<R> P) {
+  if (P.done && *P.done) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int ny = P.g.ny, T = P.t;
+  cplx<R>* tw = reinterpret_cast<cplx<R>*>(smem_raw);
+  cplx<R>* buf = tw + ny;  // [grp][ny][T]
+  for (int i = threadIdx.x; i < ny; i += blockDim.x) tw[i] = P.tw[i];
+  const int ngroups = 9 * P.g.nx;
+  const int k0 = blockIdx.x * T;
+  const int g0 = blockIdx.y * P.grp;
+  const int ng = min(P.grp, ngroups - g0);
+  const int tc = min(T, P.g.hz - k0);
+  const int hzp = P.g.hzp;
+  const int tot = ng * ny * T;
+  for (int i = threadIdx.x; i < tot; i += blockDim.x) {
+    const int t = i % T;
+    const int y = (i / T) % ny;
+    const int gg = i / (T * ny);
+    buf[i] = (t < tc) ? P.spec[((size_t)(g0 + gg) * ny + y) * hzp + k0 + t] : cplx<R>{R(0), R(0)};
+  }
+  __syncthreads();
+  const LineMap lm{T, ny * T, 1, T, 1};
+  fft_lines<R, INV>(buf, lm, ng * T, P.g.py, tw);
+  for (int i = threadIdx.x; i < tot; i += blockDim.x) {
+    const int t = i % T;
+    const int y = (i / T) % ny;
+    const int gg = i / (T * ny);
+    if (t < tc) P.spec[((size_t)(g0 + gg) * ny + y) * hzp + k0 + t] = buf[i];
+  }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(FFT_THREADS) k_fft_x_proj(const LineParams<R> P) {
+  if (P.done && *P.done) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int nx = P.g.nx, ny = P.g.ny, T = P.t;
+  cplx<R>* tw = reinterpret_cast<cplx<R>*>(smem_raw);
+  cplx<R>* buf = tw + nx;  // [9][nx][T]
+  for (int i = threadIdx.x; i < nx; i += blockDim.x) tw[i] = P.tw[i];
+  const int y = blockIdx.y;
+  const int k0 = blockIdx.x * T;
+  const int tc = min(T, P.g.hz - k0);
+  const int hzp = P.g.hzp;
+  const size_t ss = P.g.sstride;
+  const int tot = 9 * nx * T;
+  for (int i = threadIdx.x; i < tot; i += blockDim.x) {
+    const int t = i % T;
+    const int x = (i / T) % nx;
+    const int c = i / (T * nx);
+    buf[i] = (t < tc) ? P.spec[(size_t)c * ss + ((size_t)x * ny + y) * hzp + k0 + t]
+                      : cplx<R>{R(0), R(0)};
+  }
+  __syncthreads();
+  const LineMap lm{T, nx * T, 1, T, 1};
+  fft_lines<R, false>(buf, lm, 9 * T, P.g.px, tw);
+  // projection  A_ij <- xi_j (sum_l xi_l A_il) / |xi|^2, zero at q = 0,
+  // times the normalisation of the inverse transform (Eq. G_red).
+  const R qy = signed_freq<R>(y, ny) / (R)ny;
+  const R sc = (R)P.scale;
+  for (int i = threadIdx.x; i < nx * T; i += blockDim.x) {
+    const int t = i % T;
+    const int x = i / T;
+    const R qx = signed_freq<R>(x, nx) / (R)nx;
+    const R qz = (R)(k0 + t) / (R)P.g.nz;
+    const R q2 = qx * qx + qy * qy + qz * qz;
+    const R f = (q2 > R(0)) ? sc / q2 : R(0);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const cplx<R> A0 = buf[(3 * a + 0) * nx * T + i];
+      const cplx<R> A1 = buf[(3 * a + 1) * nx * T + i];
+      const cplx<R> A2 = buf[(3 * a + 2) * nx * T + i];
+      const R sx = f * (qx * A0.x + qy * A1.x + qz * A2.x);
+      const R sy = f * (qx * A0.y + qy * A1.y + qz * A2.y);
+      buf[(3 * a + 0) * nx * T + i] = {sx * qx, sy * qx};
+      buf[(3 * a + 1) * nx * T + i] = {sx * qy, sy * qy};
+      buf[(3 * a + 2) * nx * T + i] = {sx * qz, sy * qz};
+    }
+  }
+  __syncthreads();
+  fft_lines<R, true>(buf, lm, 9 * T, P.g.px, tw);
+  for (int i = threadIdx.x; i < tot; i += blockDim.x) {
+    const int t = i % T;
+    const int x = (i / T) % nx;
+    const int c = i / (T * nx);
+    if (t < tc) P.spec[(size_t)c * ss + ((size_t)x * ny + y) * hzp + k0 + t] = buf[i];
+  }
+}
+
+template <typename R, typename RC>
+struct ZinvParams {
+  GridGeom g;
+  int lz;
+  const cplx<R>* spec;
+  R* dst;
+  RC* r_out;
+  RC* x_out;
+  const RC* p_in;
+  SolverState* st;
+  double* partials;
+  const int* done;
+  const cplx<R>* tw;
+};
+
+template <typename R, typename RC, int OUT>
+__global__ void __launch_bounds__(FFT_THREADS) k_zinv(const ZinvParams<R, RC> P) {
+  if (P.done && *P.done) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int nz = P.g.nz, lz = P.lz, hz = P.g.hz, hzp = P.g.hzp;
+  cplx<R>* tw = reinterpret_cast<cplx<R>*>(smem_raw);
+  cplx<R>* buf = tw + nz;  // [5][lz][nz]
+  for (int i = threadIdx.x; i < nz; i += blockDim.x) tw[i] = P.tw[i];
+  const size_t n = P.g.n;
+  const size_t ss = P.g.sstride;
+  const int nlines = P.g.nx * P.g.ny;
+  const int l0 = blockIdx.x * lz;
+  const int nl = min(lz, nlines - l0);
+  // rebuild the full z spectrum of the packed lines z = a + i b
+  for (int i = threadIdx.x; i < 5 * lz * hz; i += blockDim.x) {
+    const int kz = i % hz;
+    const int rest = i / hz;
+    const int li = rest % lz;
+    const int k = rest / lz;
+    cplx<R> A = {R(0), R(0)}, B = {R(0), R(0)};
+    if (li < nl) {
+      const size_t o = (size_t)(l0 + li) * hzp + kz;
+      A = P.spec[(size_t)(2 * k) * ss + o];
+      if (2 * k + 1 < 9) B = P.spec[(size_t)(2 * k + 1) * ss + o];
+    }
+    cplx<R>* line = buf + (k * lz + li) * nz;
+    line[kz] = {A.x - B.y, A.y + B.x};
+    if (kz > 0) line[nz - kz] = {A.x + B.y, B.x - A.y};
+  }
+  __syncthreads();
+  const LineMap lm{1 << 30, 0, nz, 1, 0};
+  fft_lines<R, true>(buf, lm, 5 * lz, P.g.pz, tw);
+  const size_t v0 = (size_t)l0 * nz;
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < nl * nz; i += blockDim.x) {
+    R out[9];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+      const cplx<R> z = buf[k * lz * nz + i];
+      out[2 * k] = z.x;
+      if (2 * k + 1 < 9) out[2 * k + 1] = z.y;
+    }
+    const size_t v = v0 + i;
+    if (OUT == OUT_PLAIN) {
+#pragma unroll
+      for (int c = 0; c < 9; ++c) P.dst[(size_t)c * n + v] = out[c];
+    } else if (OUT == OUT_CGAP) {
+      R s = 0;
+#pragma unroll
+      for (int c = 0; c < 9; ++c) {
+        P.dst[(size_t)c * n + v] = out[c];
+        s = fma((R)P.p_in[(size_t)c * n + v], out[c], s);
+      }
+      acc += (double)s;
+    } else {
+      R s = 0;
+#pragma unroll
+      for (int c = 0; c < 9; ++c) {
+        P.r_out[(size_t)c * n + v] = (RC)out[c];
+        P.x_out[(size_t)c * n + v] = (RC)0;
+        s = fma(out[c], out[c], s);
+      }
+      acc += (double)s;
+    }
+  }
+  if (OUT == OUT_PLAIN) return;
+  double v1[1] = {acc}, tot[1];
+  const int slot = (OUT == OUT_CGAP) ? SLOT_PAP : SLOT_BB;
+  if (last_block_sum<1>(v1, P.partials, &P.st->counter[slot], tot) && threadIdx.x == 0) {
+    SolverState* st = P.st;
+    if (OUT == OUT_CGAP) {
+      const double pap = tot[0];
+      st->pAp = pap;
+      if (!isfinite(pap)) {
+        st->status = RVE_DEV_ERR_NONFINITE;
+        st->done = 1;
+      } else if (!(pap > 0.0)) {
+        st->status = RVE_DEV_ERR_CG_BREAKDOWN;
+        st->done = 1;
+      } else {
+        st->alpha = st->rr / pap;
+      }
+    } else {
+      const double bb = tot[0];
+      st->bb = bb;
+      st->rr = bb;
+      st->it = 0;
+      st->beta = 0.0;
+      st->status = 0;
+      st->tol2 = fmax(st->cg_tol * st->cg_tol * bb, st->cg_atol * st->cg_atol);
+      st->done = (bb == 0.0) ? 1 : 0;
+      if (!isfinite(bb)) {
+        st->status = RVE_DEV_ERR_NONFINITE;
+        st->done = 1;
+      }
+    }
+  }
+}
+
+// --------------------------------------------------------------------------
+// launchers
+// --------------------------------------------------------------------------
+template <typename R>
+static int lz_of(const GridGeom& g) { return sizeof(R) == 4 ? g.lz_f : g.lz_d; }
+
+template <typename R>
+void launch_zfwd(const GridGeom& g, int src, const TangentView<R>& tan, const R* field, const R* r,
+                 R* p, const double* unif, const SolverState* st, const int* done, cplx<R>* spec,
+                 const Twiddles<R>& tw, cudaStream_t s) {
+  ZfwdParams<R> P;
+  P.g = g;
+  P.lz = lz_of<R>(g);
+  P.src = src;
+  P.tan = tan;
+  P.field = field;
+  P.r = r;
+  P.p = p;
+  P.unif = unif;
+  P.st = st;
+  P.done = done;
+  P.spec = spec;
+  P.tw = tw.z;
+  const int nlines = g.nx * g.ny;
+  const dim3 grid((nlines + P.lz - 1) / P.lz);
+  const size_t sm = sizeof(cplx<R>) * ((size_t)g.nz + 5 * (size_t)P.lz * g.nz);
+#define ZF(S, T) k_zfwd<R, S, T><<<grid, FFT_THREADS, sm, s>>>(P)
+  const int tm = tan.mode;
+  if (src == SRC_FIELD) {
+    if (tm == TAN_FULL81) ZF(SRC_FIELD, TAN_FULL81);
+    else if (tm == TAN_SVK) ZF(SRC_FIELD, TAN_SVK);
+    else ZF(SRC_FIELD, 0);
+  } else if (src == SRC_CGP) {
+    if (tm == TAN_FULL81) ZF(SRC_CGP, TAN_FULL81);
+    else ZF(SRC_CGP, TAN_SVK);
+  } else {
+    if (tm == TAN_FULL81) ZF(SRC_UNIFORM, TAN_FULL81);
+    else ZF(SRC_UNIFORM, TAN_SVK);
+  }
+#undef ZF
+}
+
+template <typename R>
+void launch_fft_y(const GridGeom& g, bool inverse, cplx<R>* spec, const int* done,
+                  const Twiddles<R>& tw, cudaStream_t s) {
+  LineParams<R> P;
+  P.g = g;
+  P.t = sizeof(R) == 4 ? g.ty_f : g.ty_d;
+  P.grp = sizeof(R) == 4 ? g.gy_f : g.gy_d;
+  P.scale = 1.0;
+  P.spec = spec;
+  P.done = done;
+  P.tw = tw.y;
+  const dim3 grid((g.hz + P.t - 1) / P.t, (9 * g.nx + P.grp - 1) / P.grp);
+  const size_t sm = sizeof(cplx<R>) * ((size_t)g.ny + (size_t)P.grp * g.ny * P.t);
+  if (inverse) k_fft_y<R, true><<<grid, FFT_THREADS, sm, s>>>(P);
+  else k_fft_y<R, false><<<grid, FFT_THREADS, sm, s>>>(P);
+}
+
+template <typename R>
+void launch_fft_x_proj(const GridGeom& g, double scale, cplx<R>* spec, const int* done,
+                       const Twiddles<R>& tw, cudaStream_t s) {
+  LineParams<R> P;
+  P.g = g;
+  P.t = sizeof(R) == 4 ? g.tx_f : g.tx_d;
+  P.grp = 1;
+  P.scale = scale;
+  P.spec = spec;
+  P.done = done;
+  P.tw = tw.x;
+  const dim3 grid((g.hz + P.t - 1) / P.t, g.ny);
+  const size_t sm = sizeof(cplx<R>) * ((size_t)g.nx + 9 * (size_t)g.nx * P.t);
+  k_fft_x_proj<R><<<grid, FFT_THREADS, sm, s>>>(P);
+}
+
+template <typename R, typename RC>
+void launch_zinv(const GridGeom& g, int out, const cplx<R>* spec, R* dst, RC* r_out, RC* x_out,
+                 const RC* p_in, SolverState* st, double* partials, const int* done,
+                 const Twiddles<R>& tw, cudaStream_t s) {
+  ZinvParams<R, RC> P;
+  P.g = g;
+  P.lz = lz_of<R>(g);
+  P.spec = spec;
+  P.dst = dst;
+  P.r_out = r_out;
+  P.x_out = x_out;
+  P.p_in = p_in;
+  P.st = st;
+  P.partials = partials;
+  P.done = done;
+  P.tw = tw.z;
+  const int nlines = g.nx * g.ny;
+  const dim3 grid((nlines + P.lz - 1) / P.lz);
+  const size_t sm = sizeof(cplx<R>) * ((size_t)g.nz + 5 * (size_t)P.lz * g.nz);
+  if (out == OUT_PLAIN) k_zinv<R, RC, OUT_PLAIN><<<grid, FFT_THREADS, sm, s>>>(P);
+  else if (out == OUT_CGAP) k_zinv<R, RC, OUT_CGAP><<<grid, FFT_THREADS, sm, s>>>(P);
+  else k_zinv<R, RC, OUT_RESID><<<grid, FFT_THREADS, sm, s>>>(P);
+}
+
+size_t fft_max_blocks(const GridGeom& g) {
+  const size_t nlines = (size_t)g.nx * g.ny;
+  const int lz = g.lz_f < g.lz_d ? g.lz_f : g.lz_d;
+  return (nlines + lz - 1) / lz;
+}
+
+// Dynamic shared memory of these kernels stays below 200 KB (checked when the
+// grid geometry is built); the opt-in limit leaves room for static shared
+// memory (reduction scratch) within the 227 KB per block.
+static cudaError_t g_init_err = cudaSuccess;
+
+template <typename K>
+static void allow_big_smem(K kernel) {
+  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 208 * 1024);
+  if (e != cudaSuccess && g_init_err == cudaSuccess) g_init_err = e;
+}
+
+template <typename R>
+static void init_r() {
+  allow_big_smem(k_zfwd<R, SRC_FIELD, TAN_FULL81>);
+  allow_big_smem(k_zfwd<R, SRC_FIELD, TAN_SVK>);
+  allow_big_smem(k_zfwd<R, SRC_FIELD, 0>);
+  allow_big_smem(k_zfwd<R, SRC_CGP, TAN_FULL81>);
+  allow_big_smem(k_zfwd<R, SRC_CGP, TAN_SVK>);
+  allow_big_smem(k_zfwd<R, SRC_UNIFORM, TAN_FULL81>);
+  allow_big_smem(k_zfwd<R, SRC_UNIFORM, TAN_SVK>);
+  allow_big_smem(k_fft_y<R, true>);
+  allow_big_smem(k_fft_y<R, false>);
+  allow_big_smem(k_fft_x_proj<R>);
+}
+
+cudaError_t fft_kernels_init() {
+  g_init_err = cudaSuccess;
+  init_r<float>();
+  init_r<double>();
+  allow_big_smem(k_zinv<double, double, OUT_PLAIN>);
+  allow_big_smem(k_zinv<double, double, OUT_CGAP>);
+  allow_big_smem(k_zinv<double, double, OUT_RESID>);
+  allow_big_smem(k_zinv<double, float, OUT_RESID>);
+  allow_big_smem(k_zinv<float, float, OUT_PLAIN>);
+  allow_big_smem(k_zinv<float, float, OUT_CGAP>);
+  allow_big_smem(k_zinv<float, float, OUT_RESID>);
+  return g_init_err;
+}
+
+// explicit instantiations
+template void launch_zfwd<float>(const GridGeom&, int, const TangentView<float>&, const float*,
+                                 const float*, float*, const double*, const SolverState*,
+                                 const int*, cplx<float>*, const Twiddles<float>&, cudaStream_t);
+template void launch_zfwd<double>(const GridGeom&, int, const TangentView<double>&, const double*,
+                                  const double*, double*, const double*, const SolverState*,
+                                  const int*, cplx<double>*, const Twiddles<double>&,
+                                  cudaStream_t);
+template void launch_fft_y<float>(const GridGeom&, bool, cplx<float>*, const int*,
+                                  const Twiddles<float>&, cudaStream_t);
+template void launch_fft_y<double>(const GridGeom&, bool, cplx<double>*, const int*,
+                                   const Twiddles<double>&, cudaStream_t);
+template void launch_fft_x_proj<float>(const GridGeom&, double, cplx<float>*, const int*,
+                                       const Twiddles<float>&, cudaStream_t);
+template void launch_fft_x_proj<double>(const GridGeom&, double, cplx<double>*, const int*,
+                                        const Twiddles<double>&, cudaStream_t);
+template void launch_zinv<double, double>(const GridGeom&, int, const cplx<double>*, double*,
+                                          double*, double*, const double*, SolverState*, double*,
+                                          const int*, const Twiddles<double>&, cudaStream_t);
+template void launch_zinv<double, float>(const GridGeom&, int, const cplx<double>*, double*,
+                                         float*, float*, const float*, SolverState*, double*,
+                                         const int*, const Twiddles<double>&, cudaStream_t);
+template void launch_zinv<float, float>(const GridGeom&, int, const cplx<float>*, float*, float*,
+                                        float*, const float*, SolverState*, double*, const int*,
+                                        const Twiddles<float>&, cudaStream_t);

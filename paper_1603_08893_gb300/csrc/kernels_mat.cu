@@ -1,0 +1,315 @@
+// Per-voxel kernels: CG vector update, Newton update, reductions and the
+// Saint Venant-Kirchhoff constitutive update (Sec. 4.2-4.3).
+#include "kernels.h"
+
+#define VEC_THREADS 256
+#define VEC_BLOCKS 1216  // 152 SMs x 8 resident blocks; fixed, so reductions are deterministic
+
+size_t vec_max_blocks() { return VEC_BLOCKS; }
+
+// x += alpha p ; r -= alpha Ap ; rr_new = r.r ; then convergence test and
+// beta = rr_new / rr (standard CG, Sec. 2.6).  Fields are 9n long.
+template <typename R>
+__global__ void __launch_bounds__(VEC_THREADS) k_cg_update(size_t n9, R* __restrict__ x,
+                                                           R* __restrict__ r, const R* __restrict__ p,
+                                                           const R* __restrict__ Ap,
+                                                           SolverState* st, double* partials) {
+  if (st->done) return;
+  const R alpha = (R)st->alpha;
+  double acc = 0.0;
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n9; i += stride) {
+    const R pi = p[i];
+    x[i] = fma(alpha, pi, x[i]);
+    const R ri = fma(-alpha, Ap[i], r[i]);
+    r[i] = ri;
+    acc += (double)ri * (double)ri;
+  }
+  double v[1] = {acc}, tot[1];
+  if (last_block_sum<1>(v, partials, &st->counter[SLOT_RR], tot) && threadIdx.x == 0) {
+    const double rr_new = tot[0];
+    st->it += 1;
+    if (!isfinite(rr_new)) {
+      st->status = RVE_DEV_ERR_NONFINITE;
+      st->done = 1;
+    } else if (rr_new <= st->tol2) {
+      st->rr = rr_new;
+      st->done = 1;
+    } else if (st->it >= st->maxit) {
+      st->rr = rr_new;
+      st->status = RVE_DEV_ERR_CG_MAXIT;
+      st->done = 1;
+    } else {
+      st->beta = rr_new / st->rr;
+      st->rr = rr_new;
+    }
+  }
+}
+
+// Component means of a [9][n] field.  post selects what the last block does
+// with them: MEAN_DFBAR: dFbar = Fbar - <F>; MEAN_X: store <dF>; MEAN_PBAR:
+// store P-bar; MEAN_PLAIN: write out9.
+template <typename T>
+__global__ void __launch_bounds__(VEC_THREADS) k_mean9(const T* __restrict__ A, size_t n,
+                                                       double* out9, double* partials,
+                                                       unsigned int* counter, int post,
+                                                       SolverState* st) {
+  double s[9];
+#pragma unroll
+  for (int c = 0; c < 9; ++c) s[c] = 0.0;
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride)
+#pragma unroll
+    for (int c = 0; c < 9; ++c) s[c] += (double)A[(size_t)c * n + v];
+  double tot[9];
+  if (last_block_sum<9>(s, partials, counter, tot) && threadIdx.x == 0) {
+    for (int c = 0; c < 9; ++c) {
+      const double m = tot[c] / (double)n;
+      if (post == MEAN_DFBAR) {
+        st->meanF[c] = m;
+        st->dFbar[c] = st->Fbar[c] - m;
+      } else if (post == MEAN_X) {
+        st->meanX[c] = m;
+      } else if (post == MEAN_PBAR) {
+        st->Pbar[c] = m;
+      } else {
+        out9[c] = m;
+      }
+    }
+  }
+}
+
+// F += dFbar (uniform), ||F||^2 -> Fn2
+__global__ void __launch_bounds__(VEC_THREADS) k_add_uniform(double* __restrict__ F, size_t n,
+                                                             SolverState* st, double* partials) {
+  double d[9];
+#pragma unroll
+  for (int c = 0; c < 9; ++c) d[c] = st->dFbar[c];
+  double acc = 0.0;
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride)
+#pragma unroll
+    for (int c = 0; c < 9; ++c) {
+      const double f = F[(size_t)c * n + v] + d[c];
+      F[(size_t)c * n + v] = f;
+      acc += f * f;
+    }
+  double a[1] = {acc}, tot[1];
+  if (last_block_sum<1>(a, partials, &st->counter[SLOT_NORM], tot) && threadIdx.x == 0)
+    st->Fn2 = tot[0];
+}
+
+// F += dF - <dF> (the exact mean of dF is zero, Eq. mean:zero; the mean of
+// the computed dF is round-off and is removed), ||dF - <dF>||^2 -> dF2
+template <typename RC>
+__global__ void __launch_bounds__(VEC_THREADS) k_newton_update(double* __restrict__ F,
+                                                               const RC* __restrict__ x, size_t n,
+                                                               SolverState* st, double* partials) {
+  double m[9];
+#pragma unroll
+  for (int c = 0; c < 9; ++c) m[c] = st->meanX[c];
+  double acc = 0.0;
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride)
+#pragma unroll
+    for (int c = 0; c < 9; ++c) {
+      const double d = (double)x[(size_t)c * n + v] - m[c];
+      F[(size_t)c * n + v] += d;
+      acc += d * d;
+    }
+  double a[1] = {acc}, tot[1];
+  if (last_block_sum<1>(a, partials, &st->counter[SLOT_NORM], tot) && threadIdx.x == 0)
+    st->dF2 = tot[0];
+}
+
+// Saint Venant-Kirchhoff in FP64: E = (F^T F - I)/2, S = lambda tr(E) I +
+// 2 mu E (Eq. elas:S with Eq. elas:C), P = F S (Eq. elas:S-P).  Tangent
+// storage: FULL81 writes K_ijkl = S_li d_jk + lambda F_ji F_kl + mu F_jl F_ki
+// + mu d_il (F F^T)_jk (Eq. elas:K written out in components) in RO;
+// SVK writes F (and, in FP64, S) for on-the-fly recomputation.
+template <typename RO>
+__global__ void __launch_bounds__(VEC_THREADS) k_svk(const double* __restrict__ F, size_t n,
+                                                     MatView<double> mat, double* __restrict__ P,
+                                                     int tan_mode, RO* __restrict__ K4,
+                                                     RO* __restrict__ Fop, RO* __restrict__ Sop,
+                                                     SolverState* st) {
+  int flags = 0;
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+    double f[9];
+#pragma unroll
+    for (int c = 0; c < 9; ++c) f[c] = F[(size_t)c * n + v];
+    const double lam = mat.get(v, 0), mu = mat.get(v, 1);
+    double E[3][3], S[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b)
+        E[a][b] = 0.5 * (f[a] * f[b] + f[3 + a] * f[3 + b] + f[6 + a] * f[6 + b] - (a == b ? 1.0 : 0.0));
+    const double tr = E[0][0] + E[1][1] + E[2][2];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) S[a][b] = 2.0 * mu * E[a][b] + (a == b ? lam * tr : 0.0);
+    double pmax = 0.0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        const double pv = f[3 * a] * S[0][b] + f[3 * a + 1] * S[1][b] + f[3 * a + 2] * S[2][b];
+        P[(size_t)(3 * a + b) * n + v] = pv;
+        pmax = fmax(pmax, fabs(pv));
+      }
+    const double det = f[0] * (f[4] * f[8] - f[5] * f[7]) - f[1] * (f[3] * f[8] - f[5] * f[6]) +
+                       f[2] * (f[3] * f[7] - f[4] * f[6]);
+    if (!(det > 0.0)) flags |= 1;
+    if (!isfinite(pmax) || !isfinite(det)) flags |= 2;
+    if (tan_mode == TAN_FULL81) {
+      double B[3][3];  // F F^T
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b)
+          B[a][b] = f[3 * a] * f[3 * b] + f[3 * a + 1] * f[3 * b + 1] + f[3 * a + 2] * f[3 * b + 2];
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+#pragma unroll
+          for (int k = 0; k < 3; ++k)
+#pragma unroll
+            for (int l = 0; l < 3; ++l) {
+              double kv = lam * f[3 * j + i] * f[3 * k + l] + mu * f[3 * j + l] * f[3 * k + i];
+              if (j == k) kv += S[l][i];
+              if (i == l) kv += mu * B[j][k];
+              K4[(size_t)(((i * 3 + j) * 3 + k) * 3 + l) * n + v] = (RO)kv;
+            }
+    } else if (tan_mode == TAN_SVK) {
+      if (Fop) {
+#pragma unroll
+        for (int c = 0; c < 9; ++c) Fop[(size_t)c * n + v] = (RO)f[c];
+      }
+      if (Sop) {
+        Sop[v] = (RO)S[0][0];
+        Sop[n + v] = (RO)S[1][1];
+        Sop[2 * n + v] = (RO)S[2][2];
+        Sop[3 * n + v] = (RO)S[0][1];
+        Sop[4 * n + v] = (RO)S[0][2];
+        Sop[5 * n + v] = (RO)S[1][2];
+      }
+    }
+  }
+  if (flags) atomicOr(&st->err_flags, flags);
+}
+
+// FP64 K4 of a voxel range [v0, v0+count) into dst[81][count].
+__global__ void __launch_bounds__(VEC_THREADS) k_svk_k4(const double* __restrict__ F, size_t v0,
+                                                        size_t count, size_t n,
+                                                        MatView<double> mat, double* dst) {
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t u = (size_t)blockIdx.x * blockDim.x + threadIdx.x; u < count; u += stride) {
+    const size_t v = v0 + u;
+    double f[9];
+#pragma unroll
+    for (int c = 0; c < 9; ++c) f[c] = F[(size_t)c * n + v];
+    const double lam = mat.get(v, 0), mu = mat.get(v, 1);
+    double S[3][3], B[3][3];
+    double E[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        E[a][b] = 0.5 * (f[a] * f[b] + f[3 + a] * f[3 + b] + f[6 + a] * f[6 + b] - (a == b ? 1.0 : 0.0));
+        B[a][b] = f[3 * a] * f[3 * b] + f[3 * a + 1] * f[3 * b + 1] + f[3 * a + 2] * f[3 * b + 2];
+      }
+    const double tr = E[0][0] + E[1][1] + E[2][2];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) S[a][b] = 2.0 * mu * E[a][b] + (a == b ? lam * tr : 0.0);
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j)
+        for (int k = 0; k < 3; ++k)
+          for (int l = 0; l < 3; ++l) {
+            double kv = lam * f[3 * j + i] * f[3 * k + l] + mu * f[3 * j + l] * f[3 * k + i];
+            if (j == k) kv += S[l][i];
+            if (i == l) kv += mu * B[j][k];
+            dst[(size_t)(((i * 3 + j) * 3 + k) * 3 + l) * count + u] = kv;
+          }
+  }
+}
+
+template <typename Ti, typename To>
+__global__ void k_convert(const Ti* __restrict__ in, To* __restrict__ out, size_t count) {
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += stride)
+    out[i] = (To)in[i];
+}
+
+// --------------------------------------------------------------------------
+static unsigned int grid_for(size_t work) {
+  size_t b = (work + VEC_THREADS - 1) / VEC_THREADS;
+  if (b > VEC_BLOCKS) b = VEC_BLOCKS;
+  if (b < 1) b = 1;
+  return (unsigned int)b;
+}
+
+template <typename R>
+void launch_cg_update(size_t n9, R* x, R* r, const R* p, const R* Ap, SolverState* st,
+                      double* partials, cudaStream_t s) {
+  k_cg_update<R><<<grid_for(n9), VEC_THREADS, 0, s>>>(n9, x, r, p, Ap, st, partials);
+}
+
+template <typename T>
+void launch_mean9(const T* A, size_t n, double* out9, double* partials, unsigned int* counter,
+                  int post, SolverState* st, cudaStream_t s) {
+  k_mean9<T><<<grid_for(n), VEC_THREADS, 0, s>>>(A, n, out9, partials, counter, post, st);
+}
+
+void launch_add_uniform(double* F, size_t n, SolverState* st, double* partials, cudaStream_t s) {
+  k_add_uniform<<<grid_for(n), VEC_THREADS, 0, s>>>(F, n, st, partials);
+}
+
+template <typename RC>
+void launch_newton_update(double* F, const RC* x, size_t n, SolverState* st, double* partials,
+                          cudaStream_t s) {
+  k_newton_update<RC><<<grid_for(n), VEC_THREADS, 0, s>>>(F, x, n, st, partials);
+}
+
+template <typename RO>
+void launch_svk_constitutive(const double* F, size_t n, MatView<double> mat, double* P,
+                             int tan_mode, RO* K4, RO* Fop, RO* Sop, SolverState* st,
+                             cudaStream_t s) {
+  k_svk<RO><<<grid_for(n), VEC_THREADS, 0, s>>>(F, n, mat, P, tan_mode, K4, Fop, Sop, st);
+}
+
+void launch_svk_k4_full(const double* F, size_t v0, size_t count, size_t n,
+                        MatView<double> mat, double* dst, cudaStream_t s) {
+  k_svk_k4<<<grid_for(count), VEC_THREADS, 0, s>>>(F, v0, count, n, mat, dst);
+}
+
+template <typename Ti, typename To>
+void launch_convert(const Ti* in, To* out, size_t count, cudaStream_t s) {
+  k_convert<Ti, To><<<grid_for(count), VEC_THREADS, 0, s>>>(in, out, count);
+}
+
+template void launch_cg_update<float>(size_t, float*, float*, const float*, const float*,
+                                      SolverState*, double*, cudaStream_t);
+template void launch_cg_update<double>(size_t, double*, double*, const double*, const double*,
+                                       SolverState*, double*, cudaStream_t);
+template void launch_mean9<float>(const float*, size_t, double*, double*, unsigned int*, int,
+                                  SolverState*, cudaStream_t);
+template void launch_mean9<double>(const double*, size_t, double*, double*, unsigned int*, int,
+                                   SolverState*, cudaStream_t);
+template void launch_newton_update<float>(double*, const float*, size_t, SolverState*, double*,
+                                          cudaStream_t);
+template void launch_newton_update<double>(double*, const double*, size_t, SolverState*, double*,
+                                           cudaStream_t);
+template void launch_svk_constitutive<float>(const double*, size_t, MatView<double>, double*, int,
+                                             float*, float*, float*, SolverState*, cudaStream_t);
+template void launch_svk_constitutive<double>(const double*, size_t, MatView<double>, double*,
+                                              int, double*, double*, double*, SolverState*,
+                                              cudaStream_t);
+template void launch_convert<double, float>(const double*, float*, size_t, cudaStream_t);
+template void launch_convert<float, double>(const float*, double*, size_t, cudaStream_t);
+template void launch_convert<double, double>(const double*, double*, size_t, cudaStream_t);

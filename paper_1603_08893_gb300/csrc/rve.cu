@@ -1,0 +1,934 @@
+// C ABI and host orchestration of the Newton-CG solver (Algorithm 1).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/rve.h"
+#include "kernels.h"
+
+namespace {
+
+const double kPi = 3.14159265358979323846264338327950288;
+
+struct TimedLaunch {
+  cudaEvent_t a, b;
+  long long solve;
+  int iter;
+};
+
+struct Arena {
+  char* base = nullptr;
+  size_t off = 0, cap = 0;
+  bool dry = true;
+  template <typename T>
+  T* take(size_t count) {
+    off = (off + 255) & ~(size_t)255;
+    T* p = dry ? nullptr : reinterpret_cast<T*>(base + off);
+    off += count * sizeof(T);
+    return p;
+  }
+};
+
+bool factor_plan(int n, AxisPlan* p) {
+  p->n = n;
+  p->nst = 0;
+  int m = n;
+  const int fixed[] = {11, 7, 5, 3};
+  for (int f : fixed)
+    while (m % f == 0) {
+      if (p->nst >= RVE_MAX_STAGES) return false;
+      p->rad[p->nst++] = f;
+      m /= f;
+    }
+  for (int q = 13; m > 1; q += 2)
+    while (m % q == 0) {
+      if (p->nst >= RVE_MAX_STAGES) return false;
+      p->rad[p->nst++] = q;
+      m /= q;
+    }
+  // capacity of the in-register stage scheme with 256 threads per block
+  for (int s = 0; s < p->nst; ++s) {
+    const int r = p->rad[s];
+    const int nb = n / r;
+    if (r == 3 && nb > 512) return false;
+    if ((r == 5 || r == 7 || r == 11) && nb > 256) return false;
+    if (r > 11 && n > 512) return false;
+  }
+  return true;
+}
+
+int pick_lz(int nz, size_t csize, size_t budget) {
+  long lz = (long)((budget / csize - (size_t)nz) / (5 * (size_t)nz));
+  if (lz < 1) lz = 1;
+  if (lz > 64) lz = 64;
+  return (int)lz;
+}
+
+bool make_geom(int nx, int ny, int nz, GridGeom* g) {
+  if (nx < 1 || ny < 1 || nz < 1) return false;
+  if (nx % 2 == 0 || ny % 2 == 0 || nz % 2 == 0) return false;
+  if (nx > 2047 || ny > 2047 || nz > 2047) return false;
+  g->nx = nx;
+  g->ny = ny;
+  g->nz = nz;
+  g->hz = nz / 2 + 1;
+  g->hzp = (g->hz + 3) & ~3;
+  g->n = (size_t)nx * ny * nz;
+  g->sstride = (size_t)nx * ny * g->hzp;
+  if (!factor_plan(nx, &g->px) || !factor_plan(ny, &g->py) || !factor_plan(nz, &g->pz)) return false;
+  g->lz_f = pick_lz(nz, 8, 64 * 1024);
+  g->lz_d = pick_lz(nz, 16, 64 * 1024);
+  if ((size_t)16 * (nz + 5 * (size_t)g->lz_d * nz) > 200 * 1024) return false;
+  g->ty_f = 8;
+  g->ty_d = 4;
+  g->gy_f = std::max(1, std::min(9 * nx, (int)(32768 / (8 * (size_t)ny * g->ty_f))));
+  g->gy_d = std::max(1, std::min(9 * nx, (int)(32768 / (16 * (size_t)ny * g->ty_d))));
+  g->tx_f = 8;
+  while (g->tx_f > 1 && 8 * ((size_t)nx + 9 * (size_t)nx * g->tx_f) > 200 * 1024) g->tx_f /= 2;
+  g->tx_d = 4;
+  while (g->tx_d > 1 && 16 * ((size_t)nx + 9 * (size_t)nx * g->tx_d) > 200 * 1024) g->tx_d /= 2;
+  if (16 * ((size_t)nx + 9 * (size_t)nx * g->tx_d) > 200 * 1024) return false;
+  return true;
+}
+
+}  // namespace
+
+struct rve_s {
+  int model = RVE_SVK;
+  rve_options opt{};
+  cudaStream_t s = nullptr;
+  GridGeom g{};
+  size_t n = 0;
+  bool mixed = false;
+  int tan = TAN_SVK;
+  int nparam = 2;
+  // memory
+  char* ws = nullptr;
+  size_t ws_bytes = 0;
+  bool own_ws = false;
+  double *F = nullptr, *Ft = nullptr, *P = nullptr, *tmp64 = nullptr;
+  void *x = nullptr, *r = nullptr, *p = nullptr, *Ap = nullptr;
+  void* K4 = nullptr;
+  void* Fop = nullptr;
+  void* Sop = nullptr;
+  void* spec_op = nullptr;
+  cplx<double>* spec64 = nullptr;
+  size_t spec64_bytes = 0;
+  uint8_t* phase = nullptr;
+  double* table64 = nullptr;
+  float* table32 = nullptr;
+  double* vox64 = nullptr;
+  float* vox32 = nullptr;
+  double* partials = nullptr;
+  SolverState* st = nullptr;
+  SolverState* hst = nullptr;  // pinned mirror
+  cplx<float>* twf_all = nullptr;
+  cplx<double>* twd_all = nullptr;
+  Twiddles<float> twf{};
+  Twiddles<double> twd{};
+  double Fbar[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
+  std::string err;
+  long long launches = 0;
+  // instrumentation
+  int timing_family = -1;
+  std::vector<TimedLaunch> timed;
+  std::vector<cudaEvent_t> ev_pool;
+  long long solve_id = 0;
+  std::vector<std::pair<long long, int>> solve_iters;  // (solve id, effective iterations)
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+};
+
+namespace {
+
+int fail(rve_t h, int code, const std::string& msg) {
+  if (h) h->err = msg;
+  return code;
+}
+
+#define CK(call)                                                                       \
+  do {                                                                                 \
+    cudaError_t e_ = (call);                                                           \
+    if (e_ != cudaSuccess)                                                             \
+      return fail(h, RVE_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+cudaEvent_t ev_get(rve_t h) {
+  if (!h->ev_pool.empty()) {
+    cudaEvent_t e = h->ev_pool.back();
+    h->ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e;
+  cudaEventCreate(&e);
+  return e;
+}
+
+struct FamilyTimer {
+  rve_t h;
+  int fam, iter;
+  cudaEvent_t a = nullptr;
+  FamilyTimer(rve_t h_, int fam_, int iter_) : h(h_), fam(fam_), iter(iter_) {
+    if (h->timing_family == fam) {
+      a = ev_get(h);
+      cudaEventRecord(a, h->s);
+    }
+  }
+  ~FamilyTimer() {
+    if (a) {
+      cudaEvent_t b = ev_get(h);
+      cudaEventRecord(b, h->s);
+      h->timed.push_back({a, b, h->solve_id, iter});
+    }
+  }
+};
+
+template <typename T>
+T* as(void* p) { return reinterpret_cast<T*>(p); }
+
+template <typename R>
+MatView<R> mat_view(rve_t h) {
+  MatView<R> m;
+  m.phase = h->phase;
+  m.nparam = h->nparam;
+  m.n = h->n;
+  if (sizeof(R) == 8) {
+    m.table = reinterpret_cast<const R*>(h->table64);
+    m.vox = reinterpret_cast<const R*>(h->vox64);
+  } else {
+    m.table = reinterpret_cast<const R*>(h->table32);
+    m.vox = reinterpret_cast<const R*>(h->vox32);
+  }
+  return m;
+}
+
+template <typename R>
+TangentView<R> tangent_view(rve_t h) {
+  TangentView<R> t;
+  t.mode = h->tan;
+  t.K4 = as<R>(h->K4);
+  t.Fop = as<R>(h->Fop);
+  t.Sop = as<R>(h->Sop);
+  t.mat = mat_view<R>(h);
+  return t;
+}
+
+template <typename R>
+const Twiddles<R>& twiddles(rve_t h);
+template <>
+const Twiddles<float>& twiddles<float>(rve_t h) { return h->twf; }
+template <>
+const Twiddles<double>& twiddles<double>(rve_t h) { return h->twd; }
+
+// one CG iteration on the device: Ap = G:(K:p) with the p-update fused in
+// front and p.Ap fused at the end, then the vector update and tests.
+template <typename R>
+void enqueue_cg_iteration(rve_t h, int iter) {
+  const GridGeom& g = h->g;
+  const Twiddles<R>& tw = twiddles<R>(h);
+  const int* done = &h->st->done;
+  cplx<R>* spec = as<cplx<R>>(h->spec_op);
+  {
+    FamilyTimer t(h, 0, iter);
+    launch_zfwd<R>(g, SRC_CGP, tangent_view<R>(h), nullptr, as<R>(h->r), as<R>(h->p), nullptr,
+                   h->st, done, spec, tw, h->s);
+  }
+  {
+    FamilyTimer t(h, 1, iter);
+    launch_fft_y<R>(g, false, spec, done, tw, h->s);
+  }
+  {
+    FamilyTimer t(h, 2, iter);
+    launch_fft_x_proj<R>(g, 1.0 / (double)h->n, spec, done, tw, h->s);
+  }
+  {
+    FamilyTimer t(h, 3, iter);
+    launch_fft_y<R>(g, true, spec, done, tw, h->s);
+  }
+  {
+    FamilyTimer t(h, 4, iter);
+    launch_zinv<R, R>(g, OUT_CGAP, spec, as<R>(h->Ap), nullptr, nullptr, as<R>(h->p), h->st,
+                      h->partials, done, tw, h->s);
+  }
+  {
+    FamilyTimer t(h, 5, iter);
+    launch_cg_update<R>(9 * h->n, as<R>(h->x), as<R>(h->r), as<R>(h->p), as<R>(h->Ap), h->st,
+                        h->partials, h->s);
+  }
+  h->launches += 6;
+}
+
+// b = -G:P in float64; r = b (in the CG precision), x = 0, CG state reset.
+template <typename RC>
+void enqueue_residual(rve_t h) {
+  const GridGeom& g = h->g;
+  TangentView<double> plain{};
+  plain.mode = 0;
+  launch_zfwd<double>(g, SRC_FIELD, plain, h->P, nullptr, nullptr, nullptr, h->st, nullptr,
+                      h->spec64, h->twd, h->s);
+  launch_fft_y<double>(g, false, h->spec64, nullptr, h->twd, h->s);
+  launch_fft_x_proj<double>(g, -1.0 / (double)h->n, h->spec64, nullptr, h->twd, h->s);
+  launch_fft_y<double>(g, true, h->spec64, nullptr, h->twd, h->s);
+  launch_zinv<double, RC>(g, OUT_RESID, h->spec64, nullptr, as<RC>(h->r), as<RC>(h->x), nullptr,
+                          h->st, h->partials, nullptr, h->twd, h->s);
+  h->launches += 5;
+}
+
+// predictor right-hand side b = -G:(K_(0) : dFbar) (Eq. bc:lin) in the
+// operator precision; dFbar = Fbar - <F> computed on the device.
+template <typename R>
+void enqueue_predictor(rve_t h) {
+  const GridGeom& g = h->g;
+  const Twiddles<R>& tw = twiddles<R>(h);
+  cplx<R>* spec = as<cplx<R>>(h->spec_op);
+  launch_mean9<double>(h->F, h->n, nullptr, h->partials, &h->st->counter[SLOT_MEAN], MEAN_DFBAR,
+                       h->st, h->s);
+  launch_zfwd<R>(g, SRC_UNIFORM, tangent_view<R>(h), nullptr, nullptr, nullptr, h->st->dFbar,
+                 h->st, nullptr, spec, tw, h->s);
+  launch_fft_y<R>(g, false, spec, nullptr, tw, h->s);
+  launch_fft_x_proj<R>(g, -1.0 / (double)h->n, spec, nullptr, tw, h->s);
+  launch_fft_y<R>(g, true, spec, nullptr, tw, h->s);
+  launch_zinv<R, R>(g, OUT_RESID, spec, nullptr, as<R>(h->r), as<R>(h->x), nullptr, h->st,
+                    h->partials, nullptr, tw, h->s);
+  h->launches += 6;
+}
+
+int enqueue_constitutive(rve_t h) {
+  MatView<double> m = mat_view<double>(h);
+  if (h->mixed)
+    launch_svk_constitutive<float>(h->F, h->n, m, h->P, h->tan, as<float>(h->K4),
+                                   as<float>(h->Fop), nullptr, h->st, h->s);
+  else
+    launch_svk_constitutive<double>(h->F, h->n, m, h->P, h->tan, as<double>(h->K4), nullptr,
+                                    as<double>(h->Sop), h->st, h->s);
+  h->launches += 1;
+  return RVE_OK;
+}
+
+int sync_state(rve_t h) {
+  CK(cudaMemcpyAsync(h->hst, h->st, sizeof(SolverState), cudaMemcpyDeviceToHost, h->s));
+  CK(cudaStreamSynchronize(h->s));
+  return RVE_OK;
+}
+
+int push_state(rve_t h) {
+  CK(cudaMemcpyAsync(h->st, h->hst, sizeof(SolverState), cudaMemcpyHostToDevice, h->s));
+  return RVE_OK;
+}
+
+// CG loop: iterations are enqueued in chunks; kernels of iterations after
+// convergence return at once (device flag), so overshoot costs launches only.
+template <typename R>
+int cg_solve(rve_t h, int* iters) {
+  int launched = 0;
+  int chunk = 4;
+  h->solve_id++;
+  int rc = sync_state(h);
+  if (rc) return rc;
+  while (!h->hst->done) {
+    for (int k = 0; k < chunk; ++k) enqueue_cg_iteration<R>(h, launched + k);
+    launched += chunk;
+    CK(cudaGetLastError());
+    rc = sync_state(h);
+    if (rc) return rc;
+    if (h->hst->done) break;
+    // the device counts iterations and stops at maxit; this host bound only
+    // guards against a state that no longer advances
+    if (launched > h->hst->maxit + 4096)
+      return fail(h, RVE_ERR_TIMEOUT, "CG state stopped advancing");
+    const int it = h->hst->it;
+    const double rr = h->hst->rr, bb = h->hst->bb, tol2 = h->hst->tol2;
+    int pred = chunk;
+    if (it > 0 && rr < bb && rr > 0.0 && tol2 > 0.0) {
+      const double rate = std::log(rr / bb) / it;  // log decrease per iteration (<0)
+      const double need = std::log(tol2 / rr) / rate;
+      pred = (int)std::ceil(need * 1.05) + 1;
+    }
+    chunk = std::max(2, std::min(pred, 256));
+    chunk = std::min(chunk, std::max(1, h->hst->maxit - it));
+  }
+  *iters = h->hst->it;
+  h->solve_iters.push_back({h->solve_id, h->hst->it});
+  return h->hst->status;
+}
+
+int check_flags(rve_t h) {
+  if (h->hst->err_flags & 2) return fail(h, RVE_ERR_NONFINITE, "non-finite stress or det F");
+  if (h->hst->err_flags & 1) return fail(h, RVE_ERR_DETF, "det F <= 0 in some voxel");
+  return RVE_OK;
+}
+
+int copy_in(rve_t h, void* dst, const void* src, size_t bytes, int on_device) {
+  CK(cudaMemcpyAsync(dst, src, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                     h->s));
+  return RVE_OK;
+}
+
+int copy_out(rve_t h, void* dst, const void* src, size_t bytes, int on_device) {
+  CK(cudaMemcpyAsync(dst, src, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                     h->s));
+  CK(cudaStreamSynchronize(h->s));
+  return RVE_OK;
+}
+
+size_t layout(rve_t h, Arena& a) {
+  const size_t n = h->n, n9 = 9 * n;
+  const size_t ro = h->mixed ? 4 : 8;
+  const size_t ns = 9 * h->g.sstride;
+  h->F = a.take<double>(n9);
+  h->Ft = a.take<double>(n9);
+  h->P = a.take<double>(n9);
+  h->tmp64 = a.take<double>(n9);
+  h->x = a.take<char>(n9 * ro);
+  h->r = a.take<char>(n9 * ro);
+  h->p = a.take<char>(n9 * ro);
+  h->Ap = a.take<char>(n9 * ro);
+  h->K4 = nullptr;
+  h->Fop = nullptr;
+  h->Sop = nullptr;
+  if (h->tan == TAN_FULL81) {
+    h->K4 = a.take<char>(81 * n * ro);
+  } else {
+    if (h->mixed) h->Fop = a.take<char>(n9 * ro);
+    else h->Sop = a.take<char>(6 * n * ro);
+  }
+  h->spec64 = a.take<cplx<double>>(ns);
+  h->spec64_bytes = ns * sizeof(cplx<double>);
+  h->spec_op = h->mixed ? (void*)a.take<cplx<float>>(ns) : (void*)h->spec64;
+  h->table64 = a.take<double>(256 * 4);
+  h->table32 = a.take<float>(256 * 4);
+  h->vox64 = nullptr;
+  h->vox32 = nullptr;
+  const size_t blocks = std::max(fft_max_blocks(h->g), vec_max_blocks());
+  h->partials = a.take<double>(blocks * 9 + 64);
+  h->st = a.take<SolverState>(1);
+  const int gx[3] = {h->g.nx, h->g.ny, h->g.nz};
+  h->twf_all = a.take<cplx<float>>((size_t)gx[0] + gx[1] + gx[2]);
+  h->twd_all = a.take<cplx<double>>((size_t)gx[0] + gx[1] + gx[2]);
+  return a.off;
+}
+
+size_t layout_material(rve_t h, Arena& a, bool use_phase) {
+  if (use_phase) {
+    h->phase = a.take<uint8_t>(h->n);
+  } else {
+    h->phase = nullptr;
+    h->vox64 = a.take<double>((size_t)h->nparam * h->n);
+    h->vox32 = h->mixed ? a.take<float>((size_t)h->nparam * h->n) : nullptr;
+  }
+  return a.off;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+void rve_default_options(rve_options* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->precision = RVE_FP64;
+  o->tangent = RVE_TAN_AUTO;
+  o->max_newton = 50;
+  o->max_cg = 10000;
+  o->cg_tol_floor = 1e-5;
+  o->cg_atol = 0.0;
+}
+
+const char* rve_status_string(int code) {
+  switch (code) {
+    case RVE_OK: return "ok";
+    case RVE_ERR_INVALID: return "invalid argument";
+    case RVE_ERR_CUDA: return "CUDA error";
+    case RVE_ERR_NOMEM: return "out of device memory";
+    case RVE_ERR_CG_MAXIT: return "CG did not converge within max_cg iterations";
+    case RVE_ERR_CG_BREAKDOWN: return "CG breakdown (p.Ap <= 0)";
+    case RVE_ERR_NEWTON_MAXIT: return "Newton did not converge within max_newton iterations";
+    case RVE_ERR_NONFINITE: return "non-finite value";
+    case RVE_ERR_DETF: return "det F <= 0";
+    case RVE_ERR_TIMEOUT: return "device wait timed out";
+    case RVE_ERR_UNSUPPORTED: return "unsupported";
+    default: return "unknown status";
+  }
+}
+
+const char* rve_last_error(rve_t h) {
+  if (!h) return "null handle";
+  return h->err.c_str();
+}
+
+static int resolve_options(const rve_options* in, rve_options* out, int model, int* tan) {
+  if (in) *out = *in;
+  else rve_default_options(out);
+  if (out->precision != RVE_FP64 && out->precision != RVE_MIXED) return RVE_ERR_INVALID;
+  if (out->max_newton <= 0) out->max_newton = 50;
+  if (out->max_cg <= 0) out->max_cg = 10000;
+  if (!(out->cg_tol_floor >= 0.0)) return RVE_ERR_INVALID;
+  if (!(out->cg_atol >= 0.0)) return RVE_ERR_INVALID;
+  if (model == RVE_SVK) {
+    if (out->tangent == RVE_TAN_AUTO || out->tangent == RVE_TAN_RECOMPUTE) *tan = TAN_SVK;
+    else if (out->tangent == RVE_TAN_FULL81) *tan = TAN_FULL81;
+    else return RVE_ERR_INVALID;
+  } else {
+    return RVE_ERR_UNSUPPORTED;
+  }
+  return RVE_OK;
+}
+
+int rve_workspace_size(int nx, int ny, int nz, int model, const rve_options* opt, size_t* bytes) {
+  if (!bytes) return RVE_ERR_INVALID;
+  rve_s tmp;
+  if (!make_geom(nx, ny, nz, &tmp.g)) return RVE_ERR_INVALID;
+  int tan = 0;
+  int rc = resolve_options(opt, &tmp.opt, model, &tan);
+  if (rc) return rc;
+  tmp.n = tmp.g.n;
+  tmp.mixed = tmp.opt.precision == RVE_MIXED;
+  tmp.tan = tan;
+  tmp.nparam = (model == RVE_J2) ? 4 : 2;
+  Arena a;
+  layout(&tmp, a);
+  Arena b = a;
+  size_t with_vox = layout_material(&tmp, b, false);
+  Arena c = a;
+  size_t with_phase = layout_material(&tmp, c, true);
+  *bytes = std::max(with_vox, with_phase) + 256;
+  return RVE_OK;
+}
+
+int rve_create(rve_t* out, int nx, int ny, int nz, int model, int nphase, const uint8_t* phase,
+               const double* phase_params, const double* voxel_params, const rve_options* opt) {
+  if (!out) return RVE_ERR_INVALID;
+  *out = nullptr;
+  rve_t h = new rve_s();
+  auto bail = [&](int code, const std::string& msg) {
+    rve_destroy(h);
+    std::fprintf(stderr, "rve_create: %s\n", msg.c_str());
+    return code;
+  };
+  if (model != RVE_SVK && model != RVE_J2) return bail(RVE_ERR_INVALID, "unknown model");
+  h->model = model;
+  if (!make_geom(nx, ny, nz, &h->g))
+    return bail(RVE_ERR_INVALID, "grid sizes must be odd, positive and supported by the DFT plan");
+  int tan = 0;
+  int rc = resolve_options(opt, &h->opt, model, &tan);
+  if (rc) return bail(rc, rc == RVE_ERR_UNSUPPORTED ? "model not available in this build"
+                                                    : "invalid options");
+  h->n = h->g.n;
+  h->mixed = h->opt.precision == RVE_MIXED;
+  h->tan = tan;
+  h->nparam = (model == RVE_J2) ? 4 : 2;
+  h->s = (cudaStream_t)h->opt.stream;
+  if (phase) {
+    if (nphase < 1 || nphase > 256 || !phase_params)
+      return bail(RVE_ERR_INVALID, "phase map needs 1..256 phases with parameters");
+    for (size_t v = 0; v < h->n; ++v)
+      if (phase[v] >= nphase) return bail(RVE_ERR_INVALID, "phase index >= nphase");
+  } else if (!voxel_params) {
+    return bail(RVE_ERR_INVALID, "either a phase map or per-voxel parameters are required");
+  }
+  // sizes
+  Arena dry;
+  layout(h, dry);
+  Arena dry2 = dry;
+  const size_t need = layout_material(h, dry2, phase != nullptr) + 256;
+  if (h->opt.workspace) {
+    if (h->opt.workspace_bytes < need) return bail(RVE_ERR_NOMEM, "workspace too small");
+    h->ws = (char*)h->opt.workspace;
+    h->own_ws = false;
+  } else {
+    if (cudaMalloc(&h->ws, need) != cudaSuccess) {
+      h->ws = nullptr;
+      return bail(RVE_ERR_NOMEM, "cudaMalloc of the workspace failed");
+    }
+    h->own_ws = true;
+  }
+  h->ws_bytes = need;
+  Arena a;
+  a.dry = false;
+  a.base = h->ws;
+  a.cap = need;
+  layout(h, a);
+  layout_material(h, a, phase != nullptr);
+  if (cudaMallocHost(&h->hst, sizeof(SolverState)) != cudaSuccess) return bail(RVE_ERR_NOMEM, "pinned alloc");
+  std::memset(h->hst, 0, sizeof(SolverState));
+  {
+    cudaError_t e = fft_kernels_init();
+    if (e != cudaSuccess) return bail(RVE_ERR_CUDA, std::string("kernel attributes: ") + cudaGetErrorString(e));
+  }
+  cudaEventCreate(&h->e0);
+  cudaEventCreate(&h->e1);
+
+  cudaError_t first_err = cudaSuccess;
+  auto ck = [&](cudaError_t e) {
+    if (e != cudaSuccess && first_err == cudaSuccess) first_err = e;
+    return e == cudaSuccess;
+  };
+  bool ok = true;
+  ok &= ck(cudaMemsetAsync(h->ws, 0, need, h->s));
+  // twiddles exp(-2 pi i k / N) per axis, from float64 host evaluation
+  {
+    const int dims[3] = {h->g.nx, h->g.ny, h->g.nz};
+    std::vector<cplx<double>> td;
+    std::vector<cplx<float>> tf;
+    for (int d = 0; d < 3; ++d)
+      for (int k = 0; k < dims[d]; ++k) {
+        const double ang = 2.0 * kPi * (double)k / (double)dims[d];
+        td.push_back({std::cos(ang), -std::sin(ang)});
+        tf.push_back({(float)std::cos(ang), (float)-std::sin(ang)});
+      }
+    ok &= ck(cudaMemcpyAsync(h->twd_all, td.data(), td.size() * sizeof(td[0]), cudaMemcpyHostToDevice, h->s));
+    ok &= ck(cudaMemcpyAsync(h->twf_all, tf.data(), tf.size() * sizeof(tf[0]), cudaMemcpyHostToDevice, h->s));
+    h->twd = {h->twd_all, h->twd_all + dims[0], h->twd_all + dims[0] + dims[1]};
+    h->twf = {h->twf_all, h->twf_all + dims[0], h->twf_all + dims[0] + dims[1]};
+    ok &= ck(cudaStreamSynchronize(h->s));
+  }
+  // materials: (lambda, mu) with lambda = K - 2 mu / 3 (Eq. elas:C)
+  if (phase) {
+    std::vector<double> t64(256 * 4, 0.0);
+    std::vector<float> t32(256 * 4, 0.0f);
+    for (int k = 0; k < nphase; ++k) {
+      const double K = phase_params[k * h->nparam], mu = phase_params[k * h->nparam + 1];
+      t64[k * h->nparam] = K - 2.0 * mu / 3.0;
+      t64[k * h->nparam + 1] = mu;
+      for (int q = 2; q < h->nparam; ++q) t64[k * h->nparam + q] = phase_params[k * h->nparam + q];
+      for (int q = 0; q < h->nparam; ++q) t32[k * h->nparam + q] = (float)t64[k * h->nparam + q];
+    }
+    ok &= ck(cudaMemcpyAsync(h->table64, t64.data(), t64.size() * 8, cudaMemcpyHostToDevice, h->s));
+    ok &= ck(cudaMemcpyAsync(h->table32, t32.data(), t32.size() * 4, cudaMemcpyHostToDevice, h->s));
+    ok &= ck(cudaMemcpyAsync(h->phase, phase, h->n, cudaMemcpyHostToDevice, h->s));
+    ok &= ck(cudaStreamSynchronize(h->s));
+  } else {
+    std::vector<double> v64((size_t)h->nparam * h->n);
+    for (size_t v = 0; v < h->n; ++v) {
+      const double K = voxel_params[v], mu = voxel_params[h->n + v];
+      v64[v] = K - 2.0 * mu / 3.0;
+      v64[h->n + v] = mu;
+    }
+    for (int q = 2; q < h->nparam; ++q)
+      for (size_t v = 0; v < h->n; ++v) v64[q * h->n + v] = voxel_params[q * h->n + v];
+    ok &= ck(cudaMemcpyAsync(h->vox64, v64.data(), v64.size() * 8, cudaMemcpyHostToDevice, h->s));
+    std::vector<float> v32;
+    if (h->vox32) {
+      v32.assign(v64.begin(), v64.end());
+      ok &= ck(cudaMemcpyAsync(h->vox32, v32.data(), v32.size() * 4, cudaMemcpyHostToDevice, h->s));
+    }
+    ok &= ck(cudaStreamSynchronize(h->s));
+  }
+  if (!ok) return bail(RVE_ERR_CUDA, std::string("initial copies failed: ") + cudaGetErrorString(first_err));
+  // F = I, evaluate the material there
+  {
+    std::vector<double> I(9 * h->n, 0.0);
+    for (int c : {0, 4, 8})
+      for (size_t v = 0; v < h->n; ++v) I[c * h->n + v] = 1.0;
+    ok &= ck(cudaMemcpyAsync(h->F, I.data(), I.size() * 8, cudaMemcpyHostToDevice, h->s));
+    ok &= ck(cudaMemcpyAsync(h->Ft, I.data(), I.size() * 8, cudaMemcpyHostToDevice, h->s));
+    ok &= ck(cudaStreamSynchronize(h->s));
+  }
+  if (h->tan == TAN_SVK && !h->mixed) h->Fop = h->F;  // FP64 recompute reads F itself
+  enqueue_constitutive(h);
+  ok &= ck(cudaStreamSynchronize(h->s));
+  ok &= ck(cudaGetLastError());
+  if (!ok)
+    return bail(RVE_ERR_CUDA, std::string("initial constitutive evaluation failed: ") +
+                                  cudaGetErrorString(first_err));
+  *out = h;
+  return RVE_OK;
+}
+
+void rve_destroy(rve_t h) {
+  if (!h) return;
+  if (h->s) cudaStreamSynchronize(h->s);
+  else cudaDeviceSynchronize();
+  if (h->own_ws && h->ws) cudaFree(h->ws);
+  if (h->hst) cudaFreeHost(h->hst);
+  for (auto& t : h->timed) {
+    cudaEventDestroy(t.a);
+    cudaEventDestroy(t.b);
+  }
+  for (auto e : h->ev_pool) cudaEventDestroy(e);
+  if (h->e0) cudaEventDestroy(h->e0);
+  if (h->e1) cudaEventDestroy(h->e1);
+  delete h;
+}
+
+int rve_set_macro_F(rve_t h, const double Fbar[9]) {
+  if (!h || !Fbar) return RVE_ERR_INVALID;
+  for (int c = 0; c < 9; ++c)
+    if (!std::isfinite(Fbar[c])) return fail(h, RVE_ERR_INVALID, "non-finite F-bar");
+  std::memcpy(h->Fbar, Fbar, sizeof(h->Fbar));
+  return RVE_OK;
+}
+
+}  // extern "C"
+
+template <typename R>
+static int solve_increment_t(rve_t h, double tol_newton, double tol_cg, rve_stats* st) {
+  const size_t n9 = 9 * h->n;
+  CK(cudaEventRecord(h->e0, h->s));
+  // device state for this increment
+  SolverState* hs = h->hst;
+  std::memset(hs, 0, sizeof(SolverState));
+  hs->cg_tol = h->mixed ? std::max(tol_cg, h->opt.cg_tol_floor) : tol_cg;
+  hs->cg_atol = h->opt.cg_atol;
+  hs->maxit = h->opt.max_cg;
+  std::memcpy(hs->Fbar, h->Fbar, sizeof(hs->Fbar));
+  int rc = push_state(h);
+  if (rc) return rc;
+  // predictor (i = 0 right-hand side) and ||F_(0) + dFbar||
+  enqueue_predictor<R>(h);
+  {
+    // Fn2 = ||F + dFbar||^2 (F itself is updated together with the first dF)
+    launch_convert<double, double>(h->F, h->tmp64, n9, h->s);
+    launch_add_uniform(h->tmp64, h->n, h->st, h->partials, h->s);
+    h->launches += 2;
+  }
+  int result = RVE_OK;
+  bool converged = false;
+  int newton = 0;
+  int cg_total = 0;
+  for (int i = 0; i < h->opt.max_newton; ++i) {
+    int its = 0;
+    CK(cudaGetLastError());
+    rc = cg_solve<R>(h, &its);
+    cg_total += its;
+    if (st && i < RVE_MAX_NEWTON_LOG) st->cg_iters[i] = its;
+    if (rc) {
+      result = fail(h, rc, std::string("linear solve: ") + rve_status_string(rc));
+      break;
+    }
+    launch_mean9<R>(as<R>(h->x), h->n, nullptr, h->partials, &h->st->counter[SLOT_MEAN], MEAN_X,
+                    h->st, h->s);
+    if (i == 0) {
+      // F_(1) = F_(0) + dFbar + dF (Algorithm 1)
+      launch_convert<double, double>(h->tmp64, h->F, n9, h->s);
+      h->launches += 1;
+    }
+    launch_newton_update<R>(h->F, as<R>(h->x), h->n, h->st, h->partials, h->s);
+    enqueue_constitutive(h);
+    enqueue_residual<R>(h);
+    h->launches += 2;
+    rc = sync_state(h);
+    if (rc) {
+      result = rc;
+      break;
+    }
+    newton = i + 1;
+    const double rel = std::sqrt(hs->dF2 / hs->Fn2);
+    if (st && i < RVE_MAX_NEWTON_LOG) {
+      st->rel_update[i] = rel;
+      st->residual[i] = std::sqrt(hs->bb);
+    }
+    rc = check_flags(h);
+    if (rc) {
+      result = rc;
+      break;
+    }
+    if (!std::isfinite(rel)) {
+      result = fail(h, RVE_ERR_NONFINITE, "non-finite Newton update");
+      break;
+    }
+    if (rel < tol_newton && i > 0) {
+      converged = true;
+      break;
+    }
+  }
+  if (result == RVE_OK && !converged)
+    result = fail(h, RVE_ERR_NEWTON_MAXIT, "Newton did not converge");
+  if (result == RVE_OK) {
+    // commit: store the converged state, homogenised stress
+    CK(cudaMemcpyAsync(h->Ft, h->F, n9 * 8, cudaMemcpyDeviceToDevice, h->s));
+    launch_mean9<double>(h->P, h->n, nullptr, h->partials, &h->st->counter[SLOT_MEAN], MEAN_PBAR,
+                         h->st, h->s);
+    h->launches += 1;
+  } else {
+    // roll back to the last committed state
+    CK(cudaMemcpyAsync(h->F, h->Ft, n9 * 8, cudaMemcpyDeviceToDevice, h->s));
+    enqueue_constitutive(h);
+  }
+  CK(cudaEventRecord(h->e1, h->s));
+  rc = sync_state(h);
+  if (rc) return rc;
+  CK(cudaGetLastError());
+  if (st) {
+    st->status = result;
+    st->newton_iters = newton;
+    st->cg_iters_total = cg_total;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, h->e0, h->e1);
+    st->elapsed_ms = ms;
+  }
+  return result;
+}
+
+extern "C" {
+
+int rve_solve_increment(rve_t h, double tol_newton, double tol_cg, rve_stats* st) {
+  if (!h) return RVE_ERR_INVALID;
+  if (!(tol_newton > 0.0) || !(tol_cg > 0.0)) return fail(h, RVE_ERR_INVALID, "tolerances must be > 0");
+  if (st) std::memset(st, 0, sizeof(*st));
+  h->err.clear();
+  return h->mixed ? solve_increment_t<float>(h, tol_newton, tol_cg, st)
+                  : solve_increment_t<double>(h, tol_newton, tol_cg, st);
+}
+
+int rve_get_F(rve_t h, double* dst, int on_device) {
+  if (!h || !dst) return RVE_ERR_INVALID;
+  return copy_out(h, dst, h->F, 9 * h->n * 8, on_device);
+}
+
+int rve_get_P(rve_t h, double* dst, int on_device) {
+  if (!h || !dst) return RVE_ERR_INVALID;
+  return copy_out(h, dst, h->P, 9 * h->n * 8, on_device);
+}
+
+int rve_get_K4(rve_t h, double* dst, int on_device) {
+  if (!h || !dst) return RVE_ERR_INVALID;
+  // evaluated in float64 in chunks through the spectrum buffer
+  size_t chunk = h->spec64_bytes / (81 * sizeof(double));
+  if (chunk == 0) return fail(h, RVE_ERR_NOMEM, "scratch too small");
+  double* scratch = reinterpret_cast<double*>(h->spec64);
+  MatView<double> m = mat_view<double>(h);
+  for (size_t v0 = 0; v0 < h->n; v0 += chunk) {
+    const size_t cnt = std::min(chunk, h->n - v0);
+    launch_svk_k4_full(h->F, v0, cnt, h->n, m, scratch, h->s);
+    h->launches += 1;
+    CK(cudaMemcpy2DAsync(dst + v0, h->n * sizeof(double), scratch, cnt * sizeof(double),
+                         cnt * sizeof(double), 81,
+                         on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->s));
+  }
+  CK(cudaStreamSynchronize(h->s));
+  return RVE_OK;
+}
+
+int rve_homogenized_P(rve_t h, double Pbar[9]) {
+  if (!h || !Pbar) return RVE_ERR_INVALID;
+  launch_mean9<double>(h->P, h->n, nullptr, h->partials, &h->st->counter[SLOT_MEAN], MEAN_PBAR,
+                       h->st, h->s);
+  h->launches += 1;
+  int rc = sync_state(h);
+  if (rc) return rc;
+  std::memcpy(Pbar, h->hst->Pbar, sizeof(double) * 9);
+  return RVE_OK;
+}
+
+int rve_set_F(rve_t h, const double* F, int on_device) {
+  if (!h || !F) return RVE_ERR_INVALID;
+  int rc = copy_in(h, h->F, F, 9 * h->n * 8, on_device);
+  if (rc) return rc;
+  CK(cudaMemcpyAsync(h->Ft, h->F, 9 * h->n * 8, cudaMemcpyDeviceToDevice, h->s));
+  std::memset(h->hst, 0, sizeof(SolverState));
+  rc = push_state(h);
+  if (rc) return rc;
+  enqueue_constitutive(h);
+  rc = sync_state(h);
+  if (rc) return rc;
+  CK(cudaGetLastError());
+  return check_flags(h);
+}
+
+int rve_apply_operator(rve_t h, const double* dF, double* out, int on_device) {
+  if (!h || !dF || !out) return RVE_ERR_INVALID;
+  const size_t n9 = 9 * h->n;
+  int rc = copy_in(h, h->tmp64, dF, n9 * 8, on_device);
+  if (rc) return rc;
+  const GridGeom& g = h->g;
+  if (h->mixed) {
+    float* in = as<float>(h->p);
+    float* o = as<float>(h->Ap);
+    cplx<float>* spec = as<cplx<float>>(h->spec_op);
+    launch_convert<double, float>(h->tmp64, in, n9, h->s);
+    launch_zfwd<float>(g, SRC_FIELD, tangent_view<float>(h), in, nullptr, nullptr, nullptr, h->st,
+                       nullptr, spec, h->twf, h->s);
+    launch_fft_y<float>(g, false, spec, nullptr, h->twf, h->s);
+    launch_fft_x_proj<float>(g, 1.0 / (double)h->n, spec, nullptr, h->twf, h->s);
+    launch_fft_y<float>(g, true, spec, nullptr, h->twf, h->s);
+    launch_zinv<float, float>(g, OUT_PLAIN, spec, o, nullptr, nullptr, nullptr, h->st, h->partials,
+                              nullptr, h->twf, h->s);
+    launch_convert<float, double>(o, h->tmp64, n9, h->s);
+    h->launches += 7;
+  } else {
+    double* o = as<double>(h->Ap);
+    launch_zfwd<double>(g, SRC_FIELD, tangent_view<double>(h), h->tmp64, nullptr, nullptr, nullptr,
+                        h->st, nullptr, h->spec64, h->twd, h->s);
+    launch_fft_y<double>(g, false, h->spec64, nullptr, h->twd, h->s);
+    launch_fft_x_proj<double>(g, 1.0 / (double)h->n, h->spec64, nullptr, h->twd, h->s);
+    launch_fft_y<double>(g, true, h->spec64, nullptr, h->twd, h->s);
+    launch_zinv<double, double>(g, OUT_PLAIN, h->spec64, o, nullptr, nullptr, nullptr, h->st,
+                                h->partials, nullptr, h->twd, h->s);
+    launch_convert<double, double>(o, h->tmp64, n9, h->s);
+    h->launches += 6;
+  }
+  CK(cudaGetLastError());
+  return copy_out(h, out, h->tmp64, n9 * 8, on_device);
+}
+
+int rve_project(rve_t h, const double* A, double* out, int on_device) {
+  if (!h || !A || !out) return RVE_ERR_INVALID;
+  const size_t n9 = 9 * h->n;
+  int rc = copy_in(h, h->tmp64, A, n9 * 8, on_device);
+  if (rc) return rc;
+  const GridGeom& g = h->g;
+  TangentView<double> plain{};
+  plain.mode = 0;
+  launch_zfwd<double>(g, SRC_FIELD, plain, h->tmp64, nullptr, nullptr, nullptr, h->st, nullptr,
+                      h->spec64, h->twd, h->s);
+  launch_fft_y<double>(g, false, h->spec64, nullptr, h->twd, h->s);
+  launch_fft_x_proj<double>(g, 1.0 / (double)h->n, h->spec64, nullptr, h->twd, h->s);
+  launch_fft_y<double>(g, true, h->spec64, nullptr, h->twd, h->s);
+  launch_zinv<double, double>(g, OUT_PLAIN, h->spec64, h->tmp64, nullptr, nullptr, nullptr, h->st,
+                              h->partials, nullptr, h->twd, h->s);
+  h->launches += 5;
+  CK(cudaGetLastError());
+  return copy_out(h, out, h->tmp64, n9 * 8, on_device);
+}
+
+int rve_launch_count(rve_t h, long long* count) {
+  if (!h || !count) return RVE_ERR_INVALID;
+  *count = h->launches;
+  return RVE_OK;
+}
+
+int rve_kernel_timing(rve_t h, int family, int enable) {
+  if (!h || family < 0 || family > 5) return RVE_ERR_INVALID;
+  cudaStreamSynchronize(h->s);
+  for (auto& t : h->timed) {
+    h->ev_pool.push_back(t.a);
+    h->ev_pool.push_back(t.b);
+  }
+  h->timed.clear();
+  h->solve_iters.clear();
+  h->timing_family = enable ? family : -1;
+  return RVE_OK;
+}
+
+int rve_kernel_time(rve_t h, double* total_ms, long long* launches) {
+  if (!h || !total_ms || !launches) return RVE_ERR_INVALID;
+  CK(cudaStreamSynchronize(h->s));
+  double tot = 0.0;
+  long long cnt = 0;
+  for (auto& t : h->timed) {
+    // only launches of iterations that did work (those after convergence
+    // return at once and are not counted)
+    int eff = -1;
+    for (auto& si : h->solve_iters)
+      if (si.first == t.solve) eff = si.second;
+    if (eff < 0 || t.iter >= eff) continue;
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, t.a, t.b) == cudaSuccess) {
+      tot += ms;
+      cnt++;
+    }
+  }
+  *total_ms = tot;
+  *launches = cnt;
+  return RVE_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,266 @@
+"""Python binding of the C ABI (same function names as ``include/rve.h``).
+
+Only argument marshalling happens here.  Tensor fields are exchanged as
+float64 arrays shaped ``[3, 3, nx, ny, nz]`` (numpy on the host, or torch
+CUDA tensors on the device), which is exactly the C layout ``[9][n]``.
+Device memory for a handle is taken from PyTorch's allocator and handed to
+the library as its workspace.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import _lib
+from ._lib import lib
+
+try:
+    import torch
+except Exception:  # pragma: no cover
+    torch = None
+
+_MODELS = {"svk": _lib.RVE_SVK, "j2": _lib.RVE_J2}
+_PREC = {"fp64": _lib.RVE_FP64, "mixed": _lib.RVE_MIXED}
+_TAN = {"auto": _lib.RVE_TAN_AUTO, "full81": _lib.RVE_TAN_FULL81,
+        "recompute": _lib.RVE_TAN_RECOMPUTE}
+
+
+class RVEError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{msg} (code {code}: "
+                         f"{lib.rve_status_string(code).decode()})")
+        self.code = code
+
+
+def _check(code, h=None, what=""):
+    if code != 0:
+        msg = lib.rve_last_error(h).decode() if h else what
+        raise RVEError(code, msg or what)
+
+
+def _is_torch_cuda(a):
+    return torch is not None and isinstance(a, torch.Tensor) and a.is_cuda
+
+
+def _in_ptr(a, n):
+    """(pointer, on_device, keepalive) of a float64 [9][n] input."""
+    if _is_torch_cuda(a):
+        t = a.detach().to(torch.float64).contiguous()
+        if t.numel() != 9 * n:
+            raise ValueError("expected 9*n values")
+        return C.c_void_p(t.data_ptr()), 1, t
+    arr = np.ascontiguousarray(a, dtype=np.float64)
+    if arr.size != 9 * n:
+        raise ValueError("expected 9*n values")
+    return arr.ctypes.data_as(C.c_void_p), 0, arr
+
+
+def _options(precision="fp64", tangent="auto", max_newton=50, max_cg=10000,
+             cg_tol_floor=1e-5, cg_atol=0.0, stream=None):
+    o = _lib.rve_options()
+    lib.rve_default_options(C.byref(o))
+    o.precision = _PREC[precision]
+    o.tangent = _TAN[tangent]
+    o.max_newton = int(max_newton)
+    o.max_cg = int(max_cg)
+    o.cg_tol_floor = float(cg_tol_floor)
+    o.cg_atol = float(cg_atol)
+    if stream is None and torch is not None and torch.cuda.is_available():
+        stream = torch.cuda.current_stream().cuda_stream
+    o.stream = C.c_void_p(int(stream)) if stream else None
+    return o
+
+
+def rve_workspace_size(shape, model="svk", **opt):
+    nbytes = C.c_size_t(0)
+    o = _options(**opt)
+    _check(lib.rve_workspace_size(int(shape[0]), int(shape[1]), int(shape[2]),
+                                  _MODELS[model], C.byref(o), C.byref(nbytes)),
+           what="rve_workspace_size")
+    return int(nbytes.value)
+
+
+def rve_create(shape, model="svk", phase=None, phase_params=None,
+               voxel_params=None, torch_workspace=True, **opt):
+    """Returns (handle, keepalive) -- keepalive owns the device workspace."""
+    nx, ny, nz = (int(s) for s in shape)
+    o = _options(**opt)
+    keep = []
+    if torch_workspace and torch is not None and torch.cuda.is_available():
+        nbytes = rve_workspace_size(shape, model, **opt)
+        ws = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+        keep.append(ws)
+        o.workspace = C.c_void_p(ws.data_ptr())
+        o.workspace_bytes = nbytes
+    h = C.c_void_p()
+    ph = pp = vp = None
+    nphase = 0
+    if phase is not None:
+        ph = np.ascontiguousarray(phase, dtype=np.uint8)
+        pp = np.ascontiguousarray(phase_params, dtype=np.float64)
+        nphase = pp.shape[0]
+        keep += [ph, pp]
+    if voxel_params is not None:
+        vp = np.ascontiguousarray(voxel_params, dtype=np.float64)
+        keep.append(vp)
+    ptr = (lambda a: a.ctypes.data_as(C.c_void_p) if a is not None else None)
+    code = lib.rve_create(C.byref(h), nx, ny, nz, _MODELS[model], nphase,
+                          ptr(ph), ptr(pp), ptr(vp), C.byref(o))
+    _check(code, what="rve_create failed")
+    return h, keep
+
+
+def rve_destroy(h):
+    lib.rve_destroy(h)
+
+
+def rve_set_macro_F(h, Fbar):
+    F = np.ascontiguousarray(Fbar, dtype=np.float64).reshape(9)
+    _check(lib.rve_set_macro_F(h, F.ctypes.data_as(C.c_void_p)), h)
+
+
+def rve_solve_increment(h, tol_newton=1e-5, tol_cg=1e-8, check=True):
+    st = _lib.rve_stats()
+    code = lib.rve_solve_increment(h, float(tol_newton), float(tol_cg), C.byref(st))
+    k = min(st.newton_iters, _lib.RVE_MAX_NEWTON_LOG)
+    out = dict(status=code, newton_iters=st.newton_iters,
+               cg_iters_total=st.cg_iters_total,
+               cg_iters=list(st.cg_iters[:k]),
+               rel_update=list(st.rel_update[:k]),
+               residual=list(st.residual[:k]),
+               elapsed_ms=st.elapsed_ms)
+    if check:
+        _check(code, h)
+    return out
+
+
+def _get(fn, h, ncomp, n, out):
+    if out is not None and _is_torch_cuda(out):
+        if out.dtype != torch.float64 or not out.is_contiguous() or out.numel() != ncomp * n:
+            raise ValueError("out must be a contiguous float64 CUDA tensor")
+        _check(fn(h, C.c_void_p(out.data_ptr()), 1), h)
+        return out
+    if out is None:
+        out = np.empty(ncomp * n, dtype=np.float64)
+    _check(fn(h, out.ctypes.data_as(C.c_void_p), 0), h)
+    return out
+
+
+def rve_get_F(h, n, out=None):
+    return _get(lib.rve_get_F, h, 9, n, out)
+
+
+def rve_get_P(h, n, out=None):
+    return _get(lib.rve_get_P, h, 9, n, out)
+
+
+def rve_get_K4(h, n, out=None):
+    return _get(lib.rve_get_K4, h, 81, n, out)
+
+
+def rve_homogenized_P(h):
+    P = np.empty(9, dtype=np.float64)
+    _check(lib.rve_homogenized_P(h, P.ctypes.data_as(C.c_void_p)), h)
+    return P.reshape(3, 3)
+
+
+def rve_set_F(h, F, n):
+    p, dev, keep = _in_ptr(F, n)
+    _check(lib.rve_set_F(h, p, dev), h)
+
+
+def _unary(fn, h, A, n, out):
+    p, dev, keep = _in_ptr(A, n)
+    if dev:
+        res = out if out is not None else torch.empty_like(keep)
+        _check(fn(h, p, C.c_void_p(res.data_ptr()), 1), h)
+        return res
+    res = np.empty(9 * n, dtype=np.float64)
+    _check(fn(h, p, res.ctypes.data_as(C.c_void_p), 0), h)
+    return res
+
+
+def rve_apply_operator(h, dF, n, out=None):
+    return _unary(lib.rve_apply_operator, h, dF, n, out)
+
+
+def rve_project(h, A, n, out=None):
+    return _unary(lib.rve_project, h, A, n, out)
+
+
+def rve_launch_count(h):
+    c = C.c_longlong(0)
+    _check(lib.rve_launch_count(h, C.byref(c)), h)
+    return int(c.value)
+
+
+def rve_kernel_timing(h, family, enable=True):
+    _check(lib.rve_kernel_timing(h, int(family), int(bool(enable))), h)
+
+
+def rve_kernel_time(h):
+    ms = C.c_double(0)
+    cnt = C.c_longlong(0)
+    _check(lib.rve_kernel_time(h, C.byref(ms), C.byref(cnt)), h)
+    return float(ms.value), int(cnt.value)
+
+
+KERNEL_FAMILIES = ("zfwd", "fft_y_fwd", "fft_x_proj", "fft_y_inv", "zinv", "cg_update")
+
+
+class RVE:
+    """A periodic cell solved on the current CUDA device."""
+
+    def __init__(self, shape, phase=None, phase_params=None, voxel_params=None,
+                 model="svk", **opt):
+        self.shape = tuple(int(s) for s in shape)
+        self.n = int(np.prod(self.shape))
+        self.h, self._keep = rve_create(self.shape, model, phase, phase_params,
+                                        voxel_params, **opt)
+
+    def close(self):
+        h = getattr(self, "h", None)
+        if h:
+            rve_destroy(h)
+            self.h = None
+            self._keep = []
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _shape9(self, a):
+        return a.reshape((3, 3) + self.shape)
+
+    def set_macro_F(self, Fbar):
+        rve_set_macro_F(self.h, Fbar)
+
+    def solve_increment(self, tol_newton=1e-5, tol_cg=1e-8, check=True):
+        return rve_solve_increment(self.h, tol_newton, tol_cg, check)
+
+    def get_F(self, out=None):
+        return self._shape9(rve_get_F(self.h, self.n, out))
+
+    def get_P(self, out=None):
+        return self._shape9(rve_get_P(self.h, self.n, out))
+
+    def get_K4(self, out=None):
+        return rve_get_K4(self.h, self.n, out).reshape((3, 3, 3, 3) + self.shape)
+
+    def homogenized_P(self):
+        return rve_homogenized_P(self.h)
+
+    def set_F(self, F):
+        rve_set_F(self.h, F, self.n)
+
+    def apply_operator(self, dF, out=None):
+        return self._shape9(rve_apply_operator(self.h, dF, self.n, out))
+
+    def project(self, A, out=None):
+        return self._shape9(rve_project(self.h, A, self.n, out))
+
+    def launch_count(self):
+        return rve_launch_count(self.h)

@@ -1,0 +1,243 @@
+"""GPU parity of the CUDA path against the FP64 oracle, through the C ABI.
+
+Tolerances: float64 path 1e-12 for single operator applications and 1e-10
+(relative 2-norm over the field) for full solves; mixed path (float32 CG
+operator) 5e-6 relative for one operator application -- float32 round-off
+accumulated over three DFT passes of length <= 63 -- and P-bar 1e-8 /
+fields 1e-7 for converged solves.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import fourier, solver, svk
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_1603_08893_gb300 import RVE, RVEError  # noqa: E402
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+SHAPES = [(1, 1, 1), (3, 5, 7), (5, 1, 3), (9, 11, 13), (15, 15, 15),
+          (21, 27, 33), (31, 31, 31), (45, 45, 45), (63, 63, 63), (27, 3, 125)]
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(b), 1e-300))
+
+
+def maxrel(a, b):
+    return float(np.abs(np.asarray(a) - np.asarray(b)).max() / max(np.abs(b).max(), 1e-300))
+
+
+def _random_problem(shape, seed, prec="fp64", tangent="auto", amp=0.15):
+    rng = np.random.default_rng(seed)
+    phase = (rng.uniform(size=shape) < 0.35).astype(np.uint8)
+    params = synth.two_phase_params(7.0)
+    r = RVE(shape, phase=phase, phase_params=params, precision=prec, tangent=tangent)
+    F = synth.random_F(shape, rng, amp)
+    r.set_F(F)
+    K = params[phase, 0]
+    mu = params[phase, 1]
+    return r, F, K, mu, rng
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+def test_projection_matches_oracle(shape):
+    rng = np.random.default_rng(sum(shape))
+    r = RVE(shape, phase=np.zeros(shape, np.uint8), phase_params=[[1.0, 0.5]])
+    A = rng.standard_normal((3, 3) + shape)
+    got = r.project(A)
+    ref = fourier.G(A)
+    if np.abs(ref).max() == 0:
+        assert np.abs(got).max() < 1e-14
+    else:
+        assert maxrel(got, ref) < 1e-12
+    # device-resident input and output
+    At = torch.from_numpy(A).cuda()
+    got_d = r.project(At).cpu().numpy()
+    assert np.array_equal(got_d, got)
+    r.close()
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("tangent", ["recompute", "full81"])
+def test_operator_fp64_matches_oracle(shape, tangent):
+    r, F, K, mu, rng = _random_problem(shape, 3, "fp64", tangent)
+    _, K4 = svk.constitutive(F, K, mu)
+    dF = rng.standard_normal((3, 3) + shape)
+    got = r.apply_operator(dF)
+    ref = fourier.G(svk.tangent_apply(K4, dF))
+    if np.abs(ref).max() == 0:
+        assert np.abs(got).max() < 1e-13
+    else:
+        assert maxrel(got, ref) < 1e-12
+    r.close()
+
+
+@pytest.mark.parametrize("shape", [(9, 11, 13), (31, 31, 31), (63, 63, 63), (27, 3, 125)])
+@pytest.mark.parametrize("tangent", ["recompute", "full81"])
+def test_operator_mixed_matches_oracle(shape, tangent):
+    r, F, K, mu, rng = _random_problem(shape, 4, "mixed", tangent)
+    _, K4 = svk.constitutive(F, K, mu)
+    dF = rng.standard_normal((3, 3) + shape)
+    got = r.apply_operator(dF)
+    ref = fourier.G(svk.tangent_apply(K4, dF))
+    assert rel(got, ref) < 5e-6
+    r.close()
+
+
+@pytest.mark.parametrize("shape", [(3, 5, 7), (15, 15, 15), (33, 21, 27)])
+def test_constitutive_matches_oracle(shape):
+    r, F, K, mu, rng = _random_problem(shape, 5)
+    P_ref, K4_ref = svk.constitutive(F, K, mu)
+    assert maxrel(r.get_P(), P_ref) < 1e-13
+    assert maxrel(r.get_K4(), K4_ref) < 1e-13
+    assert np.array_equal(r.get_F(), F)
+    r.close()
+
+
+@pytest.fixture(scope="module")
+def cube31_oracle():
+    cfg = synth.config_cube31()
+    prob = solver.SVKProblem.from_phase(cfg["phase"], cfg["phase_params"])
+    res = []
+    for Fbar in cfg["schedule"][:3]:
+        prob.increment(Fbar, tol_newton=cfg["tol_newton"], tol_cg=cfg["tol_cg"])
+        res.append((prob.F.copy(), prob.P.copy()))
+    return cfg, res
+
+
+def test_cube31_fp64_schedule_matches_oracle(cube31_oracle):
+    cfg, ref = cube31_oracle
+    gold = json.load(open(os.path.join(GOLDEN, "svk31_cube_schedule.json")))
+    r = RVE(cfg["shape"], phase=cfg["phase"], phase_params=cfg["phase_params"],
+            precision="fp64")
+    for k, Fbar in enumerate(cfg["schedule"]):
+        r.set_macro_F(Fbar)
+        st = r.solve_increment(cfg["tol_newton"], cfg["tol_cg"])
+        g = gold["config_tolerances"]["increments"][k]
+        assert st["newton_iters"] == g["newton_iters"]
+        assert all(abs(a - b) <= 1 for a, b in zip(st["cg_iters"], g["cg_iters"]))
+        assert maxrel(r.homogenized_P(), np.array(g["Pbar"])) < 1e-10
+        if k < len(ref):
+            assert rel(r.get_F(), ref[k][0]) < 1e-10
+            assert rel(r.get_P(), ref[k][1]) < 1e-10
+    # the prescribed macroscopic deformation is held (Eq. mean:zero)
+    assert maxrel(r.get_F().mean(axis=(2, 3, 4)), cfg["schedule"][-1]) < 1e-14
+    r.close()
+
+
+def test_cube31_mixed_schedule_matches_tight_oracle():
+    cfg = synth.config_cube31()
+    gold = json.load(open(os.path.join(GOLDEN, "svk31_cube_schedule.json")))
+    r = RVE(cfg["shape"], phase=cfg["phase"], phase_params=cfg["phase_params"],
+            precision="mixed")
+    for k, Fbar in enumerate(cfg["schedule"]):
+        r.set_macro_F(Fbar)
+        r.solve_increment(cfg["tol_newton"], cfg["tol_cg"])
+        g = gold["tight"]["increments"][k]
+        assert maxrel(r.homogenized_P(), np.array(g["Pbar"])) < 1e-8
+        assert abs(np.linalg.norm(r.get_F()) - g["Fnorm"]) < 1e-7 * g["Fnorm"]
+    r.close()
+
+
+def test_homogeneous_cell_gives_uniform_F():
+    shape = (15, 9, 21)
+    r = RVE(shape, phase=np.zeros(shape, np.uint8), phase_params=[[0.833, 0.386]])
+    Fbar = np.eye(3) + 0.1 * np.random.default_rng(1).uniform(-1, 1, (3, 3))
+    r.set_macro_F(Fbar)
+    r.solve_increment(1e-5, 1e-8)
+    F = r.get_F()
+    assert np.abs(F - Fbar[:, :, None, None, None]).max() < 1e-14
+    assert maxrel(r.homogenized_P(), svk.stress(Fbar, 0.833, 0.386)) < 1e-13
+    r.close()
+
+
+def test_single_voxel_cell():
+    r = RVE((1, 1, 1), phase=np.ones((1, 1, 1), np.uint8), phase_params=[[1, 1], [2.0, 0.7]])
+    Fbar = synth.simple_shear(0.2)
+    r.set_macro_F(Fbar)
+    st = r.solve_increment(1e-5, 1e-8)
+    assert st["cg_iters"] == [0, 0]
+    assert np.abs(r.get_F()[:, :, 0, 0, 0] - Fbar).max() < 1e-15
+    r.close()
+
+
+@pytest.mark.parametrize("axis", [0, 1, 2])
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-9), ("mixed", 1e-7)])
+def test_laminate_closed_form(axis, prec, tol):
+    from test_oracle_solver import _laminate_exact
+    shape = [15, 15, 15]
+    shape[axis] = 27
+    shape = tuple(shape)
+    ph = synth.laminate(shape, axis, fraction=12 / 27)
+    params = synth.two_phase_params(20.0)
+    Fbar = np.eye(3) + np.array([[0.05, 0.2, -0.03], [0.01, -0.04, 0.1], [0.02, 0.03, 0.06]])
+    r = RVE(shape, phase=ph, phase_params=params, precision=prec, cg_atol=1e-12)
+    r.set_macro_F(Fbar)
+    r.solve_increment(1e-10 if prec == "fp64" else 1e-7, 1e-12)
+    n = np.zeros(3)
+    n[axis] = 1
+    F1, F0 = _laminate_exact(Fbar, n, ph.mean(), tuple(params[1]), tuple(params[0]))
+    exact = np.where(ph[None, None] == 1, F1[:, :, None, None, None], F0[:, :, None, None, None])
+    assert np.abs(r.get_F() - exact).max() < tol
+    r.close()
+
+
+def test_invalid_arguments_are_rejected():
+    with pytest.raises(RVEError) as e:
+        RVE((4, 5, 5), phase=np.zeros((4, 5, 5), np.uint8), phase_params=[[1, 1]])
+    assert e.value.code == -1
+    with pytest.raises(RVEError):
+        RVE((5, 5, 5), phase=np.full((5, 5, 5), 3, np.uint8), phase_params=[[1, 1], [2, 2]])
+
+
+def test_negative_det_rolls_back():
+    shape = (9, 9, 9)
+    ph = synth.cube_inclusion(9, 3)
+    r = RVE(shape, phase=ph, phase_params=synth.two_phase_params(5.0))
+    r.set_macro_F(synth.simple_shear(0.05))
+    r.solve_increment()
+    F_ok = r.get_F()
+    bad = np.diag([-1.0, 1.0, 1.0])  # an inversion: det F-bar < 0
+    r.set_macro_F(bad)
+    with pytest.raises(RVEError) as e:
+        r.solve_increment()
+    assert e.value.code == -8
+    assert np.array_equal(r.get_F(), F_ok)
+    r.close()
+
+
+def test_per_voxel_moduli_match_phase_table():
+    shape = (15, 15, 15)
+    ph = synth.cube_inclusion(15, 5)
+    params = synth.two_phase_params(10.0)
+    vox = np.stack([params[ph, 0], params[ph, 1]])
+    a = RVE(shape, phase=ph, phase_params=params)
+    b = RVE(shape, voxel_params=vox)
+    for r in (a, b):
+        r.set_macro_F(synth.simple_shear(0.05))
+        r.solve_increment()
+    assert np.array_equal(a.get_F(), b.get_F())
+    a.close()
+    b.close()
+
+
+def test_deterministic_repeat():
+    cfg = synth.config_cube31()
+    outs = []
+    for _ in range(2):
+        r = RVE(cfg["shape"], phase=cfg["phase"], phase_params=cfg["phase_params"],
+                precision="mixed")
+        r.set_macro_F(cfg["schedule"][0])
+        r.solve_increment()
+        outs.append(r.get_F())
+        r.close()
+    assert np.array_equal(outs[0], outs[1])
