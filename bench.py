@@ -1,0 +1,391 @@
+"""Benchmark of the Newton-CG solver on the 125^3 two-phase sphere cell.
+
+Workload (synthetic, seeded): Saint Venant-Kirchhoff, 125^3 voxels, random
+non-overlapping spheres (radii 4-10, volume fraction 0.3, stiffness contrast
+100, matrix K = 0.833, mu = 0.386), uniaxial F-bar = diag(1 + eps, 1, 1) with
+eps ramped to 0.2 in 20 equal increments; eta_NW = 1e-5, eta_CG = 1e-8.
+
+A step is one load increment: constitutive update, predictor solve, Newton
+iterations with matrix-free CG to convergence, commit.  The headline value
+is voxel * CG-iterations per second of the mixed-precision path (float32 CG
+operator, float64 residual / update / reductions), timed with CUDA events on
+the solver's stream with the cell resident in HBM; the plain float64 path is
+timed on the same increments for the solve-time ratio, and the mixed path's
+homogenised stress is compared with the float64 path's.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 (launched by torchrun) every rank solves its own replica of the
+cell (the method has no exchange step between independent cells); the value
+is the sum over ranks divided by the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "voxel*CG-iterations/s, mixed FP32-CG/FP64-residual solver (vs plain FP64 GPU solver)"
+UNIT = "voxel*CG-iter/s"
+# algorithmic bytes per voxel of each CG-iteration kernel family, float32
+# vectors, on-the-fly SVK tangent (F in float32 + 1-byte phase), half
+# spectrum of h = N//2+1 planes (nine complex values per (x, y, kz)).
+
+
+def family_bytes_per_voxel(nz, fam):
+    s = 4.0
+    spec = 9 * 2 * s * (nz // 2 + 1) / nz
+    return {
+        "zfwd": 9 * s * 3 + 9 * s + 1 + spec,   # r, p in; p out; F; phase; spectrum out
+        "fft_y_fwd": 2 * spec,
+        "fft_x_proj": 2 * spec,
+        "fft_y_inv": 2 * spec,
+        "zinv": spec + 9 * s * 2,               # spectrum in; p in; Ap out
+        "cg_update": 9 * s * 6,                 # x, r, p, Ap in; x, r out
+    }[fam]
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=0):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for k, nm in enumerate(names):
+                if r[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(rows), "reasons": sorted(reasons)}
+
+
+def dist_setup(ngpus):
+    if ngpus <= 1 or "RANK" not in os.environ:
+        return 0, 1, None
+    import torch
+    import torch.distributed as dist
+    backend = "nccl" if torch.cuda.is_available() else "gloo"
+    dist.init_process_group(backend)
+    rank, world = dist.get_rank(), dist.get_world_size()
+    if torch.cuda.is_available():
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", rank)))
+    return rank, world, dist
+
+
+def reduce_max_sum(dist, t_max, s_sum):
+    """(max over ranks of t_max, sum over ranks of s_sum)."""
+    if dist is None:
+        return t_max, s_sum
+    import torch
+    dev = "cuda" if torch.cuda.is_available() and dist.get_backend() == "nccl" else "cpu"
+    a = torch.tensor([t_max], dtype=torch.float64, device=dev)
+    b = torch.tensor([s_sum], dtype=torch.float64, device=dev)
+    dist.all_reduce(a, op=dist.ReduceOp.MAX)
+    dist.all_reduce(b, op=dist.ReduceOp.SUM)
+    return float(a.item()), float(b.item())
+
+
+def workload():
+    cfg = synth.config_spheres(125, seed=1, nincr=20, eps=0.2)
+    cfg["workload"] = "svk125_spheres_uniaxial"
+    return cfg
+
+
+def run_schedule(RVE, cfg, precision, steps, torch, e2e_buf=None, collect_pbar=False):
+    """Solve `steps` increments of the ramp on a fresh cell.  Returns a dict
+    with device time (CUDA events on the solver stream), CG iterations,
+    P-bar per increment and the kernel launch count."""
+    sched = cfg["schedule"]
+    r = RVE(cfg["shape"], phase=cfg["phase"], phase_params=cfg["phase_params"],
+            precision=precision)
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    cg = 0
+    newton = 0
+    pbars = []
+    l0 = r.launch_count()
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter()
+    ev0.record(stream)
+    for k in range(steps):
+        if k and k % len(sched) == 0:
+            r.set_F(np.broadcast_to(np.eye(3)[:, :, None, None, None],
+                                    (3, 3) + cfg["shape"]).copy())
+        r.set_macro_F(sched[k % len(sched)])
+        st = r.solve_increment(cfg["tol_newton"], cfg["tol_cg"])
+        cg += st["cg_iters_total"]
+        newton += st["newton_iters"]
+        if e2e_buf is not None:
+            r.get_P(out=e2e_buf)
+        if collect_pbar or e2e_buf is not None:
+            pbars.append(r.homogenized_P())
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t_wall
+    ms = ev0.elapsed_time(ev1)
+    out = dict(ms=ms, wall_s=wall, cg=cg, newton=newton, pbars=pbars,
+               launches=r.launch_count() - l0, rve=r)
+    return out
+
+
+def kernel_profile(RVE, cfg, torch, families, steps=1):
+    """Average device time per launch of each CG-iteration kernel family,
+    from CUDA events recorded around every launch on the solver stream."""
+    from paper_1603_08893_gb300 import rve as api
+    res = {}
+    for fi, fam in enumerate(families):
+        r = RVE(cfg["shape"], phase=cfg["phase"], phase_params=cfg["phase_params"],
+                precision="mixed")
+        api.rve_kernel_timing(r.h, fi, True)
+        for k in range(steps):
+            r.set_macro_F(cfg["schedule"][k])
+            r.solve_increment(cfg["tol_newton"], cfg["tol_cg"])
+        ms, cnt = api.rve_kernel_time(r.h)
+        res[fam] = dict(total_ms=ms, launches=cnt, avg_ms=ms / max(cnt, 1))
+        r.close()
+    return res
+
+
+def cpu_baseline_sample(cfg, iters=4):
+    """The FP64 oracle, as it stands, on a bounded sample of the workload:
+    `iters` CG iterations of the first increment's predictor solve."""
+    from oracle import solver as osolver
+    from oracle import tensor as otensor
+    prob = osolver.SVKProblem.from_phase(cfg["phase"], cfg["phase_params"])
+    t0 = time.perf_counter()
+    _, K4 = prob.constitutive(prob.F)
+    t_const = time.perf_counter() - t0
+    op = osolver.tangent_operator(K4)
+    dFbar = otensor.uniform(cfg["schedule"][0] - np.eye(3), prob.shape)
+    b = -op(dFbar)
+    t0 = time.perf_counter()
+    try:
+        osolver.cg(op, b, cfg["tol_cg"], maxiter=iters)
+    except osolver.SolverError:
+        pass
+    t_cg = time.perf_counter() - t0
+    n = int(np.prod(cfg["shape"]))
+    return dict(value=n * iters / t_cg, unit=UNIT, cores=1, kind="oracle",
+                sample=(f"{iters} CG iterations (operator G:(K:p) + vector updates) of the "
+                        f"first increment's predictor solve on the 125^3 cell, numpy FFT "
+                        f"backend, single thread; constitutive evaluation "
+                        f"({t_const:.1f} s) not counted"),
+                seconds=t_cg + t_const)
+
+
+def reference_arm(args):
+    """The oracle, as it stands, on the host cores: one step is one CG
+    iteration (operator G:(K:p) and vector updates) of the first increment's
+    predictor solve on the same 125^3 cell; the constitutive evaluation and
+    the right-hand side are set up once, untimed."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from oracle import solver as osolver
+    from oracle import tensor as otensor
+    cfg = workload()
+    prob = osolver.SVKProblem.from_phase(cfg["phase"], cfg["phase_params"])
+    _, K4 = prob.constitutive(prob.F)
+    op = osolver.tangent_operator(K4)
+    b = -op(otensor.uniform(cfg["schedule"][0] - np.eye(3), prob.shape))
+
+    def iterate(k):
+        try:
+            osolver.cg(op, b, cfg["tol_cg"], maxiter=k)
+        except osolver.SolverError:
+            pass
+
+    if args.warmup > 0:
+        iterate(args.warmup)
+    t0 = time.perf_counter()
+    iterate(args.steps)
+    dt = time.perf_counter() - t0
+    n = int(np.prod(cfg["shape"]))
+    v = n * args.steps / dt
+    sample = (f"{args.steps} CG iterations of the first increment's predictor solve on the "
+              f"125^3 cell (after {args.warmup} warm-up iterations), numpy FFT backend, "
+              f"single thread; constitutive evaluation and right-hand side untimed")
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT,
+           "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": 1e3 * dt / max(args.steps, 1),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f64", "data": "synthetic",
+           "config": {"workload": cfg["workload"], "grid": 125},
+           "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--fp64-steps", type=int, default=4)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-profile", action="store_true")
+    ap.add_argument("--mixed-only", action="store_true",
+                    help="time the mixed path only (no float64 comparison, no e2e); "
+                         "used for profiler captures")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return reference_arm(args)
+
+    import torch
+    rank, world, dist = dist_setup(args.gpus)
+    from paper_1603_08893_gb300 import KERNEL_FAMILIES, RVE
+
+    cfg = workload()
+    n = int(np.prod(cfg["shape"]))
+    # warm-up: W increments of the ramp on a separate cell (both precisions)
+    for prec in (("mixed",) if args.mixed_only else ("mixed", "fp64")):
+        w = run_schedule(RVE, cfg, prec, max(1, args.warmup if prec == "mixed" else 1), torch)
+        w["rve"].close()
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    mixed = run_schedule(RVE, cfg, "mixed", args.steps, torch)
+    ck = clocks.stop()
+    mixed["rve"].close()
+    t_max, units = reduce_max_sum(dist, mixed["ms"], float(n) * mixed["cg"])
+    value = units / (t_max / 1e3)
+
+    if args.mixed_only:
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": value, "unit": UNIT,
+                              "steps": args.steps, "cg_iters": mixed["cg"],
+                              "ms_per_step": t_max / args.steps, "mixed_only": True}))
+        return None
+    # float64 GPU path on the first increments, for the solve-time ratio and
+    # the accuracy of the mixed path
+    k64 = min(args.fp64_steps, args.steps)
+    fp64 = run_schedule(RVE, cfg, "fp64", k64, torch, collect_pbar=True)
+    fp64["rve"].close()
+    mixed_k = run_schedule(RVE, cfg, "mixed", k64, torch, collect_pbar=True)
+    mixed_k["rve"].close()
+    perr = max(float(np.abs(a - b).max() / np.abs(b).max())
+               for a, b in zip(mixed_k["pbars"], fp64["pbars"]))
+
+    # end to end through the public API: per step the macroscopic F-bar goes
+    # host -> device and the stress field P comes back into pinned host memory
+    pinned = torch.empty(9 * n, dtype=torch.float64, pin_memory=True)
+    e2e = run_schedule(RVE, cfg, "mixed", args.steps, torch, e2e_buf=pinned.numpy())
+    e2e["rve"].close()
+    t_e2e, u_e2e = reduce_max_sum(dist, e2e["wall_s"], float(n) * e2e["cg"])
+
+    result = None
+    if rank == 0:
+        peak, peak_kind = load_peaks()
+        roof = None
+        prof = None
+        if not args.no_profile:
+            prof = kernel_profile(RVE, cfg, torch, KERNEL_FAMILIES)
+            fam = max(prof, key=lambda f: prof[f]["total_ms"])
+            bpl = family_bytes_per_voxel(cfg["shape"][2], fam) * n
+            ach = bpl / (prof[fam]["avg_ms"] / 1e3) / 1e9
+            roof = {"bound": "hbm", "kernel": fam, "achieved": round(ach, 1),
+                    "peak": peak, "unit": "GB/s", "frac": round(ach / peak, 4),
+                    "traffic": None, "peak_kind": peak_kind,
+                    "algorithmic_bytes_per_launch": bpl,
+                    "avg_launch_ms": prof[fam]["avg_ms"]}
+        cpu = None if args.no_cpu_baseline else cpu_baseline_sample(cfg)
+        result = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": t_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32/f64",
+            "data": "synthetic",
+            "config": {"workload": cfg["workload"], "grid": 125, "model": "svk",
+                       "sphere_fraction": round(cfg["fraction"], 4), "contrast": 100,
+                       "increments": args.steps, "tol_newton": cfg["tol_newton"],
+                       "tol_cg": cfg["tol_cg"], "mixed_cg_tol_floor": 1e-5,
+                       "l2": "working set ~1 GB > 129 MB L2, no flush needed",
+                       "parallelism": f"replicas{world}"},
+            "cg_iters": mixed["cg"], "newton_iters": mixed["newton"],
+            "solve_ms_mixed": mixed["ms"],
+            "fp64": {"steps": k64, "value": float(n) * fp64["cg"] / (fp64["ms"] / 1e3),
+                     "cg_iters": fp64["cg"], "solve_ms": fp64["ms"],
+                     "mixed_solve_ms_same_steps": mixed_k["ms"],
+                     "mixed_cg_iters_same_steps": mixed_k["cg"],
+                     "solve_time_ratio_fp64_over_mixed": fp64["ms"] / mixed_k["ms"],
+                     "pbar_rel_err_mixed_vs_fp64": perr},
+            "roofline": roof,
+            "kernel_profile_ms": ({k: round(v["avg_ms"], 5) for k, v in prof.items()}
+                                  if prof else None),
+            "cpu_baseline": ({k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")}
+                             if cpu else None),
+            "e2e": {"value": u_e2e / t_e2e, "unit": UNIT, "h2d_bytes_per_step": 72,
+                    "d2h_bytes_per_step": 9 * n * 8 + 72},
+            "clocks": ck,
+            "gpu_launches": mixed["launches"],
+        }
+        print(json.dumps(result), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    return result
+
+
+if __name__ == "__main__":
+    main()

@@ -81,6 +81,9 @@ typedef struct {
   int max_cg;           /* default 10000 */
   double cg_tol_floor;  /* MIXED only: CG tolerance used = max(tol_cg, floor); default 1e-5 */
   double cg_atol;       /* absolute CG floor: stop when ||r|| <= max(tol ||b||, atol); default 0 */
+  int mixed_refine;     /* MIXED only: extra Newton iterations after the convergence test
+                           first passes (further refinement with the float64 residual);
+                           default 0 */
   void* stream;         /* cudaStream_t; NULL = legacy default stream */
   void* workspace;      /* optional caller-owned device memory (see rve_workspace_size) */
   size_t workspace_bytes;

@@ -68,10 +68,11 @@ void launch_cg_update(size_t n9, R* x, R* r, const R* p, const R* Ap, SolverStat
 template <typename T>
 void launch_mean9(const T* A, size_t n, double* out9, double* partials, unsigned int* counter,
                   int post, SolverState* st, cudaStream_t s);
-void launch_add_uniform(double* F, size_t n, SolverState* st, double* partials, cudaStream_t s);
+void launch_shifted_norm(const double* F, size_t n, SolverState* st, double* partials,
+                         cudaStream_t s);
 template <typename RC>
 void launch_newton_update(double* F, const RC* x, size_t n, SolverState* st, double* partials,
-                          cudaStream_t s);
+                          int add_dfbar, cudaStream_t s);
 template <typename RO>
 void launch_svk_constitutive(const double* F, size_t n, MatView<double> mat, double* P,
                              int tan_mode, RO* K4, RO* Fop, RO* Sop, SolverState* st,

@@ -79,9 +79,10 @@ __global__ void __launch_bounds__(VEC_THREADS) k_mean9(const T* __restrict__ A, 
   }
 }
 
-// F += dFbar (uniform), ||F||^2 -> Fn2
-__global__ void __launch_bounds__(VEC_THREADS) k_add_uniform(double* __restrict__ F, size_t n,
-                                                             SolverState* st, double* partials) {
+// ||F + dFbar||^2 -> Fn2 (F itself is not changed; the macroscopic increment
+// is added together with the first Newton update)
+__global__ void __launch_bounds__(VEC_THREADS) k_shifted_norm(const double* __restrict__ F, size_t n,
+                                                              SolverState* st, double* partials) {
   double d[9];
 #pragma unroll
   for (int c = 0; c < 9; ++c) d[c] = st->dFbar[c];
@@ -91,7 +92,6 @@ __global__ void __launch_bounds__(VEC_THREADS) k_add_uniform(double* __restrict_
 #pragma unroll
     for (int c = 0; c < 9; ++c) {
       const double f = F[(size_t)c * n + v] + d[c];
-      F[(size_t)c * n + v] = f;
       acc += f * f;
     }
   double a[1] = {acc}, tot[1];
@@ -99,22 +99,28 @@ __global__ void __launch_bounds__(VEC_THREADS) k_add_uniform(double* __restrict_
     st->Fn2 = tot[0];
 }
 
-// F += dF - <dF> (the exact mean of dF is zero, Eq. mean:zero; the mean of
-// the computed dF is round-off and is removed), ||dF - <dF>||^2 -> dF2
+// F += dF - <dF> (+ dFbar on the first iteration of an increment, Algorithm 1:
+// F_(1) = F_(0) + dFbar + dF).  The exact mean of dF is zero (Eq. mean:zero);
+// the mean of the computed dF is round-off and is removed.
+// ||dF - <dF>||^2 -> dF2
 template <typename RC>
 __global__ void __launch_bounds__(VEC_THREADS) k_newton_update(double* __restrict__ F,
                                                                const RC* __restrict__ x, size_t n,
-                                                               SolverState* st, double* partials) {
-  double m[9];
+                                                               SolverState* st, double* partials,
+                                                               int add_dfbar) {
+  double m[9], u[9];
 #pragma unroll
-  for (int c = 0; c < 9; ++c) m[c] = st->meanX[c];
+  for (int c = 0; c < 9; ++c) {
+    m[c] = st->meanX[c];
+    u[c] = add_dfbar ? st->dFbar[c] : 0.0;
+  }
   double acc = 0.0;
   const size_t stride = (size_t)gridDim.x * blockDim.x;
   for (size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride)
 #pragma unroll
     for (int c = 0; c < 9; ++c) {
       const double d = (double)x[(size_t)c * n + v] - m[c];
-      F[(size_t)c * n + v] += d;
+      F[(size_t)c * n + v] += u[c] + d;
       acc += d * d;
     }
   double a[1] = {acc}, tot[1];
@@ -266,14 +272,15 @@ void launch_mean9(const T* A, size_t n, double* out9, double* partials, unsigned
   k_mean9<T><<<grid_for(n), VEC_THREADS, 0, s>>>(A, n, out9, partials, counter, post, st);
 }
 
-void launch_add_uniform(double* F, size_t n, SolverState* st, double* partials, cudaStream_t s) {
-  k_add_uniform<<<grid_for(n), VEC_THREADS, 0, s>>>(F, n, st, partials);
+void launch_shifted_norm(const double* F, size_t n, SolverState* st, double* partials,
+                         cudaStream_t s) {
+  k_shifted_norm<<<grid_for(n), VEC_THREADS, 0, s>>>(F, n, st, partials);
 }
 
 template <typename RC>
 void launch_newton_update(double* F, const RC* x, size_t n, SolverState* st, double* partials,
-                          cudaStream_t s) {
-  k_newton_update<RC><<<grid_for(n), VEC_THREADS, 0, s>>>(F, x, n, st, partials);
+                          int add_dfbar, cudaStream_t s) {
+  k_newton_update<RC><<<grid_for(n), VEC_THREADS, 0, s>>>(F, x, n, st, partials, add_dfbar);
 }
 
 template <typename RO>
@@ -302,9 +309,9 @@ template void launch_mean9<float>(const float*, size_t, double*, double*, unsign
 template void launch_mean9<double>(const double*, size_t, double*, double*, unsigned int*, int,
                                    SolverState*, cudaStream_t);
 template void launch_newton_update<float>(double*, const float*, size_t, SolverState*, double*,
-                                          cudaStream_t);
+                                          int, cudaStream_t);
 template void launch_newton_update<double>(double*, const double*, size_t, SolverState*, double*,
-                                           cudaStream_t);
+                                           int, cudaStream_t);
 template void launch_svk_constitutive<float>(const double*, size_t, MatView<double>, double*, int,
                                              float*, float*, float*, SolverState*, cudaStream_t);
 template void launch_svk_constitutive<double>(const double*, size_t, MatView<double>, double*,

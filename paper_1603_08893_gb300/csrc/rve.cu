@@ -278,6 +278,21 @@ void enqueue_residual(rve_t h) {
   h->launches += 5;
 }
 
+// buf <- G : buf in float64 (Eq. weak:discr:FFT-intermediate), in place.
+void enqueue_project_fp64(rve_t h, double* buf) {
+  const GridGeom& g = h->g;
+  TangentView<double> plain{};
+  plain.mode = 0;
+  launch_zfwd<double>(g, SRC_FIELD, plain, buf, nullptr, nullptr, nullptr, h->st, nullptr,
+                      h->spec64, h->twd, h->s);
+  launch_fft_y<double>(g, false, h->spec64, nullptr, h->twd, h->s);
+  launch_fft_x_proj<double>(g, 1.0 / (double)h->n, h->spec64, nullptr, h->twd, h->s);
+  launch_fft_y<double>(g, true, h->spec64, nullptr, h->twd, h->s);
+  launch_zinv<double, double>(g, OUT_PLAIN, h->spec64, buf, nullptr, nullptr, nullptr, h->st,
+                              h->partials, nullptr, h->twd, h->s);
+  h->launches += 5;
+}
+
 // predictor right-hand side b = -G:(K_(0) : dFbar) (Eq. bc:lin) in the
 // operator precision; dFbar = Fbar - <F> computed on the device.
 template <typename R>
@@ -353,6 +368,10 @@ int cg_solve(rve_t h, int* iters) {
   }
   *iters = h->hst->it;
   h->solve_iters.push_back({h->solve_id, h->hst->it});
+  // float32 CG can lose positivity of p.Ap once its residual reaches the
+  // float32 noise level; the iterate so far is kept and the float64 Newton
+  // residual decides whether more work is needed.
+  if (h->mixed && h->hst->status == RVE_DEV_ERR_CG_BREAKDOWN && h->hst->it >= 1) return RVE_OK;
   return h->hst->status;
 }
 
@@ -439,6 +458,7 @@ void rve_default_options(rve_options* o) {
   o->max_cg = 10000;
   o->cg_tol_floor = 1e-5;
   o->cg_atol = 0.0;
+  o->mixed_refine = 0;
 }
 
 const char* rve_status_string(int code) {
@@ -471,6 +491,7 @@ static int resolve_options(const rve_options* in, rve_options* out, int model, i
   if (out->max_cg <= 0) out->max_cg = 10000;
   if (!(out->cg_tol_floor >= 0.0)) return RVE_ERR_INVALID;
   if (!(out->cg_atol >= 0.0)) return RVE_ERR_INVALID;
+  if (out->mixed_refine < 0 || out->mixed_refine > 8) return RVE_ERR_INVALID;
   if (model == RVE_SVK) {
     if (out->tangent == RVE_TAN_AUTO || out->tangent == RVE_TAN_RECOMPUTE) *tan = TAN_SVK;
     else if (out->tangent == RVE_TAN_FULL81) *tan = TAN_FULL81;
@@ -683,16 +704,14 @@ static int solve_increment_t(rve_t h, double tol_newton, double tol_cg, rve_stat
   if (rc) return rc;
   // predictor (i = 0 right-hand side) and ||F_(0) + dFbar||
   enqueue_predictor<R>(h);
-  {
-    // Fn2 = ||F + dFbar||^2 (F itself is updated together with the first dF)
-    launch_convert<double, double>(h->F, h->tmp64, n9, h->s);
-    launch_add_uniform(h->tmp64, h->n, h->st, h->partials, h->s);
-    h->launches += 2;
-  }
+  // ||F_(0) + dFbar|| (F itself is updated together with the first dF)
+  launch_shifted_norm(h->F, h->n, h->st, h->partials, h->s);
+  h->launches += 1;
   int result = RVE_OK;
   bool converged = false;
   int newton = 0;
   int cg_total = 0;
+  int extra_refine = h->mixed ? h->opt.mixed_refine : 0;
   for (int i = 0; i < h->opt.max_newton; ++i) {
     int its = 0;
     CK(cudaGetLastError());
@@ -703,14 +722,22 @@ static int solve_increment_t(rve_t h, double tol_newton, double tol_cg, rve_stat
       result = fail(h, rc, std::string("linear solve: ") + rve_status_string(rc));
       break;
     }
-    launch_mean9<R>(as<R>(h->x), h->n, nullptr, h->partials, &h->st->counter[SLOT_MEAN], MEAN_X,
-                    h->st, h->s);
-    if (i == 0) {
-      // F_(1) = F_(0) + dFbar + dF (Algorithm 1)
-      launch_convert<double, double>(h->tmp64, h->F, n9, h->s);
-      h->launches += 1;
+    if (h->mixed) {
+      // float32 CG leaves dF compatible only up to float32 round-off
+      // amplified by the cancellation in the CG sum; project it onto the
+      // compatible fields in float64 so that F stays compatible (Sec. 2.3)
+      launch_convert<R, double>(as<R>(h->x), h->tmp64, n9, h->s);
+      enqueue_project_fp64(h, h->tmp64);
+      launch_mean9<double>(h->tmp64, h->n, nullptr, h->partials, &h->st->counter[SLOT_MEAN],
+                           MEAN_X, h->st, h->s);
+      launch_newton_update<double>(h->F, h->tmp64, h->n, h->st, h->partials, i == 0, h->s);
+      h->launches += 3;
+    } else {
+      launch_mean9<R>(as<R>(h->x), h->n, nullptr, h->partials, &h->st->counter[SLOT_MEAN], MEAN_X,
+                      h->st, h->s);
+      launch_newton_update<R>(h->F, as<R>(h->x), h->n, h->st, h->partials, i == 0, h->s);
+      h->launches += 2;
     }
-    launch_newton_update<R>(h->F, as<R>(h->x), h->n, h->st, h->partials, h->s);
     enqueue_constitutive(h);
     enqueue_residual<R>(h);
     h->launches += 2;
@@ -735,6 +762,10 @@ static int solve_increment_t(rve_t h, double tol_newton, double tol_cg, rve_stat
       break;
     }
     if (rel < tol_newton && i > 0) {
+      if (extra_refine > 0) {
+        --extra_refine;
+        continue;
+      }
       converged = true;
       break;
     }
@@ -874,17 +905,7 @@ int rve_project(rve_t h, const double* A, double* out, int on_device) {
   const size_t n9 = 9 * h->n;
   int rc = copy_in(h, h->tmp64, A, n9 * 8, on_device);
   if (rc) return rc;
-  const GridGeom& g = h->g;
-  TangentView<double> plain{};
-  plain.mode = 0;
-  launch_zfwd<double>(g, SRC_FIELD, plain, h->tmp64, nullptr, nullptr, nullptr, h->st, nullptr,
-                      h->spec64, h->twd, h->s);
-  launch_fft_y<double>(g, false, h->spec64, nullptr, h->twd, h->s);
-  launch_fft_x_proj<double>(g, 1.0 / (double)h->n, h->spec64, nullptr, h->twd, h->s);
-  launch_fft_y<double>(g, true, h->spec64, nullptr, h->twd, h->s);
-  launch_zinv<double, double>(g, OUT_PLAIN, h->spec64, h->tmp64, nullptr, nullptr, nullptr, h->st,
-                              h->partials, nullptr, h->twd, h->s);
-  h->launches += 5;
+  enqueue_project_fp64(h, h->tmp64);
   CK(cudaGetLastError());
   return copy_out(h, out, h->tmp64, n9 * 8, on_device);
 }
