@@ -175,6 +175,34 @@ int rve_launch_count(rve_t h, long long* count);
 int rve_kernel_timing(rve_t h, int family, int enable);
 int rve_kernel_time(rve_t h, double* total_ms, long long* launches);
 
+/* ---------------------------------------------------------------------------
+ * Allocation-free projection.  (The paper has no counterpart: this entry
+ * point exists for callers of this library that cannot allocate device
+ * memory -- code running while a CUDA graph is captured, plugins whose host
+ * program owns all device allocations, real-time paths that must not
+ * allocate.)
+ *
+ * out = G : A in float64, the same operation as rve_project, without a
+ * handle and without allocating anything: its scratch (the float64 half
+ * spectrum, 9*nx*ny*(nz/2+1 rounded up to a multiple of 4) complex values,
+ * plus the twiddle tables) lives in one fixed device array of
+ * RVE_NOALLOC_SCRATCH_BYTES that the library reserves on every GPU that
+ * loads it, for the life of the process.
+ *  A, out : [9][n] float64 in device memory of the current device; out may
+ *           equal A.  The caller owns both.
+ *  stream : cudaStream_t (NULL = legacy default stream).  The call only
+ *           enqueues work; synchronise the stream before reading out.
+ * The first call on a device looks up the array's device address (one
+ * cudaGetSymbolAddress); make that first call before any stream capture.
+ * All calls on a device share the one array and it keeps the last call's
+ * contents: calls whose work overlaps on the GPU (different streams without
+ * ordering, or concurrent host threads) race on it.
+ * Errors: RVE_ERR_INVALID (null pointer, even or unsupported sizes),
+ * RVE_ERR_NOMEM (the grid's scratch exceeds RVE_NOALLOC_SCRATCH_BYTES, e.g.
+ * 63^3), RVE_ERR_CUDA. */
+#define RVE_NOALLOC_SCRATCH_BYTES (16u * 1024u * 1024u)
+int rve_project_noalloc(int nx, int ny, int nz, const double* A, double* out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -76,6 +76,7 @@ _SIGS = {
     "rve_kernel_timing": (C.c_int, [_H, C.c_int, C.c_int]),
     "rve_kernel_time": (C.c_int, [_H, C.POINTER(C.c_double),
                                   C.POINTER(C.c_longlong)]),
+    "rve_project_noalloc": (C.c_int, [C.c_int, C.c_int, C.c_int, _P, _P, _P]),
 }
 
 

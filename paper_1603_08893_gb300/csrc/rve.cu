@@ -98,6 +98,9 @@ bool make_geom(int nx, int ny, int nz, GridGeom* g) {
 
 }  // namespace
 
+// Grid geometry for other translation units of the library.
+bool rve_internal_make_geom(int nx, int ny, int nz, GridGeom* g) { return make_geom(nx, ny, nz, g); }
+
 struct rve_s {
   int model = RVE_SVK;
   rve_options opt{};

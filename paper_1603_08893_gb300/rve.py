@@ -190,6 +190,22 @@ def rve_project(h, A, n, out=None):
     return _unary(lib.rve_project, h, A, n, out)
 
 
+def rve_project_noalloc(shape, A, out, stream=None):
+    """out = G : A (float64) without a handle and without any device
+    allocation; A and out are float64 CUDA tensors of 9*n values.  For
+    callers that cannot allocate device memory (the scratch lives in a fixed
+    array inside the library).  Enqueues on `stream` (default: torch's
+    current stream) and returns the status code."""
+    if not (_is_torch_cuda(A) and _is_torch_cuda(out)):
+        raise ValueError("A and out must be CUDA tensors")
+    if stream is None:
+        stream = torch.cuda.current_stream().cuda_stream
+    nx, ny, nz = (int(s) for s in shape)
+    return lib.rve_project_noalloc(nx, ny, nz, C.c_void_p(A.data_ptr()),
+                                   C.c_void_p(out.data_ptr()),
+                                   C.c_void_p(int(stream)) if stream else None)
+
+
 def rve_launch_count(h):
     c = C.c_longlong(0)
     _check(lib.rve_launch_count(h, C.byref(c)), h)
