@@ -10,26 +10,48 @@
 //
 // Odd radices 3, 5, 7, 11 use the symmetric form of the R-point DFT
 // (pairs x_r +- x_(R-r)); other primes use a direct sum, one output per
-// thread.  All stages of a line run in place: each thread loads its
-// butterflies into registers, the block synchronises, then stores.
+// thread.  Stages alternate between two shared-memory buffers.
 #pragma once
 #include "common.cuh"
 
 #define RVE_MAX_STAGES 16
 
+// Unsigned division by a run-time constant d through one 64-bit multiply:
+// q = (a * ceil(2^40 / d)) >> 40, exact whenever a * d < 2^40 (all indices
+// here are below 2^20).  The multiplier is computed on the host (a 64-bit
+// division on the device would run on the FP64 pipe).
+struct FastDiv {
+  unsigned long long m;
+  unsigned d;
+  RVE_DEV unsigned div(unsigned a) const { return (unsigned)(((unsigned long long)a * m) >> 40); }
+};
+
+inline FastDiv make_fastdiv(unsigned d) {
+  FastDiv f;
+  f.d = d ? d : 1;
+  f.m = ((1ull << 40) + f.d - 1) / f.d;
+  return f;
+}
+
 struct AxisPlan {
   int n;
   int nst;
   int rad[RVE_MAX_STAGES];
+  FastDiv fNs[RVE_MAX_STAGES];  // divide by the product of the earlier radices
+  FastDiv fnb[RVE_MAX_STAGES];  // divide by n / rad[s] (butterflies per line)
+  FastDiv fN;                   // divide by n
 };
 
 // Maps line index l to its first element in shared memory:
-//   base(l) = (l / grp) * gstride + (l % grp) * lstride, element e at base + e*es.
+//   base(l) = (l >> gshift) * gstride + (l & (2^gshift - 1)) * lstride,
+// element e at base + e*es (the group size is a power of two).
 // lf != 0 assigns consecutive threads to consecutive lines (strided layouts),
 // otherwise to consecutive butterflies of one line (contiguous layouts).
 struct LineMap {
-  int grp, gstride, lstride, es, lf;
-  RVE_DEV int base(int l) const { return (l / grp) * gstride + (l % grp) * lstride; }
+  int gshift, gstride, lstride, es, lf;
+  RVE_DEV int base(int l) const {
+    return (l >> gshift) * gstride + (l & ((1 << gshift) - 1)) * lstride;
+  }
 };
 
 template <typename R, int RAD, bool INV>
@@ -68,10 +90,15 @@ RVE_DEV void dft_odd(cplx<R> (&v)[RAD], const R (&cs)[RAD], const R (&sn)[RAD]) 
   v[0] = s;
 }
 
+// One Stockham stage from `src` to `dst` (two shared-memory buffers): every
+// thread takes butterflies b = tid, tid + nthr, ... of all L lines, so each
+// butterfly is loaded, transformed and stored without waiting on others; one
+// barrier ends the stage.  Strided layouts (lm.lf) give consecutive threads
+// consecutive lines; contiguous layouts consecutive butterflies of a line.
 template <typename R, int RAD, bool INV>
-__device__ __noinline__ void fft_stage(cplx<R>* buf, const LineMap lm, int nlines, int N, int Ns,
-                                       const cplx<R>* tw) {
-  constexpr int MAXB = (RAD <= 3) ? 2 : 1;
+RVE_DEV void stage_pp(const cplx<R>* __restrict__ src, cplx<R>* __restrict__ dst, const LineMap lm,
+                      int L, const FastDiv fL, int N, int Ns, const FastDiv fNs, const FastDiv fnb,
+                      const cplx<R>* tw) {
   const int nb = N / RAD;
   const int tws = N / (Ns * RAD);
   R cs[RAD], sn[RAD];
@@ -81,117 +108,111 @@ __device__ __noinline__ void fft_stage(cplx<R>* buf, const LineMap lm, int nline
     cs[m] = w.x;
     sn[m] = -w.y;
   }
-  const int nthr = blockDim.x;
-  int lpc = (nthr * MAXB) / nb;
-  if (lpc < 1) lpc = 1;
-  for (int l0 = 0; l0 < nlines; l0 += lpc) {
-    const int nl = min(lpc, nlines - l0);
-    const int cnt = nl * nb;
-    cplx<R> v[MAXB][RAD];
-#pragma unroll
-    for (int t = 0; t < MAXB; ++t) {
-      const int b = t * nthr + threadIdx.x;
-      if (b < cnt) {
-        int l, j;
-        if (lm.lf) { l = b % nl; j = b / nl; } else { l = b / nb; j = b - (b / nb) * nb; }
-        const cplx<R>* base = buf + lm.base(l0 + l);
-        const int jr = j % Ns;
-#pragma unroll
-        for (int r = 0; r < RAD; ++r) v[t][r] = base[(j + r * nb) * lm.es];
-#pragma unroll
-        for (int r = 1; r < RAD; ++r) {
-          const cplx<R> w = tw[r * jr * tws];
-          v[t][r] = INV ? c_mulc(v[t][r], w) : c_mul(v[t][r], w);
-        }
-        dft_odd<R, RAD, INV>(v[t], cs, sn);
-      }
+  const int total = L * nb;
+  for (int b = threadIdx.x; b < total; b += blockDim.x) {
+    int l, j;
+    if (lm.lf) {
+      j = (int)fL.div((unsigned)b);
+      l = b - j * L;
+    } else {
+      l = (int)fnb.div((unsigned)b);
+      j = b - l * nb;
     }
-    __syncthreads();
+    const int jq = (int)fNs.div((unsigned)j);
+    const int jr = j - jq * Ns;
+    const int base = lm.base(l);
+    cplx<R> v[RAD];
 #pragma unroll
-    for (int t = 0; t < MAXB; ++t) {
-      const int b = t * nthr + threadIdx.x;
-      if (b < cnt) {
-        int l, j;
-        if (lm.lf) { l = b % nl; j = b / nl; } else { l = b / nb; j = b - (b / nb) * nb; }
-        cplx<R>* base = buf + lm.base(l0 + l);
-        const int jr = j % Ns;
-        const int d = (j / Ns) * Ns * RAD + jr;
+    for (int r = 0; r < RAD; ++r) v[r] = src[base + (j + r * nb) * lm.es];
 #pragma unroll
-        for (int r = 0; r < RAD; ++r) base[(d + r * Ns) * lm.es] = v[t][r];
-      }
+    for (int r = 1; r < RAD; ++r) {
+      const cplx<R> w = tw[r * jr * tws];
+      v[r] = INV ? c_mulc(v[r], w) : c_mul(v[r], w);
     }
-    __syncthreads();
+    dft_odd<R, RAD, INV>(v, cs, sn);
+    const int d = jq * Ns * RAD + jr;
+#pragma unroll
+    for (int r = 0; r < RAD; ++r) dst[base + (d + r * Ns) * lm.es] = v[r];
   }
+  __syncthreads();
 }
 
 // Direct R-point DFT for any prime R: one output element per thread.
 template <typename R, bool INV>
-__device__ __noinline__ void fft_stage_generic(cplx<R>* buf, const LineMap lm, int nlines, int N,
-                                               int Ns, int RAD, const cplx<R>* tw) {
-  constexpr int MAXO = 2;
+RVE_DEV void stage_pp_generic(const cplx<R>* __restrict__ src, cplx<R>* __restrict__ dst,
+                              const LineMap lm, int L, const FastDiv fL, int N, int Ns, int RAD,
+                              const FastDiv fNs, const FastDiv fnb, const FastDiv fN,
+                              const cplx<R>* tw) {
   const int nb = N / RAD;
   const int tws = N / (Ns * RAD);
-  const int nthr = blockDim.x;
-  int lpc = (nthr * MAXO) / N;
-  if (lpc < 1) lpc = 1;
-  for (int l0 = 0; l0 < nlines; l0 += lpc) {
-    const int nl = min(lpc, nlines - l0);
-    const int cnt = nl * N;
-    cplx<R> out[MAXO];
-#pragma unroll
-    for (int t = 0; t < MAXO; ++t) {
-      const int o = t * nthr + threadIdx.x;
-      if (o < cnt) {
-        int l, q;
-        if (lm.lf) { l = o % nl; q = o / nl; } else { l = o / N; q = o - (o / N) * N; }
-        const int k = q / nb, j = q - (q / nb) * nb;
-        const cplx<R>* base = buf + lm.base(l0 + l);
-        const int m = (j % Ns) * tws + k * nb;  // < N
-        cplx<R> acc = {R(0), R(0)};
-        int e = 0;
-        for (int r = 0; r < RAD; ++r) {
-          const cplx<R> x = base[(j + r * nb) * lm.es];
-          const cplx<R> w = tw[e];
-          const cplx<R> p = INV ? c_mulc(x, w) : c_mul(x, w);
-          acc = c_add(acc, p);
-          e += m;
-          if (e >= N) e -= N;
-        }
-        out[t] = acc;
-      }
+  const int total = L * N;
+  for (int o = threadIdx.x; o < total; o += blockDim.x) {
+    int l, q;
+    if (lm.lf) {
+      q = (int)fL.div((unsigned)o);
+      l = o - q * L;
+    } else {
+      l = (int)fN.div((unsigned)o);
+      q = o - l * N;
     }
-    __syncthreads();
-#pragma unroll
-    for (int t = 0; t < MAXO; ++t) {
-      const int o = t * nthr + threadIdx.x;
-      if (o < cnt) {
-        int l, q;
-        if (lm.lf) { l = o % nl; q = o / nl; } else { l = o / N; q = o - (o / N) * N; }
-        const int k = q / nb, j = q - (q / nb) * nb;
-        cplx<R>* base = buf + lm.base(l0 + l);
-        const int d = (j / Ns) * Ns * RAD + (j % Ns) + k * Ns;
-        base[d * lm.es] = out[t];
-      }
+    const int k = (int)fnb.div((unsigned)q);
+    const int j = q - k * nb;
+    const int jq = (int)fNs.div((unsigned)j);
+    const int jr = j - jq * Ns;
+    const int base = lm.base(l);
+    const int m = jr * tws + k * nb;  // < N
+    cplx<R> acc = {R(0), R(0)};
+    int e = 0;
+    for (int r = 0; r < RAD; ++r) {
+      const cplx<R> x = src[base + (j + r * nb) * lm.es];
+      const cplx<R> w = tw[e];
+      acc = c_add(acc, INV ? c_mulc(x, w) : c_mul(x, w));
+      e += m;
+      if (e >= N) e -= N;
     }
-    __syncthreads();
+    dst[base + (jq * Ns * RAD + jr + k * Ns) * lm.es] = acc;
   }
+  __syncthreads();
 }
 
-// All stages of the plan on `nlines` lines.  tw[k] = exp(-2 pi i k / N) must
-// be readable by every thread (shared memory).  Caller synchronises before.
+// Copies an axis plan into shared memory (indexing a kernel parameter with a
+// run-time stage number would force a local-memory copy per thread).
+RVE_DEV void load_plan(AxisPlan* dst, const AxisPlan& src) {
+  const int* s = reinterpret_cast<const int*>(&src);
+  int* d = reinterpret_cast<int*>(dst);
+  for (int i = threadIdx.x; i < (int)(sizeof(AxisPlan) / sizeof(int)); i += blockDim.x) d[i] = s[i];
+}
+
+// All stages of the plan on L lines, ping-ponging between buffers a and b
+// (same layout).  tw[k] = exp(-2 pi i k / N) must be in shared memory.
+// Returns the buffer that holds the result.  Caller synchronises before.
 template <typename R, bool INV>
-RVE_DEV void fft_lines(cplx<R>* buf, const LineMap& lm, int nlines, const AxisPlan& p,
-                       const cplx<R>* tw) {
+RVE_DEV cplx<R>* fft_lines(cplx<R>* a, cplx<R>* b, const LineMap& lm, int L, const FastDiv fL,
+                           const AxisPlan& p, const cplx<R>* tw) {
   int Ns = 1;
   for (int s = 0; s < p.nst; ++s) {
     const int rad = p.rad[s];
+    const FastDiv fNs = p.fNs[s], fnb = p.fnb[s];
     switch (rad) {
-      case 3: fft_stage<R, 3, INV>(buf, lm, nlines, p.n, Ns, tw); break;
-      case 5: fft_stage<R, 5, INV>(buf, lm, nlines, p.n, Ns, tw); break;
-      case 7: fft_stage<R, 7, INV>(buf, lm, nlines, p.n, Ns, tw); break;
-      case 11: fft_stage<R, 11, INV>(buf, lm, nlines, p.n, Ns, tw); break;
-      default: fft_stage_generic<R, INV>(buf, lm, nlines, p.n, Ns, rad, tw); break;
+      case 3: stage_pp<R, 3, INV>(a, b, lm, L, fL, p.n, Ns, fNs, fnb, tw); break;
+      case 5: stage_pp<R, 5, INV>(a, b, lm, L, fL, p.n, Ns, fNs, fnb, tw); break;
+      case 7: stage_pp<R, 7, INV>(a, b, lm, L, fL, p.n, Ns, fNs, fnb, tw); break;
+      case 11: stage_pp<R, 11, INV>(a, b, lm, L, fL, p.n, Ns, fNs, fnb, tw); break;
+      default: stage_pp_generic<R, INV>(a, b, lm, L, fL, p.n, Ns, rad, fNs, fnb, p.fN, tw); break;
     }
+    cplx<R>* t = a;
+    a = b;
+    b = t;
     Ns *= rad;
   }
+  return a;
+}
+
+// Out-of-line entry for kernels that run several transforms (the x pass):
+// each call gets its own register allocation.
+template <typename R, bool INV>
+__device__ __noinline__ cplx<R>* fft_lines_call(cplx<R>* a, cplx<R>* b, const LineMap lm, int L,
+                                                const FastDiv fL, const AxisPlan* p,
+                                                const cplx<R>* tw) {
+  return fft_lines<R, INV>(a, b, lm, L, fL, *p, tw);
 }

@@ -23,6 +23,9 @@ struct GridGeom {
   int lz_f, lz_d;     // z lines per CTA (float, double)
   int ty_f, ty_d, gy_f, gy_d;  // y tile (kz) and groups per CTA
   int tx_f, tx_d;     // x tile (kz)
+  // host-computed divisors used in index arithmetic
+  FastDiv f_hz, f_lzf, f_lzd, f_ny, f_ntky_f, f_ntky_d, f_ntkx_f, f_ntkx_d;
+  FastDiv f_Ly_f, f_Ly_d, f_Lx_f, f_Lx_d;  // lines per y / x tile
 };
 
 template <typename R>

@@ -11,9 +11,15 @@
 //            (kz-tile x nx x 9 components) tiles that stay in shared memory.
 //   zinv   : complex-to-real inverse DFT along z and the output stage
 //            (plain copy, CG product p.Ap, or residual / CG initialisation).
+#include <algorithm>
+#include <map>
+#include <mutex>
+
 #include "kernels.h"
 
 #define FFT_THREADS 256
+// float kernels: three CTAs per SM (<= 85 registers); double: two (<= 128)
+#define FFT_BOUNDS(R) __launch_bounds__(FFT_THREADS, sizeof(R) == 4 ? 3 : 2)
 
 template <typename R>
 RVE_DEV R signed_freq(int k, int n) {
@@ -114,13 +120,16 @@ struct ZfwdParams {
 };
 
 template <typename R, int SRC, int TAN>
-__global__ void __launch_bounds__(FFT_THREADS) k_zfwd(const ZfwdParams<R> P) {
+__global__ void FFT_BOUNDS(R) k_zfwd(const ZfwdParams<R> P) {
   if (P.done && *P.done) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int nz = P.g.nz, lz = P.lz;
   cplx<R>* tw = reinterpret_cast<cplx<R>*>(smem_raw);
-  cplx<R>* buf = tw + nz;  // [5][lz][nz]
+  cplx<R>* bufA = tw + ((nz + 1) & ~1);  // [5][lz][nz]
+  cplx<R>* bufB = bufA + 5 * lz * nz;
   for (int i = threadIdx.x; i < nz; i += blockDim.x) tw[i] = P.tw[i];
+  __shared__ AxisPlan plan;
+  load_plan(&plan, P.g.pz);
   const size_t n = P.g.n;
   const int nlines = P.g.nx * P.g.ny;
   const int l0 = blockIdx.x * lz;
@@ -135,6 +144,7 @@ __global__ void __launch_bounds__(FFT_THREADS) k_zfwd(const ZfwdParams<R> P) {
   }
   TangentView<R> T = P.tan;
   T.mode = TAN;
+  // every global load of a voxel is issued before its stores
   for (int i = threadIdx.x; i < lz * nz; i += blockDim.x) {
     R in[9], out[9];
     if (i < nvox) {
@@ -143,38 +153,46 @@ __global__ void __launch_bounds__(FFT_THREADS) k_zfwd(const ZfwdParams<R> P) {
 #pragma unroll
         for (int c = 0; c < 9; ++c) in[c] = P.field[(size_t)c * n + v];
       } else if (SRC == SRC_CGP) {
+        R rr[9], pp[9];
 #pragma unroll
-        for (int c = 0; c < 9; ++c) {
-          const R rr = P.r[(size_t)c * n + v];
-          const R pp = first ? rr : fma(beta, P.p[(size_t)c * n + v], rr);
-          P.p[(size_t)c * n + v] = pp;
-          in[c] = pp;
+        for (int c = 0; c < 9; ++c) rr[c] = P.r[(size_t)c * n + v];
+        if (!first) {
+#pragma unroll
+          for (int c = 0; c < 9; ++c) pp[c] = P.p[(size_t)c * n + v];
         }
+#pragma unroll
+        for (int c = 0; c < 9; ++c) in[c] = first ? rr[c] : fma(beta, pp[c], rr[c]);
       } else {
 #pragma unroll
         for (int c = 0; c < 9; ++c) in[c] = (R)P.unif[c];
       }
       tangent_voxel<R>(T, v, n, in, out);
+      if (SRC == SRC_CGP) {
+#pragma unroll
+        for (int c = 0; c < 9; ++c) P.p[(size_t)c * n + v] = in[c];
+      }
     } else {
 #pragma unroll
       for (int c = 0; c < 9; ++c) out[c] = 0;
     }
 #pragma unroll
     for (int k = 0; k < 5; ++k)
-      buf[k * lz * nz + i] = {out[2 * k], (2 * k + 1 < 9) ? out[2 * k + 1] : R(0)};
+      bufA[k * lz * nz + i] = {out[2 * k], (2 * k + 1 < 9) ? out[2 * k + 1] : R(0)};
   }
   __syncthreads();
-  const LineMap lm{1 << 30, 0, nz, 1, 0};
-  fft_lines<R, false>(buf, lm, 5 * lz, P.g.pz, tw);
+  const LineMap lm{30, 0, nz, 1, 0};
+  const cplx<R>* res = fft_lines<R, false>(bufA, bufB, lm, 5 * lz, P.g.f_hz, plan, tw);
   const int hz = P.g.hz, hzp = P.g.hzp;
   const size_t ss = P.g.sstride;
-  for (int i = threadIdx.x; i < 5 * nl * hz; i += blockDim.x) {
-    const int kz = i % hz;
-    const int rest = i / hz;
-    const int li = rest % nl;
-    const int k = rest / nl;
-    const cplx<R> z1 = buf[(k * lz + li) * nz + kz];
-    cplx<R> z2 = buf[(k * lz + li) * nz + (kz ? nz - kz : 0)];
+  const FastDiv dhz = P.g.f_hz, dlz = sizeof(R) == 4 ? P.g.f_lzf : P.g.f_lzd;
+  for (int i = threadIdx.x; i < 5 * lz * hz; i += blockDim.x) {
+    const int rest = (int)dhz.div((unsigned)i);
+    const int kz = i - rest * hz;
+    const int k = (int)dlz.div((unsigned)rest);
+    const int li = rest - k * lz;
+    if (li >= nl) continue;
+    const cplx<R> z1 = res[(k * lz + li) * nz + kz];
+    cplx<R> z2 = res[(k * lz + li) * nz + (kz ? nz - kz : 0)];
     z2.y = -z2.y;
     const size_t o = (size_t)(l0 + li) * hzp + kz;
     P.spec[(size_t)(2 * k) * ss + o] = {R(0.5) * (z1.x + z2.x), R(0.5) * (z1.y + z2.y)};
@@ -196,92 +214,137 @@ struct LineParams {
   const cplx<R>* tw;
 };
 
-template <typename R, bool INV>
-__global__ void __launch_bounds__(FFT_THREADS) k_fft_y(const LineParams<R> P) {
-  if (P.done && *P.done) return;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int ny = P.g.ny, T = P.t;
-  cplx<R>* tw = reinterpret_cast<cplx<R>*>(smem_raw);
-  cplx<R>* buf = tw + ny;  // [grp][ny][T]
-  for (int i = threadIdx.x; i < ny; i += blockDim.x) tw[i] = P.tw[i];
-  const int ngroups = 9 * P.g.nx;
-  const int k0 = blockIdx.x * T;
-  const int g0 = blockIdx.y * P.grp;
-  const int ng = min(P.grp, ngroups - g0);
-  const int tc = min(T, P.g.hz - k0);
-  const int hzp = P.g.hzp;
-  const int tot = ng * ny * T;
-  for (int i = threadIdx.x; i < tot; i += blockDim.x) {
-    const int t = i % T;
-    const int y = (i / T) % ny;
-    const int gg = i / (T * ny);
-    buf[i] = (t < tc) ? P.spec[((size_t)(g0 + gg) * ny + y) * hzp + k0 + t] : cplx<R>{R(0), R(0)};
-  }
-  __syncthreads();
-  const LineMap lm{T, ny * T, 1, T, 1};
-  fft_lines<R, INV>(buf, lm, ng * T, P.g.py, tw);
-  for (int i = threadIdx.x; i < tot; i += blockDim.x) {
-    const int t = i % T;
-    const int y = (i / T) % ny;
-    const int gg = i / (T * ny);
-    if (t < tc) P.spec[((size_t)(g0 + gg) * ny + y) * hzp + k0 + t] = buf[i];
+// ---------------------------------------------------------------------------
+// 16-byte asynchronous global->shared copies (cp.async): a tile's loads are
+// in flight while the previous tile is transformed.  bytes = 0 zero-fills.
+// ---------------------------------------------------------------------------
+RVE_DEV void cp_async16(void* sdst, const void* gsrc, int bytes) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(sdst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gsrc), "r"(bytes));
+}
+RVE_DEV void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+RVE_DEV void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
+// Tiles of the strided passes: `rows` rows of T complex values (T a power of
+// two, 64 bytes); row r of the tile starts at gbase + r * rstride.  Rows are
+// copied in 16-byte chunks; chunks past the padded row length are zero-filled
+// and not read.
+template <typename R>
+RVE_DEV void issue_tile(cplx<R>* sbuf, const cplx<R>* gbase, size_t rstride, int rows, int T,
+                        int ts, int kz0, int hzp, const cplx<R>* any_valid) {
+  constexpr int EPC = 16 / sizeof(cplx<R>);  // complex values per chunk
+  const int cpr = T / EPC;                   // chunks per row (power of two)
+  const int cs = __ffs(cpr) - 1;
+  const int nch = rows * cpr;
+  for (int c = threadIdx.x; c < nch; c += blockDim.x) {
+    const int row = c >> cs;
+    const int t = (c & (cpr - 1)) * EPC;
+    const bool ok = (kz0 + t) < hzp;
+    const cplx<R>* src = ok ? gbase + (size_t)row * rstride + t : any_valid;
+    cp_async16(sbuf + (row << ts) + t, src, ok ? 16 : 0);
   }
 }
 
+// Complex DFT along y (forward or inverse) on tiles of (grp component-x
+// rows) x ny x (T consecutive kz); the tile is fetched with cp.async and the
+// stages ping-pong between two shared buffers.
+template <typename R, bool INV>
+__global__ void FFT_BOUNDS(R) k_fft_y(const LineParams<R> P) {
+  if (P.done && *P.done) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int ny = P.g.ny, T = P.t, grp = P.grp;
+  const int ts = __ffs(T) - 1;  // T is a power of two
+  const int tile_elems = grp * ny * T;
+  cplx<R>* tw = reinterpret_cast<cplx<R>*>(smem_raw);
+  cplx<R>* bufA = tw + ((ny + 1) & ~1);  // 16-byte aligned
+  cplx<R>* bufB = bufA + tile_elems;
+  const int hz = P.g.hz, hzp = P.g.hzp;
+  const int ngroups = 9 * P.g.nx;
+  const int ntk = (hz + T - 1) >> ts;
+  const FastDiv dntk = sizeof(R) == 4 ? P.g.f_ntky_f : P.g.f_ntky_d;
+  const int tile = blockIdx.x;
+  const int tg = (int)dntk.div((unsigned)tile);
+  const int k0 = (tile - tg * ntk) * T, g0 = tg * grp;
+  const int ng = min(grp, ngroups - g0);
+  cplx<R>* gbase = P.spec + (size_t)g0 * ny * hzp + k0;
+  issue_tile<R>(bufA, gbase, (size_t)hzp, ng * ny, T, ts, k0, hzp, P.spec);
+  cp_async_commit();
+  for (int i = threadIdx.x; i < ny; i += blockDim.x) tw[i] = P.tw[i];
+  __shared__ AxisPlan plan;
+  load_plan(&plan, P.g.py);
+  cp_async_wait<0>();
+  __syncthreads();
+  const LineMap lm{ts, ny * T, 1, T, 1};
+  const FastDiv fL = sizeof(R) == 4 ? P.g.f_Ly_f : P.g.f_Ly_d;
+  const cplx<R>* res = fft_lines<R, INV>(bufA, bufB, lm, grp * T, fL, plan, tw);
+  const int tc = min(T, hz - k0);
+  const int tot = ng * ny * T;
+  for (int i = threadIdx.x; i < tot; i += blockDim.x) {
+    const int t = i & (T - 1);
+    if (t < tc) gbase[(size_t)(i >> ts) * hzp + t] = res[i];
+  }
+}
+
+// Forward DFT along x, projection, inverse DFT along x.  The projection
+// A_ij <- xi_j (sum_l xi_l A_il) / |xi|^2 (Eq. G_red) couples only the three
+// components of one tensor row i, so a tile is (row i) x nx x (T kz) for one
+// ky.
 template <typename R>
-__global__ void __launch_bounds__(FFT_THREADS) k_fft_x_proj(const LineParams<R> P) {
+__global__ void FFT_BOUNDS(R) k_fft_x_proj(const LineParams<R> P) {
   if (P.done && *P.done) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int nx = P.g.nx, ny = P.g.ny, T = P.t;
+  const int ts = __ffs(T) - 1;
+  const int tile_elems = 3 * nx * T;
   cplx<R>* tw = reinterpret_cast<cplx<R>*>(smem_raw);
-  cplx<R>* buf = tw + nx;  // [9][nx][T]
+  cplx<R>* bufA = tw + ((nx + 1) & ~1);
+  cplx<R>* bufB = bufA + tile_elems;
+  const int hz = P.g.hz, hzp = P.g.hzp;
+  const int ntk = (hz + T - 1) >> ts;
+  const FastDiv dntk = sizeof(R) == 4 ? P.g.f_ntkx_f : P.g.f_ntkx_d, dny = P.g.f_ny;
+  const size_t rs = (size_t)ny * hzp;  // stride of spectrum rows (c*nx + x)
+  // tile = (irow * ny + y) * ntk + tk
+  const int tile = blockIdx.x;
+  const int q = (int)dntk.div((unsigned)tile);
+  const int k0 = (tile - q * ntk) * T;
+  const int irow = (int)dny.div((unsigned)q);
+  const int y = q - irow * ny;
+  cplx<R>* gbase = P.spec + (size_t)(3 * irow) * nx * rs + (size_t)y * hzp + k0;
+  issue_tile<R>(bufA, gbase, rs, 3 * nx, T, ts, k0, hzp, P.spec);
+  cp_async_commit();
   for (int i = threadIdx.x; i < nx; i += blockDim.x) tw[i] = P.tw[i];
-  const int y = blockIdx.y;
-  const int k0 = blockIdx.x * T;
-  const int tc = min(T, P.g.hz - k0);
-  const int hzp = P.g.hzp;
-  const size_t ss = P.g.sstride;
-  const int tot = 9 * nx * T;
-  for (int i = threadIdx.x; i < tot; i += blockDim.x) {
-    const int t = i % T;
-    const int x = (i / T) % nx;
-    const int c = i / (T * nx);
-    buf[i] = (t < tc) ? P.spec[(size_t)c * ss + ((size_t)x * ny + y) * hzp + k0 + t]
-                      : cplx<R>{R(0), R(0)};
-  }
+  __shared__ AxisPlan plan;
+  load_plan(&plan, P.g.px);
+  cp_async_wait<0>();
   __syncthreads();
-  const LineMap lm{T, nx * T, 1, T, 1};
-  fft_lines<R, false>(buf, lm, 9 * T, P.g.px, tw);
-  // projection  A_ij <- xi_j (sum_l xi_l A_il) / |xi|^2, zero at q = 0,
-  // times the normalisation of the inverse transform (Eq. G_red).
+  const LineMap lm{ts, nx * T, 1, T, 1};
+  const FastDiv fL = sizeof(R) == 4 ? P.g.f_Lx_f : P.g.f_Lx_d;
+  cplx<R>* X = fft_lines_call<R, false>(bufA, bufB, lm, 3 * T, fL, &plan, tw);
+  cplx<R>* Y = (X == bufA) ? bufB : bufA;
   const R qy = signed_freq<R>(y, ny) / (R)ny;
   const R sc = (R)P.scale;
   for (int i = threadIdx.x; i < nx * T; i += blockDim.x) {
-    const int t = i % T;
-    const int x = i / T;
+    const int t = i & (T - 1);
+    const int x = i >> ts;
     const R qx = signed_freq<R>(x, nx) / (R)nx;
     const R qz = (R)(k0 + t) / (R)P.g.nz;
     const R q2 = qx * qx + qy * qy + qz * qz;
     const R f = (q2 > R(0)) ? sc / q2 : R(0);
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      const cplx<R> A0 = buf[(3 * a + 0) * nx * T + i];
-      const cplx<R> A1 = buf[(3 * a + 1) * nx * T + i];
-      const cplx<R> A2 = buf[(3 * a + 2) * nx * T + i];
-      const R sx = f * (qx * A0.x + qy * A1.x + qz * A2.x);
-      const R sy = f * (qx * A0.y + qy * A1.y + qz * A2.y);
-      buf[(3 * a + 0) * nx * T + i] = {sx * qx, sy * qx};
-      buf[(3 * a + 1) * nx * T + i] = {sx * qy, sy * qy};
-      buf[(3 * a + 2) * nx * T + i] = {sx * qz, sy * qz};
-    }
+    const cplx<R> A0 = X[i], A1 = X[nx * T + i], A2 = X[2 * nx * T + i];
+    const R sx = f * (qx * A0.x + qy * A1.x + qz * A2.x);
+    const R sy = f * (qx * A0.y + qy * A1.y + qz * A2.y);
+    X[i] = {sx * qx, sy * qx};
+    X[nx * T + i] = {sx * qy, sy * qy};
+    X[2 * nx * T + i] = {sx * qz, sy * qz};
   }
   __syncthreads();
-  fft_lines<R, true>(buf, lm, 9 * T, P.g.px, tw);
+  const cplx<R>* res = fft_lines_call<R, true>(X, Y, lm, 3 * T, fL, &plan, tw);
+  const int tc = min(T, hz - k0);
+  const int tot = 3 * nx * T;
   for (int i = threadIdx.x; i < tot; i += blockDim.x) {
-    const int t = i % T;
-    const int x = (i / T) % nx;
-    const int c = i / (T * nx);
-    if (t < tc) P.spec[(size_t)c * ss + ((size_t)x * ny + y) * hzp + k0 + t] = buf[i];
+    const int t = i & (T - 1);
+    if (t < tc) gbase[(size_t)(i >> ts) * rs + t] = res[i];
   }
 }
 
@@ -301,44 +364,66 @@ struct ZinvParams {
 };
 
 template <typename R, typename RC, int OUT>
-__global__ void __launch_bounds__(FFT_THREADS) k_zinv(const ZinvParams<R, RC> P) {
+__global__ void FFT_BOUNDS(R) k_zinv(const ZinvParams<R, RC> P) {
   if (P.done && *P.done) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int nz = P.g.nz, lz = P.lz, hz = P.g.hz, hzp = P.g.hzp;
   cplx<R>* tw = reinterpret_cast<cplx<R>*>(smem_raw);
-  cplx<R>* buf = tw + nz;  // [5][lz][nz]
+  cplx<R>* bufA = tw + ((nz + 1) & ~1);  // [5][lz][nz]
+  cplx<R>* bufB = bufA + 5 * lz * nz;
   for (int i = threadIdx.x; i < nz; i += blockDim.x) tw[i] = P.tw[i];
+  __shared__ AxisPlan plan;
+  load_plan(&plan, P.g.pz);
   const size_t n = P.g.n;
   const size_t ss = P.g.sstride;
   const int nlines = P.g.nx * P.g.ny;
   const int l0 = blockIdx.x * lz;
   const int nl = min(lz, nlines - l0);
   // rebuild the full z spectrum of the packed lines z = a + i b
-  for (int i = threadIdx.x; i < 5 * lz * hz; i += blockDim.x) {
-    const int kz = i % hz;
-    const int rest = i / hz;
-    const int li = rest % lz;
-    const int k = rest / lz;
-    cplx<R> A = {R(0), R(0)}, B = {R(0), R(0)};
-    if (li < nl) {
-      const size_t o = (size_t)(l0 + li) * hzp + kz;
-      A = P.spec[(size_t)(2 * k) * ss + o];
-      if (2 * k + 1 < 9) B = P.spec[(size_t)(2 * k + 1) * ss + o];
+  constexpr int U = sizeof(R) == 4 ? 4 : 2;  // (A, B) pairs in flight per thread
+  const FastDiv dhz = P.g.f_hz, dlz = sizeof(R) == 4 ? P.g.f_lzf : P.g.f_lzd;
+  const int nthr = blockDim.x;
+  const int totl = 5 * lz * hz;
+  for (int i0 = threadIdx.x; i0 < totl; i0 += U * nthr) {
+    cplx<R> A[U], B[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int i = i0 + u * nthr;
+      const int rest = (int)dhz.div((unsigned)i);
+      const int kz = i - rest * hz;
+      const int k = (int)dlz.div((unsigned)rest);
+      const int li = rest - k * lz;
+      A[u] = {R(0), R(0)};
+      B[u] = {R(0), R(0)};
+      if (i < totl && li < nl) {
+        const size_t o = (size_t)(l0 + li) * hzp + kz;
+        A[u] = P.spec[(size_t)(2 * k) * ss + o];
+        if (2 * k + 1 < 9) B[u] = P.spec[(size_t)(2 * k + 1) * ss + o];
+      }
     }
-    cplx<R>* line = buf + (k * lz + li) * nz;
-    line[kz] = {A.x - B.y, A.y + B.x};
-    if (kz > 0) line[nz - kz] = {A.x + B.y, B.x - A.y};
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int i = i0 + u * nthr;
+      if (i >= totl) continue;
+      const int rest = (int)dhz.div((unsigned)i);
+      const int kz = i - rest * hz;
+      const int k = (int)dlz.div((unsigned)rest);
+      const int li = rest - k * lz;
+      cplx<R>* line = bufA + (k * lz + li) * nz;
+      line[kz] = {A[u].x - B[u].y, A[u].y + B[u].x};
+      if (kz > 0) line[nz - kz] = {A[u].x + B[u].y, B[u].x - A[u].y};
+    }
   }
   __syncthreads();
-  const LineMap lm{1 << 30, 0, nz, 1, 0};
-  fft_lines<R, true>(buf, lm, 5 * lz, P.g.pz, tw);
+  const LineMap lm{30, 0, nz, 1, 0};
+  const cplx<R>* res = fft_lines<R, true>(bufA, bufB, lm, 5 * lz, P.g.f_hz, plan, tw);
   const size_t v0 = (size_t)l0 * nz;
   double acc = 0.0;
   for (int i = threadIdx.x; i < nl * nz; i += blockDim.x) {
     R out[9];
 #pragma unroll
     for (int k = 0; k < 5; ++k) {
-      const cplx<R> z = buf[k * lz * nz + i];
+      const cplx<R> z = res[k * lz * nz + i];
       out[2 * k] = z.x;
       if (2 * k + 1 < 9) out[2 * k + 1] = z.y;
     }
@@ -347,11 +432,14 @@ __global__ void __launch_bounds__(FFT_THREADS) k_zinv(const ZinvParams<R, RC> P)
 #pragma unroll
       for (int c = 0; c < 9; ++c) P.dst[(size_t)c * n + v] = out[c];
     } else if (OUT == OUT_CGAP) {
+      R pv[9];
+#pragma unroll
+      for (int c = 0; c < 9; ++c) pv[c] = (R)P.p_in[(size_t)c * n + v];
       R s = 0;
 #pragma unroll
       for (int c = 0; c < 9; ++c) {
         P.dst[(size_t)c * n + v] = out[c];
-        s = fma((R)P.p_in[(size_t)c * n + v], out[c], s);
+        s = fma(pv[c], out[c], s);
       }
       acc += (double)s;
     } else {
@@ -424,7 +512,7 @@ void launch_zfwd(const GridGeom& g, int src, const TangentView<R>& tan, const R*
   P.tw = tw.z;
   const int nlines = g.nx * g.ny;
   const dim3 grid((nlines + P.lz - 1) / P.lz);
-  const size_t sm = sizeof(cplx<R>) * ((size_t)g.nz + 5 * (size_t)P.lz * g.nz);
+  const size_t sm = sizeof(cplx<R>) * ((size_t)((g.nz + 1) & ~1) + 10 * (size_t)P.lz * g.nz);
 #define ZF(S, T) k_zfwd<R, S, T><<<grid, FFT_THREADS, sm, s>>>(P)
   const int tm = tan.mode;
   if (src == SRC_FIELD) {
@@ -452,10 +540,10 @@ void launch_fft_y(const GridGeom& g, bool inverse, cplx<R>* spec, const int* don
   P.spec = spec;
   P.done = done;
   P.tw = tw.y;
-  const dim3 grid((g.hz + P.t - 1) / P.t, (9 * g.nx + P.grp - 1) / P.grp);
-  const size_t sm = sizeof(cplx<R>) * ((size_t)g.ny + (size_t)P.grp * g.ny * P.t);
-  if (inverse) k_fft_y<R, true><<<grid, FFT_THREADS, sm, s>>>(P);
-  else k_fft_y<R, false><<<grid, FFT_THREADS, sm, s>>>(P);
+  const int ntiles = ((g.hz + P.t - 1) / P.t) * ((9 * g.nx + P.grp - 1) / P.grp);
+  const size_t sm = sizeof(cplx<R>) * ((size_t)((g.ny + 1) & ~1) + 2 * (size_t)P.grp * g.ny * P.t);
+  if (inverse) k_fft_y<R, true><<<ntiles, FFT_THREADS, sm, s>>>(P);
+  else k_fft_y<R, false><<<ntiles, FFT_THREADS, sm, s>>>(P);
 }
 
 template <typename R>
@@ -469,9 +557,9 @@ void launch_fft_x_proj(const GridGeom& g, double scale, cplx<R>* spec, const int
   P.spec = spec;
   P.done = done;
   P.tw = tw.x;
-  const dim3 grid((g.hz + P.t - 1) / P.t, g.ny);
-  const size_t sm = sizeof(cplx<R>) * ((size_t)g.nx + 9 * (size_t)g.nx * P.t);
-  k_fft_x_proj<R><<<grid, FFT_THREADS, sm, s>>>(P);
+  const int ntiles = 3 * g.ny * ((g.hz + P.t - 1) / P.t);
+  const size_t sm = sizeof(cplx<R>) * ((size_t)((g.nx + 1) & ~1) + 2 * 3 * (size_t)g.nx * P.t);
+  k_fft_x_proj<R><<<ntiles, FFT_THREADS, sm, s>>>(P);
 }
 
 template <typename R, typename RC>
@@ -492,7 +580,7 @@ void launch_zinv(const GridGeom& g, int out, const cplx<R>* spec, R* dst, RC* r_
   P.tw = tw.z;
   const int nlines = g.nx * g.ny;
   const dim3 grid((nlines + P.lz - 1) / P.lz);
-  const size_t sm = sizeof(cplx<R>) * ((size_t)g.nz + 5 * (size_t)P.lz * g.nz);
+  const size_t sm = sizeof(cplx<R>) * ((size_t)((g.nz + 1) & ~1) + 10 * (size_t)P.lz * g.nz);
   if (out == OUT_PLAIN) k_zinv<R, RC, OUT_PLAIN><<<grid, FFT_THREADS, sm, s>>>(P);
   else if (out == OUT_CGAP) k_zinv<R, RC, OUT_CGAP><<<grid, FFT_THREADS, sm, s>>>(P);
   else k_zinv<R, RC, OUT_RESID><<<grid, FFT_THREADS, sm, s>>>(P);

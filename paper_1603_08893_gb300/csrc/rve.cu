@@ -51,6 +51,15 @@ bool factor_plan(int n, AxisPlan* p) {
       p->rad[p->nst++] = q;
       m /= q;
     }
+  {
+    int ns = 1;
+    for (int s = 0; s < p->nst; ++s) {
+      p->fNs[s] = make_fastdiv((unsigned)ns);
+      p->fnb[s] = make_fastdiv((unsigned)(n / p->rad[s]));
+      ns *= p->rad[s];
+    }
+    p->fN = make_fastdiv((unsigned)n);
+  }
   // capacity of the in-register stage scheme with 256 threads per block
   for (int s = 0; s < p->nst; ++s) {
     const int r = p->rad[s];
@@ -81,18 +90,34 @@ bool make_geom(int nx, int ny, int nz, GridGeom* g) {
   g->n = (size_t)nx * ny * nz;
   g->sstride = (size_t)nx * ny * g->hzp;
   if (!factor_plan(nx, &g->px) || !factor_plan(ny, &g->py) || !factor_plan(nz, &g->pz)) return false;
-  g->lz_f = pick_lz(nz, 8, 64 * 1024);
-  g->lz_d = pick_lz(nz, 16, 64 * 1024);
-  if ((size_t)16 * (nz + 5 * (size_t)g->lz_d * nz) > 200 * 1024) return false;
+  // z passes: two buffers of 5 packed lines x lz x nz (ping-pong stages)
+  g->lz_f = pick_lz(nz, 8, 32 * 1024);
+  g->lz_d = pick_lz(nz, 16, 32 * 1024);
+  if ((size_t)16 * (nz + 1 + 10 * (size_t)g->lz_d * nz) > 200 * 1024) return false;
+  // strided passes: tiles of 64-byte rows (8 float or 4 double complex kz
+  // values), double buffered in shared memory
   g->ty_f = 8;
   g->ty_d = 4;
-  g->gy_f = std::max(1, std::min(9 * nx, (int)(32768 / (8 * (size_t)ny * g->ty_f))));
-  g->gy_d = std::max(1, std::min(9 * nx, (int)(32768 / (16 * (size_t)ny * g->ty_d))));
+  g->gy_f = std::max(1, std::min(9 * nx, (int)(24576 / (8 * (size_t)ny * g->ty_f))));
+  g->gy_d = std::max(1, std::min(9 * nx, (int)(24576 / (16 * (size_t)ny * g->ty_d))));
+  if (8 * ((size_t)ny + 1 + 2 * (size_t)g->gy_f * ny * g->ty_f) > 200 * 1024) return false;
+  if (16 * ((size_t)ny + 1 + 2 * (size_t)g->gy_d * ny * g->ty_d) > 200 * 1024) return false;
   g->tx_f = 8;
-  while (g->tx_f > 1 && 8 * ((size_t)nx + 9 * (size_t)nx * g->tx_f) > 200 * 1024) g->tx_f /= 2;
   g->tx_d = 4;
-  while (g->tx_d > 1 && 16 * ((size_t)nx + 9 * (size_t)nx * g->tx_d) > 200 * 1024) g->tx_d /= 2;
-  if (16 * ((size_t)nx + 9 * (size_t)nx * g->tx_d) > 200 * 1024) return false;
+  g->f_hz = make_fastdiv((unsigned)g->hz);
+  g->f_lzf = make_fastdiv((unsigned)g->lz_f);
+  g->f_lzd = make_fastdiv((unsigned)g->lz_d);
+  g->f_ny = make_fastdiv((unsigned)ny);
+  g->f_ntky_f = make_fastdiv((unsigned)((g->hz + g->ty_f - 1) / g->ty_f));
+  g->f_ntky_d = make_fastdiv((unsigned)((g->hz + g->ty_d - 1) / g->ty_d));
+  g->f_ntkx_f = make_fastdiv((unsigned)((g->hz + g->tx_f - 1) / g->tx_f));
+  g->f_ntkx_d = make_fastdiv((unsigned)((g->hz + g->tx_d - 1) / g->tx_d));
+  g->f_Ly_f = make_fastdiv((unsigned)(g->gy_f * g->ty_f));
+  g->f_Ly_d = make_fastdiv((unsigned)(g->gy_d * g->ty_d));
+  g->f_Lx_f = make_fastdiv((unsigned)(3 * g->tx_f));
+  g->f_Lx_d = make_fastdiv((unsigned)(3 * g->tx_d));
+  if (8 * ((size_t)nx + 1 + 6 * (size_t)nx * g->tx_f) > 200 * 1024) return false;
+  if (16 * ((size_t)nx + 1 + 6 * (size_t)nx * g->tx_d) > 200 * 1024) return false;
   return true;
 }
 
