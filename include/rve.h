@@ -14,7 +14,8 @@
  *
  * are solved matrix-free by conjugate gradients.  G is applied in Fourier
  * space with the closed-form G-hat of Eq. G; the per-voxel stress P and
- * tangent K come from the constitutive model (Sec. 4 Saint Venant-Kirchhoff).
+ * tangent K come from the constitutive model (Sec. 4 Saint Venant-Kirchhoff,
+ * Sec. 5 finite-strain J2 plasticity).
  *
  * Conventions (all calls):
  *  - Grids are nx x ny x nz voxels, each size odd (Eq. G is stated for odd
@@ -51,7 +52,7 @@ extern "C" {
 #define RVE_ERR_CUDA (-2)         /* a CUDA runtime call failed */
 #define RVE_ERR_NOMEM (-3)        /* device allocation failed / workspace too small */
 #define RVE_ERR_CG_MAXIT (-4)     /* CG reached max_cg iterations */
-#define RVE_ERR_CG_BREAKDOWN (-5) /* p.Ap <= 0: tangent not positive on compatible fields */
+#define RVE_ERR_CG_BREAKDOWN (-5) /* p.Ap = 0 exactly */
 #define RVE_ERR_NEWTON_MAXIT (-6) /* Newton reached max_newton iterations */
 #define RVE_ERR_NONFINITE (-7)    /* NaN or Inf in a residual, norm or stress */
 #define RVE_ERR_DETF (-8)         /* det F <= 0 in some voxel */
@@ -99,6 +100,10 @@ typedef struct {
   double rel_update[RVE_MAX_NEWTON_LOG];   /* ||dF|| / ||F|| per Newton iteration */
   double residual[RVE_MAX_NEWTON_LOG];     /* ||G:P(F)||, float64, after each update */
   double elapsed_ms;                       /* device time of the increment (CUDA events) */
+  int substeps;                            /* rve_solve_step: increments solved */
+  int cuts;                                /* rve_solve_step: halvings after a failure */
+  double substep_to[RVE_MAX_NEWTON_LOG];   /* rve_solve_step: fraction of the step reached
+                                              after each solved increment */
 } rve_stats;
 
 /* Fills *opt with the defaults listed above. */
@@ -139,11 +144,31 @@ int rve_set_macro_F(rve_t h, const double Fbar[9]);
  * error code is returned.  st may be NULL. */
 int rve_solve_increment(rve_t h, double tol_newton, double tol_cg, rve_stats* st);
 
+/* A load step to the absolute macroscopic F-bar (row-major, host) solved as
+ * one or more increments of rve_solve_increment along the straight path from
+ * the last committed F-bar: when an increment fails (Newton divergence or
+ * max iterations, CG failure, non-finite values, det F <= 0) the state has
+ * been rolled back and the increment is retried with half the step; after a
+ * success the step doubles again (up to the remainder).  Newton is declared
+ * diverged when ||dF||/||F|| > 0.5 or the update grew in two consecutive
+ * equilibrium iterations.  At most max_cuts halvings; st (may be NULL)
+ * accumulates the iterations of all attempts.  Not in the paper (its
+ * examples use fixed small increments, Sec. 5.5); the elasto-plastic switch
+ * of Sec. 5.3 makes full Newton steps diverge when an increment crosses the
+ * yield point by far. */
+int rve_solve_step(rve_t h, const double Fbar[9], double tol_newton, double tol_cg, int max_cuts,
+                   rve_stats* st);
+
 /* Copies F, P (each [9][n] float64) or the tangent K ([81][n] float64,
  * evaluated in float64 at the current F) to dst (host or device). */
 int rve_get_F(rve_t h, double* dst, int dst_on_device);
 int rve_get_P(rve_t h, double* dst, int dst_on_device);
 int rve_get_K4(rve_t h, double* dst, int dst_on_device);
+
+/* J2 only: committed history, [7][n] float64 = (Cp^-1)_00, _11, _22, _01,
+ * _02, _12 and the accumulated plastic strain eps_p (Sec. 5.2), to dst
+ * (host or device).  RVE_ERR_INVALID for models without history. */
+int rve_get_history(rve_t h, double* dst, int dst_on_device);
 
 /* Homogenised first Piola-Kirchhoff stress P-bar = <P> (voxel average),
  * row-major, host. */

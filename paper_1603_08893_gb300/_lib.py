@@ -48,7 +48,9 @@ class rve_stats(C.Structure):
                 ("cg_iters", C.c_int * RVE_MAX_NEWTON_LOG),
                 ("rel_update", C.c_double * RVE_MAX_NEWTON_LOG),
                 ("residual", C.c_double * RVE_MAX_NEWTON_LOG),
-                ("elapsed_ms", C.c_double)]
+                ("elapsed_ms", C.c_double), ("substeps", C.c_int),
+                ("cuts", C.c_int),
+                ("substep_to", C.c_double * RVE_MAX_NEWTON_LOG)]
 
 
 _H = C.c_void_p
@@ -63,9 +65,12 @@ _SIGS = {
     "rve_set_macro_F": (C.c_int, [_H, _P]),
     "rve_solve_increment": (C.c_int, [_H, C.c_double, C.c_double,
                                       C.POINTER(rve_stats)]),
+    "rve_solve_step": (C.c_int, [_H, _P, C.c_double, C.c_double, C.c_int,
+                                 C.POINTER(rve_stats)]),
     "rve_get_F": (C.c_int, [_H, _P, C.c_int]),
     "rve_get_P": (C.c_int, [_H, _P, C.c_int]),
     "rve_get_K4": (C.c_int, [_H, _P, C.c_int]),
+    "rve_get_history": (C.c_int, [_H, _P, C.c_int]),
     "rve_homogenized_P": (C.c_int, [_H, _P]),
     "rve_set_F": (C.c_int, [_H, _P, C.c_int]),
     "rve_apply_operator": (C.c_int, [_H, _P, _P, C.c_int]),

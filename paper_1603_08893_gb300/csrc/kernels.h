@@ -84,6 +84,13 @@ void launch_svk_k4_full(const double* F, size_t v0, size_t count, size_t n,
                         MatView<double> mat, double* dst, cudaStream_t s);
 template <typename Ti, typename To>
 void launch_convert(const Ti* in, To* out, size_t count, cudaStream_t s);
+
+// ---- finite-strain J2 (kernels_j2.cu) ----
+template <typename RO>
+void launch_j2_constitutive(const double* F, size_t n, MatView<double> mat, const double* hc,
+                            double* ht, double* P, RO* K4, SolverState* st, cudaStream_t s);
+void launch_j2_k4_full(const double* F, size_t v0, size_t count, size_t n, MatView<double> mat,
+                       const double* hc, double* dst, cudaStream_t s);
 size_t vec_max_blocks();
 
 // mean9 post-processing modes

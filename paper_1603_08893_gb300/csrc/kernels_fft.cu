@@ -464,7 +464,10 @@ __global__ void FFT_BOUNDS(R) k_zinv(const ZinvParams<R, RC> P) {
       if (!isfinite(pap)) {
         st->status = RVE_DEV_ERR_NONFINITE;
         st->done = 1;
-      } else if (!(pap > 0.0)) {
+      } else if (pap == 0.0) {
+        // CG as in the library routine the method is written for: the sign
+        // of p.Ap is not tested (the J2 tangent may be mildly indefinite);
+        // only an exact zero stops it
         st->status = RVE_DEV_ERR_CG_BREAKDOWN;
         st->done = 1;
       } else {

@@ -1,0 +1,293 @@
+// Finite-strain J2 elasto-plasticity (Sec. 5) per voxel, float64:
+// be = F Cp^-1 F^T, eps = ln(be)/2 (principal), Kirchhoff stress
+// tau = K tr(eps) I + 2 mu dev(eps) (Eq. elas:C acting on the logarithmic
+// strain), von Mises yield phi = tau_eq - (tau_y0 + H eps_p) (Eq. simo:flow),
+// radial return in principal logarithmic strains, P = tau F^-T (pull-back),
+// trial history Cp^-1 = F^-1 be F^-T, eps_p += dgamma.  The tangent is the
+// exact derivative dP/dF of this update (committed history frozen), with the
+// derivative of the matrix logarithm from divided differences of ln in the
+// eigenbasis of be.  Stored as K_ijkl = dP_ji / dF_kl (Eq. iter:varP).
+#include "kernels.h"
+
+#define J2_THREADS 128
+
+namespace {
+
+// Cyclic Jacobi rotations: A (symmetric, in/out, becomes diagonal) and the
+// orthogonal V with A_in = V diag(A_out) V^T.  Sweeps stop when the
+// off-diagonal part is below 1e-30 of the diagonal (at most 12 sweeps).
+RVE_DEV void jacobi3(double (&A)[3][3], double (&V)[3][3]) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) V[i][j] = (i == j) ? 1.0 : 0.0;
+  for (int sweep = 0; sweep < 12; ++sweep) {
+    const double off = A[0][1] * A[0][1] + A[0][2] * A[0][2] + A[1][2] * A[1][2];
+    const double dia = A[0][0] * A[0][0] + A[1][1] * A[1][1] + A[2][2] * A[2][2];
+    if (off <= 1e-30 * dia) break;
+#pragma unroll
+    for (int pq = 0; pq < 3; ++pq) {
+      const int p = (pq == 2) ? 1 : 0;
+      const int q = (pq == 0) ? 1 : 2;
+      const double apq = A[p][q];
+      if (apq == 0.0) continue;
+      // rotation angle zeroing A[p][q]: tan(2 phi) = 2 apq / (aqq - app)
+      const double theta = (A[q][q] - A[p][p]) / (2.0 * apq);
+      const double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+      const double c = 1.0 / sqrt(t * t + 1.0);
+      const double s = t * c;
+      // A <- R^T A R with R the rotation in the (p, q) plane
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const double akp = A[k][p], akq = A[k][q];
+        A[k][p] = c * akp - s * akq;
+        A[k][q] = s * akp + c * akq;
+      }
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const double apk = A[p][k], aqk = A[q][k];
+        A[p][k] = c * apk - s * aqk;
+        A[q][k] = s * apk + c * aqk;
+      }
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const double vkp = V[k][p], vkq = V[k][q];
+        V[k][p] = c * vkp - s * vkq;
+        V[k][q] = s * vkp + c * vkq;
+      }
+    }
+  }
+}
+
+// divided difference of ln: (ln x - ln y)/(x - y) = atanh(t)/(m t),
+// t = (x - y)/(x + y), m = (x + y)/2; 1/m at t = 0
+RVE_DEV double dd_log(double x, double y) {
+  const double m = 0.5 * (x + y);
+  const double t = (x - y) / (x + y);
+  if (t == 0.0) return 1.0 / m;
+  return atanh(t) / (m * t);
+}
+
+}  // namespace
+
+// hc: committed history [7][n] (Cp^-1: 00,11,22,01,02,12; eps_p),
+// ht: trial history written here.  K4 (RO) and/or K64 (float64, voxel range
+// [v0, v0+cnt) into [81][cnt]) are optional.
+template <typename RO>
+__global__ void __launch_bounds__(J2_THREADS) k_j2(const double* __restrict__ F, size_t n,
+                                                   size_t v0, size_t cnt, MatView<double> mat,
+                                                   const double* __restrict__ hc,
+                                                   double* __restrict__ ht, double* __restrict__ P,
+                                                   RO* __restrict__ K4, double* __restrict__ K64,
+                                                   SolverState* st) {
+  int flags = 0;
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t u = (size_t)blockIdx.x * blockDim.x + threadIdx.x; u < cnt; u += stride) {
+    const size_t v = v0 + u;
+    double f[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) f[i][j] = F[(size_t)(3 * i + j) * n + v];
+    double C[3][3];
+    C[0][0] = hc[v];
+    C[1][1] = hc[n + v];
+    C[2][2] = hc[2 * n + v];
+    C[0][1] = C[1][0] = hc[3 * n + v];
+    C[0][2] = C[2][0] = hc[4 * n + v];
+    C[1][2] = C[2][1] = hc[5 * n + v];
+    const double ep = hc[6 * n + v];
+    const double lam_l = mat.get(v, 0), mu = mat.get(v, 1), ty0 = mat.get(v, 2), H = mat.get(v, 3);
+    const double Kb = lam_l + 2.0 * mu / 3.0;  // bulk modulus
+    // FC = F Cp^-1, be = FC F^T
+    double FC[3][3], be[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) FC[i][j] = f[i][0] * C[0][j] + f[i][1] * C[1][j] + f[i][2] * C[2][j];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) be[i][j] = FC[i][0] * f[j][0] + FC[i][1] * f[j][1] + FC[i][2] * f[j][2];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = i + 1; j < 3; ++j) be[i][j] = be[j][i] = 0.5 * (be[i][j] + be[j][i]);
+    double Q[3][3];
+    jacobi3(be, Q);
+    double lam[3], eps[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      lam[a] = be[a][a];
+      eps[a] = 0.5 * log(lam[a]);
+    }
+    const double tr = eps[0] + eps[1] + eps[2];
+    double dev[3], s[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      dev[a] = eps[a] - tr / 3.0;
+      s[a] = 2.0 * mu * dev[a];
+    }
+    const double teq = sqrt(1.5 * (s[0] * s[0] + s[1] * s[1] + s[2] * s[2]));
+    const double phi = teq - (ty0 + H * ep);
+    const bool plastic = phi > 0.0;
+    const double dg = plastic ? phi / (3.0 * mu + H) : 0.0;
+    const double beta = plastic ? 1.0 - 3.0 * mu * dg / teq : 1.0;
+    double taup[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) taup[a] = Kb * tr + beta * s[a];
+    // tau = Q diag(taup) Q^T
+    double tau[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j)
+        tau[i][j] = Q[i][0] * taup[0] * Q[j][0] + Q[i][1] * taup[1] * Q[j][1] + Q[i][2] * taup[2] * Q[j][2];
+    // F^-1 by the adjugate
+    const double det = f[0][0] * (f[1][1] * f[2][2] - f[1][2] * f[2][1]) -
+                       f[0][1] * (f[1][0] * f[2][2] - f[1][2] * f[2][0]) +
+                       f[0][2] * (f[1][0] * f[2][1] - f[1][1] * f[2][0]);
+    if (!(det > 0.0)) flags |= 1;
+    const double id = 1.0 / det;
+    double Fi[3][3];  // F^-1
+    Fi[0][0] = (f[1][1] * f[2][2] - f[1][2] * f[2][1]) * id;
+    Fi[0][1] = (f[0][2] * f[2][1] - f[0][1] * f[2][2]) * id;
+    Fi[0][2] = (f[0][1] * f[1][2] - f[0][2] * f[1][1]) * id;
+    Fi[1][0] = (f[1][2] * f[2][0] - f[1][0] * f[2][2]) * id;
+    Fi[1][1] = (f[0][0] * f[2][2] - f[0][2] * f[2][0]) * id;
+    Fi[1][2] = (f[0][2] * f[1][0] - f[0][0] * f[1][2]) * id;
+    Fi[2][0] = (f[1][0] * f[2][1] - f[1][1] * f[2][0]) * id;
+    Fi[2][1] = (f[0][1] * f[2][0] - f[0][0] * f[2][1]) * id;
+    Fi[2][2] = (f[0][0] * f[1][1] - f[0][1] * f[1][0]) * id;
+    // P = tau F^-T : P_ij = tau_ik Fi_jk
+    double Pm[3][3];
+    double pmax = 0.0;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        Pm[i][j] = tau[i][0] * Fi[j][0] + tau[i][1] * Fi[j][1] + tau[i][2] * Fi[j][2];
+        pmax = fmax(pmax, fabs(Pm[i][j]));
+      }
+    if (!isfinite(pmax) || !isfinite(det)) flags |= 2;
+    if (P) {
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) P[(size_t)(3 * i + j) * n + v] = Pm[i][j];
+    }
+    if (ht) {
+      // trial history: be_new = Q diag(exp(2 eps_e)) Q^T, Cp^-1 = F^-1 be_new F^-T
+      double bn[3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) bn[a] = exp(2.0 * (tr / 3.0 + beta * dev[a]));
+      double G[3][3];  // F^-1 Q
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) G[i][a] = Fi[i][0] * Q[0][a] + Fi[i][1] * Q[1][a] + Fi[i][2] * Q[2][a];
+      double Cn[3][3];
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) Cn[i][j] = G[i][0] * bn[0] * G[j][0] + G[i][1] * bn[1] * G[j][1] + G[i][2] * bn[2] * G[j][2];
+      ht[v] = Cn[0][0];
+      ht[n + v] = Cn[1][1];
+      ht[2 * n + v] = Cn[2][2];
+      ht[3 * n + v] = 0.5 * (Cn[0][1] + Cn[1][0]);
+      ht[4 * n + v] = 0.5 * (Cn[0][2] + Cn[2][0]);
+      ht[5 * n + v] = 0.5 * (Cn[1][2] + Cn[2][1]);
+      ht[6 * n + v] = ep + dg;
+    }
+    if (!K4 && !K64) continue;
+    // ---- consistent tangent, one unit direction dF = e_k (x) e_l at a time
+    double f1[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) f1[a][b] = dd_log(lam[a], lam[b]);
+    // Qt_FC[a][l] = (Q^T FC)_al
+    double QFC[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int l = 0; l < 3; ++l) QFC[a][l] = Q[0][a] * FC[0][l] + Q[1][a] * FC[1][l] + Q[2][a] * FC[2][l];
+    const double c1 = plastic ? 1.0 / (3.0 * mu + H) - dg / teq : 0.0;
+    for (int k = 0; k < 3; ++k)
+      for (int l = 0; l < 3; ++l) {
+        // d(be) = e_k (x) v + v (x) e_k, v = FC[:, l]; in the eigenbasis
+        // (Q^T d(be) Q)_ab = Q_ka QFC_bl + QFC_al Q_kb
+        double dq[3][3];
+        double dtr = 0.0;
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+          for (int b = 0; b < 3; ++b) {
+            dq[a][b] = 0.5 * f1[a][b] * (Q[k][a] * QFC[b][l] + QFC[a][l] * Q[k][b]);  // d(eps)
+          }
+        dtr = dq[0][0] + dq[1][1] + dq[2][2];
+        double dteq = 0.0, dbeta = 0.0;
+        if (plastic) {
+          // s_tr : ds_tr = 2 mu sum_a s_a d(eps)_aa (s_tr is diagonal, traceless)
+          dteq = 1.5 * 2.0 * mu * (s[0] * dq[0][0] + s[1] * dq[1][1] + s[2] * dq[2][2]) / teq;
+          dbeta = -3.0 * mu * dteq * c1 / teq;
+        }
+        // d(tau) in the eigenbasis
+        double dt[3][3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+          for (int b = 0; b < 3; ++b) {
+            double x = beta * 2.0 * mu * (dq[a][b] - (a == b ? dtr / 3.0 : 0.0));
+            if (a == b) x += Kb * dtr + dbeta * s[a];
+            dt[a][b] = x;
+          }
+        // d(tau) global = Q dt Q^T
+        double dT[3][3], QdT[3][3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+          for (int b = 0; b < 3; ++b) QdT[i][b] = Q[i][0] * dt[0][b] + Q[i][1] * dt[1][b] + Q[i][2] * dt[2][b];
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+          for (int j = 0; j < 3; ++j) dT[i][j] = QdT[i][0] * Q[j][0] + QdT[i][1] * Q[j][1] + QdT[i][2] * Q[j][2];
+        // dP = d(tau) F^-T - P[:, l] (x) F^-T[k, :]  (F^-T[k][j] = Fi[j][k])
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+          for (int j = 0; j < 3; ++j) {
+            const double dP = dT[i][0] * Fi[j][0] + dT[i][1] * Fi[j][1] + dT[i][2] * Fi[j][2] - Pm[i][l] * Fi[j][k];
+            // K_jikl = dP_ij
+            const size_t comp = (size_t)((j * 3 + i) * 3 + k) * 3 + l;
+            if (K4) K4[comp * n + v] = (RO)dP;
+            if (K64) K64[comp * cnt + u] = dP;
+          }
+      }
+  }
+  if (flags && st) atomicOr(&st->err_flags, flags);
+}
+
+template <typename RO>
+void launch_j2_constitutive(const double* F, size_t n, MatView<double> mat, const double* hc,
+                            double* ht, double* P, RO* K4, SolverState* st, cudaStream_t s) {
+  size_t b = (n + J2_THREADS - 1) / J2_THREADS;
+  if (b > 4864) b = 4864;
+  if (b < 1) b = 1;
+  k_j2<RO><<<(unsigned)b, J2_THREADS, 0, s>>>(F, n, 0, n, mat, hc, ht, P, K4, nullptr, st);
+}
+
+void launch_j2_k4_full(const double* F, size_t v0, size_t count, size_t n, MatView<double> mat,
+                       const double* hc, double* dst, cudaStream_t s) {
+  size_t b = (count + J2_THREADS - 1) / J2_THREADS;
+  if (b > 4864) b = 4864;
+  if (b < 1) b = 1;
+  k_j2<double><<<(unsigned)b, J2_THREADS, 0, s>>>(F, n, v0, count, mat, hc, nullptr, nullptr,
+                                                   nullptr, dst, nullptr);
+}
+
+template void launch_j2_constitutive<float>(const double*, size_t, MatView<double>, const double*,
+                                            double*, double*, float*, SolverState*, cudaStream_t);
+template void launch_j2_constitutive<double>(const double*, size_t, MatView<double>,
+                                             const double*, double*, double*, double*,
+                                             SolverState*, cudaStream_t);

@@ -14,6 +14,7 @@
 namespace {
 
 const double kPi = 3.14159265358979323846264338327950288;
+const double kDivergedUpdate = 0.5;  // ||dF||/||F|| above this ends Newton as diverged
 
 struct TimedLaunch {
   cudaEvent_t a, b;
@@ -160,6 +161,9 @@ struct rve_s {
   Twiddles<float> twf{};
   Twiddles<double> twd{};
   double Fbar[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
+  double Fbar_committed[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};  // F-bar of the last committed state
+  double* hc = nullptr;  // J2 history, committed [7][n]
+  double* ht = nullptr;  // J2 history, trial [7][n]
   std::string err;
   long long launches = 0;
   // instrumentation
@@ -342,6 +346,15 @@ void enqueue_predictor(rve_t h) {
 
 int enqueue_constitutive(rve_t h) {
   MatView<double> m = mat_view<double>(h);
+  if (h->model == RVE_J2) {
+    if (h->mixed)
+      launch_j2_constitutive<float>(h->F, h->n, m, h->hc, h->ht, h->P, as<float>(h->K4), h->st, h->s);
+    else
+      launch_j2_constitutive<double>(h->F, h->n, m, h->hc, h->ht, h->P, as<double>(h->K4), h->st,
+                                     h->s);
+    h->launches += 1;
+    return RVE_OK;
+  }
   if (h->mixed)
     launch_svk_constitutive<float>(h->F, h->n, m, h->P, h->tan, as<float>(h->K4),
                                    as<float>(h->Fop), nullptr, h->st, h->s);
@@ -396,9 +409,9 @@ int cg_solve(rve_t h, int* iters) {
   }
   *iters = h->hst->it;
   h->solve_iters.push_back({h->solve_id, h->hst->it});
-  // float32 CG can lose positivity of p.Ap once its residual reaches the
-  // float32 noise level; the iterate so far is kept and the float64 Newton
-  // residual decides whether more work is needed.
+  // float32 CG can reach p.Ap = 0 once its residual is at the float32 noise
+  // level; the iterate so far is kept and the float64 Newton residual
+  // decides whether more work is needed.
   if (h->mixed && h->hst->status == RVE_DEV_ERR_CG_BREAKDOWN && h->hst->it >= 1) return RVE_OK;
   return h->hst->status;
 }
@@ -446,6 +459,12 @@ size_t layout(rve_t h, Arena& a) {
   h->spec64 = a.take<cplx<double>>(ns);
   h->spec64_bytes = ns * sizeof(cplx<double>);
   h->spec_op = h->mixed ? (void*)a.take<cplx<float>>(ns) : (void*)h->spec64;
+  if (h->model == RVE_J2) {
+    h->hc = a.take<double>(7 * n);
+    h->ht = a.take<double>(7 * n);
+  } else {
+    h->hc = h->ht = nullptr;
+  }
   h->table64 = a.take<double>(256 * 4);
   h->table32 = a.take<float>(256 * 4);
   h->vox64 = nullptr;
@@ -496,7 +515,7 @@ const char* rve_status_string(int code) {
     case RVE_ERR_CUDA: return "CUDA error";
     case RVE_ERR_NOMEM: return "out of device memory";
     case RVE_ERR_CG_MAXIT: return "CG did not converge within max_cg iterations";
-    case RVE_ERR_CG_BREAKDOWN: return "CG breakdown (p.Ap <= 0)";
+    case RVE_ERR_CG_BREAKDOWN: return "CG breakdown (p.Ap = 0)";
     case RVE_ERR_NEWTON_MAXIT: return "Newton did not converge within max_newton iterations";
     case RVE_ERR_NONFINITE: return "non-finite value";
     case RVE_ERR_DETF: return "det F <= 0";
@@ -524,8 +543,12 @@ static int resolve_options(const rve_options* in, rve_options* out, int model, i
     if (out->tangent == RVE_TAN_AUTO || out->tangent == RVE_TAN_RECOMPUTE) *tan = TAN_SVK;
     else if (out->tangent == RVE_TAN_FULL81) *tan = TAN_FULL81;
     else return RVE_ERR_INVALID;
+  } else if (model == RVE_J2) {
+    // the J2 tangent is stored (81 values per voxel)
+    if (out->tangent == RVE_TAN_AUTO || out->tangent == RVE_TAN_FULL81) *tan = TAN_FULL81;
+    else return RVE_ERR_INVALID;
   } else {
-    return RVE_ERR_UNSUPPORTED;
+    return RVE_ERR_INVALID;
   }
   return RVE_OK;
 }
@@ -541,6 +564,7 @@ int rve_workspace_size(int nx, int ny, int nz, int model, const rve_options* opt
   tmp.mixed = tmp.opt.precision == RVE_MIXED;
   tmp.tan = tan;
   tmp.nparam = (model == RVE_J2) ? 4 : 2;
+  tmp.model = model;
   Arena a;
   layout(&tmp, a);
   Arena b = a;
@@ -680,6 +704,15 @@ int rve_create(rve_t* out, int nx, int ny, int nz, int model, int nphase, const 
     ok &= ck(cudaMemcpyAsync(h->Ft, I.data(), I.size() * 8, cudaMemcpyHostToDevice, h->s));
     ok &= ck(cudaStreamSynchronize(h->s));
   }
+  if (h->model == RVE_J2) {
+    // history: Cp^-1 = I, eps_p = 0 (Algorithm 1, first line)
+    std::vector<double> H0(7 * h->n, 0.0);
+    for (int c = 0; c < 3; ++c)
+      for (size_t v = 0; v < h->n; ++v) H0[c * h->n + v] = 1.0;
+    ok &= ck(cudaMemcpyAsync(h->hc, H0.data(), H0.size() * 8, cudaMemcpyHostToDevice, h->s));
+    ok &= ck(cudaMemcpyAsync(h->ht, H0.data(), H0.size() * 8, cudaMemcpyHostToDevice, h->s));
+    ok &= ck(cudaStreamSynchronize(h->s));
+  }
   if (h->tan == TAN_SVK && !h->mixed) h->Fop = h->F;  // FP64 recompute reads F itself
   enqueue_constitutive(h);
   ok &= ck(cudaStreamSynchronize(h->s));
@@ -740,6 +773,7 @@ static int solve_increment_t(rve_t h, double tol_newton, double tol_cg, rve_stat
   int newton = 0;
   int cg_total = 0;
   int extra_refine = h->mixed ? h->opt.mixed_refine : 0;
+  double prev_rel = 0.0, prev2_rel = 0.0;
   for (int i = 0; i < h->opt.max_newton; ++i) {
     int its = 0;
     CK(cudaGetLastError());
@@ -789,6 +823,14 @@ static int solve_increment_t(rve_t h, double tol_newton, double tol_cg, rve_stat
       result = fail(h, RVE_ERR_NONFINITE, "non-finite Newton update");
       break;
     }
+    // divergence: an update larger than half of F, or updates that grew in
+    // two consecutive equilibrium iterations
+    if (rel > kDivergedUpdate || (i >= 3 && rel > prev_rel && prev_rel > prev2_rel)) {
+      result = fail(h, RVE_ERR_NEWTON_MAXIT, "Newton diverged");
+      break;
+    }
+    prev2_rel = prev_rel;
+    prev_rel = rel;
     if (rel < tol_newton && i > 0) {
       if (extra_refine > 0) {
         --extra_refine;
@@ -801,11 +843,19 @@ static int solve_increment_t(rve_t h, double tol_newton, double tol_cg, rve_stat
   if (result == RVE_OK && !converged)
     result = fail(h, RVE_ERR_NEWTON_MAXIT, "Newton did not converge");
   if (result == RVE_OK) {
-    // commit: store the converged state, homogenised stress
+    // commit: store the converged state and history, homogenised stress
     CK(cudaMemcpyAsync(h->Ft, h->F, n9 * 8, cudaMemcpyDeviceToDevice, h->s));
+    std::memcpy(h->Fbar_committed, h->Fbar, sizeof(h->Fbar));
     launch_mean9<double>(h->P, h->n, nullptr, h->partials, &h->st->counter[SLOT_MEAN], MEAN_PBAR,
                          h->st, h->s);
     h->launches += 1;
+    if (h->model == RVE_J2) {
+      // the trial history of the converged iterate becomes the committed
+      // one; the next increment starts from the constitutive response at F
+      // with it (Algorithm 1, i = 0)
+      std::swap(h->hc, h->ht);
+      enqueue_constitutive(h);
+    }
   } else {
     // roll back to the last committed state
     CK(cudaMemcpyAsync(h->F, h->Ft, n9 * 8, cudaMemcpyDeviceToDevice, h->s));
@@ -837,6 +887,57 @@ int rve_solve_increment(rve_t h, double tol_newton, double tol_cg, rve_stats* st
                   : solve_increment_t<double>(h, tol_newton, tol_cg, st);
 }
 
+int rve_solve_step(rve_t h, const double Fbar[9], double tol_newton, double tol_cg, int max_cuts,
+                   rve_stats* st) {
+  if (!h || !Fbar || max_cuts < 0) return RVE_ERR_INVALID;
+  for (int c = 0; c < 9; ++c)
+    if (!std::isfinite(Fbar[c])) return fail(h, RVE_ERR_INVALID, "non-finite F-bar");
+  double F0[9], target[9];
+  std::memcpy(F0, h->Fbar_committed, sizeof(F0));
+  std::memcpy(target, Fbar, sizeof(target));
+  rve_stats acc;
+  std::memset(&acc, 0, sizeof(acc));
+  double done = 0.0, step = 1.0;
+  int cuts = 0, sub = 0;
+  int result = RVE_OK;
+  while (done < 1.0) {
+    const double to = std::min(1.0, done + step);
+    double Fb[9];
+    for (int c = 0; c < 9; ++c) Fb[c] = (to >= 1.0) ? target[c] : F0[c] + to * (target[c] - F0[c]);
+    rve_set_macro_F(h, Fb);
+    rve_stats s1;
+    const int rc = rve_solve_increment(h, tol_newton, tol_cg, &s1);
+    acc.newton_iters += s1.newton_iters;
+    acc.cg_iters_total += s1.cg_iters_total;
+    acc.elapsed_ms += s1.elapsed_ms;
+    if (rc == RVE_OK) {
+      done = to;
+      if (sub < RVE_MAX_NEWTON_LOG) acc.substep_to[sub] = to;
+      ++sub;
+      step = std::min(2.0 * step, 1.0);
+    } else if (rc == RVE_ERR_NEWTON_MAXIT || rc == RVE_ERR_CG_MAXIT || rc == RVE_ERR_NONFINITE ||
+               rc == RVE_ERR_DETF || rc == RVE_ERR_CG_BREAKDOWN) {
+      // the state was rolled back: retry with half the step
+      if (++cuts > max_cuts) {
+        result = rc;
+        break;
+      }
+      step *= 0.5;
+    } else {
+      result = rc;
+      break;
+    }
+  }
+  std::memcpy(h->Fbar, target, sizeof(h->Fbar));
+  if (st) {
+    *st = acc;
+    st->status = result;
+    st->substeps = sub;
+    st->cuts = cuts;
+  }
+  return result;
+}
+
 int rve_get_F(rve_t h, double* dst, int on_device) {
   if (!h || !dst) return RVE_ERR_INVALID;
   return copy_out(h, dst, h->F, 9 * h->n * 8, on_device);
@@ -856,7 +957,8 @@ int rve_get_K4(rve_t h, double* dst, int on_device) {
   MatView<double> m = mat_view<double>(h);
   for (size_t v0 = 0; v0 < h->n; v0 += chunk) {
     const size_t cnt = std::min(chunk, h->n - v0);
-    launch_svk_k4_full(h->F, v0, cnt, h->n, m, scratch, h->s);
+    if (h->model == RVE_J2) launch_j2_k4_full(h->F, v0, cnt, h->n, m, h->hc, scratch, h->s);
+    else launch_svk_k4_full(h->F, v0, cnt, h->n, m, scratch, h->s);
     h->launches += 1;
     CK(cudaMemcpy2DAsync(dst + v0, h->n * sizeof(double), scratch, cnt * sizeof(double),
                          cnt * sizeof(double), 81,
@@ -864,6 +966,11 @@ int rve_get_K4(rve_t h, double* dst, int on_device) {
   }
   CK(cudaStreamSynchronize(h->s));
   return RVE_OK;
+}
+
+int rve_get_history(rve_t h, double* dst, int on_device) {
+  if (!h || !dst || h->model != RVE_J2) return RVE_ERR_INVALID;
+  return copy_out(h, dst, h->hc, 7 * h->n * 8, on_device);
 }
 
 int rve_homogenized_P(rve_t h, double Pbar[9]) {
@@ -881,6 +988,15 @@ int rve_set_F(rve_t h, const double* F, int on_device) {
   if (!h || !F) return RVE_ERR_INVALID;
   int rc = copy_in(h, h->F, F, 9 * h->n * 8, on_device);
   if (rc) return rc;
+  {
+    // the macroscopic state of the new field
+    launch_mean9<double>(h->F, h->n, nullptr, h->partials, &h->st->counter[SLOT_MEAN], MEAN_PBAR,
+                         h->st, h->s);
+    h->launches += 1;
+    rc = sync_state(h);
+    if (rc) return rc;
+    std::memcpy(h->Fbar_committed, h->hst->Pbar, sizeof(h->Fbar_committed));
+  }
   CK(cudaMemcpyAsync(h->Ft, h->F, 9 * h->n * 8, cudaMemcpyDeviceToDevice, h->s));
   std::memset(h->hst, 0, sizeof(SolverState));
   rc = push_state(h);

@@ -136,6 +136,21 @@ def rve_solve_increment(h, tol_newton=1e-5, tol_cg=1e-8, check=True):
     return out
 
 
+def rve_solve_step(h, Fbar, tol_newton=1e-5, tol_cg=1e-8, max_cuts=8, check=True):
+    """Load step to Fbar with automatic halving of failed increments."""
+    F = np.ascontiguousarray(Fbar, dtype=np.float64).reshape(9)
+    st = _lib.rve_stats()
+    code = lib.rve_solve_step(h, F.ctypes.data_as(C.c_void_p), float(tol_newton),
+                              float(tol_cg), int(max_cuts), C.byref(st))
+    out = dict(status=code, newton_iters=st.newton_iters,
+               cg_iters_total=st.cg_iters_total, substeps=st.substeps,
+               cuts=st.cuts, elapsed_ms=st.elapsed_ms,
+               substep_to=list(st.substep_to[:min(st.substeps, _lib.RVE_MAX_NEWTON_LOG)]))
+    if check:
+        _check(code, h)
+    return out
+
+
 def _get(fn, h, ncomp, n, out):
     if out is not None and _is_torch_cuda(out):
         if out.dtype != torch.float64 or not out.is_contiguous() or out.numel() != ncomp * n:
@@ -158,6 +173,13 @@ def rve_get_P(h, n, out=None):
 
 def rve_get_K4(h, n, out=None):
     return _get(lib.rve_get_K4, h, 81, n, out)
+
+
+def rve_get_history(h, n, out=None):
+    if out is None:
+        out = np.empty(7 * n, dtype=np.float64)
+    _check(lib.rve_get_history(h, out.ctypes.data_as(C.c_void_p), 0), h)
+    return out
 
 
 def rve_homogenized_P(h):
@@ -258,6 +280,9 @@ class RVE:
     def solve_increment(self, tol_newton=1e-5, tol_cg=1e-8, check=True):
         return rve_solve_increment(self.h, tol_newton, tol_cg, check)
 
+    def solve_step(self, Fbar, tol_newton=1e-5, tol_cg=1e-8, max_cuts=8, check=True):
+        return rve_solve_step(self.h, Fbar, tol_newton, tol_cg, max_cuts, check)
+
     def get_F(self, out=None):
         return self._shape9(rve_get_F(self.h, self.n, out))
 
@@ -269,6 +294,10 @@ class RVE:
 
     def homogenized_P(self):
         return rve_homogenized_P(self.h)
+
+    def get_history(self):
+        """J2: committed (Cp^-1 [6 symmetric components], eps_p) per voxel, [7, *shape]."""
+        return rve_get_history(self.h, self.n).reshape((7,) + self.shape)
 
     def set_F(self, F):
         rve_set_F(self.h, F, self.n)
