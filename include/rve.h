@@ -170,6 +170,21 @@ int rve_get_K4(rve_t h, double* dst, int dst_on_device);
  * (host or device).  RVE_ERR_INVALID for models without history. */
 int rve_get_history(rve_t h, double* dst, int dst_on_device);
 
+/* Gradient of J = W : P-bar (W row-major, host) with respect to the
+ * per-voxel shear moduli mu at fixed bulk moduli, at the current converged
+ * state, by one adjoint solve (not in the paper; derived from its
+ * equilibrium G:P = 0, Eq. weak:discr:FFT): the adjoint field lambda solves
+ * G:K:lambda = G:(K:W)/n with the same CG operator (K is symmetric for
+ * Saint Venant-Kirchhoff), and
+ *   dJ/dmu_v = (1/n) W : (dP/dmu)_v - lambda_v : (dP/dmu)_v,
+ *   dP/dmu = F . (2 dev E).
+ * The linear solve stops at ||r|| <= tol_cg ||b|| (float32 handles refine
+ * float32 CG solutions against the float64 residual).  grad: [n] float64
+ * (host or device).  cg_iters (may be NULL) receives the CG iterations.
+ * RVE_ERR_UNSUPPORTED for the J2 model (path-dependent; not built). */
+int rve_adjoint_grad_mu(rve_t h, const double W[9], double tol_cg, double* grad, int grad_on_device,
+                        int* cg_iters);
+
 /* Homogenised first Piola-Kirchhoff stress P-bar = <P> (voxel average),
  * row-major, host. */
 int rve_homogenized_P(rve_t h, double Pbar[9]);

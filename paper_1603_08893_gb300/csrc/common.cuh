@@ -49,6 +49,7 @@ struct SolverState {
   double dF2;       // ||dF||^2 of the last Newton update
   double Pbar[9];
   double meanF[9];
+  double adjW[9];   // W / n of the adjoint right-hand side G : (K : W) / n
   int err_flags;    // bit 0: det F <= 0, bit 1: non-finite value
   int pad;
   // reduction counters (one per reducing kernel family)

@@ -85,6 +85,14 @@ void launch_svk_k4_full(const double* F, size_t v0, size_t count, size_t n,
 template <typename Ti, typename To>
 void launch_convert(const Ti* in, To* out, size_t count, cudaStream_t s);
 
+template <typename RC>
+void launch_cg_init(size_t n9, const double* b, const double* Ax, RC* r, RC* x, SolverState* st,
+                    double* partials, cudaStream_t s);
+template <typename RC>
+void launch_accumulate(size_t n9, double* y, const RC* x, cudaStream_t s);
+void launch_adjoint_grad(const double* F, const double* lam, const double W[9], size_t n, double* g,
+                         cudaStream_t s);
+
 // ---- finite-strain J2 (kernels_j2.cu) ----
 template <typename RO>
 void launch_j2_constitutive(const double* F, size_t n, MatView<double> mat, const double* hc,

@@ -245,6 +245,83 @@ __global__ void __launch_bounds__(VEC_THREADS) k_svk_k4(const double* __restrict
   }
 }
 
+// CG start for A x = b - Ax0: r = b - Ax0 (in the CG precision), x = 0,
+// ||r||^2 and the CG state as after a residual evaluation.
+template <typename RC>
+__global__ void __launch_bounds__(VEC_THREADS) k_cg_init(size_t n9, const double* __restrict__ b,
+                                                         const double* __restrict__ Ax,
+                                                         RC* __restrict__ r, RC* __restrict__ x,
+                                                         SolverState* st, double* partials) {
+  double acc = 0.0;
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n9; i += stride) {
+    const double ri = b[i] - (Ax ? Ax[i] : 0.0);
+    r[i] = (RC)ri;
+    x[i] = (RC)0;
+    acc += ri * ri;
+  }
+  double a[1] = {acc}, tot[1];
+  if (last_block_sum<1>(a, partials, &st->counter[SLOT_BB], tot) && threadIdx.x == 0) {
+    const double bb = tot[0];
+    st->bb = bb;
+    st->rr = bb;
+    st->it = 0;
+    st->beta = 0.0;
+    st->status = 0;
+    st->tol2 = fmax(st->cg_tol * st->cg_tol * bb, st->cg_atol * st->cg_atol);
+    st->done = (bb == 0.0) ? 1 : 0;
+    if (!isfinite(bb)) {
+      st->status = RVE_DEV_ERR_NONFINITE;
+      st->done = 1;
+    }
+  }
+}
+
+// y += (double) x
+template <typename RC>
+__global__ void __launch_bounds__(VEC_THREADS) k_accumulate(size_t n9, double* __restrict__ y,
+                                                            const RC* __restrict__ x) {
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n9; i += stride)
+    y[i] += (double)x[i];
+}
+
+// dJ/dmu_k = (1/n) W : (dP/dmu)_k - lambda_k : (dP/dmu)_k with
+// dP/dmu = F . (2 dev E) at fixed bulk modulus (S = lambda tr(E) I + 2 mu E,
+// lambda = K - 2 mu / 3).
+struct W9 {
+  double w[9];
+};
+__global__ void __launch_bounds__(VEC_THREADS) k_adjoint_grad(const double* __restrict__ F,
+                                                              const double* __restrict__ lam,
+                                                              W9 W, size_t n, double* __restrict__ g) {
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  const double inv_n = 1.0 / (double)n;
+  for (size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+    double f[9];
+#pragma unroll
+    for (int c = 0; c < 9; ++c) f[c] = F[(size_t)c * n + v];
+    double E[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b)
+        E[a][b] = 0.5 * (f[a] * f[b] + f[3 + a] * f[3 + b] + f[6 + a] * f[6 + b] - (a == b ? 1.0 : 0.0));
+    const double tr = E[0][0] + E[1][1] + E[2][2];
+    double acc = 0.0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        double d = 0.0;  // (F . 2 dev E)_ab
+#pragma unroll
+        for (int c = 0; c < 3; ++c) d += f[3 * a + c] * 2.0 * (E[c][b] - (c == b ? tr / 3.0 : 0.0));
+        acc += (W.w[3 * a + b] * inv_n - lam[(size_t)(3 * a + b) * n + v]) * d;
+      }
+    g[v] = acc;
+  }
+}
+
 template <typename Ti, typename To>
 __global__ void k_convert(const Ti* __restrict__ in, To* __restrict__ out, size_t count) {
   const size_t stride = (size_t)gridDim.x * blockDim.x;
@@ -295,6 +372,24 @@ void launch_svk_k4_full(const double* F, size_t v0, size_t count, size_t n,
   k_svk_k4<<<grid_for(count), VEC_THREADS, 0, s>>>(F, v0, count, n, mat, dst);
 }
 
+template <typename RC>
+void launch_cg_init(size_t n9, const double* b, const double* Ax, RC* r, RC* x, SolverState* st,
+                    double* partials, cudaStream_t s) {
+  k_cg_init<RC><<<grid_for(n9), VEC_THREADS, 0, s>>>(n9, b, Ax, r, x, st, partials);
+}
+
+template <typename RC>
+void launch_accumulate(size_t n9, double* y, const RC* x, cudaStream_t s) {
+  k_accumulate<RC><<<grid_for(n9), VEC_THREADS, 0, s>>>(n9, y, x);
+}
+
+void launch_adjoint_grad(const double* F, const double* lam, const double W[9], size_t n, double* g,
+                         cudaStream_t s) {
+  W9 w;
+  for (int c = 0; c < 9; ++c) w.w[c] = W[c];
+  k_adjoint_grad<<<grid_for(n), VEC_THREADS, 0, s>>>(F, lam, w, n, g);
+}
+
 template <typename Ti, typename To>
 void launch_convert(const Ti* in, To* out, size_t count, cudaStream_t s) {
   k_convert<Ti, To><<<grid_for(count), VEC_THREADS, 0, s>>>(in, out, count);
@@ -320,3 +415,9 @@ template void launch_svk_constitutive<double>(const double*, size_t, MatView<dou
 template void launch_convert<double, float>(const double*, float*, size_t, cudaStream_t);
 template void launch_convert<float, double>(const float*, double*, size_t, cudaStream_t);
 template void launch_convert<double, double>(const double*, double*, size_t, cudaStream_t);
+template void launch_cg_init<float>(size_t, const double*, const double*, float*, float*,
+                                    SolverState*, double*, cudaStream_t);
+template void launch_cg_init<double>(size_t, const double*, const double*, double*, double*,
+                                     SolverState*, double*, cudaStream_t);
+template void launch_accumulate<float>(size_t, double*, const float*, cudaStream_t);
+template void launch_accumulate<double>(size_t, double*, const double*, cudaStream_t);

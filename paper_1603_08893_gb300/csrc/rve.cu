@@ -162,6 +162,8 @@ struct rve_s {
   Twiddles<double> twd{};
   double Fbar[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
   double Fbar_committed[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};  // F-bar of the last committed state
+  double* adj_b = nullptr;  // adjoint right-hand side [9][n] (SVK)
+  double* adj_l = nullptr;  // adjoint solution [9][n] (SVK)
   double* hc = nullptr;  // J2 history, committed [7][n]
   double* ht = nullptr;  // J2 history, trial [7][n]
   std::string err;
@@ -325,6 +327,37 @@ void enqueue_project_fp64(rve_t h, double* buf) {
   h->launches += 5;
 }
 
+// Float64 view of the SVK tangent at the current F (mixed handles keep only
+// float32 tangent data, so S is recomputed from F).
+TangentView<double> tangent64_view(rve_t h) {
+  if (!h->mixed) {
+    TangentView<double> t = tangent_view<double>(h);
+    if (t.mode == TAN_SVK) t.Fop = h->F;
+    return t;
+  }
+  TangentView<double> t{};
+  t.mode = TAN_SVK;
+  t.K4 = nullptr;
+  t.Fop = h->F;
+  t.Sop = nullptr;
+  t.mat = mat_view<double>(h);
+  return t;
+}
+
+// out = G : (K : in) in float64 (src SRC_FIELD) or G : (K : U) for the
+// uniform field U stored in the device state (src SRC_UNIFORM); scale 1/n.
+void enqueue_operator64(rve_t h, int src, const double* in, const double* unif, double* out) {
+  const GridGeom& g = h->g;
+  launch_zfwd<double>(g, src, tangent64_view(h), in, nullptr, nullptr, unif, h->st, nullptr,
+                      h->spec64, h->twd, h->s);
+  launch_fft_y<double>(g, false, h->spec64, nullptr, h->twd, h->s);
+  launch_fft_x_proj<double>(g, 1.0 / (double)h->n, h->spec64, nullptr, h->twd, h->s);
+  launch_fft_y<double>(g, true, h->spec64, nullptr, h->twd, h->s);
+  launch_zinv<double, double>(g, OUT_PLAIN, h->spec64, out, nullptr, nullptr, nullptr, h->st,
+                              h->partials, nullptr, h->twd, h->s);
+  h->launches += 5;
+}
+
 // predictor right-hand side b = -G:(K_(0) : dFbar) (Eq. bc:lin) in the
 // operator precision; dFbar = Fbar - <F> computed on the device.
 template <typename R>
@@ -462,8 +495,11 @@ size_t layout(rve_t h, Arena& a) {
   if (h->model == RVE_J2) {
     h->hc = a.take<double>(7 * n);
     h->ht = a.take<double>(7 * n);
+    h->adj_b = h->adj_l = nullptr;
   } else {
     h->hc = h->ht = nullptr;
+    h->adj_b = a.take<double>(n9);
+    h->adj_l = a.take<double>(n9);
   }
   h->table64 = a.take<double>(256 * 4);
   h->table32 = a.take<float>(256 * 4);
@@ -966,6 +1002,70 @@ int rve_get_K4(rve_t h, double* dst, int on_device) {
   }
   CK(cudaStreamSynchronize(h->s));
   return RVE_OK;
+}
+
+}  // extern "C"
+
+// Adjoint solve A lambda = G:(K:W)/n with the CG operator of the handle;
+// float32 handles refine in float64 (residual b - A64 lambda).
+template <typename RC>
+static int adjoint_solve(rve_t h, double tol, int* total_iters) {
+  const size_t n9 = 9 * h->n;
+  // b = G : (K : W/n) in float64
+  enqueue_operator64(h, SRC_UNIFORM, nullptr, h->st->adjW, h->adj_b);
+  CK(cudaMemsetAsync(h->adj_l, 0, n9 * sizeof(double), h->s));
+  double b0 = -1.0;
+  int its_total = 0;
+  const int rounds = h->mixed ? 6 : 1;
+  for (int round = 0; round < rounds; ++round) {
+    if (round > 0) enqueue_operator64(h, SRC_FIELD, h->adj_l, nullptr, h->tmp64);
+    launch_cg_init<RC>(n9, h->adj_b, round > 0 ? h->tmp64 : nullptr, as<RC>(h->r), as<RC>(h->x),
+                       h->st, h->partials, h->s);
+    h->launches += 1;
+    int rc = sync_state(h);
+    if (rc) return rc;
+    const double bb = std::sqrt(h->hst->bb);
+    if (round == 0) b0 = bb;
+    if (bb <= tol * b0 || bb == 0.0) break;
+    int its = 0;
+    rc = cg_solve<RC>(h, &its);
+    its_total += its;
+    if (rc) return fail(h, rc, std::string("adjoint solve: ") + rve_status_string(rc));
+    launch_accumulate<RC>(n9, h->adj_l, as<RC>(h->x), h->s);
+    h->launches += 1;
+    // float32 increments are compatible only up to float32 round-off; the
+    // incompatible part would enter lambda : dP/dmu directly
+    if (h->mixed) enqueue_project_fp64(h, h->adj_l);
+  }
+  *total_iters = its_total;
+  return RVE_OK;
+}
+
+extern "C" {
+
+int rve_adjoint_grad_mu(rve_t h, const double W[9], double tol_cg, double* grad, int on_device,
+                        int* cg_iters) {
+  if (!h || !W || !grad || !(tol_cg > 0.0)) return RVE_ERR_INVALID;
+  if (h->model != RVE_SVK) return fail(h, RVE_ERR_UNSUPPORTED, "adjoint: SVK only");
+  int rc = sync_state(h);
+  if (rc) return rc;
+  SolverState* hs = h->hst;
+  std::memset(hs->counter, 0, sizeof(hs->counter));
+  for (int c = 0; c < 9; ++c) hs->adjW[c] = W[c] / (double)h->n;
+  hs->cg_tol = h->mixed ? std::max(tol_cg, h->opt.cg_tol_floor) : tol_cg;
+  hs->cg_atol = h->opt.cg_atol;
+  hs->maxit = h->opt.max_cg;
+  hs->done = 0;
+  rc = push_state(h);
+  if (rc) return rc;
+  int its = 0;
+  rc = h->mixed ? adjoint_solve<float>(h, tol_cg, &its) : adjoint_solve<double>(h, tol_cg, &its);
+  if (rc) return rc;
+  if (cg_iters) *cg_iters = its;
+  launch_adjoint_grad(h->F, h->adj_l, W, h->n, h->tmp64, h->s);
+  h->launches += 1;
+  CK(cudaGetLastError());
+  return copy_out(h, grad, h->tmp64, h->n * sizeof(double), on_device);
 }
 
 int rve_get_history(rve_t h, double* dst, int on_device) {

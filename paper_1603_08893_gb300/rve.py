@@ -182,6 +182,20 @@ def rve_get_history(h, n, out=None):
     return out
 
 
+def rve_adjoint_grad_mu(h, W, n, tol_cg=1e-12, out=None):
+    """dJ/dmu per voxel for J = W : P-bar; returns (grad, cg_iterations)."""
+    Wc = np.ascontiguousarray(W, dtype=np.float64).reshape(9)
+    its = C.c_int(0)
+    if out is not None and _is_torch_cuda(out):
+        _check(lib.rve_adjoint_grad_mu(h, Wc.ctypes.data_as(C.c_void_p), float(tol_cg),
+                                       C.c_void_p(out.data_ptr()), 1, C.byref(its)), h)
+        return out, its.value
+    g = np.empty(n, dtype=np.float64)
+    _check(lib.rve_adjoint_grad_mu(h, Wc.ctypes.data_as(C.c_void_p), float(tol_cg),
+                                   g.ctypes.data_as(C.c_void_p), 0, C.byref(its)), h)
+    return g, its.value
+
+
 def rve_homogenized_P(h):
     P = np.empty(9, dtype=np.float64)
     _check(lib.rve_homogenized_P(h, P.ctypes.data_as(C.c_void_p)), h)
@@ -294,6 +308,11 @@ class RVE:
 
     def homogenized_P(self):
         return rve_homogenized_P(self.h)
+
+    def adjoint_grad_mu(self, W, tol_cg=1e-12):
+        """Gradient of W : P-bar with respect to per-voxel shear moduli, [*shape]."""
+        g, its = rve_adjoint_grad_mu(self.h, W, self.n, tol_cg)
+        return g.reshape(self.shape), its
 
     def get_history(self):
         """J2: committed (Cp^-1 [6 symmetric components], eps_p) per voxel, [7, *shape]."""
