@@ -55,7 +55,7 @@ extern "C" {
 #define RVE_ERR_CG_BREAKDOWN (-5) /* p.Ap = 0 exactly */
 #define RVE_ERR_NEWTON_MAXIT (-6) /* Newton reached max_newton iterations */
 #define RVE_ERR_NONFINITE (-7)    /* NaN or Inf in a residual, norm or stress */
-#define RVE_ERR_DETF (-8)         /* det F <= 0 in some voxel */
+#define RVE_ERR_DETF (-8)         /* det F <= 0 in some voxel of a converged state */
 #define RVE_ERR_TIMEOUT (-9)      /* a bounded device wait gave up */
 #define RVE_ERR_UNSUPPORTED (-10) /* valid request this build does not implement */
 
@@ -80,7 +80,10 @@ typedef struct {
   int tangent;          /* RVE_TAN_* (default AUTO) */
   int max_newton;       /* default 50 */
   int max_cg;           /* default 10000 */
-  double cg_tol_floor;  /* MIXED only: CG tolerance used = max(tol_cg, floor); default 1e-5 */
+  double cg_tol_floor;  /* MIXED only: CG tolerance used = max(tol_cg, floor); default 1e-5.
+                           MIXED CG also stops after 200 iterations without a 10% drop of
+                           ||r|| (float32 accuracy limit); Newton's float64 residual then
+                           decides */
   double cg_atol;       /* absolute CG floor: stop when ||r|| <= max(tol ||b||, atol); default 0 */
   int mixed_refine;     /* MIXED only: extra Newton iterations after the convergence test
                            first passes (further refinement with the float64 residual);
@@ -201,6 +204,45 @@ int rve_apply_operator(rve_t h, const double* dF, double* out, int on_device);
 /* out = G : A in float64 (Eq. weak:discr:FFT-intermediate).  A and out are
  * [9][n] float64, both on the host or both on the device. */
 int rve_project(rve_t h, const double* A, double* out, int on_device);
+
+/* ---------------------------------------------------------------------------
+ * Batches of independent cells of uneven size, solved together: each cell has
+ * its own state (as a handle); their CG iterations run as parallel branches
+ * of one CUDA graph and their Newton steps in lockstep, converged cells
+ * dropping out.  Not in the paper (one cell per run there).
+ * ------------------------------------------------------------------------- */
+typedef struct rve_batch_s* rve_batch_t;
+
+/* nrve cells; dims [nrve][3]; per cell a phase map (host [n_c] uint8), its
+ * number of phases and its parameter table [nphase_c][nparam] (host).  All
+ * cells share model and options (opt->workspace must be NULL: every cell
+ * allocates its own memory; opt->stream is not used: the batch runs on
+ * streams of its own and its calls return after they are idle). */
+int rve_batch_create(rve_batch_t* out, int nrve, const int* dims, int model, const int* nphase,
+                     const uint8_t* const* phase, const double* const* phase_params,
+                     const rve_options* opt);
+void rve_batch_destroy(rve_batch_t b);
+
+/* One load increment of every cell to its own F-bar (Fbar [nrve][9],
+ * row-major, host).  Same algorithm and tolerances as rve_solve_increment.
+ * stats: [nrve] or NULL.  Returns RVE_OK if every cell converged, else the
+ * first failure code (failed cells are rolled back; see their stats). */
+int rve_batch_solve(rve_batch_t b, const double* Fbar, double tol_newton, double tol_cg,
+                    rve_stats* stats);
+/* As rve_batch_solve, with the increment cutting of rve_solve_step applied
+ * per cell (cells whose increment failed are retried together with half
+ * their step, at most max_cuts halvings each); stats[c].substeps / cuts /
+ * substep_to report each cell's path. */
+int rve_batch_solve_step(rve_batch_t b, const double* Fbar, double tol_newton, double tol_cg,
+                         int max_cuts, rve_stats* stats);
+
+int rve_batch_size(rve_batch_t b);
+/* Handle of cell i (owned by the batch; use it for rve_get_* calls). */
+rve_t rve_batch_cell(rve_batch_t b, int i);
+/* P-bar of every cell, [nrve][9] host. */
+int rve_batch_homogenized_P(rve_batch_t b, double* Pbar);
+int rve_batch_launch_count(rve_batch_t b, long long* count);
+const char* rve_batch_last_error(rve_batch_t b);
 
 /* Text of the last error of h (never NULL); rve_status_string maps a code. */
 const char* rve_last_error(rve_t h);

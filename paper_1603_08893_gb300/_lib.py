@@ -84,6 +84,16 @@ _SIGS = {
     "rve_kernel_time": (C.c_int, [_H, C.POINTER(C.c_double),
                                   C.POINTER(C.c_longlong)]),
     "rve_project_noalloc": (C.c_int, [C.c_int, C.c_int, C.c_int, _P, _P, _P]),
+    "rve_batch_create": (C.c_int, [C.POINTER(_H), C.c_int, _P, C.c_int, _P, _P, _P,
+                                   C.POINTER(rve_options)]),
+    "rve_batch_destroy": (None, [_H]),
+    "rve_batch_solve": (C.c_int, [_H, _P, C.c_double, C.c_double, _P]),
+    "rve_batch_solve_step": (C.c_int, [_H, _P, C.c_double, C.c_double, C.c_int, _P]),
+    "rve_batch_size": (C.c_int, [_H]),
+    "rve_batch_cell": (_H, [_H, C.c_int]),
+    "rve_batch_homogenized_P": (C.c_int, [_H, _P]),
+    "rve_batch_launch_count": (C.c_int, [_H, C.POINTER(C.c_longlong)]),
+    "rve_batch_last_error": (C.c_char_p, [_H]),
 }
 
 

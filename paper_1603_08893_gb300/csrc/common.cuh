@@ -41,6 +41,9 @@ struct SolverState {
   int done;        // 1: CG finished (converged, failed or bb == 0)
   int status;      // 0 ok, else an RVE_ERR_* code
   double cg_tol, cg_atol;
+  double rr_min;    // smallest r.r so far (stagnation test)
+  int it_min;       // iteration of rr_min
+  int stag;         // > 0: stop after this many iterations without a 10% drop of ||r||
   // Newton
   double dFbar[9];  // macroscopic increment F-bar - <F>
   double Fbar[9];

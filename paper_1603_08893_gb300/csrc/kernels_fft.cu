@@ -477,6 +477,8 @@ __global__ void FFT_BOUNDS(R) k_zinv(const ZinvParams<R, RC> P) {
       const double bb = tot[0];
       st->bb = bb;
       st->rr = bb;
+      st->rr_min = bb;
+      st->it_min = 0;
       st->it = 0;
       st->beta = 0.0;
       st->status = 0;

@@ -35,6 +35,11 @@ __global__ void __launch_bounds__(VEC_THREADS) k_cg_update(size_t n9, R* __restr
     } else if (rr_new <= st->tol2) {
       st->rr = rr_new;
       st->done = 1;
+    } else if (st->stag > 0 && rr_new >= 0.81 * st->rr_min && st->it - st->it_min >= st->stag) {
+      // no 10% decrease of ||r|| for `stag` iterations: the float32 CG has
+      // reached its accuracy; the float64 Newton residual takes over
+      st->rr = rr_new;
+      st->done = 1;
     } else if (st->it >= st->maxit) {
       st->rr = rr_new;
       st->status = RVE_DEV_ERR_CG_MAXIT;
@@ -42,6 +47,10 @@ __global__ void __launch_bounds__(VEC_THREADS) k_cg_update(size_t n9, R* __restr
     } else {
       st->beta = rr_new / st->rr;
       st->rr = rr_new;
+    }
+    if (rr_new < 0.81 * st->rr_min) {
+      st->rr_min = rr_new;
+      st->it_min = st->it;
     }
   }
 }
@@ -265,6 +274,8 @@ __global__ void __launch_bounds__(VEC_THREADS) k_cg_init(size_t n9, const double
     const double bb = tot[0];
     st->bb = bb;
     st->rr = bb;
+    st->rr_min = bb;
+    st->it_min = 0;
     st->it = 0;
     st->beta = 0.0;
     st->status = 0;

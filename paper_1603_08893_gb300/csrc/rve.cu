@@ -15,6 +15,9 @@ namespace {
 
 const double kPi = 3.14159265358979323846264338327950288;
 const double kDivergedUpdate = 0.5;  // ||dF||/||F|| above this ends Newton as diverged
+// float32 CG stops after this many iterations without a 10% drop of ||r||
+// (its accuracy limit on high-contrast cells); float64 CG never does
+const int kMixedStagnation = 200;
 
 struct TimedLaunch {
   cudaEvent_t a, b;
@@ -379,6 +382,7 @@ void enqueue_predictor(rve_t h) {
 
 int enqueue_constitutive(rve_t h) {
   MatView<double> m = mat_view<double>(h);
+  cudaMemsetAsync(&h->st->err_flags, 0, sizeof(int), h->s);  // flags of this evaluation only
   if (h->model == RVE_J2) {
     if (h->mixed)
       launch_j2_constitutive<float>(h->F, h->n, m, h->hc, h->ht, h->P, as<float>(h->K4), h->st, h->s);
@@ -449,9 +453,12 @@ int cg_solve(rve_t h, int* iters) {
   return h->hst->status;
 }
 
-int check_flags(rve_t h) {
+// Flags of the last constitutive evaluation.  A Newton iterate may pass
+// through det F <= 0 in some voxel (the stress is still defined); only the
+// converged state (final = true) must have det F > 0 everywhere.
+int check_flags(rve_t h, bool final = true) {
   if (h->hst->err_flags & 2) return fail(h, RVE_ERR_NONFINITE, "non-finite stress or det F");
-  if (h->hst->err_flags & 1) return fail(h, RVE_ERR_DETF, "det F <= 0 in some voxel");
+  if (final && (h->hst->err_flags & 1)) return fail(h, RVE_ERR_DETF, "det F <= 0 in some voxel");
   return RVE_OK;
 }
 
@@ -796,6 +803,7 @@ static int solve_increment_t(rve_t h, double tol_newton, double tol_cg, rve_stat
   hs->cg_tol = h->mixed ? std::max(tol_cg, h->opt.cg_tol_floor) : tol_cg;
   hs->cg_atol = h->opt.cg_atol;
   hs->maxit = h->opt.max_cg;
+  hs->stag = h->mixed ? kMixedStagnation : 0;
   std::memcpy(hs->Fbar, h->Fbar, sizeof(hs->Fbar));
   int rc = push_state(h);
   if (rc) return rc;
@@ -850,7 +858,7 @@ static int solve_increment_t(rve_t h, double tol_newton, double tol_cg, rve_stat
       st->rel_update[i] = rel;
       st->residual[i] = std::sqrt(hs->bb);
     }
-    rc = check_flags(h);
+    rc = check_flags(h, false);
     if (rc) {
       result = rc;
       break;
@@ -873,6 +881,7 @@ static int solve_increment_t(rve_t h, double tol_newton, double tol_cg, rve_stat
         continue;
       }
       converged = true;
+      result = check_flags(h, true);  // the converged state must have det F > 0
       break;
     }
   }
@@ -1055,6 +1064,7 @@ int rve_adjoint_grad_mu(rve_t h, const double W[9], double tol_cg, double* grad,
   hs->cg_tol = h->mixed ? std::max(tol_cg, h->opt.cg_tol_floor) : tol_cg;
   hs->cg_atol = h->opt.cg_atol;
   hs->maxit = h->opt.max_cg;
+  hs->stag = h->mixed ? kMixedStagnation : 0;
   hs->done = 0;
   rc = push_state(h);
   if (rc) return rc;
@@ -1195,5 +1205,423 @@ int rve_kernel_time(rve_t h, double* total_ms, long long* launches) {
   *launches = cnt;
   return RVE_OK;
 }
+
+}  // extern "C"
+
+// ===========================================================================
+// Batches of independent cells.  Every cell keeps its own handle, buffers and
+// device state; the cells' per-iteration kernel chains run on a pool of
+// streams as independent branches of one CUDA graph (a graph launch advances
+// every cell by kGraphIters CG iterations; cells whose CG has finished return
+// at once from each kernel).  Newton steps run in lockstep on the host with
+// converged cells masked out.
+// ===========================================================================
+namespace {
+constexpr int kBatchStreams = 64;
+constexpr int kGraphIters = 2;
+
+__global__ void k_gather_cg(SolverState* const* st, int nrve, int* out) {
+  for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nrve; b += gridDim.x * blockDim.x) {
+    out[3 * b] = st[b]->done;
+    out[3 * b + 1] = st[b]->status;
+    out[3 * b + 2] = st[b]->it;
+  }
+}
+}  // namespace
+
+struct rve_batch_s {
+  std::vector<rve_t> rv;
+  std::vector<cudaStream_t> streams;
+  cudaStream_t s0 = nullptr;
+  bool mixed = false;
+  cudaGraphExec_t exec = nullptr;
+  std::vector<int> graph_members;  // cells captured in exec
+  SolverState** d_states = nullptr;
+  int* d_info = nullptr;
+  int* h_info = nullptr;
+  std::string err;
+  long long launches = 0;
+};
+
+namespace {
+
+int bfail(rve_batch_t b, int code, const std::string& msg) {
+  if (b) b->err = msg;
+  return code;
+}
+
+void batch_sync_all(rve_batch_t b) {
+  for (auto s : b->streams) cudaStreamSynchronize(s);
+  cudaStreamSynchronize(b->s0);
+}
+
+// capture kGraphIters CG iterations of the given cells as parallel branches
+template <typename R>
+int batch_capture(rve_batch_t b, const std::vector<int>& cells) {
+  if (b->exec) {
+    cudaGraphExecDestroy(b->exec);
+    b->exec = nullptr;
+  }
+  cudaGraph_t graph;
+  cudaEvent_t fork;
+  if (cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) != cudaSuccess) return RVE_ERR_CUDA;
+  std::vector<cudaEvent_t> joins(b->streams.size());
+  for (auto& e : joins) cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+  if (cudaStreamBeginCapture(b->s0, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+    return RVE_ERR_CUDA;
+  cudaEventRecord(fork, b->s0);
+  std::vector<bool> used(b->streams.size(), false);
+  for (int c : cells) {
+    rve_t h = b->rv[c];
+    const size_t si = (size_t)c % b->streams.size();
+    if (!used[si]) {
+      cudaStreamWaitEvent(b->streams[si], fork, 0);
+      used[si] = true;
+    }
+    for (int k = 0; k < kGraphIters; ++k) enqueue_cg_iteration<R>(h, -1);
+  }
+  for (size_t si = 0; si < b->streams.size(); ++si)
+    if (used[si]) {
+      cudaEventRecord(joins[si], b->streams[si]);
+      cudaStreamWaitEvent(b->s0, joins[si], 0);
+    }
+  const cudaError_t e1 = cudaStreamEndCapture(b->s0, &graph);
+  cudaEventDestroy(fork);
+  for (auto& e : joins) cudaEventDestroy(e);
+  if (e1 != cudaSuccess) return RVE_ERR_CUDA;
+  const cudaError_t e2 = cudaGraphInstantiate(&b->exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e2 != cudaSuccess) return RVE_ERR_CUDA;
+  b->graph_members = cells;
+  return RVE_OK;
+}
+
+// CG for every cell in `active` (their right-hand sides are set up):
+// graph launches until every cell's CG reports done.
+template <typename R>
+int batch_cg_phase(rve_batch_t b, const std::vector<int>& active, std::vector<int>& iters,
+                   std::vector<int>& status) {
+  const int nrve = (int)b->rv.size();
+  if (active.empty()) return RVE_OK;
+  if (b->graph_members != active) {
+    int rc = batch_capture<R>(b, active);
+    if (rc) return bfail(b, rc, "graph capture of the batched CG iteration failed");
+  }
+  batch_sync_all(b);
+  long long guard = 0;
+  const long long max_launch = (long long)b->rv[active[0]]->opt.max_cg / kGraphIters + 4096;
+  while (true) {
+    if (cudaGraphLaunch(b->exec, b->s0) != cudaSuccess) return bfail(b, RVE_ERR_CUDA, "graph launch");
+    b->launches += (long long)active.size() * 6 * kGraphIters;
+    k_gather_cg<<<(nrve + 127) / 128, 128, 0, b->s0>>>(b->d_states, nrve, b->d_info);
+    cudaMemcpyAsync(b->h_info, b->d_info, sizeof(int) * 3 * nrve, cudaMemcpyDeviceToHost, b->s0);
+    if (cudaStreamSynchronize(b->s0) != cudaSuccess) return bfail(b, RVE_ERR_CUDA, "batched CG");
+    bool all = true;
+    for (int c : active) all = all && b->h_info[3 * c];
+    if (all) break;
+    if (++guard > max_launch) return bfail(b, RVE_ERR_TIMEOUT, "batched CG state stopped advancing");
+  }
+  for (int c : active) {
+    iters[c] = b->h_info[3 * c + 2];
+    int st = b->h_info[3 * c + 1];
+    if (b->mixed && st == RVE_DEV_ERR_CG_BREAKDOWN && iters[c] >= 1) st = RVE_OK;
+    status[c] = st;
+  }
+  return RVE_OK;
+}
+
+// One increment for the cells in `cells` (F-bar of cell c at Fbar + 9 c);
+// result[c] receives each cell's status.
+template <typename R>
+int batch_solve_t(rve_batch_t b, const double* Fbar, double tol_newton, double tol_cg,
+                  rve_stats* stats, const std::vector<int>& cells, std::vector<int>& result) {
+  const int nrve = (int)b->rv.size();
+  std::vector<int> active, newton(nrve, 0), cgtot(nrve, 0);
+  std::vector<int> iters(nrve, 0), status(nrve, 0);
+  std::vector<double> prev(nrve, 0.0), prev2(nrve, 0.0);
+  for (int c : cells) result[c] = RVE_OK;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  batch_sync_all(b);
+  cudaEventRecord(e0, b->s0);
+  for (int c : cells) {
+    rve_t h = b->rv[c];
+    rve_set_macro_F(h, Fbar + 9 * c);
+    SolverState* hs = h->hst;
+    std::memset(hs, 0, sizeof(SolverState));
+    hs->cg_tol = h->mixed ? std::max(tol_cg, h->opt.cg_tol_floor) : tol_cg;
+    hs->cg_atol = h->opt.cg_atol;
+    hs->maxit = h->opt.max_cg;
+    hs->stag = h->mixed ? kMixedStagnation : 0;
+    std::memcpy(hs->Fbar, h->Fbar, sizeof(hs->Fbar));
+    push_state(h);
+    enqueue_predictor<R>(h);
+    launch_shifted_norm(h->F, h->n, h->st, h->partials, h->s);
+    h->launches += 1;
+    active.push_back(c);
+  }
+  const int max_newton = b->rv[0]->opt.max_newton;
+  for (int i = 0; i < max_newton && !active.empty(); ++i) {
+    int rc = batch_cg_phase<R>(b, active, iters, status);
+    if (rc) return rc;
+    std::vector<int> still;
+    for (int c : active) {
+      rve_t h = b->rv[c];
+      cgtot[c] += iters[c];
+      if (stats && i < RVE_MAX_NEWTON_LOG) stats[c].cg_iters[i] = iters[c];
+      if (status[c]) {
+        result[c] = status[c];
+        continue;
+      }
+      const size_t n9 = 9 * h->n;
+      if (h->mixed) {
+        launch_convert<R, double>(as<R>(h->x), h->tmp64, n9, h->s);
+        enqueue_project_fp64(h, h->tmp64);
+        launch_mean9<double>(h->tmp64, h->n, nullptr, h->partials, &h->st->counter[SLOT_MEAN],
+                             MEAN_X, h->st, h->s);
+        launch_newton_update<double>(h->F, h->tmp64, h->n, h->st, h->partials, i == 0, h->s);
+      } else {
+        launch_mean9<R>(as<R>(h->x), h->n, nullptr, h->partials, &h->st->counter[SLOT_MEAN],
+                        MEAN_X, h->st, h->s);
+        launch_newton_update<R>(h->F, as<R>(h->x), h->n, h->st, h->partials, i == 0, h->s);
+      }
+      enqueue_constitutive(h);
+      enqueue_residual<R>(h);
+      h->launches += 4;
+      still.push_back(c);
+    }
+    active.clear();
+    for (int c : still) {
+      rve_t h = b->rv[c];
+      if (sync_state(h)) return bfail(b, RVE_ERR_CUDA, "batched Newton step");
+      newton[c] = i + 1;
+      const double rel = std::sqrt(h->hst->dF2 / h->hst->Fn2);
+      if (stats && i < RVE_MAX_NEWTON_LOG) {
+        stats[c].rel_update[i] = rel;
+        stats[c].residual[i] = std::sqrt(h->hst->bb);
+      }
+      int frc = check_flags(h, false);
+      if (!frc && !std::isfinite(rel)) frc = RVE_ERR_NONFINITE;
+      if (!frc && (rel > kDivergedUpdate || (i >= 3 && rel > prev[c] && prev[c] > prev2[c])))
+        frc = RVE_ERR_NEWTON_MAXIT;
+      prev2[c] = prev[c];
+      prev[c] = rel;
+      if (frc) {
+        result[c] = frc;
+        continue;
+      }
+      if (rel < tol_newton && i > 0) {  // converged; det F > 0 required there
+        result[c] = check_flags(h, true);
+        continue;
+      }
+      active.push_back(c);
+    }
+    // cells that left the active set must not iterate in later graph launches
+    for (int c : still)
+      if (std::find(active.begin(), active.end(), c) == active.end()) {
+        const int one = 1;
+        cudaMemcpyAsync(&b->rv[c]->st->done, &one, sizeof(int), cudaMemcpyHostToDevice,
+                        b->rv[c]->s);
+      }
+  }
+  for (int c : active) result[c] = RVE_ERR_NEWTON_MAXIT;
+  int worst = RVE_OK;
+  for (int c : cells) {
+    rve_t h = b->rv[c];
+    const size_t n9 = 9 * h->n;
+    if (result[c] == RVE_OK) {
+      cudaMemcpyAsync(h->Ft, h->F, n9 * 8, cudaMemcpyDeviceToDevice, h->s);
+      std::memcpy(h->Fbar_committed, h->Fbar, sizeof(h->Fbar));
+      launch_mean9<double>(h->P, h->n, nullptr, h->partials, &h->st->counter[SLOT_MEAN],
+                           MEAN_PBAR, h->st, h->s);
+    } else {
+      cudaMemcpyAsync(h->F, h->Ft, n9 * 8, cudaMemcpyDeviceToDevice, h->s);
+      enqueue_constitutive(h);
+      if (worst == RVE_OK) worst = result[c];
+    }
+  }
+  batch_sync_all(b);
+  cudaEventRecord(e1, b->s0);
+  cudaEventSynchronize(e1);
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (stats)
+    for (int c : cells) {
+      stats[c].status = result[c];
+      stats[c].newton_iters += newton[c];
+      stats[c].cg_iters_total += cgtot[c];
+      stats[c].elapsed_ms += ms;
+    }
+  if (cudaGetLastError() != cudaSuccess) return bfail(b, RVE_ERR_CUDA, "batched increment");
+  if (worst) b->err = "at least one cell failed (see its stats)";
+  return worst;
+}
+
+}  // namespace
+
+extern "C" {
+
+int rve_batch_create(rve_batch_t* out, int nrve, const int* dims, int model, const int* nphase,
+                     const uint8_t* const* phase, const double* const* phase_params,
+                     const rve_options* opt) {
+  if (!out || nrve < 1 || !dims || !nphase || !phase || !phase_params) return RVE_ERR_INVALID;
+  *out = nullptr;
+  rve_batch_t b = new rve_batch_s();
+  rve_options o;
+  if (opt) o = *opt;
+  else rve_default_options(&o);
+  if (o.workspace) {
+    delete b;
+    return RVE_ERR_INVALID;  // every cell allocates its own workspace
+  }
+  b->mixed = o.precision == RVE_MIXED;
+  // the batch runs on streams of its own (graph capture needs a non-default
+  // stream); every batch call synchronises them before returning
+  if (cudaStreamCreateWithFlags(&b->s0, cudaStreamNonBlocking) != cudaSuccess) {
+    delete b;
+    return RVE_ERR_CUDA;
+  }
+  const int ns = std::min(nrve, kBatchStreams);
+  for (int i = 0; i < ns; ++i) {
+    cudaStream_t s;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+      rve_batch_destroy(b);
+      return RVE_ERR_CUDA;
+    }
+    b->streams.push_back(s);
+  }
+  for (int c = 0; c < nrve; ++c) {
+    rve_options oc = o;
+    oc.stream = b->streams[c % ns];
+    rve_t h = nullptr;
+    const int rc = rve_create(&h, dims[3 * c], dims[3 * c + 1], dims[3 * c + 2], model, nphase[c],
+                              phase[c], phase_params[c], nullptr, &oc);
+    if (rc) {
+      rve_batch_destroy(b);
+      return rc;
+    }
+    b->rv.push_back(h);
+  }
+  std::vector<SolverState*> ptrs(nrve);
+  for (int c = 0; c < nrve; ++c) ptrs[c] = b->rv[c]->st;
+  if (cudaMalloc(&b->d_states, sizeof(SolverState*) * nrve) != cudaSuccess ||
+      cudaMalloc(&b->d_info, sizeof(int) * 3 * nrve) != cudaSuccess ||
+      cudaMallocHost(&b->h_info, sizeof(int) * 3 * nrve) != cudaSuccess) {
+    rve_batch_destroy(b);
+    return RVE_ERR_NOMEM;
+  }
+  cudaMemcpy(b->d_states, ptrs.data(), sizeof(SolverState*) * nrve, cudaMemcpyHostToDevice);
+  *out = b;
+  return RVE_OK;
+}
+
+void rve_batch_destroy(rve_batch_t b) {
+  if (!b) return;
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  for (rve_t h : b->rv) rve_destroy(h);
+  for (auto s : b->streams) {
+    cudaStreamSynchronize(s);
+    cudaStreamDestroy(s);
+  }
+  if (b->d_states) cudaFree(b->d_states);
+  if (b->d_info) cudaFree(b->d_info);
+  if (b->h_info) cudaFreeHost(b->h_info);
+  if (b->s0) {
+    cudaStreamSynchronize(b->s0);
+    cudaStreamDestroy(b->s0);
+  }
+  delete b;
+}
+
+int rve_batch_solve(rve_batch_t b, const double* Fbar, double tol_newton, double tol_cg,
+                    rve_stats* stats) {
+  return rve_batch_solve_step(b, Fbar, tol_newton, tol_cg, 0, stats);
+}
+
+int rve_batch_solve_step(rve_batch_t b, const double* Fbar, double tol_newton, double tol_cg,
+                         int max_cuts, rve_stats* stats) {
+  if (!b || !Fbar || !(tol_newton > 0.0) || !(tol_cg > 0.0) || max_cuts < 0)
+    return RVE_ERR_INVALID;
+  b->err.clear();
+  const int nrve = (int)b->rv.size();
+  if (stats) std::memset(stats, 0, sizeof(rve_stats) * nrve);
+  // every cell follows the straight path from its committed F-bar; failed
+  // increments (rolled back) are retried with half the step, successes
+  // double it (as rve_solve_step)
+  std::vector<double> F0(9 * nrve), target(Fbar, Fbar + 9 * nrve), sub(9 * nrve);
+  std::vector<double> done(nrve, 0.0), step(nrve, 1.0);
+  std::vector<int> cuts(nrve, 0), nsub(nrve, 0), result(nrve, RVE_OK), fin(nrve, RVE_OK);
+  for (int c = 0; c < nrve; ++c) std::memcpy(&F0[9 * c], b->rv[c]->Fbar_committed, 9 * sizeof(double));
+  std::vector<int> open;
+  for (int c = 0; c < nrve; ++c) open.push_back(c);
+  int worst = RVE_OK;
+  while (!open.empty()) {
+    std::vector<double> to(nrve, 0.0);
+    for (int c : open) {
+      to[c] = std::min(1.0, done[c] + step[c]);
+      for (int k = 0; k < 9; ++k)
+        sub[9 * c + k] = (to[c] >= 1.0) ? target[9 * c + k]
+                                        : F0[9 * c + k] + to[c] * (target[9 * c + k] - F0[9 * c + k]);
+    }
+    const int rc = b->mixed ? batch_solve_t<float>(b, sub.data(), tol_newton, tol_cg, stats, open, result)
+                            : batch_solve_t<double>(b, sub.data(), tol_newton, tol_cg, stats, open, result);
+    if (rc == RVE_ERR_CUDA || rc == RVE_ERR_TIMEOUT) return rc;
+    std::vector<int> next;
+    for (int c : open) {
+      if (result[c] == RVE_OK) {
+        done[c] = to[c];
+        if (nsub[c] < RVE_MAX_NEWTON_LOG && stats) stats[c].substep_to[nsub[c]] = to[c];
+        ++nsub[c];
+        step[c] = std::min(2.0 * step[c], 1.0);
+        if (done[c] < 1.0) next.push_back(c);
+      } else if (++cuts[c] <= max_cuts) {
+        step[c] *= 0.5;
+        next.push_back(c);
+      } else {
+        fin[c] = result[c];
+        if (worst == RVE_OK) worst = result[c];
+      }
+    }
+    open.swap(next);
+  }
+  for (int c = 0; c < nrve; ++c) std::memcpy(b->rv[c]->Fbar, &target[9 * c], 9 * sizeof(double));
+  if (stats)
+    for (int c = 0; c < nrve; ++c) {
+      stats[c].status = fin[c];
+      stats[c].substeps = nsub[c];
+      stats[c].cuts = cuts[c];
+    }
+  if (worst) b->err = "at least one cell failed (see its stats)";
+  return worst;
+}
+
+int rve_batch_size(rve_batch_t b) { return b ? (int)b->rv.size() : 0; }
+
+rve_t rve_batch_cell(rve_batch_t b, int i) {
+  if (!b || i < 0 || i >= (int)b->rv.size()) return nullptr;
+  return b->rv[i];
+}
+
+int rve_batch_homogenized_P(rve_batch_t b, double* Pbar) {
+  if (!b || !Pbar) return RVE_ERR_INVALID;
+  for (size_t c = 0; c < b->rv.size(); ++c) {
+    const int rc = rve_homogenized_P(b->rv[c], Pbar + 9 * c);
+    if (rc) return rc;
+  }
+  return RVE_OK;
+}
+
+int rve_batch_launch_count(rve_batch_t b, long long* count) {
+  if (!b || !count) return RVE_ERR_INVALID;
+  long long t = b->launches;
+  for (rve_t h : b->rv) t += h->launches;
+  *count = t;
+  return RVE_OK;
+}
+
+const char* rve_batch_last_error(rve_batch_t b) { return b ? b->err.c_str() : "null batch"; }
 
 }  // extern "C"

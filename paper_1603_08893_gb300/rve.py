@@ -329,3 +329,74 @@ class RVE:
 
     def launch_count(self):
         return rve_launch_count(self.h)
+
+
+class RVEBatch:
+    """Many independent cells of uneven size solved together (one CUDA graph
+    per group of CG iterations, Newton steps in lockstep)."""
+
+    def __init__(self, shapes, phases, phase_params, model="svk", **opt):
+        n = len(shapes)
+        self.shapes = [tuple(int(s) for s in sh) for sh in shapes]
+        dims = np.ascontiguousarray(self.shapes, dtype=np.int32).reshape(-1)
+        self._keep = [np.ascontiguousarray(ph, dtype=np.uint8) for ph in phases]
+        self._keep += [np.ascontiguousarray(pp, dtype=np.float64) for pp in phase_params]
+        nph = np.array([np.asarray(pp).shape[0] for pp in phase_params], dtype=np.int32)
+        pptr = (C.c_void_p * n)(*[a.ctypes.data for a in self._keep[:n]])
+        qptr = (C.c_void_p * n)(*[a.ctypes.data for a in self._keep[n:]])
+        o = _options(**opt)
+        h = C.c_void_p()
+        code = lib.rve_batch_create(C.byref(h), n, dims.ctypes.data_as(C.c_void_p),
+                                    _MODELS[model], nph.ctypes.data_as(C.c_void_p),
+                                    C.cast(pptr, C.c_void_p), C.cast(qptr, C.c_void_p),
+                                    C.byref(o))
+        _check(code, what="rve_batch_create failed")
+        self.h = h
+        self.n = n
+        self._dims = dims
+
+    def close(self):
+        h = getattr(self, "h", None)
+        if h:
+            lib.rve_batch_destroy(h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def solve(self, Fbars, tol_newton=1e-5, tol_cg=1e-8, check=True, max_cuts=0):
+        """One increment per cell (max_cuts > 0: with per-cell increment cutting)."""
+        F = np.ascontiguousarray(Fbars, dtype=np.float64).reshape(self.n, 9)
+        st = (_lib.rve_stats * self.n)()
+        code = lib.rve_batch_solve_step(self.h, F.ctypes.data_as(C.c_void_p), float(tol_newton),
+                                        float(tol_cg), int(max_cuts), C.cast(st, C.c_void_p))
+        out = [dict(status=s.status, newton_iters=s.newton_iters,
+                    cg_iters_total=s.cg_iters_total, elapsed_ms=s.elapsed_ms,
+                    substeps=s.substeps, cuts=s.cuts) for s in st]
+        if check and code != 0:
+            raise RVEError(code, lib.rve_batch_last_error(self.h).decode())
+        return out
+
+    def homogenized_P(self):
+        P = np.empty((self.n, 9), dtype=np.float64)
+        _check(lib.rve_batch_homogenized_P(self.h, P.ctypes.data_as(C.c_void_p)),
+               what="rve_batch_homogenized_P")
+        return P.reshape(self.n, 3, 3)
+
+    def get_F(self, i):
+        h = lib.rve_batch_cell(self.h, int(i))
+        n = int(np.prod(self.shapes[i]))
+        return rve_get_F(h, n).reshape((3, 3) + self.shapes[i])
+
+    def get_P(self, i):
+        h = lib.rve_batch_cell(self.h, int(i))
+        n = int(np.prod(self.shapes[i]))
+        return rve_get_P(h, n).reshape((3, 3) + self.shapes[i])
+
+    def launch_count(self):
+        c = C.c_longlong(0)
+        _check(lib.rve_batch_launch_count(self.h, C.byref(c)), what="launch count")
+        return int(c.value)
