@@ -37,21 +37,22 @@ import synth  # noqa: E402
 
 METRIC = "voxel*CG-iterations/s, mixed FP32-CG/FP64-residual solver (vs plain FP64 GPU solver)"
 UNIT = "voxel*CG-iter/s"
-# algorithmic bytes per voxel of each CG-iteration kernel family, float32
-# vectors, on-the-fly SVK tangent (F in float32 + 1-byte phase), half
-# spectrum of h = N//2+1 planes (nine complex values per (x, y, kz)).
+# algorithmic bytes per voxel of each kernel family of the float32 CG
+# iteration (the five fused passes), on-the-fly SVK tangent (F in float32 +
+# 1-byte phase), half spectrum of h = N//2+1 planes (nine complex values per
+# (x, y, kz)).
 
 
 def family_bytes_per_voxel(nz, fam):
     s = 4.0
     spec = 9 * 2 * s * (nz // 2 + 1) / nz
     return {
-        "zfwd": 9 * s * 3 + 9 * s + 1 + spec,   # r, p in; p out; F; phase; spectrum out
+        # r, p, x in; p, x out; F; phase; spectrum out
+        "zfwd": 9 * s * 5 + 9 * s + 1 + spec,
         "fft_y_fwd": 2 * spec,
         "fft_x_proj": 2 * spec,
         "fft_y_inv": 2 * spec,
-        "zinv": spec + 9 * s * 2,               # spectrum in; p in; Ap out
-        "cg_update": 9 * s * 6,                 # x, r, p, Ap in; x, r out
+        "zinv": spec + 9 * s * 2,               # spectrum in; r in, r out
     }[fam]
 
 
@@ -197,7 +198,8 @@ def kernel_profile(RVE, cfg, torch, families, steps=1):
             r.set_macro_F(cfg["schedule"][k])
             r.solve_increment(cfg["tol_newton"], cfg["tol_cg"])
         ms, cnt = api.rve_kernel_time(r.h)
-        res[fam] = dict(total_ms=ms, launches=cnt, avg_ms=ms / max(cnt, 1))
+        if cnt:  # the float32 iteration has no separate vector-update pass
+            res[fam] = dict(total_ms=ms, launches=cnt, avg_ms=ms / cnt)
         r.close()
     return res
 

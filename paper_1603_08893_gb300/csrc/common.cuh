@@ -30,6 +30,11 @@ RVE_DEV cplx<R> c_mulc(cplx<R> a, cplx<R> b) {
 // are written only by the single "last block" of a reducing kernel, so every
 // kernel that follows in stream order sees them.
 // ---------------------------------------------------------------------------
+// Status codes mirrored from the public header.
+#define RVE_DEV_ERR_CG_MAXIT (-4)
+#define RVE_DEV_ERR_CG_BREAKDOWN (-5)
+#define RVE_DEV_ERR_NONFINITE (-7)
+
 struct SolverState {
   // CG
   double rr;       // r.r of the current iterate
@@ -68,10 +73,36 @@ enum ReduceSlot {
   SLOT_MISC = 5,
 };
 
-// Status codes mirrored from the public header.
-#define RVE_DEV_ERR_CG_MAXIT (-4)
-#define RVE_DEV_ERR_CG_BREAKDOWN (-5)
-#define RVE_DEV_ERR_NONFINITE (-7)
+
+// CG bookkeeping once r.r of the new residual is known (one thread):
+// iteration count, convergence, stagnation (float32 CG), iteration limit,
+// beta = rr_new / rr.
+RVE_DEV void cg_after_rr(SolverState* st, double rr_new) {
+  st->it += 1;
+  if (!isfinite(rr_new)) {
+    st->status = RVE_DEV_ERR_NONFINITE;
+    st->done = 1;
+  } else if (rr_new <= st->tol2) {
+    st->rr = rr_new;
+    st->done = 1;
+  } else if (st->stag > 0 && rr_new >= 0.81 * st->rr_min && st->it - st->it_min >= st->stag) {
+    // no 10% decrease of ||r|| for `stag` iterations: the float32 CG has
+    // reached its accuracy; the float64 Newton residual takes over
+    st->rr = rr_new;
+    st->done = 1;
+  } else if (st->it >= st->maxit) {
+    st->rr = rr_new;
+    st->status = RVE_DEV_ERR_CG_MAXIT;
+    st->done = 1;
+  } else {
+    st->beta = rr_new / st->rr;
+    st->rr = rr_new;
+  }
+  if (rr_new < 0.81 * st->rr_min) {
+    st->rr_min = rr_new;
+    st->it_min = st->it;
+  }
+}
 
 // ---------------------------------------------------------------------------
 // Deterministic block reduction of NV doubles: warp xor-butterflies in a fixed

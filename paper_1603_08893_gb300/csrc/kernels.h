@@ -10,9 +10,12 @@
 // tangent storage modes
 enum { TAN_FULL81 = 1, TAN_SVK = 2 };
 // sources of the forward pass input
-enum { SRC_FIELD = 0, SRC_CGP = 1, SRC_UNIFORM = 2 };
+// SRC_CGPX: fused CG iteration front: p = r + beta p, lagged x += alpha p,
+// and p.(K:p) (= p.Ap for compatible p, G being an orthogonal projector)
+enum { SRC_FIELD = 0, SRC_CGP = 1, SRC_UNIFORM = 2, SRC_CGPX = 3 };
 // outputs of the inverse z pass
-enum { OUT_PLAIN = 0, OUT_CGAP = 1, OUT_RESID = 2 };
+// OUT_CGR: fused CG iteration end: r -= alpha Ap in place, r.r, CG control
+enum { OUT_PLAIN = 0, OUT_CGAP = 1, OUT_RESID = 2, OUT_CGR = 3 };
 
 struct GridGeom {
   int nx, ny, nz;
@@ -47,8 +50,8 @@ struct Twiddles {
 // Forward transform chain front: (optional p-update) -> tangent -> R2C along z.
 template <typename R>
 void launch_zfwd(const GridGeom& g, int src, const TangentView<R>& tan, const R* field, const R* r,
-                 R* p, const double* unif, const SolverState* st, const int* done, cplx<R>* spec,
-                 const Twiddles<R>& tw, cudaStream_t s);
+                 R* p, const double* unif, SolverState* st, const int* done, cplx<R>* spec,
+                 const Twiddles<R>& tw, cudaStream_t s, R* x = nullptr, double* partials = nullptr);
 template <typename R>
 void launch_fft_y(const GridGeom& g, bool inverse, cplx<R>* spec, const int* done,
                   const Twiddles<R>& tw, cudaStream_t s);
@@ -65,6 +68,8 @@ cudaError_t fft_kernels_init();  // opt-in to large dynamic shared memory
 size_t fft_max_blocks(const GridGeom& g);
 
 // ---- vector / material kernels (kernels_mat.cu) ----
+template <typename R>
+void launch_cg_finish(size_t n9, R* x, const R* p, const SolverState* st, cudaStream_t s);
 template <typename R>
 void launch_cg_update(size_t n9, R* x, R* r, const R* p, const R* Ap, SolverState* st,
                       double* partials, cudaStream_t s);

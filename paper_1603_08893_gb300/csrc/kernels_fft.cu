@@ -113,10 +113,12 @@ struct ZfwdParams {
   const R* r;
   R* p;
   const double* unif;
-  const SolverState* st;
+  SolverState* st;
   const int* done;
   cplx<R>* spec;
   const cplx<R>* tw;
+  R* x;               // SRC_CGPX
+  double* partials;   // SRC_CGPX
 };
 
 template <typename R, int SRC, int TAN>
@@ -136,12 +138,14 @@ __global__ void FFT_BOUNDS(R) k_zfwd(const ZfwdParams<R> P) {
   const int nl = min(lz, nlines - l0);
   const int nvox = nl * nz;
   const size_t v0 = (size_t)l0 * nz;
-  R beta = 0;
+  R beta = 0, alpha_prev = 0;
   bool first = true;
-  if (SRC == SRC_CGP) {
+  if (SRC == SRC_CGP || SRC == SRC_CGPX) {
     first = (P.st->it == 0);
     beta = (R)P.st->beta;
+    alpha_prev = (R)P.st->alpha;
   }
+  double pkp = 0.0;
   TangentView<R> T = P.tan;
   T.mode = TAN;
   // every global load of a voxel is issued before its stores
@@ -162,14 +166,35 @@ __global__ void FFT_BOUNDS(R) k_zfwd(const ZfwdParams<R> P) {
         }
 #pragma unroll
         for (int c = 0; c < 9; ++c) in[c] = first ? rr[c] : fma(beta, pp[c], rr[c]);
+      } else if (SRC == SRC_CGPX) {
+        R rr[9], pp[9], xx[9];
+#pragma unroll
+        for (int c = 0; c < 9; ++c) rr[c] = P.r[(size_t)c * n + v];
+        if (!first) {
+#pragma unroll
+          for (int c = 0; c < 9; ++c) {
+            pp[c] = P.p[(size_t)c * n + v];
+            xx[c] = P.x[(size_t)c * n + v];
+          }
+#pragma unroll
+          for (int c = 0; c < 9; ++c) P.x[(size_t)c * n + v] = fma(alpha_prev, pp[c], xx[c]);
+        }
+#pragma unroll
+        for (int c = 0; c < 9; ++c) in[c] = first ? rr[c] : fma(beta, pp[c], rr[c]);
       } else {
 #pragma unroll
         for (int c = 0; c < 9; ++c) in[c] = (R)P.unif[c];
       }
       tangent_voxel<R>(T, v, n, in, out);
-      if (SRC == SRC_CGP) {
+      if (SRC == SRC_CGP || SRC == SRC_CGPX) {
 #pragma unroll
         for (int c = 0; c < 9; ++c) P.p[(size_t)c * n + v] = in[c];
+      }
+      if (SRC == SRC_CGPX) {
+        R sp = 0;
+#pragma unroll
+        for (int c = 0; c < 9; ++c) sp = fma(in[c], out[c], sp);
+        pkp += (double)sp;
       }
     } else {
 #pragma unroll
@@ -200,6 +225,28 @@ __global__ void FFT_BOUNDS(R) k_zfwd(const ZfwdParams<R> P) {
       // B = (z1 - conj(z_-k)) / (2i)
       const R dx = R(0.5) * (z1.x - z2.x), dy = R(0.5) * (z1.y - z2.y);
       P.spec[(size_t)(2 * k + 1) * ss + o] = {dy, -dx};
+    }
+  }
+  if (SRC == SRC_CGPX) {
+    // p.Ap = p.G(K p) = (G p).(K p) = p.(K p) for compatible p (G is an
+    // orthogonal projector), so the step length is known before the inverse
+    // transforms
+    double v1[1] = {pkp}, tot[1];
+    if (last_block_sum<1>(v1, P.partials, &P.st->counter[SLOT_PAP], tot) && threadIdx.x == 0) {
+      SolverState* st = P.st;
+      const double pap = tot[0];
+      st->pAp = pap;
+      if (!isfinite(pap)) {
+        st->status = RVE_DEV_ERR_NONFINITE;
+        st->alpha = 0.0;
+        st->done = 1;
+      } else if (pap == 0.0) {
+        st->status = RVE_DEV_ERR_CG_BREAKDOWN;
+        st->alpha = 0.0;
+        st->done = 1;
+      } else {
+        st->alpha = st->rr / pap;
+      }
     }
   }
 }
@@ -431,6 +478,19 @@ __global__ void FFT_BOUNDS(R) k_zinv(const ZinvParams<R, RC> P) {
     if (OUT == OUT_PLAIN) {
 #pragma unroll
       for (int c = 0; c < 9; ++c) P.dst[(size_t)c * n + v] = out[c];
+    } else if (OUT == OUT_CGR) {
+      const R alpha = (R)P.st->alpha;
+      R rv[9];
+#pragma unroll
+      for (int c = 0; c < 9; ++c) rv[c] = (R)P.r_out[(size_t)c * n + v];
+      R s = 0;
+#pragma unroll
+      for (int c = 0; c < 9; ++c) {
+        const R rn = fma(-alpha, out[c], rv[c]);
+        P.r_out[(size_t)c * n + v] = (RC)rn;
+        s = fma(rn, rn, s);
+      }
+      acc += (double)s;
     } else if (OUT == OUT_CGAP) {
       R pv[9];
 #pragma unroll
@@ -455,10 +515,12 @@ __global__ void FFT_BOUNDS(R) k_zinv(const ZinvParams<R, RC> P) {
   }
   if (OUT == OUT_PLAIN) return;
   double v1[1] = {acc}, tot[1];
-  const int slot = (OUT == OUT_CGAP) ? SLOT_PAP : SLOT_BB;
+  const int slot = (OUT == OUT_CGAP) ? SLOT_PAP : (OUT == OUT_CGR ? SLOT_RR : SLOT_BB);
   if (last_block_sum<1>(v1, P.partials, &P.st->counter[slot], tot) && threadIdx.x == 0) {
     SolverState* st = P.st;
-    if (OUT == OUT_CGAP) {
+    if (OUT == OUT_CGR) {
+      cg_after_rr(st, tot[0]);
+    } else if (OUT == OUT_CGAP) {
       const double pap = tot[0];
       st->pAp = pap;
       if (!isfinite(pap)) {
@@ -500,8 +562,8 @@ static int lz_of(const GridGeom& g) { return sizeof(R) == 4 ? g.lz_f : g.lz_d; }
 
 template <typename R>
 void launch_zfwd(const GridGeom& g, int src, const TangentView<R>& tan, const R* field, const R* r,
-                 R* p, const double* unif, const SolverState* st, const int* done, cplx<R>* spec,
-                 const Twiddles<R>& tw, cudaStream_t s) {
+                 R* p, const double* unif, SolverState* st, const int* done, cplx<R>* spec,
+                 const Twiddles<R>& tw, cudaStream_t s, R* x, double* partials) {
   ZfwdParams<R> P;
   P.g = g;
   P.lz = lz_of<R>(g);
@@ -515,6 +577,8 @@ void launch_zfwd(const GridGeom& g, int src, const TangentView<R>& tan, const R*
   P.done = done;
   P.spec = spec;
   P.tw = tw.z;
+  P.x = x;
+  P.partials = partials;
   const int nlines = g.nx * g.ny;
   const dim3 grid((nlines + P.lz - 1) / P.lz);
   const size_t sm = sizeof(cplx<R>) * ((size_t)((g.nz + 1) & ~1) + 10 * (size_t)P.lz * g.nz);
@@ -527,6 +591,9 @@ void launch_zfwd(const GridGeom& g, int src, const TangentView<R>& tan, const R*
   } else if (src == SRC_CGP) {
     if (tm == TAN_FULL81) ZF(SRC_CGP, TAN_FULL81);
     else ZF(SRC_CGP, TAN_SVK);
+  } else if (src == SRC_CGPX) {
+    if (tm == TAN_FULL81) ZF(SRC_CGPX, TAN_FULL81);
+    else ZF(SRC_CGPX, TAN_SVK);
   } else {
     if (tm == TAN_FULL81) ZF(SRC_UNIFORM, TAN_FULL81);
     else ZF(SRC_UNIFORM, TAN_SVK);
@@ -588,6 +655,7 @@ void launch_zinv(const GridGeom& g, int out, const cplx<R>* spec, R* dst, RC* r_
   const size_t sm = sizeof(cplx<R>) * ((size_t)((g.nz + 1) & ~1) + 10 * (size_t)P.lz * g.nz);
   if (out == OUT_PLAIN) k_zinv<R, RC, OUT_PLAIN><<<grid, FFT_THREADS, sm, s>>>(P);
   else if (out == OUT_CGAP) k_zinv<R, RC, OUT_CGAP><<<grid, FFT_THREADS, sm, s>>>(P);
+  else if (out == OUT_CGR) k_zinv<R, RC, OUT_CGR><<<grid, FFT_THREADS, sm, s>>>(P);
   else k_zinv<R, RC, OUT_RESID><<<grid, FFT_THREADS, sm, s>>>(P);
 }
 
@@ -615,6 +683,8 @@ static void init_r() {
   allow_big_smem(k_zfwd<R, SRC_FIELD, 0>);
   allow_big_smem(k_zfwd<R, SRC_CGP, TAN_FULL81>);
   allow_big_smem(k_zfwd<R, SRC_CGP, TAN_SVK>);
+  allow_big_smem(k_zfwd<R, SRC_CGPX, TAN_FULL81>);
+  allow_big_smem(k_zfwd<R, SRC_CGPX, TAN_SVK>);
   allow_big_smem(k_zfwd<R, SRC_UNIFORM, TAN_FULL81>);
   allow_big_smem(k_zfwd<R, SRC_UNIFORM, TAN_SVK>);
   allow_big_smem(k_fft_y<R, true>);
@@ -632,18 +702,21 @@ cudaError_t fft_kernels_init() {
   allow_big_smem(k_zinv<double, float, OUT_RESID>);
   allow_big_smem(k_zinv<float, float, OUT_PLAIN>);
   allow_big_smem(k_zinv<float, float, OUT_CGAP>);
+  allow_big_smem(k_zinv<float, float, OUT_CGR>);
+  allow_big_smem(k_zinv<double, double, OUT_CGR>);
   allow_big_smem(k_zinv<float, float, OUT_RESID>);
   return g_init_err;
 }
 
 // explicit instantiations
 template void launch_zfwd<float>(const GridGeom&, int, const TangentView<float>&, const float*,
-                                 const float*, float*, const double*, const SolverState*,
-                                 const int*, cplx<float>*, const Twiddles<float>&, cudaStream_t);
+                                 const float*, float*, const double*, SolverState*, const int*,
+                                 cplx<float>*, const Twiddles<float>&, cudaStream_t, float*,
+                                 double*);
 template void launch_zfwd<double>(const GridGeom&, int, const TangentView<double>&, const double*,
-                                  const double*, double*, const double*, const SolverState*,
-                                  const int*, cplx<double>*, const Twiddles<double>&,
-                                  cudaStream_t);
+                                  const double*, double*, const double*, SolverState*, const int*,
+                                  cplx<double>*, const Twiddles<double>&, cudaStream_t, double*,
+                                  double*);
 template void launch_fft_y<float>(const GridGeom&, bool, cplx<float>*, const int*,
                                   const Twiddles<float>&, cudaStream_t);
 template void launch_fft_y<double>(const GridGeom&, bool, cplx<double>*, const int*,

@@ -26,33 +26,21 @@ __global__ void __launch_bounds__(VEC_THREADS) k_cg_update(size_t n9, R* __restr
     acc += (double)ri * (double)ri;
   }
   double v[1] = {acc}, tot[1];
-  if (last_block_sum<1>(v, partials, &st->counter[SLOT_RR], tot) && threadIdx.x == 0) {
-    const double rr_new = tot[0];
-    st->it += 1;
-    if (!isfinite(rr_new)) {
-      st->status = RVE_DEV_ERR_NONFINITE;
-      st->done = 1;
-    } else if (rr_new <= st->tol2) {
-      st->rr = rr_new;
-      st->done = 1;
-    } else if (st->stag > 0 && rr_new >= 0.81 * st->rr_min && st->it - st->it_min >= st->stag) {
-      // no 10% decrease of ||r|| for `stag` iterations: the float32 CG has
-      // reached its accuracy; the float64 Newton residual takes over
-      st->rr = rr_new;
-      st->done = 1;
-    } else if (st->it >= st->maxit) {
-      st->rr = rr_new;
-      st->status = RVE_DEV_ERR_CG_MAXIT;
-      st->done = 1;
-    } else {
-      st->beta = rr_new / st->rr;
-      st->rr = rr_new;
-    }
-    if (rr_new < 0.81 * st->rr_min) {
-      st->rr_min = rr_new;
-      st->it_min = st->it;
-    }
-  }
+  if (last_block_sum<1>(v, partials, &st->counter[SLOT_RR], tot) && threadIdx.x == 0)
+    cg_after_rr(st, tot[0]);
+}
+
+// Completes a CG solve run with the fused iteration (x is updated one
+// iteration late): x += alpha p with the last step length.
+template <typename R>
+__global__ void __launch_bounds__(VEC_THREADS) k_cg_finish(size_t n9, R* __restrict__ x,
+                                                           const R* __restrict__ p,
+                                                           const SolverState* st) {
+  if (st->it == 0) return;
+  const R alpha = (R)st->alpha;
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n9; i += stride)
+    x[i] = fma(alpha, p[i], x[i]);
 }
 
 // Component means of a [9][n] field.  post selects what the last block does
@@ -354,6 +342,11 @@ void launch_cg_update(size_t n9, R* x, R* r, const R* p, const R* Ap, SolverStat
   k_cg_update<R><<<grid_for(n9), VEC_THREADS, 0, s>>>(n9, x, r, p, Ap, st, partials);
 }
 
+template <typename R>
+void launch_cg_finish(size_t n9, R* x, const R* p, const SolverState* st, cudaStream_t s) {
+  k_cg_finish<R><<<grid_for(n9), VEC_THREADS, 0, s>>>(n9, x, p, st);
+}
+
 template <typename T>
 void launch_mean9(const T* A, size_t n, double* out9, double* partials, unsigned int* counter,
                   int post, SolverState* st, cudaStream_t s) {
@@ -432,3 +425,5 @@ template void launch_cg_init<double>(size_t, const double*, const double*, doubl
                                      SolverState*, double*, cudaStream_t);
 template void launch_accumulate<float>(size_t, double*, const float*, cudaStream_t);
 template void launch_accumulate<double>(size_t, double*, const double*, cudaStream_t);
+template void launch_cg_finish<float>(size_t, float*, const float*, const SolverState*, cudaStream_t);
+template void launch_cg_finish<double>(size_t, double*, const double*, const SolverState*, cudaStream_t);

@@ -6,6 +6,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/rve.h"
@@ -261,18 +262,30 @@ const Twiddles<float>& twiddles<float>(rve_t h) { return h->twf; }
 template <>
 const Twiddles<double>& twiddles<double>(rve_t h) { return h->twd; }
 
-// one CG iteration on the device: Ap = G:(K:p) with the p-update fused in
-// front and p.Ap fused at the end, then the vector update and tests.
+// one CG iteration on the device, Ap = G:(K:p) through five passes.
+// float64 (the oracle's recurrence): the p-update is fused into the first
+// pass, p.Ap into the last, then a vector pass updates x and r.
+// float32: the whole iteration lives in the five passes.  The first pass
+// forms p, applies the previous step x += alpha p_prev and reduces
+// p.(K:p), which equals p.Ap because p is compatible and G an orthogonal
+// projector, so alpha is known before the inverse transforms; the last pass
+// updates r -= alpha Ap in place and Ap is never stored.  x lags one step;
+// enqueue_cg_finish adds the last one.
 template <typename R>
 void enqueue_cg_iteration(rve_t h, int iter) {
   const GridGeom& g = h->g;
   const Twiddles<R>& tw = twiddles<R>(h);
   const int* done = &h->st->done;
   cplx<R>* spec = as<cplx<R>>(h->spec_op);
+  constexpr bool fused = std::is_same<R, float>::value;
   {
     FamilyTimer t(h, 0, iter);
-    launch_zfwd<R>(g, SRC_CGP, tangent_view<R>(h), nullptr, as<R>(h->r), as<R>(h->p), nullptr,
-                   h->st, done, spec, tw, h->s);
+    if (fused)
+      launch_zfwd<R>(g, SRC_CGPX, tangent_view<R>(h), nullptr, as<R>(h->r), as<R>(h->p),
+                     nullptr, h->st, done, spec, tw, h->s, as<R>(h->x), h->partials);
+    else
+      launch_zfwd<R>(g, SRC_CGP, tangent_view<R>(h), nullptr, as<R>(h->r), as<R>(h->p),
+                     nullptr, h->st, done, spec, tw, h->s);
   }
   {
     FamilyTimer t(h, 1, iter);
@@ -286,6 +299,13 @@ void enqueue_cg_iteration(rve_t h, int iter) {
     FamilyTimer t(h, 3, iter);
     launch_fft_y<R>(g, true, spec, done, tw, h->s);
   }
+  if (fused) {
+    FamilyTimer t(h, 4, iter);
+    launch_zinv<R, R>(g, OUT_CGR, spec, nullptr, as<R>(h->r), nullptr, nullptr, h->st,
+                      h->partials, done, tw, h->s);
+    h->launches += 5;
+    return;
+  }
   {
     FamilyTimer t(h, 4, iter);
     launch_zinv<R, R>(g, OUT_CGAP, spec, as<R>(h->Ap), nullptr, nullptr, as<R>(h->p), h->st,
@@ -297,6 +317,14 @@ void enqueue_cg_iteration(rve_t h, int iter) {
                         h->partials, h->s);
   }
   h->launches += 6;
+}
+
+// The last lagged step x += alpha p of a float32 CG solve.
+template <typename R>
+void enqueue_cg_finish(rve_t h) {
+  if (!std::is_same<R, float>::value) return;
+  launch_cg_finish<R>(9 * h->n, as<R>(h->x), as<R>(h->p), h->st, h->s);
+  h->launches += 1;
 }
 
 // b = -G:P in float64; r = b (in the CG precision), x = 0, CG state reset.
@@ -444,6 +472,7 @@ int cg_solve(rve_t h, int* iters) {
     chunk = std::max(2, std::min(pred, 256));
     chunk = std::min(chunk, std::max(1, h->hst->maxit - it));
   }
+  enqueue_cg_finish<R>(h);
   *iters = h->hst->it;
   h->solve_iters.push_back({h->solve_id, h->hst->it});
   // float32 CG can reach p.Ap = 0 once its residual is at the float32 noise
@@ -1312,7 +1341,7 @@ int batch_cg_phase(rve_batch_t b, const std::vector<int>& active, std::vector<in
   const long long max_launch = (long long)b->rv[active[0]]->opt.max_cg / kGraphIters + 4096;
   while (true) {
     if (cudaGraphLaunch(b->exec, b->s0) != cudaSuccess) return bfail(b, RVE_ERR_CUDA, "graph launch");
-    b->launches += (long long)active.size() * 6 * kGraphIters;
+    b->launches += (long long)active.size() * (b->mixed ? 5 : 6) * kGraphIters;
     k_gather_cg<<<(nrve + 127) / 128, 128, 0, b->s0>>>(b->d_states, nrve, b->d_info);
     cudaMemcpyAsync(b->h_info, b->d_info, sizeof(int) * 3 * nrve, cudaMemcpyDeviceToHost, b->s0);
     if (cudaStreamSynchronize(b->s0) != cudaSuccess) return bfail(b, RVE_ERR_CUDA, "batched CG");
@@ -1322,6 +1351,7 @@ int batch_cg_phase(rve_batch_t b, const std::vector<int>& active, std::vector<in
     if (++guard > max_launch) return bfail(b, RVE_ERR_TIMEOUT, "batched CG state stopped advancing");
   }
   for (int c : active) {
+    enqueue_cg_finish<R>(b->rv[c]);
     iters[c] = b->h_info[3 * c + 2];
     int st = b->h_info[3 * c + 1];
     if (b->mixed && st == RVE_DEV_ERR_CG_BREAKDOWN && iters[c] >= 1) st = RVE_OK;
