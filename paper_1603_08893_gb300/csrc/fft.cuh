@@ -9,8 +9,9 @@
 // the conjugate, both unnormalised.
 //
 // Odd radices 3, 5, 7, 11 use the symmetric form of the R-point DFT
-// (pairs x_r +- x_(R-r)); other primes use a direct sum, one output per
-// thread.  Stages alternate between two shared-memory buffers.
+// (pairs x_r +- x_(R-r)); composite radices 9, 15, 21, 25 nest two of them
+// in registers; other primes use a direct sum, one output per thread.
+// Stages alternate between two shared-memory buffers.
 #pragma once
 #include "common.cuh"
 
@@ -51,6 +52,70 @@ struct LineMap {
   int gshift, gstride, lstride, es, lf;
   RVE_DEV int base(int l) const {
     return (l >> gshift) * gstride + (l & ((1 << gshift) - 1)) * lstride;
+  }
+};
+
+// ---------------------------------------------------------------------------
+// Roots of unity as compile-time constants: cos and sin of 2 pi m / M by
+// reduction to [0, pi/4] and the Taylor series there (the terms beyond
+// x^25 / 25! are below 1e-30).  Used only in constant expressions.
+// ---------------------------------------------------------------------------
+constexpr double kPi = 3.14159265358979323846264338327950288;
+
+constexpr double taylor_sin(double x) {
+  double t = x, s = x;
+  for (int k = 1; k < 13; ++k) {
+    t *= -x * x / ((2.0 * k) * (2.0 * k + 1.0));
+    s += t;
+  }
+  return s;
+}
+
+constexpr double taylor_cos(double x) {
+  double t = 1.0, s = 1.0;
+  for (int k = 1; k < 13; ++k) {
+    t *= -x * x / ((2.0 * k - 1.0) * (2.0 * k));
+    s += t;
+  }
+  return s;
+}
+
+// (cos, sin)(2 pi f) for f in [0, 1/4]
+constexpr double quarter_cos(double f) {
+  return f <= 0.125 ? taylor_cos(2.0 * kPi * f) : taylor_sin(2.0 * kPi * (0.25 - f));
+}
+constexpr double quarter_sin(double f) {
+  return f <= 0.125 ? taylor_sin(2.0 * kPi * f) : taylor_cos(2.0 * kPi * (0.25 - f));
+}
+
+constexpr double cos2pi(int m, int M) {
+  m %= M;
+  if (m < 0) m += M;
+  // 4m/M selects the quadrant; the remainder is exact in integers
+  const int q = (4 * m) / M;
+  const double f = (double)(4 * m - q * M) / (4.0 * M);  // in [0, 1/4)
+  return q == 0 ? quarter_cos(f) : q == 1 ? -quarter_sin(f) : q == 2 ? -quarter_cos(f)
+                                                                     : quarter_sin(f);
+}
+
+constexpr double sin2pi(int m, int M) {
+  m %= M;
+  if (m < 0) m += M;
+  const int q = (4 * m) / M;
+  const double f = (double)(4 * m - q * M) / (4.0 * M);
+  return q == 0 ? quarter_sin(f) : q == 1 ? quarter_cos(f) : q == 2 ? -quarter_sin(f)
+                                                                    : -quarter_cos(f);
+}
+
+// All M-th roots of unity exp(2 pi i m / M).
+template <int M>
+struct Roots {
+  double c[M], s[M];
+  constexpr Roots() : c(), s() {
+    for (int m = 0; m < M; ++m) {
+      c[m] = cos2pi(m, M);
+      s[m] = sin2pi(m, M);
+    }
   }
 };
 
@@ -137,6 +202,123 @@ RVE_DEV void stage_pp(const cplx<R>* __restrict__ src, cplx<R>* __restrict__ dst
   __syncthreads();
 }
 
+// R-point DFT with compile-time roots (cs[m] = cos(2 pi m/R), sn[m] =
+// sin(2 pi m/R); the forward transform multiplies by exp(-2 pi i m/R)).
+template <typename R, int RAD, bool INV>
+RVE_DEV void dft_const(cplx<R> (&v)[RAD]) {
+  constexpr Roots<RAD> T{};
+  R cs[RAD], sn[RAD];
+#pragma unroll
+  for (int m = 0; m < RAD; ++m) {
+    cs[m] = (R)T.c[m];
+    sn[m] = (R)T.s[m];
+  }
+  dft_odd<R, RAD, INV>(v, cs, sn);
+}
+
+constexpr int smallest_factor(int m) {
+  for (int p = 2; p * p <= m; ++p)
+    if (m % p == 0) return p;
+  return m;
+}
+
+template <typename R, int M, bool INV>
+RVE_DEV void dft_reg(cplx<R> (&v)[M]);
+
+// M = R1 R2 point DFT in registers, natural order in and out, by one
+// Cooley-Tukey split: with r = R2 a + b and k = k1 + R1 k2,
+//   X_k = sum_b w_R2^(b k2) [w_M^(b k1) sum_a w_R1^(a k1) x_(R2 a + b)]
+// (w_M = exp(-2 pi i / M) forward, its conjugate inverse).
+template <typename R, int R1, int R2, bool INV>
+RVE_DEV void dft_split(cplx<R> (&v)[R1 * R2]) {
+  constexpr int M = R1 * R2;
+  constexpr Roots<M> T{};
+#pragma unroll
+  for (int b = 0; b < R2; ++b) {
+    cplx<R> t[R1];
+#pragma unroll
+    for (int a = 0; a < R1; ++a) t[a] = v[R2 * a + b];
+    dft_reg<R, R1, INV>(t);
+#pragma unroll
+    for (int k1 = 0; k1 < R1; ++k1) {
+      cplx<R> y = t[k1];
+      if (b > 0 && k1 > 0) {
+        const R c = (R)T.c[(b * k1) % M];
+        const R sg = INV ? (R)T.s[(b * k1) % M] : -(R)T.s[(b * k1) % M];
+        y = {y.x * c - y.y * sg, fma(y.x, sg, y.y * c)};
+      }
+      v[R2 * k1 + b] = y;
+    }
+  }
+  cplx<R> o[M];
+#pragma unroll
+  for (int k1 = 0; k1 < R1; ++k1) {
+    cplx<R> t[R2];
+#pragma unroll
+    for (int b = 0; b < R2; ++b) t[b] = v[R2 * k1 + b];
+    dft_reg<R, R2, INV>(t);
+#pragma unroll
+    for (int k2 = 0; k2 < R2; ++k2) o[k1 + R1 * k2] = t[k2];
+  }
+#pragma unroll
+  for (int k = 0; k < M; ++k) v[k] = o[k];
+}
+
+// M-point DFT in registers for any odd M: the symmetric form for a prime,
+// otherwise split off the smallest prime factor.
+template <typename R, int M, bool INV>
+RVE_DEV void dft_reg(cplx<R> (&v)[M]) {
+  if constexpr (M == 1) {
+    return;
+  } else if constexpr (smallest_factor(M) == M) {
+    dft_const<R, M, INV>(v);
+  } else {
+    dft_split<R, smallest_factor(M), M / smallest_factor(M), INV>(v);
+  }
+}
+
+// A Stockham stage of composite radix R1 R2 (the same data movement as
+// stage_pp with RAD = R1 R2; the butterfly is dft_split): two stages for
+// the price of one pass through shared memory.
+template <typename R, int R1, int R2, bool INV>
+RVE_DEV void stage_pp2(const cplx<R>* __restrict__ src, cplx<R>* __restrict__ dst,
+                       const LineMap lm, int L, const FastDiv fL, int N, int Ns,
+                       const FastDiv fNs, const FastDiv fnb, const cplx<R>* tw) {
+  constexpr int RAD = R1 * R2;
+  const int nb = N / RAD;
+  const int tws = N / (Ns * RAD);
+  const int total = L * nb;
+  for (int b = threadIdx.x; b < total; b += blockDim.x) {
+    int l, j;
+    if (lm.lf) {
+      j = (int)fL.div((unsigned)b);
+      l = b - j * L;
+    } else {
+      l = (int)fnb.div((unsigned)b);
+      j = b - l * nb;
+    }
+    const int jq = (int)fNs.div((unsigned)j);
+    const int jr = j - jq * Ns;
+    const int base = lm.base(l);
+    cplx<R> v[RAD];
+#pragma unroll
+    for (int r = 0; r < RAD; ++r) v[r] = src[base + (j + r * nb) * lm.es];
+    if (jr != 0) {
+      const int step = jr * tws;
+#pragma unroll
+      for (int r = 1; r < RAD; ++r) {
+        const cplx<R> w = tw[r * step];
+        v[r] = INV ? c_mulc(v[r], w) : c_mul(v[r], w);
+      }
+    }
+    dft_split<R, R1, R2, INV>(v);
+    const int d = jq * Ns * RAD + jr;
+#pragma unroll
+    for (int r = 0; r < RAD; ++r) dst[base + (d + r * Ns) * lm.es] = v[r];
+  }
+  __syncthreads();
+}
+
 // Direct R-point DFT for any prime R: one output element per thread.
 template <typename R, bool INV>
 RVE_DEV void stage_pp_generic(const cplx<R>* __restrict__ src, cplx<R>* __restrict__ dst,
@@ -198,6 +380,10 @@ RVE_DEV cplx<R>* fft_lines(cplx<R>* a, cplx<R>* b, const LineMap& lm, int L, con
       case 5: stage_pp<R, 5, INV>(a, b, lm, L, fL, p.n, Ns, fNs, fnb, tw); break;
       case 7: stage_pp<R, 7, INV>(a, b, lm, L, fL, p.n, Ns, fNs, fnb, tw); break;
       case 11: stage_pp<R, 11, INV>(a, b, lm, L, fL, p.n, Ns, fNs, fnb, tw); break;
+      case 9: stage_pp2<R, 3, 3, INV>(a, b, lm, L, fL, p.n, Ns, fNs, fnb, tw); break;
+      case 15: stage_pp2<R, 5, 3, INV>(a, b, lm, L, fL, p.n, Ns, fNs, fnb, tw); break;
+      case 21: stage_pp2<R, 7, 3, INV>(a, b, lm, L, fL, p.n, Ns, fNs, fnb, tw); break;
+      case 25: stage_pp2<R, 5, 5, INV>(a, b, lm, L, fL, p.n, Ns, fNs, fnb, tw); break;
       default: stage_pp_generic<R, INV>(a, b, lm, L, fL, p.n, Ns, rad, fNs, fnb, p.fN, tw); break;
     }
     cplx<R>* t = a;
@@ -215,4 +401,81 @@ __device__ __noinline__ cplx<R>* fft_lines_call(cplx<R>* a, cplx<R>* b, const Li
                                                 const FastDiv fL, const AxisPlan* p,
                                                 const cplx<R>* tw) {
   return fft_lines<R, INV>(a, b, lm, L, fL, *p, tw);
+}
+
+// ---------------------------------------------------------------------------
+// In-place DFTs of compile-time length N = N1 N2 on L lines in one shared
+// buffer (line l, element e at lm.base(l) + e lm.es; consecutive threads take
+// consecutive lines).  Four-step split with n = N2 m + n2, k = k1 + N1 k2:
+//   phase A (per line and n2):  Y_n2(k1) = w_N^(n2 k1) sum_m w_N1^(m k1) x_(N2 m + n2)
+//   phase B (per line and k1):  X_(k1 + N1 k2) = sum_n2 w_N2^(n2 k2) Y_n2(k1)
+// Each work item reads and writes the same N1 (phase A) or N2 (phase B)
+// positions, so no second buffer is needed; the forward result is stored
+// transposed: X_(k1 + N1 k2) at position N2 k1 + k2 (fs_freq / fs_pos).  The
+// inverse runs the conjugate phases in reverse order and takes that
+// transposed order back to natural order.  tw[k] = exp(-2 pi i k / N).
+// ---------------------------------------------------------------------------
+template <int N1, int N2>
+RVE_DEV int fs_freq(int pos) { return pos / N2 + N1 * (pos % N2); }
+template <int N1, int N2>
+RVE_DEV int fs_pos(int k) { return N2 * (k % N1) + k / N1; }
+
+template <typename R, int N1, int N2, bool INV>
+RVE_DEV void fs_phase_a(cplx<R>* buf, const LineMap& lm, int L, const FastDiv fL,
+                        const cplx<R>* tw) {
+  const int total = L * N2;
+  for (int i = threadIdx.x; i < total; i += blockDim.x) {
+    const int n2 = (int)fL.div((unsigned)i);
+    const int l = i - n2 * L;
+    cplx<R>* line = buf + lm.base(l) + n2 * lm.es;
+    const int st = N2 * lm.es;
+    cplx<R> v[N1];
+#pragma unroll
+    for (int m = 0; m < N1; ++m) v[m] = line[m * st];
+    if (INV && n2 != 0) {
+#pragma unroll
+      for (int k1 = 1; k1 < N1; ++k1) v[k1] = c_mulc(v[k1], tw[n2 * k1]);
+    }
+    dft_reg<R, N1, INV>(v);
+    if (!INV && n2 != 0) {
+#pragma unroll
+      for (int k1 = 1; k1 < N1; ++k1) v[k1] = c_mul(v[k1], tw[n2 * k1]);
+    }
+#pragma unroll
+    for (int m = 0; m < N1; ++m) line[m * st] = v[m];
+  }
+}
+
+template <typename R, int N1, int N2, bool INV>
+RVE_DEV void fs_phase_b(cplx<R>* buf, const LineMap& lm, int L, const FastDiv fL) {
+  const int total = L * N1;
+  for (int i = threadIdx.x; i < total; i += blockDim.x) {
+    const int k1 = (int)fL.div((unsigned)i);
+    const int l = i - k1 * L;
+    cplx<R>* line = buf + lm.base(l) + N2 * k1 * lm.es;
+    cplx<R> u[N2];
+#pragma unroll
+    for (int j = 0; j < N2; ++j) u[j] = line[j * lm.es];
+    dft_reg<R, N2, INV>(u);
+#pragma unroll
+    for (int j = 0; j < N2; ++j) line[j * lm.es] = u[j];
+  }
+}
+
+// Forward: natural order in, transposed order out.  Inverse: transposed in,
+// natural out.  Caller synchronises before; returns after a barrier.
+template <typename R, int N1, int N2, bool INV>
+RVE_DEV void fs_lines(cplx<R>* buf, const LineMap& lm, int L, const FastDiv fL,
+                      const cplx<R>* tw) {
+  if (!INV) {
+    fs_phase_a<R, N1, N2, false>(buf, lm, L, fL, tw);
+    __syncthreads();
+    if (N2 > 1) fs_phase_b<R, N1, N2, false>(buf, lm, L, fL);
+    __syncthreads();
+  } else {
+    if (N2 > 1) fs_phase_b<R, N1, N2, true>(buf, lm, L, fL);
+    __syncthreads();
+    fs_phase_a<R, N1, N2, true>(buf, lm, L, fL, tw);
+    __syncthreads();
+  }
 }

@@ -29,7 +29,36 @@ struct GridGeom {
   // host-computed divisors used in index arithmetic
   FastDiv f_hz, f_lzf, f_lzd, f_ny, f_ntky_f, f_ntky_d, f_ntkx_f, f_ntkx_d;
   FastDiv f_Ly_f, f_Ly_d, f_Lx_f, f_Lx_d;  // lines per y / x tile
+  // float y and x passes on the in-place four-step kernels (fs_n1 != 0:
+  // the axis length has a compiled N1 x N2 split, see RVE_FS_SIZES)
+  int fsy_n1, fsx_n1;
+  int fsy_t, fsy_grp, fsx_t;
+  FastDiv f_fsy_ntk, f_fsx_ntk, f_fsy_L, f_fsx_L;
 };
+
+// Axis lengths with compiled four-step kernels: X(N, N1, N2), N = N1 N2.
+#define RVE_FS_SIZES(X) \
+  X(15, 5, 3)           \
+  X(21, 7, 3)           \
+  X(27, 9, 3)           \
+  X(33, 11, 3)          \
+  X(45, 9, 5)           \
+  X(63, 9, 7)           \
+  X(125, 5, 25)         \
+  X(243, 9, 27)         \
+  X(315, 21, 15)
+
+inline int fs_split_n1(int n) {
+  switch (n) {
+#define RVE_FS_CASE(N, A, B) \
+  case N:                    \
+    return A;
+    RVE_FS_SIZES(RVE_FS_CASE)
+#undef RVE_FS_CASE
+    default:
+      return 0;
+  }
+}
 
 template <typename R>
 struct TangentView {
@@ -63,6 +92,13 @@ template <typename R, typename RC>
 void launch_zinv(const GridGeom& g, int out, const cplx<R>* spec, R* dst, RC* r_out, RC* x_out,
                  const RC* p_in, SolverState* st, double* partials, const int* done,
                  const Twiddles<R>& tw, cudaStream_t s);
+
+// four-step float kernels (kernels_fft4.cu); used when g.fsy_n1 / g.fsx_n1
+void launch_fft_y4(const GridGeom& g, bool inverse, cplx<float>* spec, const int* done,
+                   const cplx<float>* tw, cudaStream_t s);
+void launch_fft_x4(const GridGeom& g, double scale, cplx<float>* spec, const int* done,
+                   const cplx<float>* tw, cudaStream_t s);
+cudaError_t fft4_kernels_init();
 
 cudaError_t fft_kernels_init();  // opt-in to large dynamic shared memory
 size_t fft_max_blocks(const GridGeom& g);

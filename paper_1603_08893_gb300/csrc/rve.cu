@@ -14,7 +14,6 @@
 
 namespace {
 
-const double kPi = 3.14159265358979323846264338327950288;
 const double kDivergedUpdate = 0.5;  // ||dF||/||F|| above this ends Newton as diverged
 // float32 CG stops after this many iterations without a 10% drop of ||r||
 // (its accuracy limit on high-contrast cells); float64 CG never does
@@ -43,7 +42,9 @@ bool factor_plan(int n, AxisPlan* p) {
   p->n = n;
   p->nst = 0;
   int m = n;
-  const int fixed[] = {11, 7, 5, 3};
+  // pairs of small primes become one composite stage (two radix passes for
+  // one trip through shared memory); then single radices
+  const int fixed[] = {25, 21, 15, 9, 11, 7, 5, 3};
   for (int f : fixed)
     while (m % f == 0) {
       if (p->nst >= RVE_MAX_STAGES) return false;
@@ -70,8 +71,9 @@ bool factor_plan(int n, AxisPlan* p) {
     const int r = p->rad[s];
     const int nb = n / r;
     if (r == 3 && nb > 512) return false;
-    if ((r == 5 || r == 7 || r == 11) && nb > 256) return false;
-    if (r > 11 && n > 512) return false;
+    if ((r == 5 || r == 7 || r == 11 || r == 9 || r == 15 || r == 21 || r == 25) && nb > 256)
+      return false;
+    if (r > 11 && r != 15 && r != 21 && r != 25 && n > 512) return false;
   }
   return true;
 }
@@ -123,6 +125,18 @@ bool make_geom(int nx, int ny, int nz, GridGeom* g) {
   g->f_Lx_d = make_fastdiv((unsigned)(3 * g->tx_d));
   if (8 * ((size_t)nx + 1 + 6 * (size_t)nx * g->tx_f) > 200 * 1024) return false;
   if (16 * ((size_t)nx + 1 + 6 * (size_t)nx * g->tx_d) > 200 * 1024) return false;
+  // four-step float y / x passes: 128-byte tile rows (16 kz values) where
+  // the tile fits 48-64 KB, about 48 lines per CTA
+  g->fsy_n1 = fs_split_n1(ny);
+  g->fsx_n1 = fs_split_n1(nx);
+  g->fsy_t = 16;
+  g->fsy_grp = std::max(1, std::min(9 * nx, (int)(49152 / (8 * (size_t)ny * g->fsy_t))));
+  g->fsx_t = 8 * 3 * (size_t)nx * 16 <= 65536 ? 16 : (8 * 3 * (size_t)nx * 8 <= 65536 ? 8 : 4);
+  if (8 * ((size_t)nx + 1 + 3 * (size_t)nx * g->fsx_t) > 200 * 1024) g->fsx_n1 = 0;
+  g->f_fsy_ntk = make_fastdiv((unsigned)((g->hz + g->fsy_t - 1) / g->fsy_t));
+  g->f_fsx_ntk = make_fastdiv((unsigned)((g->hz + g->fsx_t - 1) / g->fsx_t));
+  g->f_fsy_L = make_fastdiv((unsigned)(g->fsy_grp * g->fsy_t));
+  g->f_fsx_L = make_fastdiv((unsigned)(3 * g->fsx_t));
   return true;
 }
 

@@ -25,7 +25,8 @@ from paper_1603_08893_gb300 import RVE, RVEError  # noqa: E402
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
 SHAPES = [(1, 1, 1), (3, 5, 7), (5, 1, 3), (9, 11, 13), (15, 15, 15),
-          (21, 27, 33), (31, 31, 31), (45, 45, 45), (63, 63, 63), (27, 3, 125)]
+          (21, 27, 33), (31, 31, 31), (45, 45, 45), (63, 63, 63), (27, 3, 125),
+          (81, 75, 7), (105, 9, 5), (7, 5, 225)]
 
 
 def rel(a, b):
@@ -81,7 +82,8 @@ def test_operator_fp64_matches_oracle(shape, tangent):
     r.close()
 
 
-@pytest.mark.parametrize("shape", [(9, 11, 13), (31, 31, 31), (63, 63, 63), (27, 3, 125)])
+@pytest.mark.parametrize("shape", [(9, 11, 13), (31, 31, 31), (63, 63, 63), (27, 3, 125),
+                                   (81, 75, 7), (7, 5, 225)])
 @pytest.mark.parametrize("tangent", ["recompute", "full81"])
 def test_operator_mixed_matches_oracle(shape, tangent):
     r, F, K, mu, rng = _random_problem(shape, 4, "mixed", tangent)
