@@ -53,3 +53,224 @@ RVE_DEV void issue_tile(cplx<R>* sbuf, const cplx<R>* gbase, size_t rstride, int
   }
 }
 
+
+// --------------------------------------------------------------------------
+// Input stage: tangent contraction of one voxel.
+//   FULL81: out_(3a+b) = (K : in)_ab = sum_kl K_(b a k l) in_(3k+l)
+//           (delta P_ji = K_ijkl delta F_kl, Eq. iter:varP)
+//   SVK   : linearisation of P = F.S with S = lambda tr(E) I + 2 mu E:
+//           dP = dF.S + F.(lambda tr(dE) I + 2 mu dE), dE = sym(F^T dF)
+// --------------------------------------------------------------------------
+template <typename R>
+RVE_DEV void tangent_voxel(const TangentView<R>& T, size_t v, size_t n, const R (&in)[9],
+                           R (&out)[9]) {
+  if (T.mode == TAN_FULL81) {
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        R s = 0;
+#pragma unroll
+        for (int kl = 0; kl < 9; ++kl) s = fma(__ldg(T.K4 + (size_t)((b * 3 + a) * 9 + kl) * n + v), in[kl], s);
+        out[3 * a + b] = s;
+      }
+  } else if (T.mode == TAN_SVK) {
+    R F[9];
+#pragma unroll
+    for (int c = 0; c < 9; ++c) F[c] = __ldg(T.Fop + (size_t)c * n + v);
+    const R lam = T.mat.get(v, 0), mu = T.mat.get(v, 1);
+    R S[3][3];
+    if (T.Sop) {
+      const R s0 = __ldg(T.Sop + v), s1 = __ldg(T.Sop + n + v), s2 = __ldg(T.Sop + 2 * n + v);
+      const R s3 = __ldg(T.Sop + 3 * n + v), s4 = __ldg(T.Sop + 4 * n + v), s5 = __ldg(T.Sop + 5 * n + v);
+      S[0][0] = s0; S[1][1] = s1; S[2][2] = s2;
+      S[0][1] = S[1][0] = s3; S[0][2] = S[2][0] = s4; S[1][2] = S[2][1] = s5;
+    } else {
+      R E[3][3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+          R c = F[a] * F[b] + F[3 + a] * F[3 + b] + F[6 + a] * F[6 + b];
+          E[a][b] = R(0.5) * (c - (a == b ? R(1) : R(0)));
+        }
+      const R tr = E[0][0] + E[1][1] + E[2][2];
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) S[a][b] = 2 * mu * E[a][b] + (a == b ? lam * tr : R(0));
+    }
+    // dE = sym(F^T in)
+    R dE[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        const R fa = F[a] * in[b] + F[3 + a] * in[3 + b] + F[6 + a] * in[6 + b];
+        const R fb = F[b] * in[a] + F[3 + b] * in[3 + a] + F[6 + b] * in[6 + a];
+        dE[a][b] = R(0.5) * (fa + fb);
+      }
+    const R trd = dE[0][0] + dE[1][1] + dE[2][2];
+    R dS[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) dS[a][b] = 2 * mu * dE[a][b] + (a == b ? lam * trd : R(0));
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        R s = 0;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) s += in[3 * a + c] * S[c][b] + F[3 * a + c] * dS[c][b];
+        out[3 * a + b] = s;
+      }
+  } else {
+#pragma unroll
+    for (int c = 0; c < 9; ++c) out[c] = in[c];
+  }
+}
+
+template <typename R>
+struct ZfwdParams {
+  GridGeom g;
+  int lz;
+  int src;
+  TangentView<R> tan;
+  const R* field;
+  const R* r;
+  R* p;
+  const double* unif;
+  SolverState* st;
+  const int* done;
+  cplx<R>* spec;
+  const cplx<R>* tw;
+  R* x;               // SRC_CGPX
+  double* partials;   // SRC_CGPX
+};
+
+
+// CG scalars every voxel of the first pass needs, read once per CTA before
+// any block can overwrite them (the step length is written by the last
+// block of the same kernel).
+template <typename R>
+struct ZfwdScalars {
+  bool first;
+  R beta, alpha_prev;
+};
+
+template <typename R, int SRC>
+RVE_DEV ZfwdScalars<R> zfwd_scalars(const ZfwdParams<R>& P) {
+  ZfwdScalars<R> s{true, R(0), R(0)};
+  if (SRC == SRC_CGP || SRC == SRC_CGPX) {
+    s.first = (P.st->it == 0);
+    s.beta = (R)P.st->beta;
+    s.alpha_prev = (R)P.st->alpha;
+  }
+  return s;
+}
+
+// Input stage of the first pass for voxel v: the field itself, the CG
+// direction p = r + beta p (SRC_CGPX also applies the previous step
+// x += alpha p and accumulates p.(K:p)), or a uniform tensor; then the
+// tangent.  Every global load of the voxel is issued before its stores.
+template <typename R, int SRC, int TAN>
+RVE_DEV void zfwd_voxel(const ZfwdParams<R>& P, const ZfwdScalars<R>& sc, size_t v, R (&out)[9],
+                        double& pkp) {
+  const size_t n = P.g.n;
+  R in[9];
+  if (SRC == SRC_FIELD) {
+#pragma unroll
+    for (int c = 0; c < 9; ++c) in[c] = P.field[(size_t)c * n + v];
+  } else if (SRC == SRC_CGP) {
+    R rr[9], pp[9];
+#pragma unroll
+    for (int c = 0; c < 9; ++c) rr[c] = P.r[(size_t)c * n + v];
+    if (!sc.first) {
+#pragma unroll
+      for (int c = 0; c < 9; ++c) pp[c] = P.p[(size_t)c * n + v];
+    }
+#pragma unroll
+    for (int c = 0; c < 9; ++c) in[c] = sc.first ? rr[c] : fma(sc.beta, pp[c], rr[c]);
+  } else if (SRC == SRC_CGPX) {
+    R rr[9], pp[9], xx[9];
+#pragma unroll
+    for (int c = 0; c < 9; ++c) rr[c] = P.r[(size_t)c * n + v];
+    if (!sc.first) {
+#pragma unroll
+      for (int c = 0; c < 9; ++c) {
+        pp[c] = P.p[(size_t)c * n + v];
+        xx[c] = P.x[(size_t)c * n + v];
+      }
+#pragma unroll
+      for (int c = 0; c < 9; ++c) P.x[(size_t)c * n + v] = fma(sc.alpha_prev, pp[c], xx[c]);
+    }
+#pragma unroll
+    for (int c = 0; c < 9; ++c) in[c] = sc.first ? rr[c] : fma(sc.beta, pp[c], rr[c]);
+  } else {
+#pragma unroll
+    for (int c = 0; c < 9; ++c) in[c] = (R)P.unif[c];
+  }
+  TangentView<R> T = P.tan;
+  T.mode = TAN;
+  tangent_voxel<R>(T, v, n, in, out);
+  if (SRC == SRC_CGP || SRC == SRC_CGPX) {
+#pragma unroll
+    for (int c = 0; c < 9; ++c) P.p[(size_t)c * n + v] = in[c];
+  }
+  if (SRC == SRC_CGPX) {
+    R sp = 0;
+#pragma unroll
+    for (int c = 0; c < 9; ++c) sp = fma(in[c], out[c], sp);
+    pkp += (double)sp;
+  }
+}
+
+// Step length of the fused CG iteration from sum p.(K:p):
+// p.Ap = p.G(K p) = (G p).(K p) = p.(K p) for compatible p (G is an
+// orthogonal projector), so alpha is known before the inverse transforms.
+template <typename R>
+RVE_DEV void zfwd_step_length(const ZfwdParams<R>& P, double pkp) {
+  double v1[1] = {pkp}, tot[1];
+  if (last_block_sum<1>(v1, P.partials, &P.st->counter[SLOT_PAP], tot) && threadIdx.x == 0) {
+    SolverState* st = P.st;
+    const double pap = tot[0];
+    st->pAp = pap;
+    if (!isfinite(pap)) {
+      st->status = RVE_DEV_ERR_NONFINITE;
+      st->alpha = 0.0;
+      st->done = 1;
+    } else if (pap == 0.0) {
+      st->status = RVE_DEV_ERR_CG_BREAKDOWN;
+      st->alpha = 0.0;
+      st->done = 1;
+    } else {
+      st->alpha = st->rr / pap;
+    }
+  }
+}
+
+template <typename R, typename RC>
+struct ZinvParams {
+  GridGeom g;
+  int lz;
+  const cplx<R>* spec;
+  R* dst;
+  RC* r_out;
+  RC* x_out;
+  const RC* p_in;
+  SolverState* st;
+  double* partials;
+  const int* done;
+  const cplx<R>* tw;
+};
+
+// Four-step float z passes of the fused CG iteration (kernels_fft4.cu),
+// used when the z length has a compiled split (g.fsz_n1 != 0).
+void launch_zfwd4(const ZfwdParams<float>& P, cudaStream_t s);
+void launch_zinv4(const ZinvParams<float, float>& P, cudaStream_t s);
+
+RVE_DEV void cp_async4(void* sdst, const void* gsrc) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(sdst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gsrc));
+}

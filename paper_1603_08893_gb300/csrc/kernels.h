@@ -31,9 +31,9 @@ struct GridGeom {
   FastDiv f_Ly_f, f_Ly_d, f_Lx_f, f_Lx_d;  // lines per y / x tile
   // float y and x passes on the in-place four-step kernels (fs_n1 != 0:
   // the axis length has a compiled N1 x N2 split, see RVE_FS_SIZES)
-  int fsy_n1, fsx_n1;
-  int fsy_t, fsy_grp, fsx_t;
-  FastDiv f_fsy_ntk, f_fsx_ntk, f_fsy_L, f_fsx_L;
+  int fsy_n1, fsx_n1, fsz_n1;
+  int fsy_t, fsy_grp, fsx_t, fsz_lz;
+  FastDiv f_fsy_ntk, f_fsx_ntk, f_fsy_L, f_fsx_L, f_fsz_L, f_fsz_lz;
 };
 
 // Axis lengths with compiled four-step kernels: X(N, N1, N2), N = N1 N2.

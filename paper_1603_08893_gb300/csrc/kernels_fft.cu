@@ -19,101 +19,6 @@
 
 #include "fft_pass.cuh"
 
-// --------------------------------------------------------------------------
-// Input stage: tangent contraction of one voxel.
-//   FULL81: out_(3a+b) = (K : in)_ab = sum_kl K_(b a k l) in_(3k+l)
-//           (delta P_ji = K_ijkl delta F_kl, Eq. iter:varP)
-//   SVK   : linearisation of P = F.S with S = lambda tr(E) I + 2 mu E:
-//           dP = dF.S + F.(lambda tr(dE) I + 2 mu dE), dE = sym(F^T dF)
-// --------------------------------------------------------------------------
-template <typename R>
-RVE_DEV void tangent_voxel(const TangentView<R>& T, size_t v, size_t n, const R (&in)[9],
-                           R (&out)[9]) {
-  if (T.mode == TAN_FULL81) {
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
-#pragma unroll
-      for (int b = 0; b < 3; ++b) {
-        R s = 0;
-#pragma unroll
-        for (int kl = 0; kl < 9; ++kl) s = fma(__ldg(T.K4 + (size_t)((b * 3 + a) * 9 + kl) * n + v), in[kl], s);
-        out[3 * a + b] = s;
-      }
-  } else if (T.mode == TAN_SVK) {
-    R F[9];
-#pragma unroll
-    for (int c = 0; c < 9; ++c) F[c] = __ldg(T.Fop + (size_t)c * n + v);
-    const R lam = T.mat.get(v, 0), mu = T.mat.get(v, 1);
-    R S[3][3];
-    if (T.Sop) {
-      const R s0 = __ldg(T.Sop + v), s1 = __ldg(T.Sop + n + v), s2 = __ldg(T.Sop + 2 * n + v);
-      const R s3 = __ldg(T.Sop + 3 * n + v), s4 = __ldg(T.Sop + 4 * n + v), s5 = __ldg(T.Sop + 5 * n + v);
-      S[0][0] = s0; S[1][1] = s1; S[2][2] = s2;
-      S[0][1] = S[1][0] = s3; S[0][2] = S[2][0] = s4; S[1][2] = S[2][1] = s5;
-    } else {
-      R E[3][3];
-#pragma unroll
-      for (int a = 0; a < 3; ++a)
-#pragma unroll
-        for (int b = 0; b < 3; ++b) {
-          R c = F[a] * F[b] + F[3 + a] * F[3 + b] + F[6 + a] * F[6 + b];
-          E[a][b] = R(0.5) * (c - (a == b ? R(1) : R(0)));
-        }
-      const R tr = E[0][0] + E[1][1] + E[2][2];
-#pragma unroll
-      for (int a = 0; a < 3; ++a)
-#pragma unroll
-        for (int b = 0; b < 3; ++b) S[a][b] = 2 * mu * E[a][b] + (a == b ? lam * tr : R(0));
-    }
-    // dE = sym(F^T in)
-    R dE[3][3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
-#pragma unroll
-      for (int b = 0; b < 3; ++b) {
-        const R fa = F[a] * in[b] + F[3 + a] * in[3 + b] + F[6 + a] * in[6 + b];
-        const R fb = F[b] * in[a] + F[3 + b] * in[3 + a] + F[6 + b] * in[6 + a];
-        dE[a][b] = R(0.5) * (fa + fb);
-      }
-    const R trd = dE[0][0] + dE[1][1] + dE[2][2];
-    R dS[3][3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
-#pragma unroll
-      for (int b = 0; b < 3; ++b) dS[a][b] = 2 * mu * dE[a][b] + (a == b ? lam * trd : R(0));
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
-#pragma unroll
-      for (int b = 0; b < 3; ++b) {
-        R s = 0;
-#pragma unroll
-        for (int c = 0; c < 3; ++c) s += in[3 * a + c] * S[c][b] + F[3 * a + c] * dS[c][b];
-        out[3 * a + b] = s;
-      }
-  } else {
-#pragma unroll
-    for (int c = 0; c < 9; ++c) out[c] = in[c];
-  }
-}
-
-template <typename R>
-struct ZfwdParams {
-  GridGeom g;
-  int lz;
-  int src;
-  TangentView<R> tan;
-  const R* field;
-  const R* r;
-  R* p;
-  const double* unif;
-  SolverState* st;
-  const int* done;
-  cplx<R>* spec;
-  const cplx<R>* tw;
-  R* x;               // SRC_CGPX
-  double* partials;   // SRC_CGPX
-};
-
 template <typename R, int SRC, int TAN>
 __global__ void FFT_BOUNDS(R) k_zfwd(const ZfwdParams<R> P) {
   if (P.done && *P.done) return;
@@ -125,70 +30,17 @@ __global__ void FFT_BOUNDS(R) k_zfwd(const ZfwdParams<R> P) {
   for (int i = threadIdx.x; i < nz; i += blockDim.x) tw[i] = P.tw[i];
   __shared__ AxisPlan plan;
   load_plan(&plan, P.g.pz);
-  const size_t n = P.g.n;
   const int nlines = P.g.nx * P.g.ny;
   const int l0 = blockIdx.x * lz;
   const int nl = min(lz, nlines - l0);
   const int nvox = nl * nz;
   const size_t v0 = (size_t)l0 * nz;
-  R beta = 0, alpha_prev = 0;
-  bool first = true;
-  if (SRC == SRC_CGP || SRC == SRC_CGPX) {
-    first = (P.st->it == 0);
-    beta = (R)P.st->beta;
-    alpha_prev = (R)P.st->alpha;
-  }
+  const ZfwdScalars<R> sc = zfwd_scalars<R, SRC>(P);
   double pkp = 0.0;
-  TangentView<R> T = P.tan;
-  T.mode = TAN;
-  // every global load of a voxel is issued before its stores
   for (int i = threadIdx.x; i < lz * nz; i += blockDim.x) {
-    R in[9], out[9];
+    R out[9];
     if (i < nvox) {
-      const size_t v = v0 + i;
-      if (SRC == SRC_FIELD) {
-#pragma unroll
-        for (int c = 0; c < 9; ++c) in[c] = P.field[(size_t)c * n + v];
-      } else if (SRC == SRC_CGP) {
-        R rr[9], pp[9];
-#pragma unroll
-        for (int c = 0; c < 9; ++c) rr[c] = P.r[(size_t)c * n + v];
-        if (!first) {
-#pragma unroll
-          for (int c = 0; c < 9; ++c) pp[c] = P.p[(size_t)c * n + v];
-        }
-#pragma unroll
-        for (int c = 0; c < 9; ++c) in[c] = first ? rr[c] : fma(beta, pp[c], rr[c]);
-      } else if (SRC == SRC_CGPX) {
-        R rr[9], pp[9], xx[9];
-#pragma unroll
-        for (int c = 0; c < 9; ++c) rr[c] = P.r[(size_t)c * n + v];
-        if (!first) {
-#pragma unroll
-          for (int c = 0; c < 9; ++c) {
-            pp[c] = P.p[(size_t)c * n + v];
-            xx[c] = P.x[(size_t)c * n + v];
-          }
-#pragma unroll
-          for (int c = 0; c < 9; ++c) P.x[(size_t)c * n + v] = fma(alpha_prev, pp[c], xx[c]);
-        }
-#pragma unroll
-        for (int c = 0; c < 9; ++c) in[c] = first ? rr[c] : fma(beta, pp[c], rr[c]);
-      } else {
-#pragma unroll
-        for (int c = 0; c < 9; ++c) in[c] = (R)P.unif[c];
-      }
-      tangent_voxel<R>(T, v, n, in, out);
-      if (SRC == SRC_CGP || SRC == SRC_CGPX) {
-#pragma unroll
-        for (int c = 0; c < 9; ++c) P.p[(size_t)c * n + v] = in[c];
-      }
-      if (SRC == SRC_CGPX) {
-        R sp = 0;
-#pragma unroll
-        for (int c = 0; c < 9; ++c) sp = fma(in[c], out[c], sp);
-        pkp += (double)sp;
-      }
+      zfwd_voxel<R, SRC, TAN>(P, sc, v0 + i, out, pkp);
     } else {
 #pragma unroll
       for (int c = 0; c < 9; ++c) out[c] = 0;
@@ -220,28 +72,7 @@ __global__ void FFT_BOUNDS(R) k_zfwd(const ZfwdParams<R> P) {
       P.spec[(size_t)(2 * k + 1) * ss + o] = {dy, -dx};
     }
   }
-  if (SRC == SRC_CGPX) {
-    // p.Ap = p.G(K p) = (G p).(K p) = p.(K p) for compatible p (G is an
-    // orthogonal projector), so the step length is known before the inverse
-    // transforms
-    double v1[1] = {pkp}, tot[1];
-    if (last_block_sum<1>(v1, P.partials, &P.st->counter[SLOT_PAP], tot) && threadIdx.x == 0) {
-      SolverState* st = P.st;
-      const double pap = tot[0];
-      st->pAp = pap;
-      if (!isfinite(pap)) {
-        st->status = RVE_DEV_ERR_NONFINITE;
-        st->alpha = 0.0;
-        st->done = 1;
-      } else if (pap == 0.0) {
-        st->status = RVE_DEV_ERR_CG_BREAKDOWN;
-        st->alpha = 0.0;
-        st->done = 1;
-      } else {
-        st->alpha = st->rr / pap;
-      }
-    }
-  }
+  if (SRC == SRC_CGPX) zfwd_step_length<R>(P, pkp);
 }
 
 // Complex DFT along y (forward or inverse) on tiles of (grp component-x
@@ -345,21 +176,6 @@ __global__ void FFT_BOUNDS(R) k_fft_x_proj(const LineParams<R> P) {
     if (t < tc) gbase[(size_t)(i >> ts) * rs + t] = res[i];
   }
 }
-
-template <typename R, typename RC>
-struct ZinvParams {
-  GridGeom g;
-  int lz;
-  const cplx<R>* spec;
-  R* dst;
-  RC* r_out;
-  RC* x_out;
-  const RC* p_in;
-  SolverState* st;
-  double* partials;
-  const int* done;
-  const cplx<R>* tw;
-};
 
 template <typename R, typename RC, int OUT>
 __global__ void FFT_BOUNDS(R) k_zinv(const ZinvParams<R, RC> P) {
@@ -530,6 +346,10 @@ void launch_zfwd(const GridGeom& g, int src, const TangentView<R>& tan, const R*
   P.tw = tw.z;
   P.x = x;
   P.partials = partials;
+  if (sizeof(R) == 4 && g.fsz_n1 && src == SRC_CGPX) {
+    launch_zfwd4(reinterpret_cast<const ZfwdParams<float>&>(P), s);
+    return;
+  }
   const int nlines = g.nx * g.ny;
   const dim3 grid((nlines + P.lz - 1) / P.lz);
   const size_t sm = sizeof(cplx<R>) * ((size_t)((g.nz + 1) & ~1) + 10 * (size_t)P.lz * g.nz);
@@ -611,6 +431,10 @@ void launch_zinv(const GridGeom& g, int out, const cplx<R>* spec, R* dst, RC* r_
   P.partials = partials;
   P.done = done;
   P.tw = tw.z;
+  if (sizeof(R) == 4 && sizeof(RC) == 4 && g.fsz_n1 && out == OUT_CGR) {
+    launch_zinv4(reinterpret_cast<const ZinvParams<float, float>&>(P), s);
+    return;
+  }
   const int nlines = g.nx * g.ny;
   const dim3 grid((nlines + P.lz - 1) / P.lz);
   const size_t sm = sizeof(cplx<R>) * ((size_t)((g.nz + 1) & ~1) + 10 * (size_t)P.lz * g.nz);
@@ -622,7 +446,8 @@ void launch_zinv(const GridGeom& g, int out, const cplx<R>* spec, R* dst, RC* r_
 
 size_t fft_max_blocks(const GridGeom& g) {
   const size_t nlines = (size_t)g.nx * g.ny;
-  const int lz = g.lz_f < g.lz_d ? g.lz_f : g.lz_d;
+  int lz = g.lz_f < g.lz_d ? g.lz_f : g.lz_d;
+  if (g.fsz_n1 && g.fsz_lz < lz) lz = g.fsz_lz;
   return (nlines + lz - 1) / lz;
 }
 

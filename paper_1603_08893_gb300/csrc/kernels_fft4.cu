@@ -125,6 +125,158 @@ __global__ void __launch_bounds__(FFT_THREADS, (Fs4Occ<R, N1, N2>::value))
   }
 }
 
+// First pass of the fused float CG iteration on the four-step z DFT:
+// voxel stage (p, lagged x, tangent, p.(K:p)) into a transposed buffer
+// (element z of line l at z * LP + l, LP odd), in-place DFT of the 5 lz
+// packed lines, half spectrum out.
+template <typename R, int SRC, int TAN, int N1, int N2>
+__global__ void __launch_bounds__(FFT_THREADS, (Fs4Occ<R, N1, N2>::value))
+    k_zfwd4(const ZfwdParams<R> P) {
+  constexpr int N = N1 * N2;
+  if (P.done && *P.done) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int lz = P.lz;
+  const int LP = (5 * lz) | 1;
+  cplx<R>* tw = reinterpret_cast<cplx<R>*>(smem_raw);
+  cplx<R>* buf = tw + ((N + 1) & ~1);
+  for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = P.tw[i];
+  const int nlines = P.g.nx * P.g.ny;
+  const int l0 = blockIdx.x * lz;
+  const int nl = min(lz, nlines - l0);
+  const int nvox = nl * N;
+  const size_t v0 = (size_t)l0 * N;
+  const ZfwdScalars<R> sc = zfwd_scalars<R, SRC>(P);
+  double pkp = 0.0;
+  for (int i = threadIdx.x; i < lz * N; i += blockDim.x) {
+    R out[9];
+    if (i < nvox) {
+      zfwd_voxel<R, SRC, TAN>(P, sc, v0 + i, out, pkp);
+    } else {
+#pragma unroll
+      for (int c = 0; c < 9; ++c) out[c] = 0;
+    }
+    const int li = i / N;
+    cplx<R>* e = buf + (i - li * N) * LP + li;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) e[k * lz] = {out[2 * k], (2 * k + 1 < 9) ? out[2 * k + 1] : R(0)};
+  }
+  __syncthreads();
+  const LineMap lm{30, 0, 1, LP, 1};
+  fs_lines<R, N1, N2, false>(buf, lm, 5 * lz, P.g.f_fsz_L, tw);
+  const int hz = P.g.hz, hzp = P.g.hzp;
+  const size_t ss = P.g.sstride;
+  for (int i = threadIdx.x; i < 5 * lz * hz; i += blockDim.x) {
+    const int rest = (int)P.g.f_hz.div((unsigned)i);
+    const int kz = i - rest * hz;
+    const int k = (int)P.g.f_fsz_lz.div((unsigned)rest);
+    const int li = rest - k * lz;
+    if (li >= nl) continue;
+    const int l = k * lz + li;
+    const cplx<R> z1 = buf[fs_pos<N1, N2>(kz) * LP + l];
+    cplx<R> z2 = buf[fs_pos<N1, N2>(kz ? N - kz : 0) * LP + l];
+    z2.y = -z2.y;
+    const size_t o = (size_t)(l0 + li) * hzp + kz;
+    P.spec[(size_t)(2 * k) * ss + o] = {R(0.5) * (z1.x + z2.x), R(0.5) * (z1.y + z2.y)};
+    if (2 * k + 1 < 9) {
+      // B = (z1 - conj(z_-k)) / (2i)
+      const R dx = R(0.5) * (z1.x - z2.x), dy = R(0.5) * (z1.y - z2.y);
+      P.spec[(size_t)(2 * k + 1) * ss + o] = {dy, -dx};
+    }
+  }
+  if (SRC == SRC_CGPX) zfwd_step_length<R>(P, pkp);
+}
+
+// Last pass of the fused float CG iteration: the r tile is prefetched with
+// cp.async while the half spectrum is expanded into the transposed order
+// and transformed back; then r -= alpha Ap in place and r.r.
+template <typename R, int N1, int N2>
+__global__ void __launch_bounds__(FFT_THREADS, (Fs4Occ<R, N1, N2>::value))
+    k_zinv4_cgr(const ZinvParams<R, R> P) {
+  constexpr int N = N1 * N2;
+  if (P.done && *P.done) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int lz = P.lz, hz = P.g.hz, hzp = P.g.hzp;
+  const int LP = (5 * lz) | 1;
+  cplx<R>* tw = reinterpret_cast<cplx<R>*>(smem_raw);
+  cplx<R>* buf = tw + ((N + 1) & ~1);
+  R* rt = reinterpret_cast<R*>(buf + (size_t)N * LP);  // [9][lz N]
+  const size_t n = P.g.n;
+  const size_t ss = P.g.sstride;
+  const int nlines = P.g.nx * P.g.ny;
+  const int l0 = blockIdx.x * lz;
+  const int nl = min(lz, nlines - l0);
+  const int nvox = nl * N;
+  const size_t v0 = (size_t)l0 * N;
+  for (int c = 0; c < 9; ++c)
+    for (int i = threadIdx.x; i < nvox; i += blockDim.x)
+      cp_async4(rt + c * lz * N + i, P.r_out + (size_t)c * n + v0 + i);
+  cp_async_commit();
+  for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = P.tw[i];
+  // full z spectrum of the packed lines z = a + i b, written transposed
+  constexpr int U = 4;  // (A, B) pairs in flight per thread
+  const int nthr = blockDim.x;
+  const int totl = 5 * lz * hz;
+  for (int i0 = threadIdx.x; i0 < totl; i0 += U * nthr) {
+    cplx<R> A[U], B[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int i = i0 + u * nthr;
+      const int rest = (int)P.g.f_hz.div((unsigned)i);
+      const int kz = i - rest * hz;
+      const int k = (int)P.g.f_fsz_lz.div((unsigned)rest);
+      const int li = rest - k * lz;
+      A[u] = {R(0), R(0)};
+      B[u] = {R(0), R(0)};
+      if (i < totl && li < nl) {
+        const size_t o = (size_t)(l0 + li) * hzp + kz;
+        A[u] = P.spec[(size_t)(2 * k) * ss + o];
+        if (2 * k + 1 < 9) B[u] = P.spec[(size_t)(2 * k + 1) * ss + o];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int i = i0 + u * nthr;
+      if (i >= totl) continue;
+      const int rest = (int)P.g.f_hz.div((unsigned)i);
+      const int kz = i - rest * hz;
+      const int k = (int)P.g.f_fsz_lz.div((unsigned)rest);
+      const int li = rest - k * lz;
+      const int l = k * lz + li;
+      buf[fs_pos<N1, N2>(kz) * LP + l] = {A[u].x - B[u].y, A[u].y + B[u].x};
+      if (kz > 0) buf[fs_pos<N1, N2>(N - kz) * LP + l] = {A[u].x + B[u].y, B[u].x - A[u].y};
+    }
+  }
+  __syncthreads();
+  const LineMap lm{30, 0, 1, LP, 1};
+  fs_lines<R, N1, N2, true>(buf, lm, 5 * lz, P.g.f_fsz_L, tw);
+  cp_async_wait<0>();
+  __syncthreads();
+  const R alpha = (R)P.st->alpha;
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < nvox; i += blockDim.x) {
+    const int li = i / N;
+    const cplx<R>* e = buf + (i - li * N) * LP + li;
+    R out[9];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+      const cplx<R> z = e[k * lz];
+      out[2 * k] = z.x;
+      if (2 * k + 1 < 9) out[2 * k + 1] = z.y;
+    }
+    R s = 0;
+#pragma unroll
+    for (int c = 0; c < 9; ++c) {
+      const R rn = fma(-alpha, out[c], rt[c * lz * N + i]);
+      P.r_out[(size_t)c * n + v0 + i] = rn;
+      s = fma(rn, rn, s);
+    }
+    acc += (double)s;
+  }
+  double v1[1] = {acc}, tot[1];
+  if (last_block_sum<1>(v1, P.partials, &P.st->counter[SLOT_RR], tot) && threadIdx.x == 0)
+    cg_after_rr(P.st, tot[0]);
+}
+
 cudaError_t g_err4 = cudaSuccess;
 
 template <typename K>
@@ -184,12 +336,61 @@ void launch_fft_x4(const GridGeom& g, double scale, cplx<float>* spec, const int
   }
 }
 
+static size_t z4_smem(const GridGeom& g, bool with_r) {
+  const int LP = (5 * g.fsz_lz) | 1;
+  return sizeof(cplx<float>) * ((size_t)((g.nz + 1) & ~1) + (size_t)g.nz * LP) +
+         (with_r ? sizeof(float) * 9 * (size_t)g.fsz_lz * g.nz : 0);
+}
+
+void launch_zfwd4(const ZfwdParams<float>& P0, cudaStream_t s) {
+  ZfwdParams<float> P = P0;
+  const GridGeom& g = P.g;
+  P.lz = g.fsz_lz;
+  const int nlines = g.nx * g.ny;
+  const int grid = (nlines + P.lz - 1) / P.lz;
+  const size_t sm = z4_smem(g, false);
+  const bool full = P.tan.mode == TAN_FULL81;
+  switch (g.nz) {
+#define RVE_FS_ZF(N, A, B)                                                                    \
+  case N:                                                                                     \
+    if (full) k_zfwd4<float, SRC_CGPX, TAN_FULL81, A, B><<<grid, FFT_THREADS, sm, s>>>(P);   \
+    else k_zfwd4<float, SRC_CGPX, TAN_SVK, A, B><<<grid, FFT_THREADS, sm, s>>>(P);           \
+    break;
+    RVE_FS_SIZES(RVE_FS_ZF)
+#undef RVE_FS_ZF
+    default:
+      break;
+  }
+}
+
+void launch_zinv4(const ZinvParams<float, float>& P0, cudaStream_t s) {
+  ZinvParams<float, float> P = P0;
+  const GridGeom& g = P.g;
+  P.lz = g.fsz_lz;
+  const int nlines = g.nx * g.ny;
+  const int grid = (nlines + P.lz - 1) / P.lz;
+  const size_t sm = z4_smem(g, true);
+  switch (g.nz) {
+#define RVE_FS_ZI(N, A, B)                                          \
+  case N:                                                           \
+    k_zinv4_cgr<float, A, B><<<grid, FFT_THREADS, sm, s>>>(P);      \
+    break;
+    RVE_FS_SIZES(RVE_FS_ZI)
+#undef RVE_FS_ZI
+    default:
+      break;
+  }
+}
+
 cudaError_t fft4_kernels_init() {
   g_err4 = cudaSuccess;
-#define RVE_FS_INIT(N, A, B)                  \
-  allow_smem(k_fft_y4<float, A, B, true>);    \
-  allow_smem(k_fft_y4<float, A, B, false>);   \
-  allow_smem(k_fft_x4<float, A, B>);
+#define RVE_FS_INIT(N, A, B)                                \
+  allow_smem(k_fft_y4<float, A, B, true>);                  \
+  allow_smem(k_fft_y4<float, A, B, false>);                 \
+  allow_smem(k_fft_x4<float, A, B>);                        \
+  allow_smem(k_zfwd4<float, SRC_CGPX, TAN_FULL81, A, B>);   \
+  allow_smem(k_zfwd4<float, SRC_CGPX, TAN_SVK, A, B>);      \
+  allow_smem(k_zinv4_cgr<float, A, B>);
   RVE_FS_SIZES(RVE_FS_INIT)
 #undef RVE_FS_INIT
   return g_err4;

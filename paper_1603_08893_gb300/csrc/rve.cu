@@ -137,6 +137,12 @@ bool make_geom(int nx, int ny, int nz, GridGeom* g) {
   g->f_fsx_ntk = make_fastdiv((unsigned)((g->hz + g->fsx_t - 1) / g->fsx_t));
   g->f_fsy_L = make_fastdiv((unsigned)(g->fsy_grp * g->fsy_t));
   g->f_fsx_L = make_fastdiv((unsigned)(3 * g->fsx_t));
+  // four-step float z passes of the CG iteration: one buffer of
+  // 5 lz lines x nz (about 32 KB) plus, in the last pass, the r tile
+  g->fsz_n1 = fs_split_n1(nz);
+  g->fsz_lz = std::max(1, std::min(64, (int)((32768 / (8 * (size_t)nz) - 1) / 5)));
+  g->f_fsz_L = make_fastdiv((unsigned)(5 * g->fsz_lz));
+  g->f_fsz_lz = make_fastdiv((unsigned)g->fsz_lz);
   return true;
 }
 
