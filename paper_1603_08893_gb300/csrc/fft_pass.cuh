@@ -61,10 +61,34 @@ RVE_DEV void issue_tile(cplx<R>* sbuf, const cplx<R>* gbase, size_t rstride, int
 //   SVK   : linearisation of P = F.S with S = lambda tr(E) I + 2 mu E:
 //           dP = dF.S + F.(lambda tr(dE) I + 2 mu dE), dE = sym(F^T dF)
 // --------------------------------------------------------------------------
+// The SVK inputs of the tangent (F, S or its parameters) are loaded by
+// tangent_pre before the caller's other loads and stores, so that every
+// global load of a voxel is in flight at once; tangent_post contracts.
 template <typename R>
-RVE_DEV void tangent_voxel(const TangentView<R>& T, size_t v, size_t n, const R (&in)[9],
-                           R (&out)[9]) {
-  if (T.mode == TAN_FULL81) {
+struct TanPre {
+  R F[9];
+  R S[6];  // from T.Sop when given
+  R lam, mu;
+};
+
+template <typename R, int TAN>
+RVE_DEV void tangent_pre(const TangentView<R>& T, size_t v, size_t n, TanPre<R>& q) {
+  if (TAN == TAN_SVK) {
+#pragma unroll
+    for (int c = 0; c < 9; ++c) q.F[c] = __ldg(T.Fop + (size_t)c * n + v);
+    q.lam = T.mat.get(v, 0);
+    q.mu = T.mat.get(v, 1);
+    if (T.Sop) {
+#pragma unroll
+      for (int c = 0; c < 6; ++c) q.S[c] = __ldg(T.Sop + (size_t)c * n + v);
+    }
+  }
+}
+
+template <typename R, int TAN>
+RVE_DEV void tangent_post(const TangentView<R>& T, size_t v, size_t n, const TanPre<R>& q,
+                          const R (&in)[9], R (&out)[9]) {
+  if (TAN == TAN_FULL81) {
 #pragma unroll
     for (int a = 0; a < 3; ++a)
 #pragma unroll
@@ -74,17 +98,13 @@ RVE_DEV void tangent_voxel(const TangentView<R>& T, size_t v, size_t n, const R 
         for (int kl = 0; kl < 9; ++kl) s = fma(__ldg(T.K4 + (size_t)((b * 3 + a) * 9 + kl) * n + v), in[kl], s);
         out[3 * a + b] = s;
       }
-  } else if (T.mode == TAN_SVK) {
-    R F[9];
-#pragma unroll
-    for (int c = 0; c < 9; ++c) F[c] = __ldg(T.Fop + (size_t)c * n + v);
-    const R lam = T.mat.get(v, 0), mu = T.mat.get(v, 1);
+  } else if (TAN == TAN_SVK) {
+    const R* F = q.F;
+    const R lam = q.lam, mu = q.mu;
     R S[3][3];
     if (T.Sop) {
-      const R s0 = __ldg(T.Sop + v), s1 = __ldg(T.Sop + n + v), s2 = __ldg(T.Sop + 2 * n + v);
-      const R s3 = __ldg(T.Sop + 3 * n + v), s4 = __ldg(T.Sop + 4 * n + v), s5 = __ldg(T.Sop + 5 * n + v);
-      S[0][0] = s0; S[1][1] = s1; S[2][2] = s2;
-      S[0][1] = S[1][0] = s3; S[0][2] = S[2][0] = s4; S[1][2] = S[2][1] = s5;
+      S[0][0] = q.S[0]; S[1][1] = q.S[1]; S[2][2] = q.S[2];
+      S[0][1] = S[1][0] = q.S[3]; S[0][2] = S[2][0] = q.S[4]; S[1][2] = S[2][1] = q.S[5];
     } else {
       R E[3][3];
 #pragma unroll
@@ -178,6 +198,8 @@ template <typename R, int SRC, int TAN>
 RVE_DEV void zfwd_voxel(const ZfwdParams<R>& P, const ZfwdScalars<R>& sc, size_t v, R (&out)[9],
                         double& pkp) {
   const size_t n = P.g.n;
+  TanPre<R> q;
+  tangent_pre<R, TAN>(P.tan, v, n, q);
   R in[9];
   if (SRC == SRC_FIELD) {
 #pragma unroll
@@ -211,9 +233,7 @@ RVE_DEV void zfwd_voxel(const ZfwdParams<R>& P, const ZfwdScalars<R>& sc, size_t
 #pragma unroll
     for (int c = 0; c < 9; ++c) in[c] = (R)P.unif[c];
   }
-  TangentView<R> T = P.tan;
-  T.mode = TAN;
-  tangent_voxel<R>(T, v, n, in, out);
+  tangent_post<R, TAN>(P.tan, v, n, q, in, out);
   if (SRC == SRC_CGP || SRC == SRC_CGPX) {
 #pragma unroll
     for (int c = 0; c < 9; ++c) P.p[(size_t)c * n + v] = in[c];

@@ -58,15 +58,20 @@ __global__ void __launch_bounds__(FFT_THREADS, (Fs4Occ<R, N1, N2>::value))
   __syncthreads();
   const LineMap lm{ts, N * T, 1, T, 1};
   fs_lines<R, N1, N2, INV>(buf, lm, grp * T, P.g.f_fsy_L, tw);
+  // 16-byte stores of kz pairs; a pair may reach one column into the row
+  // padding (kz = hz when hz is odd), which no pass reads as data
   const int tc = min(T, hz - k0);
-  const int tot = ng * N * T;
-  for (int i = threadIdx.x; i < tot; i += blockDim.x) {
+  const int tot2 = ng * N * T / 2;
+  for (int i2 = threadIdx.x; i2 < tot2; i2 += blockDim.x) {
+    const int i = 2 * i2;
     const int t = i & (T - 1);
     const int srow = i >> ts;
     const int gi = srow / N;
     const int pos = srow - gi * N;
     const int y = INV ? pos : fs_freq<N1, N2>(pos);
-    if (t < tc) gbase[(size_t)(gi * N + y) * hzp + t] = buf[i];
+    if (t < tc)
+      *reinterpret_cast<float4*>(gbase + (size_t)(gi * N + y) * hzp + t) =
+          *reinterpret_cast<const float4*>(buf + i);
   }
 }
 
@@ -74,7 +79,7 @@ __global__ void __launch_bounds__(FFT_THREADS, (Fs4Occ<R, N1, N2>::value))
 // (Eq. G_red) in the transposed order, inverse DFT along x; tile = (tensor
 // row i) x nx x (T kz) for one ky.
 template <typename R, int N1, int N2>
-__global__ void __launch_bounds__(FFT_THREADS, (Fs4Occ<R, N1, N2>::value))
+__global__ void __launch_bounds__(FFT_THREADS, (N1 * N2 > 100 ? 2 : Fs4Occ<R, N1, N2>::value))
     k_fft_x4(const LineParams<R> P) {
   constexpr int N = N1 * N2;
   if (P.done && *P.done) return;
@@ -118,10 +123,13 @@ __global__ void __launch_bounds__(FFT_THREADS, (Fs4Occ<R, N1, N2>::value))
   __syncthreads();
   fs_lines<R, N1, N2, true>(buf, lm, 3 * T, P.g.f_fsx_L, tw);
   const int tc = min(T, hz - k0);
-  const int tot = 3 * N * T;
-  for (int i = threadIdx.x; i < tot; i += blockDim.x) {
+  const int tot2 = 3 * N * T / 2;
+  for (int i2 = threadIdx.x; i2 < tot2; i2 += blockDim.x) {
+    const int i = 2 * i2;
     const int t = i & (T - 1);
-    if (t < tc) gbase[(size_t)(i >> ts) * rs + t] = buf[i];
+    if (t < tc)
+      *reinterpret_cast<float4*>(gbase + (size_t)(i >> ts) * rs + t) =
+          *reinterpret_cast<const float4*>(buf + i);
   }
 }
 
