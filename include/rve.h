@@ -250,7 +250,9 @@ const char* rve_status_string(int code);
 
 /* Instrumentation: number of kernels this handle has launched, and optional
  * CUDA-event timing of every launch of one kernel family
- * (0 zfwd, 1 fft_y fwd, 2 fft_x+projection, 3 fft_y inv, 4 zinv, 5 cg_update).
+ * (0 zfwd, 1 fft_y fwd, 2 fft_x+projection, 3 fft_y inv, 4 zinv, 5 cg_update;
+ * the float32 CG iteration of RVE_MIXED has no family 5: its vector update
+ * is fused into families 0 and 4).
  * rve_kernel_time returns the summed milliseconds and launches since the
  * timing was enabled (synchronises the stream). */
 int rve_launch_count(rve_t h, long long* count);
