@@ -73,6 +73,11 @@ extern "C" {
 #define RVE_TAN_FULL81 1    /* K_ijkl stored, 81 reals per voxel */
 #define RVE_TAN_RECOMPUTE 2 /* SVK: dP = dF.S + F.dS recomputed from F (and S) */
 
+/* arithmetic of the mixed path's float64-accuracy transforms */
+#define RVE_RES_FLOATFLOAT 0 /* float-float on the float32 pipe: hi + lo float pairs,
+                                ~48-bit significand, float64 inputs and outputs */
+#define RVE_RES_FP64 1       /* hardware float64 */
+
 typedef struct rve_s* rve_t;
 
 typedef struct {
@@ -88,6 +93,9 @@ typedef struct {
   int mixed_refine;     /* MIXED only: extra Newton iterations after the convergence test
                            first passes (further refinement with the float64 residual);
                            default 0 */
+  int residual;         /* MIXED only: arithmetic of the float64-accuracy transforms (the
+                           residual G:P and the projection of dF): RVE_RES_FLOATFLOAT
+                           (default) or RVE_RES_FP64 */
   void* stream;         /* cudaStream_t; NULL = legacy default stream */
   void* workspace;      /* optional caller-owned device memory (see rve_workspace_size) */
   size_t workspace_bytes;

@@ -37,7 +37,7 @@ class rve_options(C.Structure):
     _fields_ = [("precision", C.c_int), ("tangent", C.c_int),
                 ("max_newton", C.c_int), ("max_cg", C.c_int),
                 ("cg_tol_floor", C.c_double), ("cg_atol", C.c_double),
-                ("mixed_refine", C.c_int),
+                ("mixed_refine", C.c_int), ("residual", C.c_int),
                 ("stream", C.c_void_p), ("workspace", C.c_void_p),
                 ("workspace_bytes", C.c_size_t)]
 

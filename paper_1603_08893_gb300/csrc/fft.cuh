@@ -14,6 +14,7 @@
 // Stages alternate between two shared-memory buffers.
 #pragma once
 #include "common.cuh"
+#include "dfloat.cuh"
 
 #define RVE_MAX_STAGES 16
 
@@ -189,10 +190,12 @@ RVE_DEV void stage_pp(const cplx<R>* __restrict__ src, cplx<R>* __restrict__ dst
     cplx<R> v[RAD];
 #pragma unroll
     for (int r = 0; r < RAD; ++r) v[r] = src[base + (j + r * nb) * lm.es];
+    if (jr != 0) {  // all twiddles are 1 for the first butterfly of a group
 #pragma unroll
-    for (int r = 1; r < RAD; ++r) {
-      const cplx<R> w = tw[r * jr * tws];
-      v[r] = INV ? c_mulc(v[r], w) : c_mul(v[r], w);
+      for (int r = 1; r < RAD; ++r) {
+        const cplx<R> w = tw[r * jr * tws];
+        v[r] = INV ? c_mulc(v[r], w) : c_mul(v[r], w);
+      }
     }
     dft_odd<R, RAD, INV>(v, cs, sn);
     const int d = jq * Ns * RAD + jr;
@@ -380,11 +383,24 @@ RVE_DEV cplx<R>* fft_lines(cplx<R>* a, cplx<R>* b, const LineMap& lm, int L, con
       case 5: stage_pp<R, 5, INV>(a, b, lm, L, fL, p.n, Ns, fNs, fnb, tw); break;
       case 7: stage_pp<R, 7, INV>(a, b, lm, L, fL, p.n, Ns, fNs, fnb, tw); break;
       case 11: stage_pp<R, 11, INV>(a, b, lm, L, fL, p.n, Ns, fNs, fnb, tw); break;
-      case 9: stage_pp2<R, 3, 3, INV>(a, b, lm, L, fL, p.n, Ns, fNs, fnb, tw); break;
-      case 15: stage_pp2<R, 5, 3, INV>(a, b, lm, L, fL, p.n, Ns, fNs, fnb, tw); break;
-      case 21: stage_pp2<R, 7, 3, INV>(a, b, lm, L, fL, p.n, Ns, fNs, fnb, tw); break;
-      case 25: stage_pp2<R, 5, 5, INV>(a, b, lm, L, fL, p.n, Ns, fNs, fnb, tw); break;
-      default: stage_pp_generic<R, INV>(a, b, lm, L, fL, p.n, Ns, rad, fNs, fnb, p.fN, tw); break;
+      default:
+        if constexpr (!is_dfl<R>::value) {  // float-float plans have no composite radices
+          if (rad == 9) {
+            stage_pp2<R, 3, 3, INV>(a, b, lm, L, fL, p.n, Ns, fNs, fnb, tw);
+            break;
+          } else if (rad == 15) {
+            stage_pp2<R, 5, 3, INV>(a, b, lm, L, fL, p.n, Ns, fNs, fnb, tw);
+            break;
+          } else if (rad == 21) {
+            stage_pp2<R, 7, 3, INV>(a, b, lm, L, fL, p.n, Ns, fNs, fnb, tw);
+            break;
+          } else if (rad == 25) {
+            stage_pp2<R, 5, 5, INV>(a, b, lm, L, fL, p.n, Ns, fNs, fnb, tw);
+            break;
+          }
+        }
+        stage_pp_generic<R, INV>(a, b, lm, L, fL, p.n, Ns, rad, fNs, fnb, p.fN, tw);
+        break;
     }
     cplx<R>* t = a;
     a = b;

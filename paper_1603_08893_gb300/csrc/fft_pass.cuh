@@ -73,7 +73,7 @@ struct TanPre {
 
 template <typename R, int TAN>
 RVE_DEV void tangent_pre(const TangentView<R>& T, size_t v, size_t n, TanPre<R>& q) {
-  if (TAN == TAN_SVK) {
+  if constexpr (TAN == TAN_SVK) {
 #pragma unroll
     for (int c = 0; c < 9; ++c) q.F[c] = __ldg(T.Fop + (size_t)c * n + v);
     q.lam = T.mat.get(v, 0);
@@ -88,7 +88,7 @@ RVE_DEV void tangent_pre(const TangentView<R>& T, size_t v, size_t n, TanPre<R>&
 template <typename R, int TAN>
 RVE_DEV void tangent_post(const TangentView<R>& T, size_t v, size_t n, const TanPre<R>& q,
                           const R (&in)[9], R (&out)[9]) {
-  if (TAN == TAN_FULL81) {
+  if constexpr (TAN == TAN_FULL81) {
 #pragma unroll
     for (int a = 0; a < 3; ++a)
 #pragma unroll
@@ -98,7 +98,7 @@ RVE_DEV void tangent_post(const TangentView<R>& T, size_t v, size_t n, const Tan
         for (int kl = 0; kl < 9; ++kl) s = fma(__ldg(T.K4 + (size_t)((b * 3 + a) * 9 + kl) * n + v), in[kl], s);
         out[3 * a + b] = s;
       }
-  } else if (TAN == TAN_SVK) {
+  } else if constexpr (TAN == TAN_SVK) {
     const R* F = q.F;
     const R lam = q.lam, mu = q.mu;
     R S[3][3];
@@ -158,6 +158,7 @@ struct ZfwdParams {
   int src;
   TangentView<R> tan;
   const R* field;
+  const double* field64;  // SRC_FIELD input of the float-float passes
   const R* r;
   R* p;
   const double* unif;
@@ -201,10 +202,15 @@ RVE_DEV void zfwd_voxel(const ZfwdParams<R>& P, const ZfwdScalars<R>& sc, size_t
   TanPre<R> q;
   tangent_pre<R, TAN>(P.tan, v, n, q);
   R in[9];
-  if (SRC == SRC_FIELD) {
+  if constexpr (SRC == SRC_FIELD) {
+    if constexpr (is_dfl<R>::value) {
 #pragma unroll
-    for (int c = 0; c < 9; ++c) in[c] = P.field[(size_t)c * n + v];
-  } else if (SRC == SRC_CGP) {
+      for (int c = 0; c < 9; ++c) in[c] = R(P.field64[(size_t)c * n + v]);
+    } else {
+#pragma unroll
+      for (int c = 0; c < 9; ++c) in[c] = P.field[(size_t)c * n + v];
+    }
+  } else if constexpr (SRC == SRC_CGP) {
     R rr[9], pp[9];
 #pragma unroll
     for (int c = 0; c < 9; ++c) rr[c] = P.r[(size_t)c * n + v];
@@ -214,7 +220,7 @@ RVE_DEV void zfwd_voxel(const ZfwdParams<R>& P, const ZfwdScalars<R>& sc, size_t
     }
 #pragma unroll
     for (int c = 0; c < 9; ++c) in[c] = sc.first ? rr[c] : fma(sc.beta, pp[c], rr[c]);
-  } else if (SRC == SRC_CGPX) {
+  } else if constexpr (SRC == SRC_CGPX) {
     R rr[9], pp[9], xx[9];
 #pragma unroll
     for (int c = 0; c < 9; ++c) rr[c] = P.r[(size_t)c * n + v];
@@ -234,11 +240,11 @@ RVE_DEV void zfwd_voxel(const ZfwdParams<R>& P, const ZfwdScalars<R>& sc, size_t
     for (int c = 0; c < 9; ++c) in[c] = (R)P.unif[c];
   }
   tangent_post<R, TAN>(P.tan, v, n, q, in, out);
-  if (SRC == SRC_CGP || SRC == SRC_CGPX) {
+  if constexpr (SRC == SRC_CGP || SRC == SRC_CGPX) {
 #pragma unroll
     for (int c = 0; c < 9; ++c) P.p[(size_t)c * n + v] = in[c];
   }
-  if (SRC == SRC_CGPX) {
+  if constexpr (SRC == SRC_CGPX) {
     R sp = 0;
 #pragma unroll
     for (int c = 0; c < 9; ++c) sp = fma(in[c], out[c], sp);
@@ -276,6 +282,7 @@ struct ZinvParams {
   int lz;
   const cplx<R>* spec;
   R* dst;
+  double* dst64;  // OUT_PLAIN output of the float-float passes
   RC* r_out;
   RC* x_out;
   const RC* p_in;
@@ -293,4 +300,12 @@ void launch_zinv4(const ZinvParams<float, float>& P, cudaStream_t s);
 RVE_DEV void cp_async4(void* sdst, const void* gsrc) {
   const unsigned s = (unsigned)__cvta_generic_to_shared(sdst);
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gsrc));
+}
+
+// Axis plans: the float-float passes use prime radices only (a composite
+// float-float butterfly does not fit the register budget).
+template <typename R>
+RVE_DEV const AxisPlan& axis_plan(const GridGeom& g, int axis) {
+  if constexpr (is_dfl<R>::value) return axis == 0 ? g.pxs : (axis == 1 ? g.pys : g.pzs);
+  else return axis == 0 ? g.px : (axis == 1 ? g.py : g.pz);
 }

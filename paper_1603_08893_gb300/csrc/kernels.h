@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include "common.cuh"
+#include "dfloat.cuh"
 #include "fft.cuh"
 
 // tangent storage modes
@@ -23,6 +24,7 @@ struct GridGeom {
   size_t n;           // nx*ny*nz
   size_t sstride;     // nx*ny*hzp (complex elements per spectrum component)
   AxisPlan px, py, pz;
+  AxisPlan pxs, pys, pzs;  // prime radices only (float-float passes)
   int lz_f, lz_d;     // z lines per CTA (float, double)
   int ty_f, ty_d, gy_f, gy_d;  // y tile (kz) and groups per CTA
   int tx_f, tx_d;     // x tile (kz)
@@ -99,6 +101,13 @@ void launch_fft_y4(const GridGeom& g, bool inverse, cplx<float>* spec, const int
 void launch_fft_x4(const GridGeom& g, double scale, cplx<float>* spec, const int* done,
                    const cplx<float>* tw, cudaStream_t s);
 cudaError_t fft4_kernels_init();
+
+// G : in in float-float arithmetic on the float32 pipe (float64 in and out):
+// out_mode OUT_PLAIN writes out64 = scale * G:in; OUT_RESID writes
+// r_out = scale * G:in (float32), x_out = 0 and initialises the CG state.
+void launch_G_df(const GridGeom& g, const double* in, double scale, int out_mode, double* out64,
+                 float* r_out, float* x_out, SolverState* st, double* partials, cplx<dfl>* spec,
+                 const Twiddles<dfl>& tw, cudaStream_t s);
 
 cudaError_t fft_kernels_init();  // opt-in to large dynamic shared memory
 size_t fft_max_blocks(const GridGeom& g);

@@ -29,7 +29,7 @@ __global__ void FFT_BOUNDS(R) k_zfwd(const ZfwdParams<R> P) {
   cplx<R>* bufB = bufA + 5 * lz * nz;
   for (int i = threadIdx.x; i < nz; i += blockDim.x) tw[i] = P.tw[i];
   __shared__ AxisPlan plan;
-  load_plan(&plan, P.g.pz);
+  load_plan(&plan, axis_plan<R>(P.g, 2));
   const int nlines = P.g.nx * P.g.ny;
   const int l0 = blockIdx.x * lz;
   const int nl = min(lz, nlines - l0);
@@ -43,7 +43,7 @@ __global__ void FFT_BOUNDS(R) k_zfwd(const ZfwdParams<R> P) {
       zfwd_voxel<R, SRC, TAN>(P, sc, v0 + i, out, pkp);
     } else {
 #pragma unroll
-      for (int c = 0; c < 9; ++c) out[c] = 0;
+      for (int c = 0; c < 9; ++c) out[c] = R(0);
     }
 #pragma unroll
     for (int k = 0; k < 5; ++k)
@@ -101,7 +101,7 @@ __global__ void FFT_BOUNDS(R) k_fft_y(const LineParams<R> P) {
   cp_async_commit();
   for (int i = threadIdx.x; i < ny; i += blockDim.x) tw[i] = P.tw[i];
   __shared__ AxisPlan plan;
-  load_plan(&plan, P.g.py);
+  load_plan(&plan, axis_plan<R>(P.g, 1));
   cp_async_wait<0>();
   __syncthreads();
   const LineMap lm{ts, ny * T, 1, T, 1};
@@ -144,22 +144,25 @@ __global__ void FFT_BOUNDS(R) k_fft_x_proj(const LineParams<R> P) {
   cp_async_commit();
   for (int i = threadIdx.x; i < nx; i += blockDim.x) tw[i] = P.tw[i];
   __shared__ AxisPlan plan;
-  load_plan(&plan, P.g.px);
+  load_plan(&plan, axis_plan<R>(P.g, 0));
   cp_async_wait<0>();
   __syncthreads();
   const LineMap lm{ts, nx * T, 1, T, 1};
   const FastDiv fL = sizeof(R) == 4 ? P.g.f_Lx_f : P.g.f_Lx_d;
   cplx<R>* X = fft_lines_call<R, false>(bufA, bufB, lm, 3 * T, fL, &plan, tw);
   cplx<R>* Y = (X == bufA) ? bufB : bufA;
-  const R qy = signed_freq<R>(y, ny) / (R)ny;
-  const R sc = (R)P.scale;
+  using RQ = typename std::conditional<is_dfl<R>::value, double, R>::type;
+  const RQ qy_ = signed_freq<RQ>(y, ny) / (RQ)ny;
+  const RQ sc_ = (RQ)P.scale;
   for (int i = threadIdx.x; i < nx * T; i += blockDim.x) {
     const int t = i & (T - 1);
     const int x = i >> ts;
-    const R qx = signed_freq<R>(x, nx) / (R)nx;
-    const R qz = (R)(k0 + t) / (R)P.g.nz;
-    const R q2 = qx * qx + qy * qy + qz * qz;
-    const R f = (q2 > R(0)) ? sc / q2 : R(0);
+    // frequencies and 1/|xi|^2 in R (float-float: in float64, then split)
+    const RQ qx_ = signed_freq<RQ>(x, nx) / (RQ)nx;
+    const RQ qz_ = (RQ)(k0 + t) / (RQ)P.g.nz;
+    const RQ q2 = qx_ * qx_ + qy_ * qy_ + qz_ * qz_;
+    const R f = R((q2 > RQ(0)) ? sc_ / q2 : RQ(0));
+    const R qx = R(qx_), qy = R(qy_), qz = R(qz_);
     const cplx<R> A0 = X[i], A1 = X[nx * T + i], A2 = X[2 * nx * T + i];
     const R sx = f * (qx * A0.x + qy * A1.x + qz * A2.x);
     const R sy = f * (qx * A0.y + qy * A1.y + qz * A2.y);
@@ -187,7 +190,7 @@ __global__ void FFT_BOUNDS(R) k_zinv(const ZinvParams<R, RC> P) {
   cplx<R>* bufB = bufA + 5 * lz * nz;
   for (int i = threadIdx.x; i < nz; i += blockDim.x) tw[i] = P.tw[i];
   __shared__ AxisPlan plan;
-  load_plan(&plan, P.g.pz);
+  load_plan(&plan, axis_plan<R>(P.g, 2));
   const size_t n = P.g.n;
   const size_t ss = P.g.sstride;
   const int nlines = P.g.nx * P.g.ny;
@@ -242,10 +245,15 @@ __global__ void FFT_BOUNDS(R) k_zinv(const ZinvParams<R, RC> P) {
       if (2 * k + 1 < 9) out[2 * k + 1] = z.y;
     }
     const size_t v = v0 + i;
-    if (OUT == OUT_PLAIN) {
+    if constexpr (OUT == OUT_PLAIN) {
+      if constexpr (is_dfl<R>::value) {
 #pragma unroll
-      for (int c = 0; c < 9; ++c) P.dst[(size_t)c * n + v] = out[c];
-    } else if (OUT == OUT_CGR) {
+        for (int c = 0; c < 9; ++c) P.dst64[(size_t)c * n + v] = (double)out[c];
+      } else {
+#pragma unroll
+        for (int c = 0; c < 9; ++c) P.dst[(size_t)c * n + v] = out[c];
+      }
+    } else if constexpr (OUT == OUT_CGR) {
       const R alpha = (R)P.st->alpha;
       R rv[9];
 #pragma unroll
@@ -258,7 +266,7 @@ __global__ void FFT_BOUNDS(R) k_zinv(const ZinvParams<R, RC> P) {
         s = fma(rn, rn, s);
       }
       acc += (double)s;
-    } else if (OUT == OUT_CGAP) {
+    } else if constexpr (OUT == OUT_CGAP) {
       R pv[9];
 #pragma unroll
       for (int c = 0; c < 9; ++c) pv[c] = (R)P.p_in[(size_t)c * n + v];
@@ -270,7 +278,7 @@ __global__ void FFT_BOUNDS(R) k_zinv(const ZinvParams<R, RC> P) {
       }
       acc += (double)s;
     } else {
-      R s = 0;
+      R s = R(0);
 #pragma unroll
       for (int c = 0; c < 9; ++c) {
         P.r_out[(size_t)c * n + v] = (RC)out[c];
@@ -331,7 +339,7 @@ template <typename R>
 void launch_zfwd(const GridGeom& g, int src, const TangentView<R>& tan, const R* field, const R* r,
                  R* p, const double* unif, SolverState* st, const int* done, cplx<R>* spec,
                  const Twiddles<R>& tw, cudaStream_t s, R* x, double* partials) {
-  ZfwdParams<R> P;
+  ZfwdParams<R> P{};
   P.g = g;
   P.lz = lz_of<R>(g);
   P.src = src;
@@ -380,7 +388,7 @@ void launch_fft_y(const GridGeom& g, bool inverse, cplx<R>* spec, const int* don
                   reinterpret_cast<const cplx<float>*>(tw.y), s);
     return;
   }
-  LineParams<R> P;
+  LineParams<R> P{};
   P.g = g;
   P.t = sizeof(R) == 4 ? g.ty_f : g.ty_d;
   P.grp = sizeof(R) == 4 ? g.gy_f : g.gy_d;
@@ -402,7 +410,7 @@ void launch_fft_x_proj(const GridGeom& g, double scale, cplx<R>* spec, const int
                   reinterpret_cast<const cplx<float>*>(tw.x), s);
     return;
   }
-  LineParams<R> P;
+  LineParams<R> P{};
   P.g = g;
   P.t = sizeof(R) == 4 ? g.tx_f : g.tx_d;
   P.grp = 1;
@@ -419,7 +427,7 @@ template <typename R, typename RC>
 void launch_zinv(const GridGeom& g, int out, const cplx<R>* spec, R* dst, RC* r_out, RC* x_out,
                  const RC* p_in, SolverState* st, double* partials, const int* done,
                  const Twiddles<R>& tw, cudaStream_t s) {
-  ZinvParams<R, RC> P;
+  ZinvParams<R, RC> P{};
   P.g = g;
   P.lz = lz_of<R>(g);
   P.spec = spec;
@@ -478,6 +486,51 @@ static void init_r() {
   allow_big_smem(k_fft_x_proj<R>);
 }
 
+void launch_G_df(const GridGeom& g, const double* in, double scale, int out_mode, double* out64,
+                 float* r_out, float* x_out, SolverState* st, double* partials, cplx<dfl>* spec,
+                 const Twiddles<dfl>& tw, cudaStream_t s) {
+  const int nlines = g.nx * g.ny;
+  const int lz = g.lz_d;
+  const dim3 grid((nlines + lz - 1) / lz);
+  const size_t smz = sizeof(cplx<dfl>) * ((size_t)((g.nz + 1) & ~1) + 10 * (size_t)lz * g.nz);
+  {
+    ZfwdParams<dfl> P{};
+    P.g = g;
+    P.lz = lz;
+    P.src = SRC_FIELD;
+    P.field64 = in;
+    P.st = st;
+    P.spec = spec;
+    P.tw = tw.z;
+    k_zfwd<dfl, SRC_FIELD, 0><<<grid, FFT_THREADS, smz, s>>>(P);
+  }
+  launch_fft_y<dfl>(g, false, spec, nullptr, tw, s);
+  launch_fft_x_proj<dfl>(g, scale, spec, nullptr, tw, s);
+  launch_fft_y<dfl>(g, true, spec, nullptr, tw, s);
+  if (out_mode == OUT_PLAIN) {
+    ZinvParams<dfl, double> P{};
+    P.g = g;
+    P.lz = lz;
+    P.spec = spec;
+    P.dst64 = out64;
+    P.st = st;
+    P.partials = partials;
+    P.tw = tw.z;
+    k_zinv<dfl, double, OUT_PLAIN><<<grid, FFT_THREADS, smz, s>>>(P);
+  } else {
+    ZinvParams<dfl, float> P{};
+    P.g = g;
+    P.lz = lz;
+    P.spec = spec;
+    P.r_out = r_out;
+    P.x_out = x_out;
+    P.st = st;
+    P.partials = partials;
+    P.tw = tw.z;
+    k_zinv<dfl, float, OUT_RESID><<<grid, FFT_THREADS, smz, s>>>(P);
+  }
+}
+
 cudaError_t fft_kernels_init() {
   g_init_err = cudaSuccess;
   init_r<float>();
@@ -491,6 +544,12 @@ cudaError_t fft_kernels_init() {
   allow_big_smem(k_zinv<float, float, OUT_CGR>);
   allow_big_smem(k_zinv<double, double, OUT_CGR>);
   allow_big_smem(k_zinv<float, float, OUT_RESID>);
+  allow_big_smem(k_zfwd<dfl, SRC_FIELD, 0>);
+  allow_big_smem(k_fft_y<dfl, true>);
+  allow_big_smem(k_fft_y<dfl, false>);
+  allow_big_smem(k_fft_x_proj<dfl>);
+  allow_big_smem(k_zinv<dfl, double, OUT_PLAIN>);
+  allow_big_smem(k_zinv<dfl, float, OUT_RESID>);
   if (g_init_err == cudaSuccess) g_init_err = fft4_kernels_init();
   return g_init_err;
 }
@@ -521,3 +580,7 @@ template void launch_zinv<double, float>(const GridGeom&, int, const cplx<double
 template void launch_zinv<float, float>(const GridGeom&, int, const cplx<float>*, float*, float*,
                                         float*, const float*, SolverState*, double*, const int*,
                                         const Twiddles<float>&, cudaStream_t);
+template void launch_fft_y<dfl>(const GridGeom&, bool, cplx<dfl>*, const int*,
+                                const Twiddles<dfl>&, cudaStream_t);
+template void launch_fft_x_proj<dfl>(const GridGeom&, double, cplx<dfl>*, const int*,
+                                     const Twiddles<dfl>&, cudaStream_t);

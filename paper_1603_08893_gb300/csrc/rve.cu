@@ -38,7 +38,7 @@ struct Arena {
   }
 };
 
-bool factor_plan(int n, AxisPlan* p) {
+bool factor_plan(int n, AxisPlan* p, bool composite = true) {
   p->n = n;
   p->nst = 0;
   int m = n;
@@ -46,7 +46,7 @@ bool factor_plan(int n, AxisPlan* p) {
   // one trip through shared memory); then single radices
   const int fixed[] = {25, 21, 15, 9, 11, 7, 5, 3};
   for (int f : fixed)
-    while (m % f == 0) {
+    while (m % f == 0 && (composite || f == 11 || f == 7 || f == 5 || f == 3)) {
       if (p->nst >= RVE_MAX_STAGES) return false;
       p->rad[p->nst++] = f;
       m /= f;
@@ -97,6 +97,9 @@ bool make_geom(int nx, int ny, int nz, GridGeom* g) {
   g->n = (size_t)nx * ny * nz;
   g->sstride = (size_t)nx * ny * g->hzp;
   if (!factor_plan(nx, &g->px) || !factor_plan(ny, &g->py) || !factor_plan(nz, &g->pz)) return false;
+  if (!factor_plan(nx, &g->pxs, false) || !factor_plan(ny, &g->pys, false) ||
+      !factor_plan(nz, &g->pzs, false))
+    return false;
   // z passes: two buffers of 5 packed lines x lz x nz (ping-pong stages)
   g->lz_f = pick_lz(nz, 8, 32 * 1024);
   g->lz_d = pick_lz(nz, 16, 32 * 1024);
@@ -182,8 +185,11 @@ struct rve_s {
   SolverState* hst = nullptr;  // pinned mirror
   cplx<float>* twf_all = nullptr;
   cplx<double>* twd_all = nullptr;
+  cplx<dfl>* twdf_all = nullptr;
   Twiddles<float> twf{};
   Twiddles<double> twd{};
+  Twiddles<dfl> twdf{};
+  bool floatfloat = false;  // mixed: float64-accuracy transforms in float-float
   double Fbar[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
   double Fbar_committed[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};  // F-bar of the last committed state
   double* adj_b = nullptr;  // adjoint right-hand side [9][n] (SVK)
@@ -347,10 +353,18 @@ void enqueue_cg_finish(rve_t h) {
   h->launches += 1;
 }
 
-// b = -G:P in float64; r = b (in the CG precision), x = 0, CG state reset.
+// b = -G:P in float64 (float-float for mixed handles by default); r = b (in
+// the CG precision), x = 0, CG state reset.
 template <typename RC>
 void enqueue_residual(rve_t h) {
   const GridGeom& g = h->g;
+  if (std::is_same<RC, float>::value && h->floatfloat) {
+    launch_G_df(g, h->P, -1.0 / (double)h->n, OUT_RESID, nullptr, as<float>(h->r),
+                as<float>(h->x), h->st, h->partials, reinterpret_cast<cplx<dfl>*>(h->spec64),
+                h->twdf, h->s);
+    h->launches += 5;
+    return;
+  }
   TangentView<double> plain{};
   plain.mode = 0;
   launch_zfwd<double>(g, SRC_FIELD, plain, h->P, nullptr, nullptr, nullptr, h->st, nullptr,
@@ -363,9 +377,17 @@ void enqueue_residual(rve_t h) {
   h->launches += 5;
 }
 
-// buf <- G : buf in float64 (Eq. weak:discr:FFT-intermediate), in place.
-void enqueue_project_fp64(rve_t h, double* buf) {
+// buf <- G : buf in float64 (Eq. weak:discr:FFT-intermediate), in place;
+// in float-float arithmetic for mixed handles unless hardware float64 is
+// asked for.
+void enqueue_project_fp64(rve_t h, double* buf, bool allow_floatfloat = true) {
   const GridGeom& g = h->g;
+  if (h->floatfloat && allow_floatfloat) {
+    launch_G_df(g, buf, 1.0 / (double)h->n, OUT_PLAIN, buf, nullptr, nullptr, h->st, h->partials,
+                reinterpret_cast<cplx<dfl>*>(h->spec64), h->twdf, h->s);
+    h->launches += 5;
+    return;
+  }
   TangentView<double> plain{};
   plain.mode = 0;
   launch_zfwd<double>(g, SRC_FIELD, plain, buf, nullptr, nullptr, nullptr, h->st, nullptr,
@@ -567,6 +589,7 @@ size_t layout(rve_t h, Arena& a) {
   const int gx[3] = {h->g.nx, h->g.ny, h->g.nz};
   h->twf_all = a.take<cplx<float>>((size_t)gx[0] + gx[1] + gx[2]);
   h->twd_all = a.take<cplx<double>>((size_t)gx[0] + gx[1] + gx[2]);
+  h->twdf_all = a.take<cplx<dfl>>((size_t)gx[0] + gx[1] + gx[2]);
   return a.off;
 }
 
@@ -598,6 +621,7 @@ void rve_default_options(rve_options* o) {
   o->cg_tol_floor = 1e-5;
   o->cg_atol = 0.0;
   o->mixed_refine = 0;
+  o->residual = RVE_RES_FLOATFLOAT;
 }
 
 const char* rve_status_string(int code) {
@@ -631,6 +655,7 @@ static int resolve_options(const rve_options* in, rve_options* out, int model, i
   if (!(out->cg_tol_floor >= 0.0)) return RVE_ERR_INVALID;
   if (!(out->cg_atol >= 0.0)) return RVE_ERR_INVALID;
   if (out->mixed_refine < 0 || out->mixed_refine > 8) return RVE_ERR_INVALID;
+  if (out->residual != RVE_RES_FLOATFLOAT && out->residual != RVE_RES_FP64) return RVE_ERR_INVALID;
   if (model == RVE_SVK) {
     if (out->tangent == RVE_TAN_AUTO || out->tangent == RVE_TAN_RECOMPUTE) *tan = TAN_SVK;
     else if (out->tangent == RVE_TAN_FULL81) *tan = TAN_FULL81;
@@ -687,6 +712,7 @@ int rve_create(rve_t* out, int nx, int ny, int nz, int model, int nphase, const 
                                                     : "invalid options");
   h->n = h->g.n;
   h->mixed = h->opt.precision == RVE_MIXED;
+  h->floatfloat = h->mixed && h->opt.residual == RVE_RES_FLOATFLOAT;
   h->tan = tan;
   h->nparam = (model == RVE_J2) ? 4 : 2;
   h->s = (cudaStream_t)h->opt.stream;
@@ -742,16 +768,20 @@ int rve_create(rve_t* out, int nx, int ny, int nz, int model, int nphase, const 
     const int dims[3] = {h->g.nx, h->g.ny, h->g.nz};
     std::vector<cplx<double>> td;
     std::vector<cplx<float>> tf;
+    std::vector<cplx<dfl>> tdf;
     for (int d = 0; d < 3; ++d)
       for (int k = 0; k < dims[d]; ++k) {
         const double ang = 2.0 * kPi * (double)k / (double)dims[d];
         td.push_back({std::cos(ang), -std::sin(ang)});
         tf.push_back({(float)std::cos(ang), (float)-std::sin(ang)});
+        tdf.push_back({dfl(std::cos(ang)), dfl(-std::sin(ang))});
       }
     ok &= ck(cudaMemcpyAsync(h->twd_all, td.data(), td.size() * sizeof(td[0]), cudaMemcpyHostToDevice, h->s));
     ok &= ck(cudaMemcpyAsync(h->twf_all, tf.data(), tf.size() * sizeof(tf[0]), cudaMemcpyHostToDevice, h->s));
+    ok &= ck(cudaMemcpyAsync(h->twdf_all, tdf.data(), tdf.size() * sizeof(tdf[0]), cudaMemcpyHostToDevice, h->s));
     h->twd = {h->twd_all, h->twd_all + dims[0], h->twd_all + dims[0] + dims[1]};
     h->twf = {h->twf_all, h->twf_all + dims[0], h->twf_all + dims[0] + dims[1]};
+    h->twdf = {h->twdf_all, h->twdf_all + dims[0], h->twdf_all + dims[0] + dims[1]};
     ok &= ck(cudaStreamSynchronize(h->s));
   }
   // materials: (lambda, mu) with lambda = K - 2 mu / 3 (Eq. elas:C)
@@ -1208,7 +1238,7 @@ int rve_project(rve_t h, const double* A, double* out, int on_device) {
   const size_t n9 = 9 * h->n;
   int rc = copy_in(h, h->tmp64, A, n9 * 8, on_device);
   if (rc) return rc;
-  enqueue_project_fp64(h, h->tmp64);
+  enqueue_project_fp64(h, h->tmp64, false);
   CK(cudaGetLastError());
   return copy_out(h, out, h->tmp64, n9 * 8, on_device);
 }

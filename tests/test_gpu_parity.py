@@ -170,6 +170,26 @@ def test_mixed_solve_matches_tight_oracle(shape):
     r.close()
 
 
+@pytest.mark.parametrize("shape", [(31, 31, 31), (27, 33, 45)])
+def test_floatfloat_residual_matches_fp64_residual(shape):
+    """The mixed path's float64-accuracy transforms in float-float arithmetic
+    (default) against hardware float64: same Newton path, P-bar within 1e-11,
+    F within 1e-10."""
+    rng = np.random.default_rng(12)
+    phase = (rng.uniform(size=shape) < 0.3).astype(np.uint8)
+    params = synth.two_phase_params(10.0)
+    out = {}
+    for res in ("floatfloat", "fp64"):
+        r = RVE(shape, phase=phase, phase_params=params, precision="mixed", residual=res)
+        r.set_macro_F(synth.simple_shear(0.03))
+        st = r.solve_increment(1e-5, 1e-8)
+        out[res] = (st["newton_iters"], r.homogenized_P(), r.get_F())
+        r.close()
+    assert out["floatfloat"][0] == out["fp64"][0]
+    assert maxrel(out["floatfloat"][1], out["fp64"][1]) < 1e-11
+    assert rel(out["floatfloat"][2], out["fp64"][2]) < 1e-10
+
+
 def test_homogeneous_cell_gives_uniform_F():
     shape = (15, 9, 21)
     r = RVE(shape, phase=np.zeros(shape, np.uint8), phase_params=[[0.833, 0.386]])
