@@ -252,6 +252,8 @@ RVE_DEV void zfwd_voxel(const ZfwdParams<R>& P, const ZfwdScalars<R>& sc, size_t
   }
 }
 
+RVE_DEV void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
+
 // Step length of the fused CG iteration from sum p.(K:p):
 // p.Ap = p.G(K p) = (G p).(K p) = p.(K p) for compatible p (G is an
 // orthogonal projector), so alpha is known before the inverse transforms.

@@ -219,6 +219,18 @@ __global__ void __launch_bounds__(FFT_THREADS, (Fs4Occ<R, N1, N2>::value))
     for (int i = threadIdx.x; i < nvox; i += blockDim.x)
       cp_async4(rt + c * lz * N + i, P.r_out + (size_t)c * n + v0 + i);
   cp_async_commit();
+  // the tile's half spectrum: per component nl consecutive rows of hzp
+  // values, contiguous; L2 prefetch of all its 128-byte lines
+  {
+    const int lines_per_comp = (int)(((size_t)nl * hzp * sizeof(cplx<R>) + 127) / 128);
+    for (int j = threadIdx.x; j < 9 * lines_per_comp; j += blockDim.x) {
+      const int c = j / lines_per_comp;
+      const int q = j - c * lines_per_comp;
+      const char* base = reinterpret_cast<const char*>(P.spec + (size_t)c * ss + (size_t)l0 * hzp);
+      const size_t off = min((size_t)q * 128, (size_t)nl * hzp * sizeof(cplx<R>) - 1);
+      prefetch_l2(base + off);
+    }
+  }
   for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = P.tw[i];
   // full z spectrum of the packed lines z = a + i b, written transposed
   constexpr int U = 4;  // (A, B) pairs in flight per thread
@@ -361,8 +373,8 @@ void launch_zfwd4(const ZfwdParams<float>& P0, cudaStream_t s) {
   switch (g.nz) {
 #define RVE_FS_ZF(N, A, B)                                                                    \
   case N:                                                                                     \
-    if (full) k_zfwd4<float, SRC_CGPX, TAN_FULL81, A, B><<<grid, FFT_THREADS, sm, s>>>(P);   \
-    else k_zfwd4<float, SRC_CGPX, TAN_SVK, A, B><<<grid, FFT_THREADS, sm, s>>>(P);           \
+    if (full) k_zfwd4<float, SRC_CGPX, TAN_FULL81, A, B><<<grid, FFT_THREADS, sm, s>>>(P);    \
+    else k_zfwd4<float, SRC_CGPX, TAN_SVK, A, B><<<grid, FFT_THREADS, sm, s>>>(P);            \
     break;
     RVE_FS_SIZES(RVE_FS_ZF)
 #undef RVE_FS_ZF
@@ -381,7 +393,7 @@ void launch_zinv4(const ZinvParams<float, float>& P0, cudaStream_t s) {
   switch (g.nz) {
 #define RVE_FS_ZI(N, A, B)                                          \
   case N:                                                           \
-    k_zinv4_cgr<float, A, B><<<grid, FFT_THREADS, sm, s>>>(P);      \
+    k_zinv4_cgr<float, A, B><<<grid, FFT_THREADS, sm, s>>>(P);       \
     break;
     RVE_FS_SIZES(RVE_FS_ZI)
 #undef RVE_FS_ZI
