@@ -5,6 +5,8 @@
 // place and written back; the transposed order the forward transform leaves
 // is undone in the addressing of the global stores (forward y), loads
 // (inverse y) or of the projection (x pass).
+#include <algorithm>
+
 #include "fft_pass.cuh"
 
 namespace {
@@ -133,10 +135,42 @@ __global__ void __launch_bounds__(FFT_THREADS, (N1 * N2 > 100 ? 2 : Fs4Occ<R, N1
   }
 }
 
-// First pass of the fused float CG iteration on the four-step z DFT:
-// voxel stage (p, lagged x, tangent, p.(K:p)) into a transposed buffer
+// L2 prefetch of the first-pass inputs of a tile (r and F, after the first
+// iteration p and x, the phase bytes): every 128-byte line of each
+// component's range, addresses clamped into the range.
+template <typename R, int SRC, int TAN>
+RVE_DEV void zfwd_prefetch_tile(const ZfwdParams<R>& P, const ZfwdScalars<R>& sc, size_t v0,
+                                int nvox) {
+  if constexpr (SRC == SRC_CGPX && TAN == TAN_SVK) {
+    const size_t n = P.g.n;
+    const bool ph = P.tan.mat.phase != nullptr;
+    const int nf = sc.first ? 18 : 36;
+    const int narr = nf + (ph ? 1 : 0);
+    const int lpa = (int)(((size_t)nvox * sizeof(R)) / 128) + 2;  // lines per array (bound)
+    for (int j = threadIdx.x; j < narr * lpa; j += blockDim.x) {
+      const int a = j / lpa, q = j - a * lpa;
+      const char* lo;
+      size_t len;
+      if (a < nf) {
+        const R* b = a < 9 ? P.r : a < 18 ? P.tan.Fop : a < 27 ? P.p : P.x;
+        lo = reinterpret_cast<const char*>(b + (size_t)(a % 9) * n + v0);
+        len = (size_t)nvox * sizeof(R);
+      } else {
+        lo = reinterpret_cast<const char*>(P.tan.mat.phase + v0);
+        len = (size_t)nvox;
+      }
+      const size_t off = (size_t)q * 128 < len ? (size_t)q * 128 : len - 1;
+      prefetch_l2(lo + off);
+    }
+  }
+}
+
+// First pass of the fused float CG iteration on the four-step z DFT,
+// persistent: each thread block walks tiles of lz z-lines (stride gridDim.x)
+// -- voxel stage (p, lagged x, tangent, p.(K:p)) into a transposed buffer
 // (element z of line l at z * LP + l, LP odd), in-place DFT of the 5 lz
-// packed lines, half spectrum out.
+// packed lines, half spectrum out -- and prefetches its next tile's inputs
+// into L2 before the DFT, so that they arrive while it computes.
 template <typename R, int SRC, int TAN, int N1, int N2>
 __global__ void __launch_bounds__(FFT_THREADS, (Fs4Occ<R, N1, N2>::value))
     k_zfwd4(const ZfwdParams<R> P) {
@@ -149,47 +183,56 @@ __global__ void __launch_bounds__(FFT_THREADS, (Fs4Occ<R, N1, N2>::value))
   cplx<R>* buf = tw + ((N + 1) & ~1);
   for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = P.tw[i];
   const int nlines = P.g.nx * P.g.ny;
-  const int l0 = blockIdx.x * lz;
-  const int nl = min(lz, nlines - l0);
-  const int nvox = nl * N;
-  const size_t v0 = (size_t)l0 * N;
+  const int ntiles = (nlines + lz - 1) / lz;
   const ZfwdScalars<R> sc = zfwd_scalars<R, SRC>(P);
-  double pkp = 0.0;
-  for (int i = threadIdx.x; i < lz * N; i += blockDim.x) {
-    R out[9];
-    if (i < nvox) {
-      zfwd_voxel<R, SRC, TAN>(P, sc, v0 + i, out, pkp);
-    } else {
-#pragma unroll
-      for (int c = 0; c < 9; ++c) out[c] = 0;
-    }
-    const int li = i / N;
-    cplx<R>* e = buf + (i - li * N) * LP + li;
-#pragma unroll
-    for (int k = 0; k < 5; ++k) e[k * lz] = {out[2 * k], (2 * k + 1 < 9) ? out[2 * k + 1] : R(0)};
-  }
-  __syncthreads();
-  const LineMap lm{30, 0, 1, LP, 1};
-  fs_lines<R, N1, N2, false>(buf, lm, 5 * lz, P.g.f_fsz_L, tw);
   const int hz = P.g.hz, hzp = P.g.hzp;
   const size_t ss = P.g.sstride;
-  for (int i = threadIdx.x; i < 5 * lz * hz; i += blockDim.x) {
-    const int rest = (int)P.g.f_hz.div((unsigned)i);
-    const int kz = i - rest * hz;
-    const int k = (int)P.g.f_fsz_lz.div((unsigned)rest);
-    const int li = rest - k * lz;
-    if (li >= nl) continue;
-    const int l = k * lz + li;
-    const cplx<R> z1 = buf[fs_pos<N1, N2>(kz) * LP + l];
-    cplx<R> z2 = buf[fs_pos<N1, N2>(kz ? N - kz : 0) * LP + l];
-    z2.y = -z2.y;
-    const size_t o = (size_t)(l0 + li) * hzp + kz;
-    P.spec[(size_t)(2 * k) * ss + o] = {R(0.5) * (z1.x + z2.x), R(0.5) * (z1.y + z2.y)};
-    if (2 * k + 1 < 9) {
-      // B = (z1 - conj(z_-k)) / (2i)
-      const R dx = R(0.5) * (z1.x - z2.x), dy = R(0.5) * (z1.y - z2.y);
-      P.spec[(size_t)(2 * k + 1) * ss + o] = {dy, -dx};
+  const LineMap lm{30, 0, 1, LP, 1};
+  double pkp = 0.0;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int l0 = tile * lz;
+    const int nl = min(lz, nlines - l0);
+    const int nvox = nl * N;
+    const size_t v0 = (size_t)l0 * N;
+    for (int i = threadIdx.x; i < lz * N; i += blockDim.x) {
+      R out[9];
+      if (i < nvox) {
+        zfwd_voxel<R, SRC, TAN>(P, sc, v0 + i, out, pkp);
+      } else {
+#pragma unroll
+        for (int c = 0; c < 9; ++c) out[c] = 0;
+      }
+      const int li = i / N;
+      cplx<R>* e = buf + (i - li * N) * LP + li;
+#pragma unroll
+      for (int k = 0; k < 5; ++k) e[k * lz] = {out[2 * k], (2 * k + 1 < 9) ? out[2 * k + 1] : R(0)};
     }
+    __syncthreads();
+    const int next = tile + gridDim.x;
+    if (next < ntiles) {
+      const int nl2 = min(lz, nlines - next * lz);
+      zfwd_prefetch_tile<R, SRC, TAN>(P, sc, (size_t)next * lz * N, nl2 * N);
+    }
+    fs_lines<R, N1, N2, false>(buf, lm, 5 * lz, P.g.f_fsz_L, tw);
+    for (int i = threadIdx.x; i < 5 * lz * hz; i += blockDim.x) {
+      const int rest = (int)P.g.f_hz.div((unsigned)i);
+      const int kz = i - rest * hz;
+      const int k = (int)P.g.f_fsz_lz.div((unsigned)rest);
+      const int li = rest - k * lz;
+      if (li >= nl) continue;
+      const int l = k * lz + li;
+      const cplx<R> z1 = buf[fs_pos<N1, N2>(kz) * LP + l];
+      cplx<R> z2 = buf[fs_pos<N1, N2>(kz ? N - kz : 0) * LP + l];
+      z2.y = -z2.y;
+      const size_t o = (size_t)(l0 + li) * hzp + kz;
+      P.spec[(size_t)(2 * k) * ss + o] = {R(0.5) * (z1.x + z2.x), R(0.5) * (z1.y + z2.y)};
+      if (2 * k + 1 < 9) {
+        // B = (z1 - conj(z_-k)) / (2i)
+        const R dx = R(0.5) * (z1.x - z2.x), dy = R(0.5) * (z1.y - z2.y);
+        P.spec[(size_t)(2 * k + 1) * ss + o] = {dy, -dx};
+      }
+    }
+    __syncthreads();  // the buffer is refilled by the next tile
   }
   if (SRC == SRC_CGPX) zfwd_step_length<R>(P, pkp);
 }
@@ -367,7 +410,15 @@ void launch_zfwd4(const ZfwdParams<float>& P0, cudaStream_t s) {
   const GridGeom& g = P.g;
   P.lz = g.fsz_lz;
   const int nlines = g.nx * g.ny;
-  const int grid = (nlines + P.lz - 1) / P.lz;
+  // persistent: as many thread blocks as are resident at once
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms < 1) sms = 1;
+  }
+  const int grid = std::min((nlines + P.lz - 1) / P.lz, 3 * sms);
   const size_t sm = z4_smem(g, false);
   const bool full = P.tan.mode == TAN_FULL81;
   switch (g.nz) {
