@@ -237,9 +237,38 @@ __global__ void __launch_bounds__(FFT_THREADS, (Fs4Occ<R, N1, N2>::value))
   if (SRC == SRC_CGPX) zfwd_step_length<R>(P, pkp);
 }
 
-// Last pass of the fused float CG iteration: the r tile is prefetched with
-// cp.async while the half spectrum is expanded into the transposed order
-// and transformed back; then r -= alpha Ap in place and r.r.
+// L2 prefetch of the last pass's inputs of a tile: the tile's half spectrum
+// (per component nl consecutive rows of hzp values, contiguous) and its r
+// range.
+template <typename R>
+RVE_DEV void zinv_prefetch_tile(const ZinvParams<R, R>& P, int l0, int nl, size_t v0, int nvox) {
+  const size_t ss = P.g.sstride;
+  const int hzp = P.g.hzp;
+  const size_t slen = (size_t)nl * hzp * sizeof(cplx<R>);
+  const size_t rlen = (size_t)nvox * sizeof(R);
+  const int lps = (int)(slen / 128) + 2, lpr = (int)(rlen / 128) + 2;
+  for (int j = threadIdx.x; j < 9 * (lps + lpr); j += blockDim.x) {
+    const int c = j / (lps + lpr), q = j - c * (lps + lpr);
+    const char* lo;
+    size_t len, off;
+    if (q < lps) {
+      lo = reinterpret_cast<const char*>(P.spec + (size_t)c * ss + (size_t)l0 * hzp);
+      len = slen;
+      off = (size_t)q * 128;
+    } else {
+      lo = reinterpret_cast<const char*>(P.r_out + (size_t)c * P.g.n + v0);
+      len = rlen;
+      off = (size_t)(q - lps) * 128;
+    }
+    prefetch_l2(lo + (off < len ? off : len - 1));
+  }
+}
+
+// Last pass of the fused float CG iteration, persistent like k_zfwd4: per
+// tile the r range is fetched with cp.async while the half spectrum is
+// expanded into the transposed order and transformed back; then
+// r -= alpha Ap in place and r.r.  The next tile's inputs are prefetched
+// into L2 before the DFT stage.
 template <typename R, int N1, int N2>
 __global__ void __launch_bounds__(FFT_THREADS, (Fs4Occ<R, N1, N2>::value))
     k_zinv4_cgr(const ZinvParams<R, R> P) {
@@ -254,86 +283,83 @@ __global__ void __launch_bounds__(FFT_THREADS, (Fs4Occ<R, N1, N2>::value))
   const size_t n = P.g.n;
   const size_t ss = P.g.sstride;
   const int nlines = P.g.nx * P.g.ny;
-  const int l0 = blockIdx.x * lz;
-  const int nl = min(lz, nlines - l0);
-  const int nvox = nl * N;
-  const size_t v0 = (size_t)l0 * N;
-  for (int c = 0; c < 9; ++c)
-    for (int i = threadIdx.x; i < nvox; i += blockDim.x)
-      cp_async4(rt + c * lz * N + i, P.r_out + (size_t)c * n + v0 + i);
-  cp_async_commit();
-  // the tile's half spectrum: per component nl consecutive rows of hzp
-  // values, contiguous; L2 prefetch of all its 128-byte lines
-  {
-    const int lines_per_comp = (int)(((size_t)nl * hzp * sizeof(cplx<R>) + 127) / 128);
-    for (int j = threadIdx.x; j < 9 * lines_per_comp; j += blockDim.x) {
-      const int c = j / lines_per_comp;
-      const int q = j - c * lines_per_comp;
-      const char* base = reinterpret_cast<const char*>(P.spec + (size_t)c * ss + (size_t)l0 * hzp);
-      const size_t off = min((size_t)q * 128, (size_t)nl * hzp * sizeof(cplx<R>) - 1);
-      prefetch_l2(base + off);
-    }
-  }
+  const int ntiles = (nlines + lz - 1) / lz;
   for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = P.tw[i];
-  // full z spectrum of the packed lines z = a + i b, written transposed
-  constexpr int U = 4;  // (A, B) pairs in flight per thread
-  const int nthr = blockDim.x;
-  const int totl = 5 * lz * hz;
-  for (int i0 = threadIdx.x; i0 < totl; i0 += U * nthr) {
-    cplx<R> A[U], B[U];
+  const R alpha = (R)P.st->alpha;
+  const LineMap lm{30, 0, 1, LP, 1};
+  double acc = 0.0;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int l0 = tile * lz;
+    const int nl = min(lz, nlines - l0);
+    const int nvox = nl * N;
+    const size_t v0 = (size_t)l0 * N;
+    for (int c = 0; c < 9; ++c)
+      for (int i = threadIdx.x; i < nvox; i += blockDim.x)
+        cp_async4(rt + c * lz * N + i, P.r_out + (size_t)c * n + v0 + i);
+    cp_async_commit();
+    // full z spectrum of the packed lines z = a + i b, written transposed
+    constexpr int U = 4;  // (A, B) pairs in flight per thread
+    const int nthr = blockDim.x;
+    const int totl = 5 * lz * hz;
+    for (int i0 = threadIdx.x; i0 < totl; i0 += U * nthr) {
+      cplx<R> A[U], B[U];
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int i = i0 + u * nthr;
-      const int rest = (int)P.g.f_hz.div((unsigned)i);
-      const int kz = i - rest * hz;
-      const int k = (int)P.g.f_fsz_lz.div((unsigned)rest);
-      const int li = rest - k * lz;
-      A[u] = {R(0), R(0)};
-      B[u] = {R(0), R(0)};
-      if (i < totl && li < nl) {
-        const size_t o = (size_t)(l0 + li) * hzp + kz;
-        A[u] = P.spec[(size_t)(2 * k) * ss + o];
-        if (2 * k + 1 < 9) B[u] = P.spec[(size_t)(2 * k + 1) * ss + o];
+      for (int u = 0; u < U; ++u) {
+        const int i = i0 + u * nthr;
+        const int rest = (int)P.g.f_hz.div((unsigned)i);
+        const int kz = i - rest * hz;
+        const int k = (int)P.g.f_fsz_lz.div((unsigned)rest);
+        const int li = rest - k * lz;
+        A[u] = {R(0), R(0)};
+        B[u] = {R(0), R(0)};
+        if (i < totl && li < nl) {
+          const size_t o = (size_t)(l0 + li) * hzp + kz;
+          A[u] = P.spec[(size_t)(2 * k) * ss + o];
+          if (2 * k + 1 < 9) B[u] = P.spec[(size_t)(2 * k + 1) * ss + o];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int i = i0 + u * nthr;
+        if (i >= totl) continue;
+        const int rest = (int)P.g.f_hz.div((unsigned)i);
+        const int kz = i - rest * hz;
+        const int k = (int)P.g.f_fsz_lz.div((unsigned)rest);
+        const int li = rest - k * lz;
+        const int l = k * lz + li;
+        buf[fs_pos<N1, N2>(kz) * LP + l] = {A[u].x - B[u].y, A[u].y + B[u].x};
+        if (kz > 0) buf[fs_pos<N1, N2>(N - kz) * LP + l] = {A[u].x + B[u].y, B[u].x - A[u].y};
       }
     }
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int i = i0 + u * nthr;
-      if (i >= totl) continue;
-      const int rest = (int)P.g.f_hz.div((unsigned)i);
-      const int kz = i - rest * hz;
-      const int k = (int)P.g.f_fsz_lz.div((unsigned)rest);
-      const int li = rest - k * lz;
-      const int l = k * lz + li;
-      buf[fs_pos<N1, N2>(kz) * LP + l] = {A[u].x - B[u].y, A[u].y + B[u].x};
-      if (kz > 0) buf[fs_pos<N1, N2>(N - kz) * LP + l] = {A[u].x + B[u].y, B[u].x - A[u].y};
+    __syncthreads();
+    const int next = tile + gridDim.x;
+    if (next < ntiles) {
+      const int nl2 = min(lz, nlines - next * lz);
+      zinv_prefetch_tile<R>(P, next * lz, nl2, (size_t)next * lz * N, nl2 * N);
     }
-  }
-  __syncthreads();
-  const LineMap lm{30, 0, 1, LP, 1};
-  fs_lines<R, N1, N2, true>(buf, lm, 5 * lz, P.g.f_fsz_L, tw);
-  cp_async_wait<0>();
-  __syncthreads();
-  const R alpha = (R)P.st->alpha;
-  double acc = 0.0;
-  for (int i = threadIdx.x; i < nvox; i += blockDim.x) {
-    const int li = i / N;
-    const cplx<R>* e = buf + (i - li * N) * LP + li;
-    R out[9];
+    fs_lines<R, N1, N2, true>(buf, lm, 5 * lz, P.g.f_fsz_L, tw);
+    cp_async_wait<0>();
+    __syncthreads();
+    for (int i = threadIdx.x; i < nvox; i += blockDim.x) {
+      const int li = i / N;
+      const cplx<R>* e = buf + (i - li * N) * LP + li;
+      R out[9];
 #pragma unroll
-    for (int k = 0; k < 5; ++k) {
-      const cplx<R> z = e[k * lz];
-      out[2 * k] = z.x;
-      if (2 * k + 1 < 9) out[2 * k + 1] = z.y;
-    }
-    R s = 0;
+      for (int k = 0; k < 5; ++k) {
+        const cplx<R> z = e[k * lz];
+        out[2 * k] = z.x;
+        if (2 * k + 1 < 9) out[2 * k + 1] = z.y;
+      }
+      R s = 0;
 #pragma unroll
-    for (int c = 0; c < 9; ++c) {
-      const R rn = fma(-alpha, out[c], rt[c * lz * N + i]);
-      P.r_out[(size_t)c * n + v0 + i] = rn;
-      s = fma(rn, rn, s);
+      for (int c = 0; c < 9; ++c) {
+        const R rn = fma(-alpha, out[c], rt[c * lz * N + i]);
+        P.r_out[(size_t)c * n + v0 + i] = rn;
+        s = fma(rn, rn, s);
+      }
+      acc += (double)s;
     }
-    acc += (double)s;
+    __syncthreads();  // buffer and r tile are refilled by the next tile
   }
   double v1[1] = {acc}, tot[1];
   if (last_block_sum<1>(v1, P.partials, &P.st->counter[SLOT_RR], tot) && threadIdx.x == 0)
@@ -399,6 +425,20 @@ void launch_fft_x4(const GridGeom& g, double scale, cplx<float>* spec, const int
   }
 }
 
+// SMs of the current device (persistent grids: three blocks per SM)
+static int sm_count() {
+  static int cache[64] = {0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) dev = 0;
+  if (!cache[dev]) {
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cache[dev] = sms > 0 ? sms : 1;
+  }
+  return cache[dev];
+}
+
 static size_t z4_smem(const GridGeom& g, bool with_r) {
   const int LP = (5 * g.fsz_lz) | 1;
   return sizeof(cplx<float>) * ((size_t)((g.nz + 1) & ~1) + (size_t)g.nz * LP) +
@@ -411,14 +451,7 @@ void launch_zfwd4(const ZfwdParams<float>& P0, cudaStream_t s) {
   P.lz = g.fsz_lz;
   const int nlines = g.nx * g.ny;
   // persistent: as many thread blocks as are resident at once
-  static int sms = 0;
-  if (!sms) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (sms < 1) sms = 1;
-  }
-  const int grid = std::min((nlines + P.lz - 1) / P.lz, 3 * sms);
+  const int grid = std::min((nlines + P.lz - 1) / P.lz, 3 * sm_count());
   const size_t sm = z4_smem(g, false);
   const bool full = P.tan.mode == TAN_FULL81;
   switch (g.nz) {
@@ -439,7 +472,7 @@ void launch_zinv4(const ZinvParams<float, float>& P0, cudaStream_t s) {
   const GridGeom& g = P.g;
   P.lz = g.fsz_lz;
   const int nlines = g.nx * g.ny;
-  const int grid = (nlines + P.lz - 1) / P.lz;
+  const int grid = std::min((nlines + P.lz - 1) / P.lz, 3 * sm_count());
   const size_t sm = z4_smem(g, true);
   switch (g.nz) {
 #define RVE_FS_ZI(N, A, B)                                          \
