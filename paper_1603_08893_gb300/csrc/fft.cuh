@@ -420,78 +420,93 @@ __device__ __noinline__ cplx<R>* fft_lines_call(cplx<R>* a, cplx<R>* b, const Li
 }
 
 // ---------------------------------------------------------------------------
-// In-place DFTs of compile-time length N = N1 N2 on L lines in one shared
-// buffer (line l, element e at lm.base(l) + e lm.es; consecutive threads take
-// consecutive lines).  Four-step split with n = N2 m + n2, k = k1 + N1 k2:
+// In-place DFTs of compile-time length N = N1 N2 on the L lines of a
+// compile-time layout LM in one shared buffer (line l, element e at
+// LM::base(l) + e LM::ES; consecutive threads take consecutive lines, and
+// every shared-memory offset inside a work item is a constant).  Four-step
+// split with n = N2 m + n2, k = k1 + N1 k2:
 //   phase A (per line and n2):  Y_n2(k1) = w_N^(n2 k1) sum_m w_N1^(m k1) x_(N2 m + n2)
 //   phase B (per line and k1):  X_(k1 + N1 k2) = sum_n2 w_N2^(n2 k2) Y_n2(k1)
 // Each work item reads and writes the same N1 (phase A) or N2 (phase B)
 // positions, so no second buffer is needed; the forward result is stored
 // transposed: X_(k1 + N1 k2) at position N2 k1 + k2 (fs_freq / fs_pos).  The
 // inverse runs the conjugate phases in reverse order and takes that
-// transposed order back to natural order.  tw[k] = exp(-2 pi i k / N).
+// transposed order back to natural order.  tw2[n2 N1 + k1] = w_N^(n2 k1).
 // ---------------------------------------------------------------------------
+template <int G_, int GS_, int LS_, int ES_, int L_>
+struct FsLayout {
+  static constexpr int G = G_, GS = GS_, LS = LS_, ES = ES_, L = L_;
+  static RVE_DEV int base(int l) { return (l / G) * GS + (l % G) * LS; }
+};
+
 template <int N1, int N2>
 RVE_DEV int fs_freq(int pos) { return pos / N2 + N1 * (pos % N2); }
 template <int N1, int N2>
 RVE_DEV int fs_pos(int k) { return N2 * (k % N1) + k / N1; }
 
-template <typename R, int N1, int N2, bool INV>
-RVE_DEV void fs_phase_a(cplx<R>* buf, const LineMap& lm, int L, const FastDiv fL,
-                        const cplx<R>* tw) {
-  const int total = L * N2;
+// tw2[n2 N1 + k1] = tw[n2 k1] (tw[k] = exp(-2 pi i k / N)), built by the block
+template <typename R, int N1, int N2>
+RVE_DEV void fs_twiddles(cplx<R>* tw2, const cplx<R>* tw) {
+  for (int j = threadIdx.x; j < N1 * N2; j += blockDim.x) {
+    const int n2 = j / N1, k1 = j - (j / N1) * N1;
+    tw2[j] = tw[n2 * k1];
+  }
+}
+
+template <typename R, int N1, int N2, bool INV, typename LM>
+RVE_DEV void fs_phase_a(cplx<R>* buf, const cplx<R>* tw2) {
+  constexpr int total = LM::L * N2;
   for (int i = threadIdx.x; i < total; i += blockDim.x) {
-    const int n2 = (int)fL.div((unsigned)i);
-    const int l = i - n2 * L;
-    cplx<R>* line = buf + lm.base(l) + n2 * lm.es;
-    const int st = N2 * lm.es;
+    const int n2 = i / LM::L;
+    const int l = i - n2 * LM::L;
+    cplx<R>* line = buf + LM::base(l) + n2 * LM::ES;
+    const cplx<R>* w = tw2 + n2 * N1;
     cplx<R> v[N1];
 #pragma unroll
-    for (int m = 0; m < N1; ++m) v[m] = line[m * st];
+    for (int m = 0; m < N1; ++m) v[m] = line[m * N2 * LM::ES];
     if (INV && n2 != 0) {
 #pragma unroll
-      for (int k1 = 1; k1 < N1; ++k1) v[k1] = c_mulc(v[k1], tw[n2 * k1]);
+      for (int k1 = 1; k1 < N1; ++k1) v[k1] = c_mulc(v[k1], w[k1]);
     }
     dft_reg<R, N1, INV>(v);
     if (!INV && n2 != 0) {
 #pragma unroll
-      for (int k1 = 1; k1 < N1; ++k1) v[k1] = c_mul(v[k1], tw[n2 * k1]);
+      for (int k1 = 1; k1 < N1; ++k1) v[k1] = c_mul(v[k1], w[k1]);
     }
 #pragma unroll
-    for (int m = 0; m < N1; ++m) line[m * st] = v[m];
+    for (int m = 0; m < N1; ++m) line[m * N2 * LM::ES] = v[m];
   }
 }
 
-template <typename R, int N1, int N2, bool INV>
-RVE_DEV void fs_phase_b(cplx<R>* buf, const LineMap& lm, int L, const FastDiv fL) {
-  const int total = L * N1;
+template <typename R, int N1, int N2, bool INV, typename LM>
+RVE_DEV void fs_phase_b(cplx<R>* buf) {
+  constexpr int total = LM::L * N1;
   for (int i = threadIdx.x; i < total; i += blockDim.x) {
-    const int k1 = (int)fL.div((unsigned)i);
-    const int l = i - k1 * L;
-    cplx<R>* line = buf + lm.base(l) + N2 * k1 * lm.es;
+    const int k1 = i / LM::L;
+    const int l = i - k1 * LM::L;
+    cplx<R>* line = buf + LM::base(l) + N2 * k1 * LM::ES;
     cplx<R> u[N2];
 #pragma unroll
-    for (int j = 0; j < N2; ++j) u[j] = line[j * lm.es];
+    for (int j = 0; j < N2; ++j) u[j] = line[j * LM::ES];
     dft_reg<R, N2, INV>(u);
 #pragma unroll
-    for (int j = 0; j < N2; ++j) line[j * lm.es] = u[j];
+    for (int j = 0; j < N2; ++j) line[j * LM::ES] = u[j];
   }
 }
 
 // Forward: natural order in, transposed order out.  Inverse: transposed in,
 // natural out.  Caller synchronises before; returns after a barrier.
-template <typename R, int N1, int N2, bool INV>
-RVE_DEV void fs_lines(cplx<R>* buf, const LineMap& lm, int L, const FastDiv fL,
-                      const cplx<R>* tw) {
+template <typename R, int N1, int N2, bool INV, typename LM>
+RVE_DEV void fs_lines(cplx<R>* buf, const cplx<R>* tw2) {
   if (!INV) {
-    fs_phase_a<R, N1, N2, false>(buf, lm, L, fL, tw);
+    fs_phase_a<R, N1, N2, false, LM>(buf, tw2);
     __syncthreads();
-    if (N2 > 1) fs_phase_b<R, N1, N2, false>(buf, lm, L, fL);
+    if (N2 > 1) fs_phase_b<R, N1, N2, false, LM>(buf);
     __syncthreads();
   } else {
-    if (N2 > 1) fs_phase_b<R, N1, N2, true>(buf, lm, L, fL);
+    if (N2 > 1) fs_phase_b<R, N1, N2, true, LM>(buf);
     __syncthreads();
-    fs_phase_a<R, N1, N2, true>(buf, lm, L, fL, tw);
+    fs_phase_a<R, N1, N2, true, LM>(buf, tw2);
     __syncthreads();
   }
 }

@@ -50,6 +50,17 @@ struct GridGeom {
   X(243, 9, 27)         \
   X(315, 21, 15)
 
+// Tile shapes of the four-step kernels, compile-time functions of the axis
+// length so that every shared-memory offset of a DFT work item is constant.
+constexpr int fs_y_t() { return 16; }  // kz values per y tile row (128 bytes)
+constexpr int fs_y_grp(int n) { return 49152 / (8 * n * 16) > 1 ? 49152 / (8 * n * 16) : 1; }
+constexpr int fs_x_t(int n) {
+  return 8 * 3 * n * 16 <= 65536 ? 16 : (8 * 3 * n * 8 <= 65536 ? 8 : 4);
+}
+constexpr int fs_z_lz(int n) {
+  return (32768 / (8 * n) - 1) / 5 < 1 ? 1 : ((32768 / (8 * n) - 1) / 5 > 64 ? 64 : (32768 / (8 * n) - 1) / 5);
+}
+
 inline int fs_split_n1(int n) {
   switch (n) {
 #define RVE_FS_CASE(N, A, B) \

@@ -17,57 +17,56 @@ struct Fs4Occ {
   static constexpr int value = (sizeof(R) == 4 && N1 <= 27 && N2 <= 27) ? 3 : 2;
 };
 
-// Complex DFT along y on tiles of (grp component-x rows) x ny x (T kz).
-// Forward: natural rows in, transposed order in shared memory, natural rows
-// out.  Inverse: rows loaded into transposed positions, natural out.
+// Complex DFT along y on tiles of (GRP component-x rows) x ny x (T kz),
+// T and GRP compile-time (fs_y_t, fs_y_grp).  Forward: natural rows in,
+// transposed order in shared memory, natural rows out.  Inverse: rows loaded
+// into transposed positions, natural out.
 template <typename R, int N1, int N2, bool INV>
-__global__ void __launch_bounds__(FFT_THREADS, (Fs4Occ<R, N1, N2>::value))
+__global__ void __launch_bounds__(FFT_THREADS, (Fs4Occ<R, N1, N2>::value) + (N1 * N2 <= 125 ? 1 : 0))
     k_fft_y4(const LineParams<R> P) {
   constexpr int N = N1 * N2;
+  constexpr int T = fs_y_t(), GRP = fs_y_grp(N);
+  using LM = FsLayout<T, N * T, 1, T, GRP * T>;
   if (P.done && *P.done) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int T = P.t, grp = P.grp;
-  const int ts = __ffs(T) - 1;
-  cplx<R>* tw = reinterpret_cast<cplx<R>*>(smem_raw);
-  cplx<R>* buf = tw + ((N + 1) & ~1);
-  const int hz = P.g.hz, hzp = P.g.hzp;
+  cplx<R>* tw2 = reinterpret_cast<cplx<R>*>(smem_raw);
+  cplx<R>* buf = tw2 + ((N + 1) & ~1);
+  const int hz = P.g.hz, hzp = P.g.hzp;  // kz extent (z axis), not this axis
   const int ngroups = 9 * P.g.nx;
-  const int ntk = (hz + T - 1) >> ts;
+  const int ntk = (hz + T - 1) / T;
   const int tile = blockIdx.x;
   const int tg = (int)P.g.f_fsy_ntk.div((unsigned)tile);
-  const int k0 = (tile - tg * ntk) * T, g0 = tg * grp;
-  const int ng = min(grp, ngroups - g0);
+  const int k0 = (tile - tg * ntk) * T, g0 = tg * GRP;
+  const int ng = min(GRP, ngroups - g0);
   cplx<R>* gbase = P.spec + (size_t)g0 * N * hzp + k0;
   {
     constexpr int EPC = 16 / sizeof(cplx<R>);
-    const int cpr = T / EPC;
-    const int cs = __ffs(cpr) - 1;
-    const int nch = ng * N * cpr;
+    constexpr int CPR = T / EPC;  // 16-byte chunks per row
+    const int nch = ng * N * CPR;
     for (int c = threadIdx.x; c < nch; c += blockDim.x) {
-      const int row = c >> cs;
-      const int t = (c & (cpr - 1)) * EPC;
+      const int row = c / CPR;
+      const int t = (c - row * CPR) * EPC;
       const int gi = row / N;
       const int y = row - gi * N;
       const int srow = INV ? gi * N + fs_pos<N1, N2>(y) : row;
       const bool ok = (k0 + t) < hzp;
       const cplx<R>* src = ok ? gbase + (size_t)row * hzp + t : P.spec;
-      cp_async16(buf + (srow << ts) + t, src, ok ? 16 : 0);
+      cp_async16(buf + srow * T + t, src, ok ? 16 : 0);
     }
   }
   cp_async_commit();
-  for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = P.tw[i];
+  fs_twiddles<R, N1, N2>(tw2, P.tw);
   cp_async_wait<0>();
   __syncthreads();
-  const LineMap lm{ts, N * T, 1, T, 1};
-  fs_lines<R, N1, N2, INV>(buf, lm, grp * T, P.g.f_fsy_L, tw);
+  fs_lines<R, N1, N2, INV, LM>(buf, tw2);
   // 16-byte stores of kz pairs; a pair may reach one column into the row
   // padding (kz = hz when hz is odd), which no pass reads as data
   const int tc = min(T, hz - k0);
   const int tot2 = ng * N * T / 2;
   for (int i2 = threadIdx.x; i2 < tot2; i2 += blockDim.x) {
     const int i = 2 * i2;
-    const int t = i & (T - 1);
-    const int srow = i >> ts;
+    const int t = i % T;
+    const int srow = i / T;
     const int gi = srow / N;
     const int pos = srow - gi * N;
     const int y = INV ? pos : fs_freq<N1, N2>(pos);
@@ -79,19 +78,20 @@ __global__ void __launch_bounds__(FFT_THREADS, (Fs4Occ<R, N1, N2>::value))
 
 // Forward DFT along x, projection A_ij <- xi_j (sum_l xi_l A_il) / |xi|^2
 // (Eq. G_red) in the transposed order, inverse DFT along x; tile = (tensor
-// row i) x nx x (T kz) for one ky.
+// row i) x nx x (T kz) for one ky, T compile-time (fs_x_t).
 template <typename R, int N1, int N2>
-__global__ void __launch_bounds__(FFT_THREADS, (N1 * N2 > 100 ? 2 : Fs4Occ<R, N1, N2>::value))
+__global__ void __launch_bounds__(FFT_THREADS, (Fs4Occ<R, N1, N2>::value))
     k_fft_x4(const LineParams<R> P) {
   constexpr int N = N1 * N2;
+  constexpr int T = fs_x_t(N);
+  using LM = FsLayout<T, N * T, 1, T, 3 * T>;
   if (P.done && *P.done) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int ny = P.g.ny, T = P.t;
-  const int ts = __ffs(T) - 1;
-  cplx<R>* tw = reinterpret_cast<cplx<R>*>(smem_raw);
-  cplx<R>* buf = tw + ((N + 1) & ~1);
+  cplx<R>* tw2 = reinterpret_cast<cplx<R>*>(smem_raw);
+  cplx<R>* buf = tw2 + ((N + 1) & ~1);
+  const int ny = P.g.ny;
   const int hz = P.g.hz, hzp = P.g.hzp;
-  const int ntk = (hz + T - 1) >> ts;
+  const int ntk = (hz + T - 1) / T;
   const size_t rs = (size_t)ny * hzp;  // stride of spectrum rows (c*nx + x)
   const int tile = blockIdx.x;
   const int q = (int)P.g.f_fsx_ntk.div((unsigned)tile);
@@ -99,18 +99,27 @@ __global__ void __launch_bounds__(FFT_THREADS, (N1 * N2 > 100 ? 2 : Fs4Occ<R, N1
   const int irow = (int)P.g.f_ny.div((unsigned)q);
   const int y = q - irow * ny;
   cplx<R>* gbase = P.spec + (size_t)(3 * irow) * N * rs + (size_t)y * hzp + k0;
-  issue_tile<R>(buf, gbase, rs, 3 * N, T, ts, k0, hzp, P.spec);
+  {
+    constexpr int EPC = 16 / sizeof(cplx<R>);
+    constexpr int CPR = T / EPC;
+    for (int c = threadIdx.x; c < 3 * N * CPR; c += blockDim.x) {
+      const int row = c / CPR;
+      const int t = (c - row * CPR) * EPC;
+      const bool ok = (k0 + t) < hzp;
+      const cplx<R>* src = ok ? gbase + (size_t)row * rs + t : P.spec;
+      cp_async16(buf + row * T + t, src, ok ? 16 : 0);
+    }
+  }
   cp_async_commit();
-  for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = P.tw[i];
+  fs_twiddles<R, N1, N2>(tw2, P.tw);
   cp_async_wait<0>();
   __syncthreads();
-  const LineMap lm{ts, N * T, 1, T, 1};
-  fs_lines<R, N1, N2, false>(buf, lm, 3 * T, P.g.f_fsx_L, tw);
+  fs_lines<R, N1, N2, false, LM>(buf, tw2);
   const R qy = signed_freq<R>(y, ny) / (R)ny;
   const R sc = (R)P.scale;
   for (int i = threadIdx.x; i < N * T; i += blockDim.x) {
-    const int t = i & (T - 1);
-    const int kx = fs_freq<N1, N2>(i >> ts);
+    const int t = i % T;
+    const int kx = fs_freq<N1, N2>(i / T);
     const R qx = signed_freq<R>(kx, N) / (R)N;
     const R qz = (R)(k0 + t) / (R)P.g.nz;
     const R q2 = qx * qx + qy * qy + qz * qz;
@@ -123,14 +132,14 @@ __global__ void __launch_bounds__(FFT_THREADS, (N1 * N2 > 100 ? 2 : Fs4Occ<R, N1
     buf[2 * N * T + i] = {sx * qz, sy * qz};
   }
   __syncthreads();
-  fs_lines<R, N1, N2, true>(buf, lm, 3 * T, P.g.f_fsx_L, tw);
+  fs_lines<R, N1, N2, true, LM>(buf, tw2);
   const int tc = min(T, hz - k0);
   const int tot2 = 3 * N * T / 2;
   for (int i2 = threadIdx.x; i2 < tot2; i2 += blockDim.x) {
     const int i = 2 * i2;
-    const int t = i & (T - 1);
+    const int t = i % T;
     if (t < tc)
-      *reinterpret_cast<float4*>(gbase + (size_t)(i >> ts) * rs + t) =
+      *reinterpret_cast<float4*>(gbase + (size_t)(i / T) * rs + t) =
           *reinterpret_cast<const float4*>(buf + i);
   }
 }
@@ -175,19 +184,18 @@ template <typename R, int SRC, int TAN, int N1, int N2>
 __global__ void __launch_bounds__(FFT_THREADS, (Fs4Occ<R, N1, N2>::value))
     k_zfwd4(const ZfwdParams<R> P) {
   constexpr int N = N1 * N2;
+  constexpr int lz = fs_z_lz(N), LP = (5 * lz) | 1, hz = N / 2 + 1;
+  using LM = FsLayout<5 * lz, 0, 1, LP, 5 * lz>;
   if (P.done && *P.done) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int lz = P.lz;
-  const int LP = (5 * lz) | 1;
-  cplx<R>* tw = reinterpret_cast<cplx<R>*>(smem_raw);
-  cplx<R>* buf = tw + ((N + 1) & ~1);
-  for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = P.tw[i];
+  cplx<R>* tw2 = reinterpret_cast<cplx<R>*>(smem_raw);
+  cplx<R>* buf = tw2 + ((N + 1) & ~1);
+  fs_twiddles<R, N1, N2>(tw2, P.tw);
   const int nlines = P.g.nx * P.g.ny;
   const int ntiles = (nlines + lz - 1) / lz;
   const ZfwdScalars<R> sc = zfwd_scalars<R, SRC>(P);
-  const int hz = P.g.hz, hzp = P.g.hzp;
+  const int hzp = P.g.hzp;
   const size_t ss = P.g.sstride;
-  const LineMap lm{30, 0, 1, LP, 1};
   double pkp = 0.0;
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int l0 = tile * lz;
@@ -213,11 +221,11 @@ __global__ void __launch_bounds__(FFT_THREADS, (Fs4Occ<R, N1, N2>::value))
       const int nl2 = min(lz, nlines - next * lz);
       zfwd_prefetch_tile<R, SRC, TAN>(P, sc, (size_t)next * lz * N, nl2 * N);
     }
-    fs_lines<R, N1, N2, false>(buf, lm, 5 * lz, P.g.f_fsz_L, tw);
+    fs_lines<R, N1, N2, false, LM>(buf, tw2);
     for (int i = threadIdx.x; i < 5 * lz * hz; i += blockDim.x) {
-      const int rest = (int)P.g.f_hz.div((unsigned)i);
+      const int rest = i / hz;
       const int kz = i - rest * hz;
-      const int k = (int)P.g.f_fsz_lz.div((unsigned)rest);
+      const int k = rest / lz;
       const int li = rest - k * lz;
       if (li >= nl) continue;
       const int l = k * lz + li;
@@ -273,20 +281,20 @@ template <typename R, int N1, int N2>
 __global__ void __launch_bounds__(FFT_THREADS, (Fs4Occ<R, N1, N2>::value))
     k_zinv4_cgr(const ZinvParams<R, R> P) {
   constexpr int N = N1 * N2;
+  constexpr int lz = fs_z_lz(N), LP = (5 * lz) | 1, hz = N / 2 + 1;
+  using LM = FsLayout<5 * lz, 0, 1, LP, 5 * lz>;
   if (P.done && *P.done) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int lz = P.lz, hz = P.g.hz, hzp = P.g.hzp;
-  const int LP = (5 * lz) | 1;
-  cplx<R>* tw = reinterpret_cast<cplx<R>*>(smem_raw);
-  cplx<R>* buf = tw + ((N + 1) & ~1);
+  const int hzp = P.g.hzp;
+  cplx<R>* tw2 = reinterpret_cast<cplx<R>*>(smem_raw);
+  cplx<R>* buf = tw2 + ((N + 1) & ~1);
   R* rt = reinterpret_cast<R*>(buf + (size_t)N * LP);  // [9][lz N]
   const size_t n = P.g.n;
   const size_t ss = P.g.sstride;
   const int nlines = P.g.nx * P.g.ny;
   const int ntiles = (nlines + lz - 1) / lz;
-  for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = P.tw[i];
+  fs_twiddles<R, N1, N2>(tw2, P.tw);
   const R alpha = (R)P.st->alpha;
-  const LineMap lm{30, 0, 1, LP, 1};
   double acc = 0.0;
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int l0 = tile * lz;
@@ -306,9 +314,9 @@ __global__ void __launch_bounds__(FFT_THREADS, (Fs4Occ<R, N1, N2>::value))
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         const int i = i0 + u * nthr;
-        const int rest = (int)P.g.f_hz.div((unsigned)i);
+        const int rest = i / hz;
         const int kz = i - rest * hz;
-        const int k = (int)P.g.f_fsz_lz.div((unsigned)rest);
+        const int k = rest / lz;
         const int li = rest - k * lz;
         A[u] = {R(0), R(0)};
         B[u] = {R(0), R(0)};
@@ -322,9 +330,9 @@ __global__ void __launch_bounds__(FFT_THREADS, (Fs4Occ<R, N1, N2>::value))
       for (int u = 0; u < U; ++u) {
         const int i = i0 + u * nthr;
         if (i >= totl) continue;
-        const int rest = (int)P.g.f_hz.div((unsigned)i);
+        const int rest = i / hz;
         const int kz = i - rest * hz;
-        const int k = (int)P.g.f_fsz_lz.div((unsigned)rest);
+        const int k = rest / lz;
         const int li = rest - k * lz;
         const int l = k * lz + li;
         buf[fs_pos<N1, N2>(kz) * LP + l] = {A[u].x - B[u].y, A[u].y + B[u].x};
@@ -337,7 +345,7 @@ __global__ void __launch_bounds__(FFT_THREADS, (Fs4Occ<R, N1, N2>::value))
       const int nl2 = min(lz, nlines - next * lz);
       zinv_prefetch_tile<R>(P, next * lz, nl2, (size_t)next * lz * N, nl2 * N);
     }
-    fs_lines<R, N1, N2, true>(buf, lm, 5 * lz, P.g.f_fsz_L, tw);
+    fs_lines<R, N1, N2, true, LM>(buf, tw2);
     cp_async_wait<0>();
     __syncthreads();
     for (int i = threadIdx.x; i < nvox; i += blockDim.x) {

@@ -132,9 +132,9 @@ bool make_geom(int nx, int ny, int nz, GridGeom* g) {
   // the tile fits 48-64 KB, about 48 lines per CTA
   g->fsy_n1 = fs_split_n1(ny);
   g->fsx_n1 = fs_split_n1(nx);
-  g->fsy_t = 16;
-  g->fsy_grp = std::max(1, std::min(9 * nx, (int)(49152 / (8 * (size_t)ny * g->fsy_t))));
-  g->fsx_t = 8 * 3 * (size_t)nx * 16 <= 65536 ? 16 : (8 * 3 * (size_t)nx * 8 <= 65536 ? 8 : 4);
+  g->fsy_t = fs_y_t();
+  g->fsy_grp = fs_y_grp(ny);
+  g->fsx_t = fs_x_t(nx);
   if (8 * ((size_t)nx + 1 + 3 * (size_t)nx * g->fsx_t) > 200 * 1024) g->fsx_n1 = 0;
   g->f_fsy_ntk = make_fastdiv((unsigned)((g->hz + g->fsy_t - 1) / g->fsy_t));
   g->f_fsx_ntk = make_fastdiv((unsigned)((g->hz + g->fsx_t - 1) / g->fsx_t));
@@ -143,7 +143,7 @@ bool make_geom(int nx, int ny, int nz, GridGeom* g) {
   // four-step float z passes of the CG iteration: one buffer of
   // 5 lz lines x nz (about 32 KB) plus, in the last pass, the r tile
   g->fsz_n1 = fs_split_n1(nz);
-  g->fsz_lz = std::max(1, std::min(64, (int)((32768 / (8 * (size_t)nz) - 1) / 5)));
+  g->fsz_lz = fs_z_lz(nz);
   g->f_fsz_L = make_fastdiv((unsigned)(5 * g->fsz_lz));
   g->f_fsz_lz = make_fastdiv((unsigned)g->fsz_lz);
   return true;

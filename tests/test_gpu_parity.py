@@ -83,7 +83,7 @@ def test_operator_fp64_matches_oracle(shape, tangent):
 
 
 @pytest.mark.parametrize("shape", [(9, 11, 13), (31, 31, 31), (63, 63, 63), (27, 3, 125),
-                                   (81, 75, 7), (7, 5, 225)])
+                                   (81, 75, 7), (7, 5, 225), (15, 21, 125), (45, 63, 27)])
 @pytest.mark.parametrize("tangent", ["recompute", "full81"])
 def test_operator_mixed_matches_oracle(shape, tangent):
     r, F, K, mu, rng = _random_problem(shape, 4, "mixed", tangent)
