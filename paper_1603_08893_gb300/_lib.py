@@ -38,6 +38,7 @@ class rve_options(C.Structure):
                 ("max_newton", C.c_int), ("max_cg", C.c_int),
                 ("cg_tol_floor", C.c_double), ("cg_atol", C.c_double),
                 ("mixed_refine", C.c_int), ("residual", C.c_int),
+                ("autotune", C.c_int),
                 ("stream", C.c_void_p), ("workspace", C.c_void_p),
                 ("workspace_bytes", C.c_size_t)]
 
@@ -80,6 +81,7 @@ _SIGS = {
     "rve_last_error": (C.c_char_p, [_H]),
     "rve_status_string": (C.c_char_p, [C.c_int]),
     "rve_launch_count": (C.c_int, [_H, C.POINTER(C.c_longlong)]),
+    "rve_tuning": (C.c_int, [_H, C.POINTER(C.c_int)]),
     "rve_kernel_timing": (C.c_int, [_H, C.c_int, C.c_int]),
     "rve_kernel_time": (C.c_int, [_H, C.POINTER(C.c_double),
                                   C.POINTER(C.c_longlong)]),

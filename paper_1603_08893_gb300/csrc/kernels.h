@@ -34,6 +34,7 @@ struct GridGeom {
   // float y and x passes on the in-place four-step kernels (fs_n1 != 0:
   // the axis length has a compiled N1 x N2 split, see RVE_FS_SIZES)
   int fsy_n1, fsx_n1, fsz_n1;
+  int zblk;  // persistent four-step z passes: thread blocks per SM in the grid
   int fsy_t, fsy_grp, fsx_t, fsz_lz;
   FastDiv f_fsy_ntk, f_fsx_ntk, f_fsy_L, f_fsx_L, f_fsz_L, f_fsz_lz;
 };

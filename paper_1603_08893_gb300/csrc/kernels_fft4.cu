@@ -459,7 +459,7 @@ void launch_zfwd4(const ZfwdParams<float>& P0, cudaStream_t s) {
   P.lz = g.fsz_lz;
   const int nlines = g.nx * g.ny;
   // persistent: as many thread blocks as are resident at once
-  const int grid = std::min((nlines + P.lz - 1) / P.lz, 3 * sm_count());
+  const int grid = std::min((nlines + P.lz - 1) / P.lz, std::max(1, g.zblk) * sm_count());
   const size_t sm = z4_smem(g, false);
   const bool full = P.tan.mode == TAN_FULL81;
   switch (g.nz) {
@@ -480,7 +480,7 @@ void launch_zinv4(const ZinvParams<float, float>& P0, cudaStream_t s) {
   const GridGeom& g = P.g;
   P.lz = g.fsz_lz;
   const int nlines = g.nx * g.ny;
-  const int grid = std::min((nlines + P.lz - 1) / P.lz, 3 * sm_count());
+  const int grid = std::min((nlines + P.lz - 1) / P.lz, std::max(1, g.zblk) * sm_count());
   const size_t sm = z4_smem(g, true);
   switch (g.nz) {
 #define RVE_FS_ZI(N, A, B)                                          \

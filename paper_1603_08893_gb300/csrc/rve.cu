@@ -2,6 +2,10 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <tuple>
+#include <mutex>
+#include <map>
+#include <array>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -144,6 +148,7 @@ bool make_geom(int nx, int ny, int nz, GridGeom* g) {
   // 5 lz lines x nz (about 32 KB) plus, in the last pass, the r tile
   g->fsz_n1 = fs_split_n1(nz);
   g->fsz_lz = fs_z_lz(nz);
+  g->zblk = 3;
   g->f_fsz_L = make_fastdiv((unsigned)(5 * g->fsz_lz));
   g->f_fsz_lz = make_fastdiv((unsigned)g->fsz_lz);
   return true;
@@ -190,6 +195,7 @@ struct rve_s {
   Twiddles<double> twd{};
   Twiddles<dfl> twdf{};
   bool floatfloat = false;  // mixed: float64-accuracy transforms in float-float
+  int knobs[6] = {1, 3, 1, 1, 1, 0};  // kernel variants (rve_tuning)
   double Fbar[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
   double Fbar_committed[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};  // F-bar of the last committed state
   double* adj_b = nullptr;  // adjoint right-hand side [9][n] (SVK)
@@ -604,6 +610,104 @@ size_t layout_material(rve_t h, Arena& a, bool use_phase) {
   return a.off;
 }
 
+// ---------------------------------------------------------------------------
+// Autotuner of the float32 CG iteration (not in the paper).  Knobs: the
+// DFT engine of each pass (four-step kernels where the axis length has a
+// compiled split, else Stockham), the grid of the persistent z passes
+// (blocks per SM) and composite radices in the Stockham plans.  Coordinate
+// descent from the defaults; each candidate is timed on the handle itself
+// (CUDA events, the best of three runs of eight CG iterations on a predictor
+// right-hand side, after two warm-up iterations).  Results are cached per
+// (grid, device, tangent) for the process.
+// ---------------------------------------------------------------------------
+struct TuneKey {
+  int nx, ny, nz, dev, tan;
+  bool operator<(const TuneKey& o) const {
+    return std::tie(nx, ny, nz, dev, tan) < std::tie(o.nx, o.ny, o.nz, o.dev, o.tan);
+  }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, std::array<int, 5>> g_tune_cache;
+
+void apply_knobs(rve_t h, const std::array<int, 5>& k) {
+  GridGeom& g = h->g;
+  GridGeom base;
+  make_geom(g.nx, g.ny, g.nz, &base);
+  g.fsz_n1 = k[0] ? base.fsz_n1 : 0;
+  g.zblk = k[1];
+  g.fsy_n1 = k[2] ? base.fsy_n1 : 0;
+  g.fsx_n1 = k[3] ? base.fsx_n1 : 0;
+  g.px = k[4] ? base.px : base.pxs;
+  g.py = k[4] ? base.py : base.pys;
+  g.pz = k[4] ? base.pz : base.pzs;
+  for (int i = 0; i < 5; ++i) h->knobs[i] = k[i];
+}
+
+// Milliseconds per float32 CG iteration with the current knobs; < 0 if the
+// CG state did not stay active.
+double time_cg_iteration(rve_t h) {
+  SolverState* hs = h->hst;
+  std::memset(hs, 0, sizeof(SolverState));
+  hs->cg_tol = 0.0;
+  hs->cg_atol = 0.0;
+  hs->maxit = 1 << 30;
+  for (int c = 0; c < 9; ++c) hs->Fbar[c] = (c % 4 == 0 ? 1.0 : 0.0) + (c == 1 ? 0.01 : 0.0);
+  if (push_state(h)) return -1.0;
+  enqueue_predictor<float>(h);
+  for (int k = 0; k < 2; ++k) enqueue_cg_iteration<float>(h, -1);
+  double best = 1e30;
+  for (int rep = 0; rep < 3; ++rep) {
+    cudaEventRecord(h->e0, h->s);
+    for (int k = 0; k < 8; ++k) enqueue_cg_iteration<float>(h, -1);
+    cudaEventRecord(h->e1, h->s);
+    if (cudaEventSynchronize(h->e1) != cudaSuccess) return -1.0;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, h->e0, h->e1);
+    best = std::min(best, (double)ms / 8.0);
+  }
+  if (sync_state(h) || h->hst->done) return -1.0;
+  return best;
+}
+
+int autotune(rve_t h) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const TuneKey key{h->g.nx, h->g.ny, h->g.nz, dev, h->tan};
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) {
+      apply_knobs(h, it->second);
+      h->knobs[5] = 1;
+      return RVE_OK;
+    }
+  }
+  std::array<int, 5> best = {1, 3, 1, 1, 1};
+  apply_knobs(h, best);
+  double tbest = time_cg_iteration(h);
+  if (tbest < 0) return fail(h, RVE_ERR_CUDA, "autotune: CG timing run failed");
+  const std::vector<int> choices[5] = {{1, 0}, {3, 2, 1}, {1, 0}, {1, 0}, {1, 0}};
+  for (int knob = 0; knob < 5; ++knob)
+    for (int v : choices[knob]) {
+      if (v == best[knob]) continue;
+      std::array<int, 5> cand = best;
+      cand[knob] = v;
+      apply_knobs(h, cand);
+      const double t = time_cg_iteration(h);
+      if (t > 0 && t < tbest) {
+        tbest = t;
+        best = cand;
+      }
+    }
+  apply_knobs(h, best);
+  h->knobs[5] = 1;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_cache[key] = best;
+  }
+  return RVE_OK;
+}
+
 }  // namespace
 
 // ===========================================================================
@@ -622,6 +726,7 @@ void rve_default_options(rve_options* o) {
   o->cg_atol = 0.0;
   o->mixed_refine = 0;
   o->residual = RVE_RES_FLOATFLOAT;
+  o->autotune = 0;
 }
 
 const char* rve_status_string(int code) {
@@ -656,6 +761,7 @@ static int resolve_options(const rve_options* in, rve_options* out, int model, i
   if (!(out->cg_atol >= 0.0)) return RVE_ERR_INVALID;
   if (out->mixed_refine < 0 || out->mixed_refine > 8) return RVE_ERR_INVALID;
   if (out->residual != RVE_RES_FLOATFLOAT && out->residual != RVE_RES_FP64) return RVE_ERR_INVALID;
+  if (out->autotune != 0 && out->autotune != 1) return RVE_ERR_INVALID;
   if (model == RVE_SVK) {
     if (out->tangent == RVE_TAN_AUTO || out->tangent == RVE_TAN_RECOMPUTE) *tan = TAN_SVK;
     else if (out->tangent == RVE_TAN_FULL81) *tan = TAN_FULL81;
@@ -842,7 +948,17 @@ int rve_create(rve_t* out, int nx, int ny, int nz, int model, int nphase, const 
   if (!ok)
     return bail(RVE_ERR_CUDA, std::string("initial constitutive evaluation failed: ") +
                                   cudaGetErrorString(first_err));
+  if (h->mixed && h->opt.autotune) {
+    const int arc = autotune(h);
+    if (arc) return bail(arc, "autotune failed");
+  }
   *out = h;
+  return RVE_OK;
+}
+
+int rve_tuning(rve_t h, int knobs[6]) {
+  if (!h || !knobs) return RVE_ERR_INVALID;
+  for (int i = 0; i < 6; ++i) knobs[i] = h->knobs[i];
   return RVE_OK;
 }
 

@@ -58,7 +58,7 @@ def _in_ptr(a, n):
 
 def _options(precision="fp64", tangent="auto", max_newton=50, max_cg=10000,
              cg_tol_floor=1e-5, cg_atol=0.0, mixed_refine=0, residual="floatfloat",
-             stream=None):
+             autotune=False, stream=None):
     o = _lib.rve_options()
     lib.rve_default_options(C.byref(o))
     o.precision = _PREC[precision]
@@ -69,6 +69,7 @@ def _options(precision="fp64", tangent="auto", max_newton=50, max_cg=10000,
     o.cg_atol = float(cg_atol)
     o.mixed_refine = int(mixed_refine)
     o.residual = {"floatfloat": 0, "fp64": 1}[residual]
+    o.autotune = 1 if autotune else 0
     if stream is None and torch is not None and torch.cuda.is_available():
         stream = torch.cuda.current_stream().cuda_stream
     o.stream = C.c_void_p(int(stream)) if stream else None
@@ -250,6 +251,17 @@ def rve_launch_count(h):
     return int(c.value)
 
 
+TUNING_KNOBS = ("four_step_z", "z_blocks_per_sm", "four_step_y", "four_step_x",
+                "composite_radices", "autotuned")
+
+
+def rve_tuning(h):
+    """Kernel variants in use (set by the autotuner or the defaults)."""
+    k = (C.c_int * 6)()
+    _check(lib.rve_tuning(h, k), h)
+    return dict(zip(TUNING_KNOBS, (int(v) for v in k)))
+
+
 def rve_kernel_timing(h, family, enable=True):
     _check(lib.rve_kernel_timing(h, int(family), int(bool(enable))), h)
 
@@ -331,6 +343,9 @@ class RVE:
 
     def launch_count(self):
         return rve_launch_count(self.h)
+
+    def tuning(self):
+        return rve_tuning(self.h)
 
 
 class RVEBatch:

@@ -283,3 +283,48 @@ def test_deterministic_repeat():
         outs.append(r.get_F())
         r.close()
     assert np.array_equal(outs[0], outs[1])
+
+
+@pytest.mark.parametrize("shape", [(15, 21, 125), (31, 31, 31)])
+def test_projection_matches_cufft_cross_check(shape):
+    """Cross-check of the library's transforms against cuFFT (through
+    torch.fft, test-only): G:A = IFFT(G-hat : FFT(A)) with the reduced form
+    of Eq. G_red, float64, on the device."""
+    rng = np.random.default_rng(5)
+    A = rng.standard_normal((3, 3) + shape)
+    r = RVE(shape, phase=np.zeros(shape, np.uint8), phase_params=[[1.0, 0.5]])
+    got = r.project(A)
+    r.close()
+    At = torch.from_numpy(A).cuda()
+    Ah = torch.fft.fftn(At, dim=(2, 3, 4))
+    q = [torch.fft.fftfreq(n, d=1.0 / n, dtype=torch.float64, device="cuda") / n for n in shape]
+    qx, qy, qz = torch.meshgrid(*q, indexing="ij")
+    xi = torch.stack([qx, qy, qz])
+    q2 = (xi * xi).sum(0)
+    inv = torch.where(q2 > 0, 1.0 / torch.where(q2 > 0, q2, torch.ones_like(q2)), torch.zeros_like(q2))
+    s = torch.einsum("ilxyz,lxyz->ixyz", Ah, xi.to(Ah.dtype))
+    Gh = torch.einsum("ixyz,jxyz->ijxyz", s, xi.to(Ah.dtype)) * inv
+    ref = torch.fft.ifftn(Gh, dim=(2, 3, 4)).real.cpu().numpy()
+    assert maxrel(got, ref) < 1e-12
+
+
+def test_autotuned_handle_matches_oracle():
+    """A mixed handle with the autotuner on picks kernel variants (reported by
+    rve_tuning), caches them per grid, and still reaches the oracle's
+    converged state (P-bar 1e-8, fields 1e-7)."""
+    shape = (27, 33, 45)
+    rng = np.random.default_rng(13)
+    phase = (rng.uniform(size=shape) < 0.3).astype(np.uint8)
+    params = synth.two_phase_params(10.0)
+    Fbar = synth.simple_shear(0.03)
+    prob = solver.SVKProblem.from_phase(phase, params)
+    prob.increment(Fbar, tol_newton=1e-10, tol_cg=1e-12, cg_atol=1e-13)
+    for _ in range(2):  # second handle takes the cached choice
+        r = RVE(shape, phase=phase, phase_params=params, precision="mixed", autotune=True)
+        t = r.tuning()
+        assert t["autotuned"] == 1 and t["z_blocks_per_sm"] in (1, 2, 3)
+        r.set_macro_F(Fbar)
+        r.solve_increment(1e-5, 1e-8)
+        assert maxrel(r.homogenized_P(), prob.homogenized_P()) < 1e-8
+        assert rel(r.get_F(), prob.F) < 1e-7
+        r.close()
