@@ -276,6 +276,166 @@ def reference_arm(args):
     print(json.dumps(out), flush=True)
 
 
+# ---------------------------------------------------------------------------
+# Secondary workloads (one JSON line each; `--workload NAME`).  The default
+# workload above is the headline; these measure the other synthetic configs
+# and the stored-vs-recomputed tangent choice on one GPU.
+# ---------------------------------------------------------------------------
+def _line(workload, metric, value, unit, **extra):
+    d = {"workload": workload, "metric": metric, "value": value, "unit": unit,
+         "n_gpus": 1, "data": "synthetic"}
+    d.update(extra)
+    print(json.dumps(d), flush=True)
+
+
+def _events(torch):
+    return (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+            torch.cuda.current_stream())
+
+
+def bench_cube31(args, torch, RVE):
+    """31^3 corner cube, contrast 10, simple shear to 0.1 in 10 increments,
+    plain float64 path (config 1)."""
+    cfg = synth.config_cube31()
+    n = int(np.prod(cfg["shape"]))
+    w = RVE(cfg["shape"], phase=cfg["phase"], phase_params=cfg["phase_params"], precision="fp64")
+    w.set_macro_F(cfg["schedule"][0])
+    w.solve_increment(cfg["tol_newton"], cfg["tol_cg"])
+    w.close()
+    r = RVE(cfg["shape"], phase=cfg["phase"], phase_params=cfg["phase_params"], precision="fp64")
+    e0, e1, s = _events(torch)
+    cg = newton = 0
+    torch.cuda.synchronize()
+    e0.record(s)
+    for Fb in cfg["schedule"]:
+        r.set_macro_F(Fb)
+        st = r.solve_increment(cfg["tol_newton"], cfg["tol_cg"])
+        cg += st["cg_iters_total"]
+        newton += st["newton_iters"]
+    e1.record(s)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    _line("svk31_cube_shear_fp64", "voxel*CG-iterations/s, float64 GPU solver", n * cg / (ms / 1e3),
+          UNIT, dtype="f64", increments=len(cfg["schedule"]), cg_iters=cg, newton_iters=newton,
+          solve_ms=ms, pbar_xy=float(r.homogenized_P()[0, 1]))
+    r.close()
+
+
+def bench_j2_315(args, torch, RVE):
+    """315^3 Voronoi, J2 plasticity, simple shear to 0.2 in 20 increments,
+    mixed path with increment cutting (config 3); the first --steps
+    increments."""
+    cfg = synth.config_voronoi_j2()
+    n = int(np.prod(cfg["shape"]))
+    r = RVE(cfg["shape"], model="j2", phase=cfg["phase"], phase_params=cfg["phase_params"],
+            precision="mixed")
+    e0, e1, s = _events(torch)
+    cg = newton = subs = cuts = 0
+    steps = min(args.steps, len(cfg["schedule"]))
+    torch.cuda.synchronize()
+    e0.record(s)
+    for Fb in cfg["schedule"][:steps]:
+        st = r.solve_step(Fb, cfg["tol_newton"], cfg["tol_cg"], max_cuts=8)
+        cg += st["cg_iters_total"]
+        newton += st["newton_iters"]
+        subs += st["substeps"]
+        cuts += st["cuts"]
+    e1.record(s)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    ep = r.get_history()[6]
+    _line("j2_315_voronoi_shear_mixed", METRIC, n * cg / (ms / 1e3), UNIT, dtype="f32/f64",
+          increments=steps, substeps=subs, cuts=cuts, cg_iters=cg, newton_iters=newton,
+          solve_ms=ms, pbar_xy=float(r.homogenized_P()[0, 1]), max_eps_p=float(ep.max()),
+          plastic_fraction=float((ep > 0).mean()))
+    r.close()
+
+
+def bench_batch256(args, torch):
+    """256 SVK cells of uneven size, one increment each, CUDA graph, autotuned
+    kernels, mixed path with per-cell increment cutting (config 4)."""
+    from paper_1603_08893_gb300 import RVEBatch
+    cells = synth.config_batch()
+    shapes = [c["shape"] for c in cells]
+    t0 = time.perf_counter()
+    b = RVEBatch(shapes, [c["phase"] for c in cells], [c["phase_params"] for c in cells],
+                 precision="mixed", autotune=True)
+    setup_s = time.perf_counter() - t0
+    F = np.stack([c["Fbar"] for c in cells])
+    e0, e1, s = _events(torch)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    stats = b.solve(F, 1e-5, 1e-8, check=False, max_cuts=4)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    units = sum(int(np.prod(sh)) * st["cg_iters_total"] for sh, st in zip(shapes, stats))
+    failed = sum(1 for st in stats if st["status"] != 0)
+    _line("svk_batch256_uneven_mixed", METRIC, units / wall, UNIT, dtype="f32/f64",
+          cells=len(cells), voxels=int(sum(int(np.prod(sh)) for sh in shapes)),
+          failed_cells=failed, solve_s=wall, setup_and_autotune_s=setup_s,
+          cg_iters=int(sum(st["cg_iters_total"] for st in stats)),
+          timing="host wall clock around the batch solve (its calls return when idle)")
+    b.close()
+
+
+def bench_adjoint243(args, torch, RVE):
+    """243^3 lognormal shear modulus, simple shear 0.05, one increment, then
+    the adjoint gradient of P-bar_xy (config 5), mixed path."""
+    cfg = synth.config_lognormal()
+    n = int(np.prod(cfg["shape"]))
+    r = RVE(cfg["shape"], voxel_params=cfg["voxel_params"], precision="mixed")
+    e0, e1, s = _events(torch)
+    torch.cuda.synchronize()
+    e0.record(s)
+    r.set_macro_F(cfg["schedule"][0])
+    st = r.solve_increment(cfg["tol_newton"], cfg["tol_cg"])
+    e1.record(s)
+    torch.cuda.synchronize()
+    ms_fwd = e0.elapsed_time(e1)
+    W = np.zeros((3, 3))
+    W[0, 1] = 1.0
+    e0.record(s)
+    g, its = r.adjoint_grad_mu(W, tol_cg=1e-8)
+    e1.record(s)
+    torch.cuda.synchronize()
+    ms_adj = e0.elapsed_time(e1)
+    _line("svk243_lognormal_adjoint_mixed", "voxel*CG-iterations/s of the adjoint solve",
+          n * its / (ms_adj / 1e3), UNIT, dtype="f32/f64", adjoint_cg_iters=its,
+          adjoint_ms=ms_adj, forward_ms=ms_fwd, forward_cg_iters=st["cg_iters_total"],
+          forward_value=n * st["cg_iters_total"] / (ms_fwd / 1e3),
+          grad_abs_max=float(np.abs(g).max()))
+    r.close()
+
+
+def bench_tangent125(args, torch, RVE):
+    """Stored K4 (81 float32 per voxel) against the recomputed SVK tangent in
+    the first pass of the float32 CG iteration, 125^3 spheres: device time per
+    launch of that kernel family and whole-increment throughput."""
+    cfg = workload()
+    from paper_1603_08893_gb300 import rve as api
+    out = {}
+    for tan in ("recompute", "full81"):
+        r = RVE(cfg["shape"], phase=cfg["phase"], phase_params=cfg["phase_params"],
+                precision="mixed", tangent=tan)
+        api.rve_kernel_timing(r.h, 0, True)
+        e0, e1, s = _events(torch)
+        torch.cuda.synchronize()
+        e0.record(s)
+        r.set_macro_F(cfg["schedule"][0])
+        st = r.solve_increment(cfg["tol_newton"], cfg["tol_cg"])
+        e1.record(s)
+        torch.cuda.synchronize()
+        zms, cnt = api.rve_kernel_time(r.h)
+        out[tan] = {"first_pass_ms": zms / max(cnt, 1), "increment_ms": e0.elapsed_time(e1),
+                    "cg_iters": st["cg_iters_total"]}
+        r.close()
+    n = int(np.prod(cfg["shape"]))
+    best = min(out, key=lambda k: out[k]["first_pass_ms"])
+    _line("svk125_tangent_choice", "first-pass ms per CG iteration", out[best]["first_pass_ms"],
+          "ms", chosen=best, variants=out,
+          algorithmic_bytes_per_voxel={"recompute": 253.3, "full81": 253.3 - 36 - 1 + 324})
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -288,9 +448,22 @@ def main():
     ap.add_argument("--mixed-only", action="store_true",
                     help="time the mixed path only (no float64 comparison, no e2e); "
                          "used for profiler captures")
+    ap.add_argument("--workload", default="svk125",
+                    choices=["svk125", "cube31", "j2_315", "batch256", "adjoint243", "tangent125"],
+                    help="svk125 (default) is the headline; the others print one line each")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
+    if args.workload != "svk125":
+        import torch
+        from paper_1603_08893_gb300 import RVE
+        fn = {"cube31": lambda: bench_cube31(args, torch, RVE),
+              "j2_315": lambda: bench_j2_315(args, torch, RVE),
+              "batch256": lambda: bench_batch256(args, torch),
+              "adjoint243": lambda: bench_adjoint243(args, torch, RVE),
+              "tangent125": lambda: bench_tangent125(args, torch, RVE)}[args.workload]
+        fn()
+        return None
 
     import torch
     rank, world, dist = dist_setup(args.gpus)
