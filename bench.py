@@ -323,7 +323,7 @@ def bench_cube31(args, torch, RVE):
 
 def bench_j2_315(args, torch, RVE):
     """315^3 Voronoi, J2 plasticity, simple shear to 0.2 in 20 increments,
-    mixed path with increment cutting (config 3); the first --steps
+    mixed path with increment cutting (config 3); the first --j2-steps
     increments."""
     cfg = synth.config_voronoi_j2()
     n = int(np.prod(cfg["shape"]))
@@ -331,11 +331,11 @@ def bench_j2_315(args, torch, RVE):
             precision="mixed")
     e0, e1, s = _events(torch)
     cg = newton = subs = cuts = 0
-    steps = min(args.steps, len(cfg["schedule"]))
+    steps = min(args.j2_steps, len(cfg["schedule"]))
     torch.cuda.synchronize()
     e0.record(s)
     for Fb in cfg["schedule"][:steps]:
-        st = r.solve_step(Fb, cfg["tol_newton"], cfg["tol_cg"], max_cuts=8)
+        st = r.solve_step(Fb, cfg["tol_newton"], cfg["tol_cg"], max_cuts=10)
         cg += st["cg_iters_total"]
         newton += st["newton_iters"]
         subs += st["substeps"]
@@ -448,6 +448,8 @@ def main():
     ap.add_argument("--mixed-only", action="store_true",
                     help="time the mixed path only (no float64 comparison, no e2e); "
                          "used for profiler captures")
+    ap.add_argument("--j2-steps", type=int, default=2,
+                    help="increments of the 315^3 J2 ramp timed by --workload j2_315")
     ap.add_argument("--workload", default="svk125",
                     choices=["svk125", "cube31", "j2_315", "batch256", "adjoint243", "tangent125"],
                     help="svk125 (default) is the headline; the others print one line each")

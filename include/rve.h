@@ -163,11 +163,13 @@ int rve_solve_increment(rve_t h, double tol_newton, double tol_cg, rve_stats* st
  * one or more increments of rve_solve_increment along the straight path from
  * the last committed F-bar: when an increment fails (Newton divergence or
  * max iterations, CG failure, non-finite values, det F <= 0) the state has
- * been rolled back and the increment is retried with half the step; after a
- * success the step doubles again (up to the remainder).  Newton is declared
- * diverged when ||dF||/||F|| > 0.5 or the update grew in two consecutive
- * equilibrium iterations.  At most max_cuts halvings; st (may be NULL)
- * accumulates the iterations of all attempts.  Not in the paper (its
+ * been rolled back and the increment is retried with half the step; after
+ * two successes in a row at one step size the step doubles again (up to the
+ * remainder).  Newton is declared diverged when ||dF||/||F|| > 0.5 or the
+ * update grew in two consecutive equilibrium iterations.  The step never
+ * falls below 2^-max_cuts of the load step (the call fails there); st (may
+ * be NULL) accumulates the iterations of all attempts and counts the
+ * halvings in st->cuts.  Not in the paper (its
  * examples use fixed small increments, Sec. 5.5); the elasto-plastic switch
  * of Sec. 5.3 makes full Newton steps diverge when an increment crosses the
  * yield point by far. */
@@ -243,7 +245,7 @@ int rve_batch_solve(rve_batch_t b, const double* Fbar, double tol_newton, double
                     rve_stats* stats);
 /* As rve_batch_solve, with the increment cutting of rve_solve_step applied
  * per cell (cells whose increment failed are retried together with half
- * their step, at most max_cuts halvings each); stats[c].substeps / cuts /
+ * their step, same step control as rve_solve_step); stats[c].substeps / cuts /
  * substep_to report each cell's path. */
 int rve_batch_solve_step(rve_batch_t b, const double* Fbar, double tol_newton, double tol_cg,
                          int max_cuts, rve_stats* stats);

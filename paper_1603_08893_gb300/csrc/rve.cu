@@ -1138,7 +1138,8 @@ int rve_solve_step(rve_t h, const double Fbar[9], double tol_newton, double tol_
   rve_stats acc;
   std::memset(&acc, 0, sizeof(acc));
   double done = 0.0, step = 1.0;
-  int cuts = 0, sub = 0;
+  const double min_step = std::ldexp(1.0, -max_cuts);
+  int cuts = 0, sub = 0, streak = 0;
   int result = RVE_OK;
   while (done < 1.0) {
     const double to = std::min(1.0, done + step);
@@ -1154,15 +1155,22 @@ int rve_solve_step(rve_t h, const double Fbar[9], double tol_newton, double tol_
       done = to;
       if (sub < RVE_MAX_NEWTON_LOG) acc.substep_to[sub] = to;
       ++sub;
-      step = std::min(2.0 * step, 1.0);
+      // grow only after two successes at this size (growing after every
+      // success alternates success and failure on a hard stretch)
+      if (++streak >= 2) {
+        step = std::min(2.0 * step, 1.0);
+        streak = 0;
+      }
     } else if (rc == RVE_ERR_NEWTON_MAXIT || rc == RVE_ERR_CG_MAXIT || rc == RVE_ERR_NONFINITE ||
                rc == RVE_ERR_DETF || rc == RVE_ERR_CG_BREAKDOWN) {
       // the state was rolled back: retry with half the step
-      if (++cuts > max_cuts) {
+      ++cuts;
+      streak = 0;
+      step *= 0.5;
+      if (step < min_step) {
         result = rc;
         break;
       }
-      step *= 0.5;
     } else {
       result = rc;
       break;
@@ -1745,11 +1753,13 @@ int rve_batch_solve_step(rve_batch_t b, const double* Fbar, double tol_newton, d
   const int nrve = (int)b->rv.size();
   if (stats) std::memset(stats, 0, sizeof(rve_stats) * nrve);
   // every cell follows the straight path from its committed F-bar; failed
-  // increments (rolled back) are retried with half the step, successes
-  // double it (as rve_solve_step)
+  // increments (rolled back) are retried with half the step, two successes
+  // in a row double it (as rve_solve_step)
   std::vector<double> F0(9 * nrve), target(Fbar, Fbar + 9 * nrve), sub(9 * nrve);
   std::vector<double> done(nrve, 0.0), step(nrve, 1.0);
   std::vector<int> cuts(nrve, 0), nsub(nrve, 0), result(nrve, RVE_OK), fin(nrve, RVE_OK);
+  std::vector<int> streak(nrve, 0);
+  const double min_step = std::ldexp(1.0, -max_cuts);
   for (int c = 0; c < nrve; ++c) std::memcpy(&F0[9 * c], b->rv[c]->Fbar_committed, 9 * sizeof(double));
   std::vector<int> open;
   for (int c = 0; c < nrve; ++c) open.push_back(c);
@@ -1771,14 +1781,21 @@ int rve_batch_solve_step(rve_batch_t b, const double* Fbar, double tol_newton, d
         done[c] = to[c];
         if (nsub[c] < RVE_MAX_NEWTON_LOG && stats) stats[c].substep_to[nsub[c]] = to[c];
         ++nsub[c];
-        step[c] = std::min(2.0 * step[c], 1.0);
+        if (++streak[c] >= 2) {
+          step[c] = std::min(2.0 * step[c], 1.0);
+          streak[c] = 0;
+        }
         if (done[c] < 1.0) next.push_back(c);
-      } else if (++cuts[c] <= max_cuts) {
-        step[c] *= 0.5;
-        next.push_back(c);
       } else {
-        fin[c] = result[c];
-        if (worst == RVE_OK) worst = result[c];
+        ++cuts[c];
+        streak[c] = 0;
+        step[c] *= 0.5;
+        if (step[c] >= min_step) {
+          next.push_back(c);
+        } else {
+          fin[c] = result[c];
+          if (worst == RVE_OK) worst = result[c];
+        }
       }
     }
     open.swap(next);
