@@ -56,6 +56,12 @@ def family_bytes_per_voxel(nz, fam):
     }[fam]
 
 
+# dram__bytes_read.sum + dram__bytes_write.sum per launch of the current
+# kernel version from one ncu capture of this workload; a kernel changed
+# since its capture has no entry (traffic null)
+NCU_TRAFFIC_BYTES = {"zfwd": 305.032960e6 + 156.752640e6}
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -523,7 +529,7 @@ def main():
             ach = bpl / (prof[fam]["avg_ms"] / 1e3) / 1e9
             roof = {"bound": "hbm", "kernel": fam, "achieved": round(ach, 1),
                     "peak": peak, "unit": "GB/s", "frac": round(ach / peak, 4),
-                    "traffic": None, "peak_kind": peak_kind,
+                    "traffic": NCU_TRAFFIC_BYTES.get(fam), "peak_kind": peak_kind,
                     "algorithmic_bytes_per_launch": bpl,
                     "avg_launch_ms": prof[fam]["avg_ms"]}
         cpu = None if args.no_cpu_baseline else cpu_baseline_sample(cfg)
