@@ -97,9 +97,10 @@ typedef struct {
                            residual G:P and the projection of dF): RVE_RES_FLOATFLOAT
                            (default) or RVE_RES_FP64 */
   int autotune;         /* MIXED only: 1 = time the float32 CG iteration's kernel
-                           variants (DFT engine per axis, z-pass grid) on this grid at
-                           rve_create and keep the fastest; the choice is cached per
-                           (grid, device, tangent) for the process; default 0 */
+                           variants (DFT engine per axis, z-pass grid and staging) at
+                           rve_create on this grid and keep the fastest; the choice
+                           is cached per (grid, device, tangent) for the process;
+                           default 0 */
   void* stream;         /* cudaStream_t; NULL = legacy default stream */
   void* workspace;      /* optional caller-owned device memory (see rve_workspace_size) */
   size_t workspace_bytes;
@@ -263,11 +264,11 @@ const char* rve_last_error(rve_t h);
 const char* rve_status_string(int code);
 
 /* Kernel variants in use (not in the paper; set by rve_options.autotune or
- * the defaults): knobs[0..4] = four-step z pass, blocks per SM of the
+ * the defaults): knobs[0..5] = four-step z pass, blocks per SM of the
  * persistent z passes, four-step y pass, four-step x pass, composite radices
- * in the Stockham plans (1 = on); knobs[5] = 1 if they were autotuned.
- * Returns RVE_OK. */
-int rve_tuning(rve_t h, int knobs[6]);
+ * in the Stockham plans, TMA-staged first z pass (1 = on); knobs[6] = 1 if
+ * they were autotuned.  Returns RVE_OK. */
+int rve_tuning(rve_t h, int knobs[7]);
 
 /* Instrumentation: number of kernels this handle has launched, and optional
  * CUDA-event timing of every launch of one kernel family

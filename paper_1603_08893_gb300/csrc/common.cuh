@@ -34,6 +34,7 @@ RVE_DEV cplx<R> c_mulc(cplx<R> a, cplx<R> b) {
 #define RVE_DEV_ERR_CG_MAXIT (-4)
 #define RVE_DEV_ERR_CG_BREAKDOWN (-5)
 #define RVE_DEV_ERR_NONFINITE (-7)
+#define RVE_DEV_ERR_TIMEOUT (-9)
 
 struct SolverState {
   // CG
@@ -59,7 +60,7 @@ struct SolverState {
   double meanF[9];
   double adjW[9];   // W / n of the adjoint right-hand side G : (K : W) / n
   int err_flags;    // bit 0: det F <= 0, bit 1: non-finite value
-  int pad;
+  int dev_timeout;  // set by a thread block whose bounded wait on its own copies gave up
   // reduction counters (one per reducing kernel family)
   unsigned int counter[8];
 };

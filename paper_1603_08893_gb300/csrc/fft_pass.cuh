@@ -264,7 +264,11 @@ RVE_DEV void zfwd_step_length(const ZfwdParams<R>& P, double pkp) {
     SolverState* st = P.st;
     const double pap = tot[0];
     st->pAp = pap;
-    if (!isfinite(pap)) {
+    if (st->dev_timeout) {
+      st->status = RVE_DEV_ERR_TIMEOUT;
+      st->alpha = 0.0;
+      st->done = 1;
+    } else if (!isfinite(pap)) {
       st->status = RVE_DEV_ERR_NONFINITE;
       st->alpha = 0.0;
       st->done = 1;
@@ -310,4 +314,45 @@ template <typename R>
 RVE_DEV const AxisPlan& axis_plan(const GridGeom& g, int axis) {
   if constexpr (is_dfl<R>::value) return axis == 0 ? g.pxs : (axis == 1 ? g.pys : g.pzs);
   else return axis == 0 ? g.px : (axis == 1 ? g.py : g.pz);
+}
+
+// ---------------------------------------------------------------------------
+// Bulk asynchronous copies (TMA, cp.async.bulk) into shared memory with
+// completion on an mbarrier.  Addresses and sizes are multiples of 16 bytes.
+// ---------------------------------------------------------------------------
+RVE_DEV unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+RVE_DEV void mbar_init(unsigned long long* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+RVE_DEV void mbar_arrive_expect_tx(unsigned long long* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+RVE_DEV void bulk_load(void* sdst, const void* gsrc, unsigned bytes, unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(sdst)),
+      "l"(gsrc), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+RVE_DEV bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}" : "=r"(ok) : "r"(smem_u32(bar)), "r"(parity) : "memory");
+  return ok != 0;
+}
+
+// Waits for phase `parity` of the barrier, giving up after `limit` polls
+// (each poll itself suspends for a bounded time); returns false on giving up.
+RVE_DEV bool mbar_wait_bounded(unsigned long long* bar, unsigned parity, unsigned limit) {
+  for (unsigned it = 0; it < limit; ++it)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
 }

@@ -34,7 +34,10 @@ struct GridGeom {
   // float y and x passes on the in-place four-step kernels (fs_n1 != 0:
   // the axis length has a compiled N1 x N2 split, see RVE_FS_SIZES)
   int fsy_n1, fsx_n1, fsz_n1;
-  int zblk;  // persistent four-step z passes: thread blocks per SM in the grid
+  int zblk;    // persistent four-step z passes: thread blocks per SM in the grid
+  int zstage;  // first z pass with TMA-staged, pipelined inputs (SVK, phase map);
+               // off by default (slower at 125^3: its tiles are half as large),
+               // a candidate of the autotuner
   int fsy_t, fsy_grp, fsx_t, fsz_lz;
   FastDiv f_fsy_ntk, f_fsx_ntk, f_fsy_L, f_fsx_L, f_fsz_L, f_fsz_lz;
 };
@@ -60,6 +63,34 @@ constexpr int fs_x_t(int n) {
 }
 constexpr int fs_z_lz(int n) {
   return (32768 / (8 * n) - 1) / 5 < 1 ? 1 : ((32768 / (8 * n) - 1) / 5 > 64 ? 64 : (32768 / (8 * n) - 1) / 5);
+}
+
+// Shared-memory layout (bytes) of the TMA-staged first z pass: twiddles |
+// transposed DFT buffer | staged inputs [36][sp] floats | staged phase bytes.
+struct Z4tLayout {
+  int lp, sp, spb;
+  size_t stage_off, phase_off, total;
+};
+
+__host__ __device__ constexpr Z4tLayout z4t_layout(int nz, int lz) {
+  Z4tLayout L{};
+  L.lp = (5 * lz) | 1;
+  L.sp = (lz * nz + 8 + 3) & ~3;
+  L.spb = (lz * nz + 32 + 15) & ~15;
+  const size_t head = 8 * ((size_t)((nz + 1) & ~1) + (size_t)nz * L.lp);
+  L.stage_off = (head + 15) & ~(size_t)15;
+  L.phase_off = L.stage_off + 4 * 36 * (size_t)L.sp;
+  L.total = L.phase_off + (size_t)L.spb;
+  return L;
+}
+
+// z lines per tile of the staged pass: the most that fit 72 KB (three
+// thread blocks per SM); 0 if not even one line fits
+constexpr int fs_zt_lz(int nz) {
+  int best = 0;
+  for (int lz = 1; lz <= 64; ++lz)
+    if (z4t_layout(nz, lz).total <= 72 * 1024) best = lz;
+  return best;
 }
 
 inline int fs_split_n1(int n) {

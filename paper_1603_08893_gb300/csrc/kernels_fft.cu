@@ -456,6 +456,7 @@ size_t fft_max_blocks(const GridGeom& g) {
   const size_t nlines = (size_t)g.nx * g.ny;
   int lz = g.lz_f < g.lz_d ? g.lz_f : g.lz_d;
   if (g.fsz_n1 && g.fsz_lz < lz) lz = g.fsz_lz;
+  if (g.fsz_n1 && fs_zt_lz(g.nz) >= 1 && fs_zt_lz(g.nz) < lz) lz = fs_zt_lz(g.nz);
   return (nlines + lz - 1) / lz;
 }
 

@@ -245,6 +245,160 @@ __global__ void __launch_bounds__(FFT_THREADS, (Fs4Occ<R, N1, N2>::value))
   if (SRC == SRC_CGPX) zfwd_step_length<R>(P, pkp);
 }
 
+// First pass of the fused float CG iteration for the SVK tangent with a
+// phase map, persistent and pipelined: the inputs of a tile -- r and F,
+// after the first iteration also p and x, and the phase bytes -- arrive in
+// shared memory by bulk asynchronous copies (TMA) that one thread issues for
+// the block's NEXT tile as soon as the current tile's voxel stage has read
+// its staged copy, so that they land while the block runs the current
+// tile's DFT and stores.  Each copy covers the 16-byte-aligned span around
+// one component's range of the tile (the arrays start 256-byte aligned
+// inside one allocation with slack after the last one, so the span stays in
+// it); soffs[a] is where the range starts in its staged copy.  Completion is
+// tracked by one mbarrier whose phase flips per tile; a bounded wait that
+// gives up marks the solver state (the last block then reports a timeout).
+template <int N1, int N2>
+__global__ void __launch_bounds__(FFT_THREADS, 3) k_zfwd4p(const ZfwdParams<float> P) {
+  using R = float;
+  constexpr int N = N1 * N2;
+  constexpr int lz = fs_zt_lz(N), hz = N / 2 + 1;
+  constexpr Z4tLayout Lt = z4t_layout(N, lz);
+  constexpr int LP = Lt.lp, SP = Lt.sp;
+  using LM = FsLayout<5 * lz, 0, 1, LP, 5 * lz>;
+  if (P.done && *P.done) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ __align__(8) unsigned long long bar;
+  __shared__ int soffs[37];
+  cplx<R>* tw2 = reinterpret_cast<cplx<R>*>(smem_raw);
+  cplx<R>* buf = tw2 + ((N + 1) & ~1);
+  float* stage = reinterpret_cast<float*>(smem_raw + Lt.stage_off);
+  unsigned char* sphase = smem_raw + Lt.phase_off;
+  const size_t n = P.g.n;
+  const int nlines = P.g.nx * P.g.ny;
+  const int ntiles = (nlines + lz - 1) / lz;
+  const int hzp = P.g.hzp;
+  const size_t ss = P.g.sstride;
+  const ZfwdScalars<R> sc = zfwd_scalars<R, SRC_CGPX>(P);
+  const int narr = sc.first ? 18 : 36;  // r, F, then p, x
+  // thread 0: stage the inputs of tile t (expected bytes first, then copies)
+  auto issue = [&](int t) {
+    const int nl = min(lz, nlines - t * lz);
+    const int nvox = nl * N;
+    const size_t v0 = (size_t)t * lz * N;
+    auto span = [&](int a, uintptr_t& lo16, unsigned& bytes) {
+      uintptr_t lo, hi;
+      if (a < narr) {
+        const float* b = a < 9 ? P.r : a < 18 ? P.tan.Fop : a < 27 ? P.p : P.x;
+        const float* src = b + (size_t)(a % 9) * n + v0;
+        lo = reinterpret_cast<uintptr_t>(src);
+        hi = reinterpret_cast<uintptr_t>(src + nvox);
+      } else {
+        lo = reinterpret_cast<uintptr_t>(P.tan.mat.phase + v0);
+        hi = lo + (uintptr_t)nvox;
+      }
+      lo16 = lo & ~(uintptr_t)15;
+      bytes = (unsigned)(((hi + 15) & ~(uintptr_t)15) - lo16);
+      return (int)(lo - lo16) / (a < narr ? 4 : 1);
+    };
+    unsigned total = 0;
+    for (int a = 0; a <= narr; ++a) {
+      uintptr_t lo16;
+      unsigned bytes;
+      soffs[a] = span(a, lo16, bytes);
+      total += bytes;
+    }
+    mbar_arrive_expect_tx(&bar, total);
+    for (int a = 0; a <= narr; ++a) {
+      uintptr_t lo16;
+      unsigned bytes;
+      span(a, lo16, bytes);
+      void* dst = a < narr ? (void*)(stage + (size_t)a * SP) : (void*)sphase;
+      bulk_load(dst, reinterpret_cast<const void*>(lo16), bytes, &bar);
+    }
+  };
+  if (threadIdx.x == 0) mbar_init(&bar, 1);
+  __syncthreads();
+  if (threadIdx.x == 0 && (int)blockIdx.x < ntiles) issue(blockIdx.x);
+  fs_twiddles<R, N1, N2>(tw2, P.tw);
+  double pkp = 0.0;
+  unsigned parity = 0;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int l0 = tile * lz;
+    const int nl = min(lz, nlines - l0);
+    const int nvox = nl * N;
+    const size_t v0 = (size_t)l0 * N;
+    if (!mbar_wait_bounded(&bar, parity, 1u << 20)) {
+      atomicOr(&P.st->dev_timeout, 1);
+      mbar_wait_bounded(&bar, parity, 1u << 20);  // let the copies land before going on
+    }
+    parity ^= 1u;
+    const int pofs = soffs[narr];
+    for (int i = threadIdx.x; i < lz * N; i += blockDim.x) {
+      R out[9];
+      if (i < nvox) {
+        const size_t v = v0 + i;
+        TanPre<R> q;
+#pragma unroll
+        for (int c = 0; c < 9; ++c) q.F[c] = stage[(9 + c) * SP + soffs[9 + c] + i];
+        const int ph = sphase[pofs + i];
+        q.lam = P.tan.mat.table[ph * P.tan.mat.nparam];
+        q.mu = P.tan.mat.table[ph * P.tan.mat.nparam + 1];
+        R in[9];
+        if (sc.first) {
+#pragma unroll
+          for (int c = 0; c < 9; ++c) in[c] = stage[c * SP + soffs[c] + i];
+        } else {
+#pragma unroll
+          for (int c = 0; c < 9; ++c) {
+            const R rr = stage[c * SP + soffs[c] + i];
+            const R pp = stage[(18 + c) * SP + soffs[18 + c] + i];
+            const R xx = stage[(27 + c) * SP + soffs[27 + c] + i];
+            P.x[(size_t)c * n + v] = fma(sc.alpha_prev, pp, xx);
+            in[c] = fma(sc.beta, pp, rr);
+          }
+        }
+        tangent_post<R, TAN_SVK>(P.tan, v, n, q, in, out);
+        R sp = 0;
+#pragma unroll
+        for (int c = 0; c < 9; ++c) {
+          P.p[(size_t)c * n + v] = in[c];
+          sp = fma(in[c], out[c], sp);
+        }
+        pkp += (double)sp;
+      } else {
+#pragma unroll
+        for (int c = 0; c < 9; ++c) out[c] = 0;
+      }
+      const int li = i / N;
+      cplx<R>* e = buf + (i - li * N) * LP + li;
+#pragma unroll
+      for (int k = 0; k < 5; ++k) e[k * lz] = {out[2 * k], (2 * k + 1 < 9) ? out[2 * k + 1] : R(0)};
+    }
+    __syncthreads();  // staged copy consumed: refill it with the next tile
+    if (threadIdx.x == 0 && tile + (int)gridDim.x < ntiles) issue(tile + gridDim.x);
+    fs_lines<R, N1, N2, false, LM>(buf, tw2);
+    for (int i = threadIdx.x; i < 5 * lz * hz; i += blockDim.x) {
+      const int rest = i / hz;
+      const int kz = i - rest * hz;
+      const int k = rest / lz;
+      const int li = rest - k * lz;
+      if (li >= nl) continue;
+      const int l = k * lz + li;
+      const cplx<R> z1 = buf[fs_pos<N1, N2>(kz) * LP + l];
+      cplx<R> z2 = buf[fs_pos<N1, N2>(kz ? N - kz : 0) * LP + l];
+      z2.y = -z2.y;
+      const size_t o = (size_t)(l0 + li) * hzp + kz;
+      P.spec[(size_t)(2 * k) * ss + o] = {R(0.5) * (z1.x + z2.x), R(0.5) * (z1.y + z2.y)};
+      if (2 * k + 1 < 9) {
+        const R dx = R(0.5) * (z1.x - z2.x), dy = R(0.5) * (z1.y - z2.y);
+        P.spec[(size_t)(2 * k + 1) * ss + o] = {dy, -dx};
+      }
+    }
+    __syncthreads();  // the DFT buffer is refilled by the next tile
+  }
+  zfwd_step_length<R>(P, pkp);
+}
+
 // L2 prefetch of the last pass's inputs of a tile: the tile's half spectrum
 // (per component nl consecutive rows of hzp values, contiguous) and its r
 // range.
@@ -456,6 +610,22 @@ static size_t z4_smem(const GridGeom& g, bool with_r) {
 void launch_zfwd4(const ZfwdParams<float>& P0, cudaStream_t s) {
   ZfwdParams<float> P = P0;
   const GridGeom& g = P.g;
+  if (g.zstage && P.tan.mode == TAN_SVK && P.tan.mat.phase && !P.tan.Sop && fs_zt_lz(g.nz) >= 1) {
+    const int lz = fs_zt_lz(g.nz);
+    P.lz = lz;
+    const int grid = std::min((g.nx * g.ny + lz - 1) / lz, std::max(1, g.zblk) * sm_count());
+    const size_t sm = z4t_layout(g.nz, lz).total;
+    switch (g.nz) {
+#define RVE_FS_ZP(N, A, B)                                    \
+  case N:                                                     \
+    k_zfwd4p<A, B><<<grid, FFT_THREADS, sm, s>>>(P);          \
+    return;
+      RVE_FS_SIZES(RVE_FS_ZP)
+#undef RVE_FS_ZP
+      default:
+        break;
+    }
+  }
   P.lz = g.fsz_lz;
   const int nlines = g.nx * g.ny;
   // persistent: as many thread blocks as are resident at once
@@ -502,7 +672,8 @@ cudaError_t fft4_kernels_init() {
   allow_smem(k_fft_x4<float, A, B>);                        \
   allow_smem(k_zfwd4<float, SRC_CGPX, TAN_FULL81, A, B>);   \
   allow_smem(k_zfwd4<float, SRC_CGPX, TAN_SVK, A, B>);      \
-  allow_smem(k_zinv4_cgr<float, A, B>);
+  allow_smem(k_zinv4_cgr<float, A, B>);                     \
+  allow_smem(k_zfwd4p<A, B>);
   RVE_FS_SIZES(RVE_FS_INIT)
 #undef RVE_FS_INIT
   return g_err4;

@@ -149,6 +149,7 @@ bool make_geom(int nx, int ny, int nz, GridGeom* g) {
   g->fsz_n1 = fs_split_n1(nz);
   g->fsz_lz = fs_z_lz(nz);
   g->zblk = 3;
+  g->zstage = 0;
   g->f_fsz_L = make_fastdiv((unsigned)(5 * g->fsz_lz));
   g->f_fsz_lz = make_fastdiv((unsigned)g->fsz_lz);
   return true;
@@ -195,7 +196,7 @@ struct rve_s {
   Twiddles<double> twd{};
   Twiddles<dfl> twdf{};
   bool floatfloat = false;  // mixed: float64-accuracy transforms in float-float
-  int knobs[6] = {1, 3, 1, 1, 1, 0};  // kernel variants (rve_tuning)
+  int knobs[7] = {1, 3, 1, 1, 1, 0, 0};  // kernel variants (rve_tuning)
   double Fbar[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
   double Fbar_committed[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};  // F-bar of the last committed state
   double* adj_b = nullptr;  // adjoint right-hand side [9][n] (SVK)
@@ -607,6 +608,9 @@ size_t layout_material(rve_t h, Arena& a, bool use_phase) {
     h->vox64 = a.take<double>((size_t)h->nparam * h->n);
     h->vox32 = h->mixed ? a.take<float>((size_t)h->nparam * h->n) : nullptr;
   }
+  // slack after the last array: bulk copies read the 16-byte-aligned span
+  // around a range, up to 15 bytes past an array's end
+  a.take<char>(256);
   return a.off;
 }
 
@@ -614,7 +618,8 @@ size_t layout_material(rve_t h, Arena& a, bool use_phase) {
 // Autotuner of the float32 CG iteration (not in the paper).  Knobs: the
 // DFT engine of each pass (four-step kernels where the axis length has a
 // compiled split, else Stockham), the grid of the persistent z passes
-// (blocks per SM) and composite radices in the Stockham plans.  Coordinate
+// (blocks per SM), composite radices in the Stockham plans and the
+// TMA-staged first z pass.  Coordinate
 // descent from the defaults; each candidate is timed on the handle itself
 // (CUDA events, the best of three runs of eight CG iterations on a predictor
 // right-hand side, after two warm-up iterations).  Results are cached per
@@ -627,9 +632,9 @@ struct TuneKey {
   }
 };
 std::mutex g_tune_mu;
-std::map<TuneKey, std::array<int, 5>> g_tune_cache;
+std::map<TuneKey, std::array<int, 6>> g_tune_cache;
 
-void apply_knobs(rve_t h, const std::array<int, 5>& k) {
+void apply_knobs(rve_t h, const std::array<int, 6>& k) {
   GridGeom& g = h->g;
   GridGeom base;
   make_geom(g.nx, g.ny, g.nz, &base);
@@ -640,7 +645,8 @@ void apply_knobs(rve_t h, const std::array<int, 5>& k) {
   g.px = k[4] ? base.px : base.pxs;
   g.py = k[4] ? base.py : base.pys;
   g.pz = k[4] ? base.pz : base.pzs;
-  for (int i = 0; i < 5; ++i) h->knobs[i] = k[i];
+  g.zstage = k[5];
+  for (int i = 0; i < 6; ++i) h->knobs[i] = k[i];
 }
 
 // Milliseconds per float32 CG iteration with the current knobs; < 0 if the
@@ -678,19 +684,19 @@ int autotune(rve_t h) {
     auto it = g_tune_cache.find(key);
     if (it != g_tune_cache.end()) {
       apply_knobs(h, it->second);
-      h->knobs[5] = 1;
+      h->knobs[6] = 1;
       return RVE_OK;
     }
   }
-  std::array<int, 5> best = {1, 3, 1, 1, 1};
+  std::array<int, 6> best = {1, 3, 1, 1, 1, 0};
   apply_knobs(h, best);
   double tbest = time_cg_iteration(h);
   if (tbest < 0) return fail(h, RVE_ERR_CUDA, "autotune: CG timing run failed");
-  const std::vector<int> choices[5] = {{1, 0}, {3, 2, 1}, {1, 0}, {1, 0}, {1, 0}};
-  for (int knob = 0; knob < 5; ++knob)
+  const std::vector<int> choices[6] = {{1, 0}, {3, 2, 1}, {1, 0}, {1, 0}, {1, 0}, {0, 1}};
+  for (int knob = 0; knob < 6; ++knob)
     for (int v : choices[knob]) {
       if (v == best[knob]) continue;
-      std::array<int, 5> cand = best;
+      std::array<int, 6> cand = best;
       cand[knob] = v;
       apply_knobs(h, cand);
       const double t = time_cg_iteration(h);
@@ -700,7 +706,7 @@ int autotune(rve_t h) {
       }
     }
   apply_knobs(h, best);
-  h->knobs[5] = 1;
+  h->knobs[6] = 1;
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_tune_cache[key] = best;
@@ -956,9 +962,9 @@ int rve_create(rve_t* out, int nx, int ny, int nz, int model, int nphase, const 
   return RVE_OK;
 }
 
-int rve_tuning(rve_t h, int knobs[6]) {
+int rve_tuning(rve_t h, int knobs[7]) {
   if (!h || !knobs) return RVE_ERR_INVALID;
-  for (int i = 0; i < 6; ++i) knobs[i] = h->knobs[i];
+  for (int i = 0; i < 7; ++i) knobs[i] = h->knobs[i];
   return RVE_OK;
 }
 

@@ -252,12 +252,12 @@ def rve_launch_count(h):
 
 
 TUNING_KNOBS = ("four_step_z", "z_blocks_per_sm", "four_step_y", "four_step_x",
-                "composite_radices", "autotuned")
+                "composite_radices", "staged_z", "autotuned")
 
 
 def rve_tuning(h):
     """Kernel variants in use (set by the autotuner or the defaults)."""
-    k = (C.c_int * 6)()
+    k = (C.c_int * 7)()
     _check(lib.rve_tuning(h, k), h)
     return dict(zip(TUNING_KNOBS, (int(v) for v in k)))
 
