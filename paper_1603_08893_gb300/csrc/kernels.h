@@ -84,6 +84,13 @@ __host__ __device__ constexpr Z4tLayout z4t_layout(int nz, int lz) {
   return L;
 }
 
+// Last z pass: twiddles | transposed DFT buffer | r staged per component
+// ([9][sp] floats, 16-byte aligned)
+__host__ __device__ constexpr int z4inv_sp(int nz, int lz) { return (lz * nz + 8 + 3) & ~3; }
+__host__ __device__ constexpr size_t z4inv_stage_off(int nz, int lz) {
+  return (8 * ((size_t)((nz + 1) & ~1) + (size_t)nz * ((5 * lz) | 1)) + 15) & ~(size_t)15;
+}
+
 // z lines per tile of the staged pass: the most that fit 72 KB (three
 // thread blocks per SM); 0 if not even one line fits
 constexpr int fs_zt_lz(int nz) {

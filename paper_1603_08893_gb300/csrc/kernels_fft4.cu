@@ -117,13 +117,19 @@ __global__ void __launch_bounds__(FFT_THREADS, (Fs4Occ<R, N1, N2>::value))
   fs_lines<R, N1, N2, false, LM>(buf, tw2);
   const R qy = signed_freq<R>(y, ny) / (R)ny;
   const R sc = (R)P.scale;
+  // xi_x of each transposed position and xi_z of each kz of the tile
+  R* qxs = reinterpret_cast<R*>(buf + 3 * N * T);  // [N]
+  R* qzs = qxs + N;                                // [T]
+  for (int i = threadIdx.x; i < N + T; i += blockDim.x) {
+    if (i < N) qxs[i] = signed_freq<R>(fs_freq<N1, N2>(i), N) / (R)N;
+    else qzs[i - N] = (R)(k0 + i - N) / (R)P.g.nz;
+  }
+  __syncthreads();
   for (int i = threadIdx.x; i < N * T; i += blockDim.x) {
-    const int t = i % T;
-    const int kx = fs_freq<N1, N2>(i / T);
-    const R qx = signed_freq<R>(kx, N) / (R)N;
-    const R qz = (R)(k0 + t) / (R)P.g.nz;
+    const R qx = qxs[i / T];
+    const R qz = qzs[i % T];
     const R q2 = qx * qx + qy * qy + qz * qz;
-    const R f = (q2 > R(0)) ? sc / q2 : R(0);
+    const R f = (q2 > R(0)) ? sc * __frcp_rn(q2) : R(0);
     const cplx<R> A0 = buf[i], A1 = buf[N * T + i], A2 = buf[2 * N * T + i];
     const R sx = f * (qx * A0.x + qy * A1.x + qz * A2.x);
     const R sy = f * (qx * A0.y + qy * A1.y + qz * A2.y);
@@ -427,70 +433,82 @@ RVE_DEV void zinv_prefetch_tile(const ZinvParams<R, R>& P, int l0, int nl, size_
 }
 
 // Last pass of the fused float CG iteration, persistent like k_zfwd4: per
-// tile the r range is fetched with cp.async while the half spectrum is
-// expanded into the transposed order and transformed back; then
-// r -= alpha Ap in place and r.r.  The next tile's inputs are prefetched
-// into L2 before the DFT stage.
+// tile the nine r ranges are fetched by bulk asynchronous copies (TMA, one
+// thread, completion on an mbarrier whose phase flips per tile; the spans
+// are the 16-byte-aligned ones around each range, rofs[c] the offset of the
+// range in its copy) while the half spectrum is expanded into the
+// transposed order (two kz per thread, 16-byte loads) and transformed back;
+// then r -= alpha Ap in place and r.r.  The next tile's inputs are
+// prefetched into L2 before the DFT stage.
 template <typename R, int N1, int N2>
 __global__ void __launch_bounds__(FFT_THREADS, (Fs4Occ<R, N1, N2>::value))
     k_zinv4_cgr(const ZinvParams<R, R> P) {
+  static_assert(sizeof(R) == 4, "float32 CG iteration");
   constexpr int N = N1 * N2;
   constexpr int lz = fs_z_lz(N), LP = (5 * lz) | 1, hz = N / 2 + 1;
+  constexpr int SP = (lz * N + 8 + 3) & ~3;  // staged floats per r component
+  constexpr int hz2 = (hz + 1) / 2;          // kz pairs per line
   using LM = FsLayout<5 * lz, 0, 1, LP, 5 * lz>;
   if (P.done && *P.done) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ __align__(8) unsigned long long bar;
+  __shared__ int rofs[9];
   const int hzp = P.g.hzp;
   cplx<R>* tw2 = reinterpret_cast<cplx<R>*>(smem_raw);
   cplx<R>* buf = tw2 + ((N + 1) & ~1);
-  R* rt = reinterpret_cast<R*>(buf + (size_t)N * LP);  // [9][lz N]
+  R* rt = reinterpret_cast<R*>(smem_raw + z4inv_stage_off(N, lz));  // [9][SP]
   const size_t n = P.g.n;
   const size_t ss = P.g.sstride;
   const int nlines = P.g.nx * P.g.ny;
   const int ntiles = (nlines + lz - 1) / lz;
+  if (threadIdx.x == 0) mbar_init(&bar, 1);
   fs_twiddles<R, N1, N2>(tw2, P.tw);
   const R alpha = (R)P.st->alpha;
+  __syncthreads();
   double acc = 0.0;
+  unsigned parity = 0;
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int l0 = tile * lz;
     const int nl = min(lz, nlines - l0);
     const int nvox = nl * N;
     const size_t v0 = (size_t)l0 * N;
-    for (int c = 0; c < 9; ++c)
-      for (int i = threadIdx.x; i < nvox; i += blockDim.x)
-        cp_async4(rt + c * lz * N + i, P.r_out + (size_t)c * n + v0 + i);
-    cp_async_commit();
-    // full z spectrum of the packed lines z = a + i b, written transposed
-    constexpr int U = 4;  // (A, B) pairs in flight per thread
-    const int nthr = blockDim.x;
-    const int totl = 5 * lz * hz;
-    for (int i0 = threadIdx.x; i0 < totl; i0 += U * nthr) {
-      cplx<R> A[U], B[U];
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const int i = i0 + u * nthr;
-        const int rest = i / hz;
-        const int kz = i - rest * hz;
-        const int k = rest / lz;
-        const int li = rest - k * lz;
-        A[u] = {R(0), R(0)};
-        B[u] = {R(0), R(0)};
-        if (i < totl && li < nl) {
-          const size_t o = (size_t)(l0 + li) * hzp + kz;
-          A[u] = P.spec[(size_t)(2 * k) * ss + o];
-          if (2 * k + 1 < 9) B[u] = P.spec[(size_t)(2 * k + 1) * ss + o];
-        }
+    if (threadIdx.x == 0) {
+      unsigned total = 0;
+      uintptr_t lo16[9];
+      unsigned bytes[9];
+      for (int c = 0; c < 9; ++c) {
+        const uintptr_t lo = reinterpret_cast<uintptr_t>(P.r_out + (size_t)c * n + v0);
+        const uintptr_t hi = lo + sizeof(R) * (uintptr_t)nvox;
+        lo16[c] = lo & ~(uintptr_t)15;
+        bytes[c] = (unsigned)(((hi + 15) & ~(uintptr_t)15) - lo16[c]);
+        rofs[c] = (int)(lo - lo16[c]) / (int)sizeof(R);
+        total += bytes[c];
       }
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const int i = i0 + u * nthr;
-        if (i >= totl) continue;
-        const int rest = i / hz;
-        const int kz = i - rest * hz;
-        const int k = rest / lz;
-        const int li = rest - k * lz;
-        const int l = k * lz + li;
-        buf[fs_pos<N1, N2>(kz) * LP + l] = {A[u].x - B[u].y, A[u].y + B[u].x};
-        if (kz > 0) buf[fs_pos<N1, N2>(N - kz) * LP + l] = {A[u].x + B[u].y, B[u].x - A[u].y};
+      mbar_arrive_expect_tx(&bar, total);
+      for (int c = 0; c < 9; ++c)
+        bulk_load(rt + (size_t)c * SP, reinterpret_cast<const void*>(lo16[c]), bytes[c], &bar);
+    }
+    // full z spectrum of the packed lines z = a + i b, written transposed;
+    // item = (component pair k, line li, kz pair); a pair's second kz may
+    // lie in the row padding (hz odd), where nothing is read or written
+    const int totl = 5 * lz * hz2;
+    for (int i = threadIdx.x; i < totl; i += blockDim.x) {
+      const int rest = i / hz2;
+      const int kz = 2 * (i - rest * hz2);
+      const int k = rest / lz;
+      const int li = rest - k * lz;
+      float4 A = {0.f, 0.f, 0.f, 0.f}, B = {0.f, 0.f, 0.f, 0.f};
+      if (li < nl) {
+        const size_t o = (size_t)(l0 + li) * hzp + kz;
+        A = *reinterpret_cast<const float4*>(P.spec + (size_t)(2 * k) * ss + o);
+        if (2 * k + 1 < 9) B = *reinterpret_cast<const float4*>(P.spec + (size_t)(2 * k + 1) * ss + o);
+      }
+      const int l = k * lz + li;
+      buf[fs_pos<N1, N2>(kz) * LP + l] = {A.x - B.y, A.y + B.x};
+      if (kz > 0) buf[fs_pos<N1, N2>(N - kz) * LP + l] = {A.x + B.y, B.x - A.y};
+      if (kz + 1 < hz) {
+        buf[fs_pos<N1, N2>(kz + 1) * LP + l] = {A.z - B.w, A.w + B.z};
+        buf[fs_pos<N1, N2>(N - kz - 1) * LP + l] = {A.z + B.w, B.z - A.w};
       }
     }
     __syncthreads();
@@ -500,8 +518,11 @@ __global__ void __launch_bounds__(FFT_THREADS, (Fs4Occ<R, N1, N2>::value))
       zinv_prefetch_tile<R>(P, next * lz, nl2, (size_t)next * lz * N, nl2 * N);
     }
     fs_lines<R, N1, N2, true, LM>(buf, tw2);
-    cp_async_wait<0>();
-    __syncthreads();
+    if (!mbar_wait_bounded(&bar, parity, 1u << 20)) {
+      atomicOr(&P.st->dev_timeout, 1);
+      mbar_wait_bounded(&bar, parity, 1u << 20);  // let the copies land before going on
+    }
+    parity ^= 1u;
     for (int i = threadIdx.x; i < nvox; i += blockDim.x) {
       const int li = i / N;
       const cplx<R>* e = buf + (i - li * N) * LP + li;
@@ -515,17 +536,23 @@ __global__ void __launch_bounds__(FFT_THREADS, (Fs4Occ<R, N1, N2>::value))
       R s = 0;
 #pragma unroll
       for (int c = 0; c < 9; ++c) {
-        const R rn = fma(-alpha, out[c], rt[c * lz * N + i]);
+        const R rn = fma(-alpha, out[c], rt[c * SP + rofs[c] + i]);
         P.r_out[(size_t)c * n + v0 + i] = rn;
         s = fma(rn, rn, s);
       }
       acc += (double)s;
     }
-    __syncthreads();  // buffer and r tile are refilled by the next tile
+    __syncthreads();  // buffer, r copy and rofs are refilled by the next tile
   }
   double v1[1] = {acc}, tot[1];
-  if (last_block_sum<1>(v1, P.partials, &P.st->counter[SLOT_RR], tot) && threadIdx.x == 0)
-    cg_after_rr(P.st, tot[0]);
+  if (last_block_sum<1>(v1, P.partials, &P.st->counter[SLOT_RR], tot) && threadIdx.x == 0) {
+    if (P.st->dev_timeout) {
+      P.st->status = RVE_DEV_ERR_TIMEOUT;
+      P.st->done = 1;
+    } else {
+      cg_after_rr(P.st, tot[0]);
+    }
+  }
 }
 
 cudaError_t g_err4 = cudaSuccess;
@@ -574,7 +601,8 @@ void launch_fft_x4(const GridGeom& g, double scale, cplx<float>* spec, const int
   P.done = done;
   P.tw = tw;
   const int ntiles = 3 * g.ny * ((g.hz + P.t - 1) / P.t);
-  const size_t sm = sizeof(cplx<float>) * ((size_t)((g.nx + 1) & ~1) + 3 * (size_t)g.nx * P.t);
+  const size_t sm = sizeof(cplx<float>) * ((size_t)((g.nx + 1) & ~1) + 3 * (size_t)g.nx * P.t) +
+                    sizeof(float) * ((size_t)g.nx + P.t);
   switch (g.nx) {
 #define RVE_FS_X(N, A, B)                                       \
   case N:                                                       \
@@ -602,9 +630,9 @@ static int sm_count() {
 }
 
 static size_t z4_smem(const GridGeom& g, bool with_r) {
+  if (with_r) return z4inv_stage_off(g.nz, g.fsz_lz) + sizeof(float) * 9 * (size_t)z4inv_sp(g.nz, g.fsz_lz);
   const int LP = (5 * g.fsz_lz) | 1;
-  return sizeof(cplx<float>) * ((size_t)((g.nz + 1) & ~1) + (size_t)g.nz * LP) +
-         (with_r ? sizeof(float) * 9 * (size_t)g.fsz_lz * g.nz : 0);
+  return sizeof(cplx<float>) * ((size_t)((g.nz + 1) & ~1) + (size_t)g.nz * LP);
 }
 
 void launch_zfwd4(const ZfwdParams<float>& P0, cudaStream_t s) {
