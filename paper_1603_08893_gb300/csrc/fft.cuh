@@ -510,3 +510,106 @@ RVE_DEV void fs_lines(cplx<R>* buf, const cplx<R>* tw2) {
     __syncthreads();
   }
 }
+
+// ---------------------------------------------------------------------------
+// The same two phases with one end in global memory, for passes whose lines
+// are tile rows: `gl(l)` gives line l's first element in global memory, its
+// element stride and whether it may be read / written (the caller's tile
+// bounds).  A phase reading global memory loads its N1 (or N2) values
+// straight into registers, a phase writing global memory stores them from
+// registers, so the tile makes a single trip through shared memory.
+// ---------------------------------------------------------------------------
+template <typename R>
+struct GLine {
+  cplx<R>* p;
+  size_t stride;
+  bool rd, wr;
+};
+
+// forward phase A: natural order from global, result to shared memory
+template <typename R, int N1, int N2, typename LM, typename GL>
+RVE_DEV void fs_phase_a_g2s(cplx<R>* buf, const cplx<R>* tw2, const GL& gl) {
+  constexpr int total = LM::L * N2;
+  for (int i = threadIdx.x; i < total; i += blockDim.x) {
+    const int n2 = i / LM::L;
+    const int l = i - n2 * LM::L;
+    const GLine<R> g = gl(l);
+    cplx<R> v[N1];
+#pragma unroll
+    for (int m = 0; m < N1; ++m)
+      v[m] = g.rd ? g.p[(size_t)(N2 * m + n2) * g.stride] : cplx<R>{R(0), R(0)};
+    dft_reg<R, N1, false>(v);
+    if (n2 != 0) {
+      const cplx<R>* w = tw2 + n2 * N1;
+#pragma unroll
+      for (int k1 = 1; k1 < N1; ++k1) v[k1] = c_mul(v[k1], w[k1]);
+    }
+    cplx<R>* line = buf + LM::base(l) + n2 * LM::ES;
+#pragma unroll
+    for (int m = 0; m < N1; ++m) line[m * N2 * LM::ES] = v[m];
+  }
+}
+
+// forward phase B: from shared memory, natural-order result to global
+template <typename R, int N1, int N2, typename LM, typename GL>
+RVE_DEV void fs_phase_b_s2g(const cplx<R>* buf, const GL& gl) {
+  constexpr int total = LM::L * N1;
+  for (int i = threadIdx.x; i < total; i += blockDim.x) {
+    const int k1 = i / LM::L;
+    const int l = i - k1 * LM::L;
+    const cplx<R>* line = buf + LM::base(l) + N2 * k1 * LM::ES;
+    cplx<R> u[N2];
+#pragma unroll
+    for (int j = 0; j < N2; ++j) u[j] = line[j * LM::ES];
+    dft_reg<R, N2, false>(u);
+    const GLine<R> g = gl(l);
+    if (g.wr) {
+#pragma unroll
+      for (int k2 = 0; k2 < N2; ++k2) g.p[(size_t)(k1 + N1 * k2) * g.stride] = u[k2];
+    }
+  }
+}
+
+// inverse phase B: natural-order spectrum from global, to shared memory
+template <typename R, int N1, int N2, typename LM, typename GL>
+RVE_DEV void fs_phase_b_g2s(cplx<R>* buf, const GL& gl) {
+  constexpr int total = LM::L * N1;
+  for (int i = threadIdx.x; i < total; i += blockDim.x) {
+    const int k1 = i / LM::L;
+    const int l = i - k1 * LM::L;
+    const GLine<R> g = gl(l);
+    cplx<R> u[N2];
+#pragma unroll
+    for (int j = 0; j < N2; ++j)
+      u[j] = g.rd ? g.p[(size_t)(k1 + N1 * j) * g.stride] : cplx<R>{R(0), R(0)};
+    dft_reg<R, N2, true>(u);
+    cplx<R>* line = buf + LM::base(l) + N2 * k1 * LM::ES;
+#pragma unroll
+    for (int j = 0; j < N2; ++j) line[j * LM::ES] = u[j];
+  }
+}
+
+// inverse phase A: from shared memory, natural-order result to global
+template <typename R, int N1, int N2, typename LM, typename GL>
+RVE_DEV void fs_phase_a_s2g(const cplx<R>* buf, const cplx<R>* tw2, const GL& gl) {
+  constexpr int total = LM::L * N2;
+  for (int i = threadIdx.x; i < total; i += blockDim.x) {
+    const int n2 = i / LM::L;
+    const int l = i - n2 * LM::L;
+    const cplx<R>* line = buf + LM::base(l) + n2 * LM::ES;
+    cplx<R> v[N1];
+#pragma unroll
+    for (int k1 = 0; k1 < N1; ++k1) v[k1] = line[k1 * N2 * LM::ES];
+    if (n2 != 0) {
+      const cplx<R>* w = tw2 + n2 * N1;
+#pragma unroll
+      for (int k1 = 1; k1 < N1; ++k1) v[k1] = c_mulc(v[k1], w[k1]);
+    }
+    dft_reg<R, N1, true>(v);
+    const GLine<R> g = gl(l);
+    if (g.wr) {
+#pragma unroll
+      for (int m = 0; m < N1; ++m) g.p[(size_t)(N2 * m + n2) * g.stride] = v[m];
+    }
+  }
+}

@@ -18,9 +18,11 @@ struct Fs4Occ {
 };
 
 // Complex DFT along y on tiles of (GRP component-x rows) x ny x (T kz),
-// T and GRP compile-time (fs_y_t, fs_y_grp).  Forward: natural rows in,
-// transposed order in shared memory, natural rows out.  Inverse: rows loaded
-// into transposed positions, natural out.
+// T and GRP compile-time (fs_y_t, fs_y_grp).  The last phase writes its
+// values straight to global memory (forward: phase A then B; inverse: B
+// then A), and the inverse's first phase reads them straight from global
+// memory (N2 = 25 loads per thread in flight), so the transposed
+// intermediate order never leaves shared memory.
 template <typename R, int N1, int N2, bool INV>
 __global__ void __launch_bounds__(FFT_THREADS, (Fs4Occ<R, N1, N2>::value) + (N1 * N2 <= 125 ? 1 : 0))
     k_fft_y4(const LineParams<R> P) {
@@ -39,40 +41,38 @@ __global__ void __launch_bounds__(FFT_THREADS, (Fs4Occ<R, N1, N2>::value) + (N1 
   const int k0 = (tile - tg * ntk) * T, g0 = tg * GRP;
   const int ng = min(GRP, ngroups - g0);
   cplx<R>* gbase = P.spec + (size_t)g0 * N * hzp + k0;
-  {
+  // line l = (group l / T, kz k0 + l % T): rows y at stride hzp
+  auto gl = [&](int l) {
+    const int gi = l / T, t = l - (l / T) * T;
+    return GLine<R>{gbase + (size_t)gi * N * hzp + t, (size_t)hzp, gi < ng && k0 + t < hz,
+                    gi < ng && k0 + t < hz};
+  };
+  if (!INV) {
+    // forward: the whole tile by cp.async first (phase A alone would keep
+    // only N1 loads in flight per thread), phase A in place, phase B to global
     constexpr int EPC = 16 / sizeof(cplx<R>);
     constexpr int CPR = T / EPC;  // 16-byte chunks per row
     const int nch = ng * N * CPR;
     for (int c = threadIdx.x; c < nch; c += blockDim.x) {
       const int row = c / CPR;
       const int t = (c - row * CPR) * EPC;
-      const int gi = row / N;
-      const int y = row - gi * N;
-      const int srow = INV ? gi * N + fs_pos<N1, N2>(y) : row;
       const bool ok = (k0 + t) < hzp;
       const cplx<R>* src = ok ? gbase + (size_t)row * hzp + t : P.spec;
-      cp_async16(buf + srow * T + t, src, ok ? 16 : 0);
+      cp_async16(buf + row * T + t, src, ok ? 16 : 0);
     }
-  }
-  cp_async_commit();
-  fs_twiddles<R, N1, N2>(tw2, P.tw);
-  cp_async_wait<0>();
-  __syncthreads();
-  fs_lines<R, N1, N2, INV, LM>(buf, tw2);
-  // 16-byte stores of kz pairs; a pair may reach one column into the row
-  // padding (kz = hz when hz is odd), which no pass reads as data
-  const int tc = min(T, hz - k0);
-  const int tot2 = ng * N * T / 2;
-  for (int i2 = threadIdx.x; i2 < tot2; i2 += blockDim.x) {
-    const int i = 2 * i2;
-    const int t = i % T;
-    const int srow = i / T;
-    const int gi = srow / N;
-    const int pos = srow - gi * N;
-    const int y = INV ? pos : fs_freq<N1, N2>(pos);
-    if (t < tc)
-      *reinterpret_cast<float4*>(gbase + (size_t)(gi * N + y) * hzp + t) =
-          *reinterpret_cast<const float4*>(buf + i);
+    cp_async_commit();
+    fs_twiddles<R, N1, N2>(tw2, P.tw);
+    cp_async_wait<0>();
+    __syncthreads();
+    fs_phase_a<R, N1, N2, false, LM>(buf, tw2);
+    __syncthreads();
+    fs_phase_b_s2g<R, N1, N2, LM>(buf, gl);
+  } else {
+    fs_twiddles<R, N1, N2>(tw2, P.tw);
+    __syncthreads();
+    fs_phase_b_g2s<R, N1, N2, LM>(buf, gl);
+    __syncthreads();
+    fs_phase_a_s2g<R, N1, N2, LM>(buf, tw2, gl);
   }
 }
 
@@ -99,22 +99,16 @@ __global__ void __launch_bounds__(FFT_THREADS, (Fs4Occ<R, N1, N2>::value))
   const int irow = (int)P.g.f_ny.div((unsigned)q);
   const int y = q - irow * ny;
   cplx<R>* gbase = P.spec + (size_t)(3 * irow) * N * rs + (size_t)y * hzp + k0;
-  {
-    constexpr int EPC = 16 / sizeof(cplx<R>);
-    constexpr int CPR = T / EPC;
-    for (int c = threadIdx.x; c < 3 * N * CPR; c += blockDim.x) {
-      const int row = c / CPR;
-      const int t = (c - row * CPR) * EPC;
-      const bool ok = (k0 + t) < hzp;
-      const cplx<R>* src = ok ? gbase + (size_t)row * rs + t : P.spec;
-      cp_async16(buf + row * T + t, src, ok ? 16 : 0);
-    }
-  }
-  cp_async_commit();
+  // line l = (component l / T of the row, kz k0 + l % T): rows x at stride rs
+  auto gl = [&](int l) {
+    const int c = l / T, t = l - (l / T) * T;
+    return GLine<R>{gbase + (size_t)c * N * rs + t, rs, k0 + t < hz, k0 + t < hz};
+  };
   fs_twiddles<R, N1, N2>(tw2, P.tw);
-  cp_async_wait<0>();
   __syncthreads();
-  fs_lines<R, N1, N2, false, LM>(buf, tw2);
+  fs_phase_a_g2s<R, N1, N2, LM>(buf, tw2, gl);
+  __syncthreads();
+  fs_phase_b<R, N1, N2, false, LM>(buf);
   const R qy = signed_freq<R>(y, ny) / (R)ny;
   const R sc = (R)P.scale;
   // xi_x of each transposed position and xi_z of each kz of the tile
@@ -138,16 +132,9 @@ __global__ void __launch_bounds__(FFT_THREADS, (Fs4Occ<R, N1, N2>::value))
     buf[2 * N * T + i] = {sx * qz, sy * qz};
   }
   __syncthreads();
-  fs_lines<R, N1, N2, true, LM>(buf, tw2);
-  const int tc = min(T, hz - k0);
-  const int tot2 = 3 * N * T / 2;
-  for (int i2 = threadIdx.x; i2 < tot2; i2 += blockDim.x) {
-    const int i = 2 * i2;
-    const int t = i % T;
-    if (t < tc)
-      *reinterpret_cast<float4*>(gbase + (size_t)(i / T) * rs + t) =
-          *reinterpret_cast<const float4*>(buf + i);
-  }
+  fs_phase_b<R, N1, N2, true, LM>(buf);
+  __syncthreads();
+  fs_phase_a_s2g<R, N1, N2, LM>(buf, tw2, gl);
 }
 
 // L2 prefetch of the first-pass inputs of a tile (r and F, after the first
