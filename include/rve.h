@@ -203,6 +203,14 @@ int rve_get_history(rve_t h, double* dst, int dst_on_device);
 int rve_adjoint_grad_mu(rve_t h, const double W[9], double tol_cg, double* grad, int grad_on_device,
                         int* cg_iters);
 
+/* As rve_adjoint_grad_mu, and with the same adjoint field also the gradient
+ * with respect to the per-voxel bulk moduli K at fixed shear moduli:
+ *   dJ/dK_v = (1/n) W : (dP/dK)_v - lambda_v : (dP/dK)_v,
+ *   dP/dK = F . (tr(E) I)   (S = (K - 2 mu/3) tr(E) I + 2 mu E, Eq. elas:S, elas:C).
+ * grad_K, grad_mu: [n] float64 each (host or device), either may be NULL. */
+int rve_adjoint_grad(rve_t h, const double W[9], double tol_cg, double* grad_K, double* grad_mu,
+                     int grads_on_device, int* cg_iters);
+
 /* Homogenised first Piola-Kirchhoff stress P-bar = <P> (voxel average),
  * row-major, host. */
 int rve_homogenized_P(rve_t h, double Pbar[9]);

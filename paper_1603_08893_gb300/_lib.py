@@ -74,6 +74,8 @@ _SIGS = {
     "rve_get_history": (C.c_int, [_H, _P, C.c_int]),
     "rve_adjoint_grad_mu": (C.c_int, [_H, _P, C.c_double, _P, C.c_int,
                                       C.POINTER(C.c_int)]),
+    "rve_adjoint_grad": (C.c_int, [_H, _P, C.c_double, _P, _P, C.c_int,
+                                   C.POINTER(C.c_int)]),
     "rve_homogenized_P": (C.c_int, [_H, _P]),
     "rve_set_F": (C.c_int, [_H, _P, C.c_int]),
     "rve_apply_operator": (C.c_int, [_H, _P, _P, C.c_int]),

@@ -1,9 +1,10 @@
 """torch.autograd wrapper: homogenised stress of an SVK cell as a
-differentiable function of its per-voxel shear moduli.
+differentiable function of its per-voxel shear and bulk moduli.
 
 forward solves the cell (Newton-CG through the C ABI) for the macroscopic
 deformation; backward is one adjoint CG solve with the same operator
-followed by the per-voxel sensitivity kernel (rve_adjoint_grad_mu).
+followed by the per-voxel sensitivity kernel (rve_adjoint_grad), which
+gives both gradients from the same adjoint field.
 """
 from __future__ import annotations
 
@@ -14,7 +15,8 @@ from .rve import RVE
 
 
 class HomogenizedStress(torch.autograd.Function):
-    """P-bar(mu) for fixed bulk moduli K and macroscopic F-bar."""
+    """P-bar(mu, K) for a fixed macroscopic F-bar (K: tensor of the same
+    shape as mu, or a scalar / array treated as constant)."""
 
     @staticmethod
     def forward(ctx, mu, K, Fbar, increments=1, tol_newton=1e-5, tol_cg=1e-8,
@@ -33,14 +35,16 @@ class HomogenizedStress(torch.autograd.Function):
         ctx.rve = r
         ctx.adjoint_tol = adjoint_tol
         ctx.device = mu.device
+        ctx.K_is_tensor = isinstance(K, torch.Tensor)
         return torch.from_numpy(r.homogenized_P()).to(mu.device)
 
     @staticmethod
     def backward(ctx, grad_P):
         W = grad_P.detach().cpu().numpy().astype(np.float64)
-        g, _ = ctx.rve.adjoint_grad_mu(W, ctx.adjoint_tol)
+        gK, gmu, _ = ctx.rve.adjoint_grad(W, ctx.adjoint_tol)
         ctx.rve.close()
-        return (torch.from_numpy(g).to(ctx.device),) + (None,) * 8
+        dK = torch.from_numpy(gK).to(ctx.device) if ctx.K_is_tensor else None
+        return (torch.from_numpy(gmu).to(ctx.device), dK) + (None,) * 7
 
 
 def homogenized_stress(mu, K, Fbar, **kw):

@@ -191,7 +191,7 @@ void launch_cg_init(size_t n9, const double* b, const double* Ax, RC* r, RC* x, 
 template <typename RC>
 void launch_accumulate(size_t n9, double* y, const RC* x, cudaStream_t s);
 void launch_adjoint_grad(const double* F, const double* lam, const double W[9], size_t n, double* g,
-                         cudaStream_t s);
+                         double* gK, cudaStream_t s);
 
 // ---- finite-strain J2 (kernels_j2.cu) ----
 template <typename RO>

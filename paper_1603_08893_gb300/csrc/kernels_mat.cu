@@ -291,9 +291,12 @@ __global__ void __launch_bounds__(VEC_THREADS) k_accumulate(size_t n9, double* _
 struct W9 {
   double w[9];
 };
+// dJ/dmu (g) and, when gK != null, dJ/dK per voxel from the adjoint field:
+// (W/n - lambda) : dP/dq with dP/dmu = F . (2 dev E), dP/dK = F . (tr(E) I).
 __global__ void __launch_bounds__(VEC_THREADS) k_adjoint_grad(const double* __restrict__ F,
                                                               const double* __restrict__ lam,
-                                                              W9 W, size_t n, double* __restrict__ g) {
+                                                              W9 W, size_t n, double* __restrict__ g,
+                                                              double* __restrict__ gK) {
   const size_t stride = (size_t)gridDim.x * blockDim.x;
   const double inv_n = 1.0 / (double)n;
   for (size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
@@ -307,7 +310,7 @@ __global__ void __launch_bounds__(VEC_THREADS) k_adjoint_grad(const double* __re
       for (int b = 0; b < 3; ++b)
         E[a][b] = 0.5 * (f[a] * f[b] + f[3 + a] * f[3 + b] + f[6 + a] * f[6 + b] - (a == b ? 1.0 : 0.0));
     const double tr = E[0][0] + E[1][1] + E[2][2];
-    double acc = 0.0;
+    double acc = 0.0, accK = 0.0;
 #pragma unroll
     for (int a = 0; a < 3; ++a)
 #pragma unroll
@@ -315,9 +318,12 @@ __global__ void __launch_bounds__(VEC_THREADS) k_adjoint_grad(const double* __re
         double d = 0.0;  // (F . 2 dev E)_ab
 #pragma unroll
         for (int c = 0; c < 3; ++c) d += f[3 * a + c] * 2.0 * (E[c][b] - (c == b ? tr / 3.0 : 0.0));
-        acc += (W.w[3 * a + b] * inv_n - lam[(size_t)(3 * a + b) * n + v]) * d;
+        const double wl = W.w[3 * a + b] * inv_n - lam[(size_t)(3 * a + b) * n + v];
+        acc += wl * d;
+        accK += wl * f[3 * a + b] * tr;  // (F . tr(E) I)_ab
       }
     g[v] = acc;
+    if (gK) gK[v] = accK;
   }
 }
 
@@ -388,10 +394,10 @@ void launch_accumulate(size_t n9, double* y, const RC* x, cudaStream_t s) {
 }
 
 void launch_adjoint_grad(const double* F, const double* lam, const double W[9], size_t n, double* g,
-                         cudaStream_t s) {
+                         double* gK, cudaStream_t s) {
   W9 w;
   for (int c = 0; c < 9; ++c) w.w[c] = W[c];
-  k_adjoint_grad<<<grid_for(n), VEC_THREADS, 0, s>>>(F, lam, w, n, g);
+  k_adjoint_grad<<<grid_for(n), VEC_THREADS, 0, s>>>(F, lam, w, n, g, gK);
 }
 
 template <typename Ti, typename To>

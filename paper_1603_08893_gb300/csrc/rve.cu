@@ -1263,7 +1263,13 @@ extern "C" {
 
 int rve_adjoint_grad_mu(rve_t h, const double W[9], double tol_cg, double* grad, int on_device,
                         int* cg_iters) {
-  if (!h || !W || !grad || !(tol_cg > 0.0)) return RVE_ERR_INVALID;
+  if (!grad) return RVE_ERR_INVALID;
+  return rve_adjoint_grad(h, W, tol_cg, nullptr, grad, on_device, cg_iters);
+}
+
+int rve_adjoint_grad(rve_t h, const double W[9], double tol_cg, double* grad_K, double* grad_mu,
+                     int on_device, int* cg_iters) {
+  if (!h || !W || !(grad_K || grad_mu) || !(tol_cg > 0.0)) return RVE_ERR_INVALID;
   if (h->model != RVE_SVK) return fail(h, RVE_ERR_UNSUPPORTED, "adjoint: SVK only");
   int rc = sync_state(h);
   if (rc) return rc;
@@ -1281,10 +1287,15 @@ int rve_adjoint_grad_mu(rve_t h, const double W[9], double tol_cg, double* grad,
   rc = h->mixed ? adjoint_solve<float>(h, tol_cg, &its) : adjoint_solve<double>(h, tol_cg, &its);
   if (rc) return rc;
   if (cg_iters) *cg_iters = its;
-  launch_adjoint_grad(h->F, h->adj_l, W, h->n, h->tmp64, h->s);
+  launch_adjoint_grad(h->F, h->adj_l, W, h->n, h->tmp64, h->tmp64 + h->n, h->s);
   h->launches += 1;
   CK(cudaGetLastError());
-  return copy_out(h, grad, h->tmp64, h->n * sizeof(double), on_device);
+  if (grad_mu) {
+    rc = copy_out(h, grad_mu, h->tmp64, h->n * sizeof(double), on_device);
+    if (rc) return rc;
+  }
+  if (grad_K) return copy_out(h, grad_K, h->tmp64 + h->n, h->n * sizeof(double), on_device);
+  return RVE_OK;
 }
 
 int rve_get_history(rve_t h, double* dst, int on_device) {

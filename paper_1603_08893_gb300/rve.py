@@ -199,6 +199,19 @@ def rve_adjoint_grad_mu(h, W, n, tol_cg=1e-12, out=None):
     return g, its.value
 
 
+def rve_adjoint_grad(h, W, n, tol_cg=1e-12):
+    """(dJ/dK, dJ/dmu) per voxel for J = W : P-bar from one adjoint solve;
+    returns (grad_K, grad_mu, cg_iterations)."""
+    Wc = np.ascontiguousarray(W, dtype=np.float64).reshape(9)
+    its = C.c_int(0)
+    gK = np.empty(n, dtype=np.float64)
+    gm = np.empty(n, dtype=np.float64)
+    _check(lib.rve_adjoint_grad(h, Wc.ctypes.data_as(C.c_void_p), float(tol_cg),
+                                gK.ctypes.data_as(C.c_void_p), gm.ctypes.data_as(C.c_void_p), 0,
+                                C.byref(its)), h)
+    return gK, gm, its.value
+
+
 def rve_homogenized_P(h):
     P = np.empty(9, dtype=np.float64)
     _check(lib.rve_homogenized_P(h, P.ctypes.data_as(C.c_void_p)), h)
@@ -327,6 +340,11 @@ class RVE:
         """Gradient of W : P-bar with respect to per-voxel shear moduli, [*shape]."""
         g, its = rve_adjoint_grad_mu(self.h, W, self.n, tol_cg)
         return g.reshape(self.shape), its
+
+    def adjoint_grad(self, W, tol_cg=1e-12):
+        """(dJ/dK, dJ/dmu), each [*shape], for J = W : P-bar, and the CG iterations."""
+        gK, gm, its = rve_adjoint_grad(self.h, W, self.n, tol_cg)
+        return gK.reshape(self.shape), gm.reshape(self.shape), its
 
     def get_history(self):
         """J2: committed (Cp^-1 [6 symmetric components], eps_p) per voxel, [7, *shape]."""

@@ -78,3 +78,48 @@ def test_envelope_identity_for_mean_energy(state):
             vals.append(np.mean(svk.energy(q.F, q.K, q.mu)))
         fd = (vals[0] - vals[1]) / (2 * h)
         assert abs(fd - expected[idx]) < 1e-6 * np.abs(expected).max()
+
+
+def _problem_K(shape, mu, K):
+    return solver.SVKProblem(shape, K, mu)
+
+
+def test_bulk_gradient_matches_finite_differences(state):
+    shape, mu, Fbar, p, rng = state
+    W = np.diag([1.0, 0.5, -0.3])
+    W[0, 1] = 0.7
+    gK, gmu = adjoint.grad_params(p, W, tol_cg=1e-13, cg_atol=1e-15)
+    assert np.abs(gmu - adjoint.grad_mu(p, W, tol_cg=1e-13, cg_atol=1e-15)).max() < 1e-12 * np.abs(gmu).max()
+    K = np.full(shape, 0.833)
+    for flat in rng.choice(mu.size, 4, replace=False):
+        idx = np.unravel_index(flat, shape)
+        h = 1e-4 * K[idx]
+        vals = []
+        for s in (+1, -1):
+            K2 = K.copy()
+            K2[idx] += s * h
+            q = _problem_K(shape, mu, K2)
+            q.increment(Fbar, **TIGHT)
+            vals.append(np.sum(W * q.homogenized_P()))
+        fd = (vals[0] - vals[1]) / (2 * h)
+        assert abs(gK[idx] - fd) < 1e-6 * np.abs(gK).max()
+
+
+def test_bulk_envelope_identity(state):
+    """dW-bar/dK_k = (1/n) (tr E_k)^2 / 2 at fixed F-bar (W = K tr^2(E)/2 + ...)."""
+    shape, mu, Fbar, p, rng = state
+    E = svk.green_lagrange(p.F)
+    expected = 0.5 * np.trace(E) ** 2 / mu.size
+    K = np.full(shape, 0.833)
+    for flat in rng.choice(mu.size, 3, replace=False):
+        idx = np.unravel_index(flat, shape)
+        h = 1e-3 * K[idx]
+        vals = []
+        for s in (+1, -1):
+            K2 = K.copy()
+            K2[idx] += s * h
+            q = _problem_K(shape, mu, K2)
+            q.increment(Fbar, **TIGHT)
+            vals.append(np.mean(svk.energy(q.F, q.K, q.mu)))
+        fd = (vals[0] - vals[1]) / (2 * h)
+        assert abs(fd - expected[idx]) < 1e-6 * np.abs(expected).max() + 1e-14
