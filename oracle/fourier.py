@@ -1,8 +1,9 @@
 """Discrete Fourier transform and the compatibility projection G.
 
 Follows Sec. 2.3-2.5 (Eq. weak:discr:FFT-intermediate, Eq. G) and
-Appendix D (Eq. G_red).  Grids must have an odd number of nodes along every
-axis (Eq. G is stated for odd grids; even grids are Appendix C).
+Appendix D (Eq. G_red); grids of even size along an axis follow Appendix C:
+G-hat is zero at every frequency vector with a Nyquist component (the
+variant that keeps the deformation gradient compatible).
 
 Readings of the paper used here:
 * The ``fftshift``/``ifftshift`` pair of the paper's listing only re-centres
@@ -11,8 +12,9 @@ Readings of the paper used here:
   frequencies are used.
 * xi_i = q_i / L_i with L_i the cell size; voxels are unit cubes, so
   L_i = N_i.  On cubic grids the scaling cancels in xi (x) xi / |xi|^2.
-* The inverse transform's result is real for odd grids (G-hat is real and
-  even in q); the imaginary round-off is dropped, as the listing does.
+* The inverse transform's result is real (G-hat is real and even in q, with
+  the Nyquist frequencies of even axes zeroed); the imaginary round-off is
+  dropped, as the listing does.
 """
 import numpy as np
 
@@ -40,13 +42,20 @@ def get_backend():
 
 
 def frequencies(n: int) -> np.ndarray:
-    """Signed integer frequencies in standard DFT order for odd ``n``:
-    k for k <= (n-1)/2, else k - n.  Same set as the centred range
-    -(n-1)/2 .. (n-1)/2 of the paper's listing, in unshifted order."""
-    if n % 2 != 1:
-        raise ValueError("odd grid sizes only (Eq. G)")
+    """Signed integer frequencies in standard DFT order: k for
+    k <= (n-1)/2, else k - n.  Odd n: the centred range -(n-1)/2 .. (n-1)/2
+    of the paper's listing, in unshifted order; even n: -n/2 .. n/2-1 (the
+    listing of Appendix C), the Nyquist index n/2 carrying -n/2."""
     k = np.arange(n)
     return np.where(k <= (n - 1) // 2, k, k - n)
+
+
+def nyquist_mask(grid_shape) -> np.ndarray:
+    """True at the frequency vectors with a component at the Nyquist index
+    n/2 of an axis of even size n (Appendix C), shape [nx, ny, nz]."""
+    m = [(np.arange(n) == n // 2) & (n % 2 == 0) for n in grid_shape]
+    X, Y, Z = np.meshgrid(*m, indexing="ij")
+    return X | Y | Z
 
 
 def dft_matrix(n: int, inverse: bool = False) -> np.ndarray:
@@ -96,20 +105,21 @@ def scaled_frequencies(grid_shape):
 
 
 def ghat_reduced(grid_shape):
-    """g-hat_jl(q) = xi_j xi_l / |xi|^2, zero at q = 0 (Eq. G_red).
-    Shape [3, 3, nx, ny, nz]."""
+    """g-hat_jl(q) = xi_j xi_l / |xi|^2, zero at q = 0 (Eq. G_red) and at
+    Nyquist frequencies (Appendix C).  Shape [3, 3, nx, ny, nz]."""
     xi = scaled_frequencies(grid_shape)
     n2 = (xi * xi).sum(axis=0)
     g = np.einsum("j...,l...->jl...", xi, xi)
-    nz_ = n2 != 0
-    g[:, :, nz_] /= n2[nz_]
-    g[:, :, ~nz_] = 0.0
+    keep = (n2 != 0) & ~nyquist_mask(grid_shape)
+    g[:, :, keep] /= n2[keep]
+    g[:, :, ~keep] = 0.0
     return g
 
 
 def ghat4(grid_shape):
     """The full G-hat_ijlm(q) = d_im xi_j xi_l / |xi|^2 (Eq. G), zero at
-    q = 0.  Shape [3,3,3,3,*grid] -- for small grids only (81 reals/node)."""
+    q = 0 and at Nyquist frequencies.  Shape [3,3,3,3,*grid] -- for small
+    grids only (81 reals/node)."""
     g = ghat_reduced(grid_shape)
     return np.einsum("im,jl...->ijlm...", np.eye(3), g)
 

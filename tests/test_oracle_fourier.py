@@ -55,8 +55,13 @@ def test_frequencies_are_centred_set():
         q = fourier.frequencies(n)
         assert sorted(q) == list(range(-(n - 1) // 2, (n - 1) // 2 + 1))
         assert q[0] == 0
-    with pytest.raises(ValueError):
-        fourier.frequencies(4)
+    # even sizes: the listing's range -n/2 .. n/2 - 1 (Appendix C)
+    for n in (2, 4, 6, 16):
+        q = fourier.frequencies(n)
+        assert sorted(q) == list(range(-n // 2, n // 2))
+        assert q[0] == 0 and q[n // 2] == -n // 2
+    m = fourier.nyquist_mask((4, 3, 6))
+    assert m.sum() == 3 * 6 + 4 * 3 - 3 and m[2, 0, 0] and m[0, 1, 3] and not m[1, 1, 1]
 
 
 @pytest.mark.parametrize("shape", [(5, 7, 9), (31, 31, 31), (3, 11, 5)])
@@ -141,3 +146,54 @@ def test_literal_and_reduced_projection_agree():
     rng = np.random.default_rng(4)
     A = rng.standard_normal((3, 3, 5, 3, 7))
     assert np.abs(fourier.G_literal(A) - fourier.G(A)).max() < 1e-14
+
+
+# ---- even grids (Appendix C): Nyquist frequencies zeroed ----
+
+def _compatible_field_no_nyquist(shape, rng):
+    phi = rng.standard_normal((3,) + shape)
+    phihat = np.fft.fftn(phi, axes=(-3, -2, -1))
+    phihat[:, fourier.nyquist_mask(shape)] = 0.0
+    xi = fourier.scaled_frequencies(shape)
+    Ahat = 2j * np.pi * np.einsum("i...,j...->ij...", phihat, xi)
+    return np.real(np.fft.ifftn(Ahat, axes=(-3, -2, -1)))
+
+
+@pytest.mark.parametrize("shape", [(4, 6, 8), (2, 5, 4), (16, 16, 16)])
+def test_even_grid_projection(shape):
+    rng = np.random.default_rng(8)
+    A = rng.standard_normal((3, 3) + shape)
+    B = rng.standard_normal((3, 3) + shape)
+    GA, GB = fourier.G(A), fourier.G(B)
+    scale = np.abs(GA).max()
+    assert np.abs(fourier.G(GA) - GA).max() < 1e-13 * scale
+    assert abs((A * GB).sum() - (GA * B).sum()) < 1e-12 * np.abs(A).sum()
+    assert np.abs(t.grid_mean(GA)).max() < 1e-14 * scale
+    # nothing at the Nyquist frequencies; the listing's explicit loop agrees
+    GAh = np.fft.fftn(GA, axes=(-3, -2, -1))
+    assert np.abs(GAh[:, :, fourier.nyquist_mask(shape)]).max() < 1e-12 * np.abs(GAh).max()
+    assert np.abs(fourier.G_literal(A) - GA).max() < 1e-13 * scale
+    # compatible fields without Nyquist content are kept
+    C = _compatible_field_no_nyquist(shape, rng)
+    assert np.abs(fourier.G(C) - C).max() < 1e-12 * np.abs(C).max()
+
+
+@pytest.mark.parametrize("shape", [(4, 3, 3), (2, 4, 3)])
+def test_even_grid_matrix_equals_least_squares_projector(shape):
+    """On even grids G is the orthogonal projector onto the gradients of
+    trigonometric displacements without Nyquist content."""
+    M = _matrix_of(fourier.G, shape)
+    n = int(np.prod(shape))
+    xi = fourier.scaled_frequencies(shape)
+    mask = fourier.nyquist_mask(shape)
+    D = np.zeros((9 * n, 3 * n))
+    for k in range(3 * n):
+        e = np.zeros(3 * n)
+        e[k] = 1.0
+        uh = np.fft.fftn(e.reshape((3,) + shape), axes=(-3, -2, -1))
+        uh[:, mask] = 0.0
+        gh = 2j * np.pi * np.einsum("i...,j...->ij...", uh, xi)
+        D[:, k] = np.real(np.fft.ifftn(gh, axes=(-3, -2, -1))).reshape(-1)
+    Pd = D @ np.linalg.pinv(D, rcond=1e-10)
+    assert np.abs(M - Pd).max() < 1e-12
+    assert np.linalg.matrix_rank(M, tol=1e-9) == 3 * (n - 1 - int(mask.sum()))

@@ -185,3 +185,34 @@ def test_paper_example_iteration_count():
     assert abs(st.newton_iters - g["newton_iterations"]) <= g["newton_iterations_tolerance"]
     # the prescribed macroscopic deformation is held exactly (Eq. mean:zero)
     assert np.abs(t.grid_mean(prob.F) - synth.simple_shear(1.0)).max() < 1e-13
+
+
+# ---- even grids (Appendix C: Nyquist frequencies of G-hat zeroed) ----
+
+def test_even_grid_newton_cg_matches_newton_dense():
+    shape = (4, 3, 4)
+    Fbar = synth.simple_shear(0.2)
+    p1 = _problem(shape, 5)
+    p2 = _problem(shape, 5)
+    p1.increment(Fbar, tol_newton=1e-10, tol_cg=1e-12, cg_atol=TIGHT_ATOL)
+    p2.increment(Fbar, tol_newton=1e-10, tol_cg=1e-12, cg_atol=TIGHT_ATOL,
+                 linear_solver=_dense_solver(shape))
+    assert np.abs(p1.F - p2.F).max() < 1e-11
+    # F stays compatible: no Nyquist content in its fluctuation
+    Fh = np.fft.fftn(p1.F - t.uniform(Fbar, shape), axes=(-3, -2, -1))
+    assert np.abs(Fh[:, :, fourier.nyquist_mask(shape)]).max() < 1e-12
+
+
+def test_even_grid_laminate_closed_form():
+    """Layers of even thickness on an even grid: the exact piecewise-constant
+    solution has no Nyquist content, so the Appendix C projection reproduces
+    it exactly."""
+    shape = (8, 4, 6)
+    ph = synth.laminate(shape, 0, fraction=0.5)
+    params = synth.two_phase_params(5.0)
+    prob = solver.SVKProblem.from_phase(ph, params)
+    Fbar = np.eye(3) + np.array([[0.05, 0.2, -0.03], [0.01, -0.04, 0.1], [0.02, 0.03, 0.06]])
+    prob.increment(Fbar, tol_newton=1e-10, tol_cg=1e-12, cg_atol=TIGHT_ATOL)
+    F1, F0 = _laminate_exact(Fbar, np.eye(3)[0], ph.mean(), tuple(params[1]), tuple(params[0]))
+    exact = np.where(ph[None, None] == 1, F1[:, :, None, None, None], F0[:, :, None, None, None])
+    assert np.abs(prob.F - exact).max() < 1e-10
