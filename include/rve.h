@@ -18,8 +18,10 @@
  * Sec. 5 finite-strain J2 plasticity).
  *
  * Conventions (all calls):
- *  - Grids are nx x ny x nz voxels, each size odd (Eq. G is stated for odd
- *    grids); n = nx*ny*nz.  Voxel v = (x*ny + y)*nz + z (z fastest).
+ *  - Grids are nx x ny x nz voxels, n = nx*ny*nz, voxel v = (x*ny + y)*nz + z
+ *    (z fastest).  Eq. G is stated for odd sizes; an axis of even size gets
+ *    the treatment of Appendix C: G-hat is zero at every frequency vector
+ *    with a Nyquist component (the deformation gradient stays compatible).
  *  - Second-order tensor fields are [9][n] float64, component 3*i+j holding
  *    A_ij; F_ij = dx_i/dX_j (Appendix A).  Fourth-order tangents are [81][n]
  *    with component ((i*3+j)*3+k)*3+l holding K_ijkl in the convention of

@@ -10,7 +10,8 @@
 //
 // Odd radices 3, 5, 7, 11 use the symmetric form of the R-point DFT
 // (pairs x_r +- x_(R-r)); composite radices 9, 15, 21, 25 nest two of them
-// in registers; other primes use a direct sum, one output per thread.
+// in registers; even radices 2, 4, 8 (even grids, Appendix C) nest the
+// two-point butterfly; other primes use a direct sum, one output per thread.
 // Stages alternate between two shared-memory buffers.
 #pragma once
 #include "common.cuh"
@@ -267,12 +268,16 @@ RVE_DEV void dft_split(cplx<R> (&v)[R1 * R2]) {
   for (int k = 0; k < M; ++k) v[k] = o[k];
 }
 
-// M-point DFT in registers for any odd M: the symmetric form for a prime,
-// otherwise split off the smallest prime factor.
+// M-point DFT in registers: the two-point butterfly, the symmetric form for
+// an odd prime, otherwise split off the smallest prime factor.
 template <typename R, int M, bool INV>
 RVE_DEV void dft_reg(cplx<R> (&v)[M]) {
   if constexpr (M == 1) {
     return;
+  } else if constexpr (M == 2) {
+    const cplx<R> a = v[0];
+    v[0] = c_add(a, v[1]);
+    v[1] = c_sub(a, v[1]);
   } else if constexpr (smallest_factor(M) == M) {
     dft_const<R, M, INV>(v);
   } else {
@@ -318,6 +323,46 @@ RVE_DEV void stage_pp2(const cplx<R>* __restrict__ src, cplx<R>* __restrict__ ds
     const int d = jq * Ns * RAD + jr;
 #pragma unroll
     for (int r = 0; r < RAD; ++r) dst[base + (d + r * Ns) * lm.es] = v[r];
+  }
+  __syncthreads();
+}
+
+// A Stockham stage of any compile-time radix M (used for the even radices
+// 2, 4, 8): the data movement of stage_pp, butterfly dft_reg<M>.
+template <typename R, int M, bool INV>
+RVE_DEV void stage_ppM(const cplx<R>* __restrict__ src, cplx<R>* __restrict__ dst,
+                       const LineMap lm, int L, const FastDiv fL, int N, int Ns,
+                       const FastDiv fNs, const FastDiv fnb, const cplx<R>* tw) {
+  const int nb = N / M;
+  const int tws = N / (Ns * M);
+  const int total = L * nb;
+  for (int b = threadIdx.x; b < total; b += blockDim.x) {
+    int l, j;
+    if (lm.lf) {
+      j = (int)fL.div((unsigned)b);
+      l = b - j * L;
+    } else {
+      l = (int)fnb.div((unsigned)b);
+      j = b - l * nb;
+    }
+    const int jq = (int)fNs.div((unsigned)j);
+    const int jr = j - jq * Ns;
+    const int base = lm.base(l);
+    cplx<R> v[M];
+#pragma unroll
+    for (int r = 0; r < M; ++r) v[r] = src[base + (j + r * nb) * lm.es];
+    if (jr != 0) {
+      const int step = jr * tws;
+#pragma unroll
+      for (int r = 1; r < M; ++r) {
+        const cplx<R> w = tw[r * step];
+        v[r] = INV ? c_mulc(v[r], w) : c_mul(v[r], w);
+      }
+    }
+    dft_reg<R, M, INV>(v);
+    const int d = jq * Ns * M + jr;
+#pragma unroll
+    for (int r = 0; r < M; ++r) dst[base + (d + r * Ns) * lm.es] = v[r];
   }
   __syncthreads();
 }
@@ -383,6 +428,9 @@ RVE_DEV cplx<R>* fft_lines(cplx<R>* a, cplx<R>* b, const LineMap& lm, int L, con
       case 5: stage_pp<R, 5, INV>(a, b, lm, L, fL, p.n, Ns, fNs, fnb, tw); break;
       case 7: stage_pp<R, 7, INV>(a, b, lm, L, fL, p.n, Ns, fNs, fnb, tw); break;
       case 11: stage_pp<R, 11, INV>(a, b, lm, L, fL, p.n, Ns, fNs, fnb, tw); break;
+      case 2: stage_ppM<R, 2, INV>(a, b, lm, L, fL, p.n, Ns, fNs, fnb, tw); break;
+      case 4: stage_ppM<R, 4, INV>(a, b, lm, L, fL, p.n, Ns, fNs, fnb, tw); break;
+      case 8: stage_ppM<R, 8, INV>(a, b, lm, L, fL, p.n, Ns, fNs, fnb, tw); break;
       default:
         if constexpr (!is_dfl<R>::value) {  // float-float plans have no composite radices
           if (rad == 9) {

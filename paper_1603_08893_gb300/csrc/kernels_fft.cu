@@ -154,6 +154,8 @@ __global__ void FFT_BOUNDS(R) k_fft_x_proj(const LineParams<R> P) {
   using RQ = typename std::conditional<is_dfl<R>::value, double, R>::type;
   const RQ qy_ = signed_freq<RQ>(y, ny) / (RQ)ny;
   const RQ sc_ = (RQ)P.scale;
+  // Nyquist frequencies of even axes: G-hat = 0 there (Appendix C)
+  const bool nyq_y = (ny % 2 == 0) && (2 * y == ny);
   for (int i = threadIdx.x; i < nx * T; i += blockDim.x) {
     const int t = i & (T - 1);
     const int x = i >> ts;
@@ -161,7 +163,9 @@ __global__ void FFT_BOUNDS(R) k_fft_x_proj(const LineParams<R> P) {
     const RQ qx_ = signed_freq<RQ>(x, nx) / (RQ)nx;
     const RQ qz_ = (RQ)(k0 + t) / (RQ)P.g.nz;
     const RQ q2 = qx_ * qx_ + qy_ * qy_ + qz_ * qz_;
-    const R f = R((q2 > RQ(0)) ? sc_ / q2 : RQ(0));
+    const bool nyq = nyq_y || ((nx % 2 == 0) && (2 * x == nx)) ||
+                     ((P.g.nz % 2 == 0) && (2 * (k0 + t) == P.g.nz));
+    const R f = R((q2 > RQ(0) && !nyq) ? sc_ / q2 : RQ(0));
     const R qx = R(qx_), qy = R(qy_), qz = R(qz_);
     const cplx<R> A0 = X[i], A1 = X[nx * T + i], A2 = X[2 * nx * T + i];
     const R sx = f * (qx * A0.x + qy * A1.x + qz * A2.x);

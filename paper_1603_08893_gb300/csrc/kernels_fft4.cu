@@ -119,11 +119,16 @@ __global__ void __launch_bounds__(FFT_THREADS, (Fs4Occ<R, N1, N2>::value))
     else qzs[i - N] = (R)(k0 + i - N) / (R)P.g.nz;
   }
   __syncthreads();
+  // Nyquist frequencies of even y / z axes: G-hat = 0 there (Appendix C;
+  // this kernel's x length is odd)
+  const bool nyq_y = (ny % 2 == 0) && (2 * y == ny);
+  const int kz_nyq = (P.g.nz % 2 == 0) ? P.g.nz / 2 : -1;
   for (int i = threadIdx.x; i < N * T; i += blockDim.x) {
     const R qx = qxs[i / T];
     const R qz = qzs[i % T];
     const R q2 = qx * qx + qy * qy + qz * qz;
-    const R f = (q2 > R(0)) ? sc * __frcp_rn(q2) : R(0);
+    const bool nyq = nyq_y || (k0 + i % T == kz_nyq);
+    const R f = (q2 > R(0) && !nyq) ? sc * __frcp_rn(q2) : R(0);
     const cplx<R> A0 = buf[i], A1 = buf[N * T + i], A2 = buf[2 * N * T + i];
     const R sx = f * (qx * A0.x + qy * A1.x + qz * A2.x);
     const R sy = f * (qx * A0.y + qy * A1.y + qz * A2.y);

@@ -48,9 +48,9 @@ bool factor_plan(int n, AxisPlan* p, bool composite = true) {
   int m = n;
   // pairs of small primes become one composite stage (two radix passes for
   // one trip through shared memory); then single radices
-  const int fixed[] = {25, 21, 15, 9, 11, 7, 5, 3};
+  const int fixed[] = {25, 21, 15, 9, 8, 11, 7, 5, 4, 3, 2};
   for (int f : fixed)
-    while (m % f == 0 && (composite || f == 11 || f == 7 || f == 5 || f == 3)) {
+    while (m % f == 0 && (composite || f == 11 || f == 7 || f == 5 || f == 3 || f <= 8)) {
       if (p->nst >= RVE_MAX_STAGES) return false;
       p->rad[p->nst++] = f;
       m /= f;
@@ -75,7 +75,8 @@ bool factor_plan(int n, AxisPlan* p, bool composite = true) {
     const int r = p->rad[s];
     const int nb = n / r;
     if (r == 3 && nb > 512) return false;
-    if ((r == 5 || r == 7 || r == 11 || r == 9 || r == 15 || r == 21 || r == 25) && nb > 256)
+    if ((r == 5 || r == 7 || r == 11 || r == 9 || r == 15 || r == 21 || r == 25 || r == 2 ||
+         r == 4 || r == 8) && nb > 1024)
       return false;
     if (r > 11 && r != 15 && r != 21 && r != 25 && n > 512) return false;
   }
@@ -91,7 +92,6 @@ int pick_lz(int nz, size_t csize, size_t budget) {
 
 bool make_geom(int nx, int ny, int nz, GridGeom* g) {
   if (nx < 1 || ny < 1 || nz < 1) return false;
-  if (nx % 2 == 0 || ny % 2 == 0 || nz % 2 == 0) return false;
   if (nx > 2047 || ny > 2047 || nz > 2047) return false;
   g->nx = nx;
   g->ny = ny;
@@ -817,7 +817,7 @@ int rve_create(rve_t* out, int nx, int ny, int nz, int model, int nphase, const 
   if (model != RVE_SVK && model != RVE_J2) return bail(RVE_ERR_INVALID, "unknown model");
   h->model = model;
   if (!make_geom(nx, ny, nz, &h->g))
-    return bail(RVE_ERR_INVALID, "grid sizes must be odd, positive and supported by the DFT plan");
+    return bail(RVE_ERR_INVALID, "grid sizes must be positive and supported by the DFT plan");
   int tan = 0;
   int rc = resolve_options(opt, &h->opt, model, &tan);
   if (rc) return bail(rc, rc == RVE_ERR_UNSUPPORTED ? "model not available in this build"

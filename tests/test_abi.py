@@ -46,8 +46,9 @@ def test_options_and_status_without_gpu(lib):
     assert o.max_newton == 50 and o.max_cg == 10000 and o.precision == 0
     assert _lib.lib.rve_status_string(-5).decode().startswith("CG breakdown")
     n = ctypes.c_size_t(0)
-    # even grid sizes are rejected (Eq. G is stated for odd grids)
-    assert _lib.lib.rve_workspace_size(4, 5, 5, 0, ctypes.byref(o), ctypes.byref(n)) == -1
+    # even sizes are accepted (Appendix C); non-positive sizes are not
+    assert _lib.lib.rve_workspace_size(4, 5, 5, 0, ctypes.byref(o), ctypes.byref(n)) == 0
+    assert _lib.lib.rve_workspace_size(0, 5, 5, 0, ctypes.byref(o), ctypes.byref(n)) == -1
     assert _lib.lib.rve_workspace_size(125, 125, 125, 0, ctypes.byref(o), ctypes.byref(n)) == 0
     assert n.value > 9 * 125 ** 3 * 8 * 4
     o.precision = 1

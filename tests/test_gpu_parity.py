@@ -26,7 +26,9 @@ GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
 SHAPES = [(1, 1, 1), (3, 5, 7), (5, 1, 3), (9, 11, 13), (15, 15, 15),
           (21, 27, 33), (31, 31, 31), (45, 45, 45), (63, 63, 63), (27, 3, 125),
-          (81, 75, 7), (105, 9, 5), (7, 5, 225)]
+          (81, 75, 7), (105, 9, 5), (7, 5, 225),
+          # even sizes (Appendix C: G-hat zeroed at Nyquist frequencies)
+          (4, 6, 8), (16, 16, 16), (15, 16, 17), (2, 3, 4), (10, 12, 14)]
 
 
 def rel(a, b):
@@ -83,7 +85,8 @@ def test_operator_fp64_matches_oracle(shape, tangent):
 
 
 @pytest.mark.parametrize("shape", [(9, 11, 13), (31, 31, 31), (63, 63, 63), (27, 3, 125),
-                                   (81, 75, 7), (7, 5, 225), (15, 21, 125), (45, 63, 27)])
+                                   (81, 75, 7), (7, 5, 225), (15, 21, 125), (45, 63, 27),
+                                   (16, 20, 24), (15, 16, 17), (125, 16, 32)])
 @pytest.mark.parametrize("tangent", ["recompute", "full81"])
 def test_operator_mixed_matches_oracle(shape, tangent):
     r, F, K, mu, rng = _random_problem(shape, 4, "mixed", tangent)
@@ -150,7 +153,7 @@ def test_cube31_mixed_schedule_matches_tight_oracle():
     r.close()
 
 
-@pytest.mark.parametrize("shape", [(15, 21, 125), (27, 33, 45)])
+@pytest.mark.parametrize("shape", [(15, 21, 125), (27, 33, 45), (16, 18, 20)])
 def test_mixed_solve_matches_tight_oracle(shape):
     """Converged mixed solve on axis lengths served by the four-step kernels
     (the fused float CG iteration on every pass) against the tightly
@@ -235,7 +238,7 @@ def test_laminate_closed_form(axis, prec, tol):
 
 def test_invalid_arguments_are_rejected():
     with pytest.raises(RVEError) as e:
-        RVE((4, 5, 5), phase=np.zeros((4, 5, 5), np.uint8), phase_params=[[1, 1]])
+        RVE((0, 5, 5), phase=np.zeros((0, 5, 5), np.uint8), phase_params=[[1, 1]])
     assert e.value.code == -1
     with pytest.raises(RVEError):
         RVE((5, 5, 5), phase=np.full((5, 5, 5), 3, np.uint8), phase_params=[[1, 1], [2, 2]])

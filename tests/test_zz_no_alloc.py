@@ -55,6 +55,6 @@ def test_noalloc_rejects_grids_beyond_its_scratch():
     code = lib.rve_project_noalloc(63, 63, 63, ctypes.c_void_p(A.data_ptr()),
                                    ctypes.c_void_p(A.data_ptr()), None)
     assert code == RVE_ERR_NOMEM
-    code = lib.rve_project_noalloc(4, 5, 5, ctypes.c_void_p(A.data_ptr()),
+    code = lib.rve_project_noalloc(0, 5, 5, ctypes.c_void_p(A.data_ptr()),
                                    ctypes.c_void_p(A.data_ptr()), None)
     assert code == -1
