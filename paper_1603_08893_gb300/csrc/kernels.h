@@ -38,7 +38,7 @@ struct GridGeom {
   int zstage;  // first z pass with TMA-staged, pipelined inputs (SVK, phase map);
                // off by default (slower at 125^3: its tiles are half as large),
                // a candidate of the autotuner
-  int fsy_t, fsy_grp, fsx_t, fsz_lz;
+  int fsy_t, fsy_grp, fsx_t, fsz_lz, fszf_lz;
   FastDiv f_fsy_ntk, f_fsx_ntk, f_fsy_L, f_fsx_L, f_fsz_L, f_fsz_lz;
 };
 
@@ -60,6 +60,10 @@ constexpr int fs_y_t() { return 16; }  // kz values per y tile row (128 bytes)
 constexpr int fs_y_grp(int n) { return 49152 / (8 * n * 16) > 1 ? 49152 / (8 * n * 16) : 1; }
 constexpr int fs_x_t(int n) {
   return 8 * 3 * n * 16 <= 65536 ? 16 : (8 * 3 * n * 8 <= 65536 ? 8 : 4);
+}
+// first z pass: tiles of about 32 KB (larger tiles measured slower)
+constexpr int fs_zf_lz(int n) {
+  return (32768 / (8 * n) - 1) / 5 < 1 ? 1 : ((32768 / (8 * n) - 1) / 5 > 64 ? 64 : (32768 / (8 * n) - 1) / 5);
 }
 constexpr int fs_z_lz(int n) {
   return (32768 / (8 * n) - 1) / 5 < 1 ? 1 : ((32768 / (8 * n) - 1) / 5 > 64 ? 64 : (32768 / (8 * n) - 1) / 5);

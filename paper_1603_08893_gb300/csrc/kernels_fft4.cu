@@ -182,7 +182,7 @@ template <typename R, int SRC, int TAN, int N1, int N2>
 __global__ void __launch_bounds__(FFT_THREADS, (Fs4Occ<R, N1, N2>::value))
     k_zfwd4(const ZfwdParams<R> P) {
   constexpr int N = N1 * N2;
-  constexpr int lz = fs_z_lz(N), LP = (5 * lz) | 1, hz = N / 2 + 1;
+  constexpr int lz = fs_zf_lz(N), LP = (5 * lz) | 1, hz = N / 2 + 1;
   using LM = FsLayout<5 * lz, 0, 1, LP, 5 * lz>;
   if (P.done && *P.done) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -220,23 +220,41 @@ __global__ void __launch_bounds__(FFT_THREADS, (Fs4Occ<R, N1, N2>::value))
       zfwd_prefetch_tile<R, SRC, TAN>(P, sc, (size_t)next * lz * N, nl2 * N);
     }
     fs_lines<R, N1, N2, false, LM>(buf, tw2);
-    for (int i = threadIdx.x; i < 5 * lz * hz; i += blockDim.x) {
-      const int rest = i / hz;
-      const int kz = i - rest * hz;
+    // half spectrum, two kz per thread (16-byte stores); with hz odd the
+    // last pair's second value lands in the row padding as zero
+    constexpr int hz2 = (hz + 1) / 2;
+    for (int i = threadIdx.x; i < 5 * lz * hz2; i += blockDim.x) {
+      const int rest = i / hz2;
+      const int kz = 2 * (i - rest * hz2);
       const int k = rest / lz;
       const int li = rest - k * lz;
       if (li >= nl) continue;
       const int l = k * lz + li;
-      const cplx<R> z1 = buf[fs_pos<N1, N2>(kz) * LP + l];
-      cplx<R> z2 = buf[fs_pos<N1, N2>(kz ? N - kz : 0) * LP + l];
-      z2.y = -z2.y;
-      const size_t o = (size_t)(l0 + li) * hzp + kz;
-      P.spec[(size_t)(2 * k) * ss + o] = {R(0.5) * (z1.x + z2.x), R(0.5) * (z1.y + z2.y)};
-      if (2 * k + 1 < 9) {
-        // B = (z1 - conj(z_-k)) / (2i)
-        const R dx = R(0.5) * (z1.x - z2.x), dy = R(0.5) * (z1.y - z2.y);
-        P.spec[(size_t)(2 * k + 1) * ss + o] = {dy, -dx};
+      float4 a, b;
+      {
+        const cplx<R> z1 = buf[fs_pos<N1, N2>(kz) * LP + l];
+        cplx<R> z2 = buf[fs_pos<N1, N2>(kz ? N - kz : 0) * LP + l];
+        z2.y = -z2.y;
+        // A = (z1 + conj(z_-k)) / 2, B = (z1 - conj(z_-k)) / (2i)
+        a.x = R(0.5) * (z1.x + z2.x);
+        a.y = R(0.5) * (z1.y + z2.y);
+        b.x = R(0.5) * (z1.y - z2.y);
+        b.y = -R(0.5) * (z1.x - z2.x);
       }
+      if (kz + 1 < hz) {
+        const cplx<R> z1 = buf[fs_pos<N1, N2>(kz + 1) * LP + l];
+        cplx<R> z2 = buf[fs_pos<N1, N2>(N - kz - 1) * LP + l];
+        z2.y = -z2.y;
+        a.z = R(0.5) * (z1.x + z2.x);
+        a.w = R(0.5) * (z1.y + z2.y);
+        b.z = R(0.5) * (z1.y - z2.y);
+        b.w = -R(0.5) * (z1.x - z2.x);
+      } else {
+        a.z = a.w = b.z = b.w = R(0);
+      }
+      const size_t o = (size_t)(l0 + li) * hzp + kz;
+      *reinterpret_cast<float4*>(P.spec + (size_t)(2 * k) * ss + o) = a;
+      if (2 * k + 1 < 9) *reinterpret_cast<float4*>(P.spec + (size_t)(2 * k + 1) * ss + o) = b;
     }
     __syncthreads();  // the buffer is refilled by the next tile
   }
@@ -623,7 +641,7 @@ static int sm_count() {
 
 static size_t z4_smem(const GridGeom& g, bool with_r) {
   if (with_r) return z4inv_stage_off(g.nz, g.fsz_lz) + sizeof(float) * 9 * (size_t)z4inv_sp(g.nz, g.fsz_lz);
-  const int LP = (5 * g.fsz_lz) | 1;
+  const int LP = (5 * g.fszf_lz) | 1;
   return sizeof(cplx<float>) * ((size_t)((g.nz + 1) & ~1) + (size_t)g.nz * LP);
 }
 
@@ -646,7 +664,7 @@ void launch_zfwd4(const ZfwdParams<float>& P0, cudaStream_t s) {
         break;
     }
   }
-  P.lz = g.fsz_lz;
+  P.lz = g.fszf_lz;
   const int nlines = g.nx * g.ny;
   // persistent: as many thread blocks as are resident at once
   const int grid = std::min((nlines + P.lz - 1) / P.lz, std::max(1, g.zblk) * sm_count());

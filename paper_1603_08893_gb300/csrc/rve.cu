@@ -148,6 +148,7 @@ bool make_geom(int nx, int ny, int nz, GridGeom* g) {
   // 5 lz lines x nz (about 32 KB) plus, in the last pass, the r tile
   g->fsz_n1 = fs_split_n1(nz);
   g->fsz_lz = fs_z_lz(nz);
+  g->fszf_lz = fs_zf_lz(nz);
   g->zblk = 3;
   g->zstage = 0;
   g->f_fsz_L = make_fastdiv((unsigned)(5 * g->fsz_lz));
