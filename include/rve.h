@@ -273,6 +273,21 @@ const char* rve_batch_last_error(rve_batch_t b);
 const char* rve_last_error(rve_t h);
 const char* rve_status_string(int code);
 
+/* Checkpoint of the converged state (the paper keeps the converged state and
+ * history between increments, Algorithm 1): F, the committed F, P, the
+ * tangent data, the J2 history, the material in its internal form, F-bar
+ * and the kernel variants, written to `path` (host byte order).
+ * rve_load creates a new handle from such a file: every solver option comes
+ * from the file; opt (may be NULL) supplies only stream and workspace (NULL
+ * workspace: the library allocates).  Continuing from a loaded handle gives
+ * bit-identical results to continuing the saved one.  RVE_ERR_INVALID for
+ * unreadable or malformed files. */
+int rve_save(rve_t h, const char* path);
+int rve_load(rve_t* out, const char* path, const rve_options* opt);
+
+/* Grid sizes of a handle. */
+int rve_grid(rve_t h, int dims[3]);
+
 /* Kernel variants in use (not in the paper; set by rve_options.autotune or
  * the defaults): knobs[0..5] = four-step z pass, blocks per SM of the
  * persistent z passes, four-step y pass, four-step x pass, composite radices

@@ -963,6 +963,194 @@ int rve_create(rve_t* out, int nx, int ny, int nz, int model, int nphase, const 
   return RVE_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Checkpoint / resume.  File: a fixed header (CkptHeader) followed by tagged
+// blocks {char tag[8]; uint64 bytes; data}, host byte order.  Saved: F, the
+// committed F, P, the tangent data, the J2 histories, the material buffers
+// in their internal form (so that a resumed run is bit-identical), and on
+// the host F-bar, the committed F-bar and the kernel variants.
+// ---------------------------------------------------------------------------
+struct CkptHeader {
+  char magic[8];
+  int version, nx, ny, nz, model, nparam, use_phase, precision, tangent, residual;
+  int max_newton, max_cg, mixed_refine;
+  double cg_tol_floor, cg_atol;
+  int knobs[7];
+  double Fbar[9], Fbar_committed[9];
+};
+
+struct CkptBlock {
+  const char* tag;
+  void* dev;
+  size_t bytes;
+};
+
+static std::vector<CkptBlock> ckpt_blocks(rve_t h) {
+  const size_t n = h->n, ro = h->mixed ? 4 : 8;
+  std::vector<CkptBlock> b = {{"F", h->F, 9 * n * 8}, {"Ft", h->Ft, 9 * n * 8}, {"P", h->P, 9 * n * 8}};
+  if (h->K4) b.push_back({"K4", h->K4, 81 * n * ro});
+  if (h->Fop && h->Fop != (void*)h->F) b.push_back({"Fop", h->Fop, 9 * n * ro});
+  if (h->Sop) b.push_back({"Sop", h->Sop, 6 * n * ro});
+  if (h->hc) b.push_back({"hc", h->hc, 7 * n * 8});
+  if (h->ht) b.push_back({"ht", h->ht, 7 * n * 8});
+  if (h->phase) {
+    b.push_back({"phase", h->phase, n});
+    b.push_back({"t64", h->table64, 256 * 4 * 8});
+    b.push_back({"t32", h->table32, 256 * 4 * 4});
+  } else {
+    b.push_back({"v64", h->vox64, (size_t)h->nparam * n * 8});
+    if (h->vox32) b.push_back({"v32", h->vox32, (size_t)h->nparam * n * 4});
+  }
+  return b;
+}
+
+int rve_save(rve_t h, const char* path) {
+  if (!h || !path) return RVE_ERR_INVALID;
+  FILE* f = std::fopen(path, "wb");
+  if (!f) return fail(h, RVE_ERR_INVALID, std::string("cannot open ") + path);
+  CkptHeader hd;
+  std::memset(&hd, 0, sizeof(hd));
+  std::memcpy(hd.magic, "RVECKPT1", 8);
+  hd.version = 1;
+  hd.nx = h->g.nx;
+  hd.ny = h->g.ny;
+  hd.nz = h->g.nz;
+  hd.model = h->model;
+  hd.nparam = h->nparam;
+  hd.use_phase = h->phase != nullptr;
+  hd.precision = h->opt.precision;
+  hd.tangent = h->tan == TAN_FULL81 ? RVE_TAN_FULL81 : RVE_TAN_RECOMPUTE;
+  hd.residual = h->opt.residual;
+  hd.max_newton = h->opt.max_newton;
+  hd.max_cg = h->opt.max_cg;
+  hd.mixed_refine = h->opt.mixed_refine;
+  hd.cg_tol_floor = h->opt.cg_tol_floor;
+  hd.cg_atol = h->opt.cg_atol;
+  std::memcpy(hd.knobs, h->knobs, sizeof(hd.knobs));
+  std::memcpy(hd.Fbar, h->Fbar, sizeof(hd.Fbar));
+  std::memcpy(hd.Fbar_committed, h->Fbar_committed, sizeof(hd.Fbar_committed));
+  bool ok = std::fwrite(&hd, sizeof(hd), 1, f) == 1;
+  std::vector<char> host;
+  for (const CkptBlock& b : ckpt_blocks(h)) {
+    if (!ok) break;
+    host.resize(b.bytes);
+    if (cudaMemcpyAsync(host.data(), b.dev, b.bytes, cudaMemcpyDeviceToHost, h->s) != cudaSuccess ||
+        cudaStreamSynchronize(h->s) != cudaSuccess) {
+      std::fclose(f);
+      return fail(h, RVE_ERR_CUDA, "checkpoint copy failed");
+    }
+    char tag[8] = {0};
+    std::strncpy(tag, b.tag, 8);
+    const unsigned long long nb = b.bytes;
+    ok = std::fwrite(tag, 8, 1, f) == 1 && std::fwrite(&nb, 8, 1, f) == 1 &&
+         std::fwrite(host.data(), 1, b.bytes, f) == b.bytes;
+  }
+  ok = (std::fclose(f) == 0) && ok;
+  return ok ? RVE_OK : fail(h, RVE_ERR_INVALID, std::string("write failed: ") + path);
+}
+
+int rve_load(rve_t* out, const char* path, const rve_options* opt) {
+  if (!out || !path) return RVE_ERR_INVALID;
+  *out = nullptr;
+  FILE* f = std::fopen(path, "rb");
+  if (!f) return RVE_ERR_INVALID;
+  CkptHeader hd;
+  if (std::fread(&hd, sizeof(hd), 1, f) != 1 || std::memcmp(hd.magic, "RVECKPT1", 8) != 0 ||
+      hd.version != 1) {
+    std::fclose(f);
+    return RVE_ERR_INVALID;
+  }
+  // all blocks into host memory first
+  std::map<std::string, std::vector<char>> blocks;
+  for (;;) {
+    char tag[9] = {0};
+    unsigned long long nb = 0;
+    if (std::fread(tag, 8, 1, f) != 1) break;
+    if (std::fread(&nb, 8, 1, f) != 1 || nb > ((unsigned long long)1 << 40)) {
+      std::fclose(f);
+      return RVE_ERR_INVALID;
+    }
+    std::vector<char> data(nb);
+    if (std::fread(data.data(), 1, nb, f) != nb) {
+      std::fclose(f);
+      return RVE_ERR_INVALID;
+    }
+    blocks[tag] = std::move(data);
+  }
+  std::fclose(f);
+  const size_t n = (size_t)hd.nx * hd.ny * hd.nz;
+  // material in the user's form (the internal buffers are restored below)
+  std::vector<double> params;
+  std::vector<uint8_t> ph;
+  int nphase = 0;
+  if (hd.use_phase) {
+    auto& pb = blocks["phase"];
+    auto& tb = blocks["t64"];
+    if (pb.size() != n || tb.size() != 256 * 4 * 8) return RVE_ERR_INVALID;
+    ph.assign(pb.begin(), pb.end());
+    for (uint8_t v : ph) nphase = std::max(nphase, (int)v + 1);
+    const double* t = reinterpret_cast<const double*>(tb.data());
+    params.assign((size_t)nphase * hd.nparam, 0.0);
+    for (int k = 0; k < nphase; ++k) {
+      for (int q = 0; q < hd.nparam; ++q) params[k * hd.nparam + q] = t[k * hd.nparam + q];
+      params[k * hd.nparam] = t[k * hd.nparam] + 2.0 * t[k * hd.nparam + 1] / 3.0;  // K
+    }
+  } else {
+    auto& vb = blocks["v64"];
+    if (vb.size() != (size_t)hd.nparam * n * 8) return RVE_ERR_INVALID;
+    const double* v = reinterpret_cast<const double*>(vb.data());
+    params.assign(v, v + (size_t)hd.nparam * n);
+    for (size_t i = 0; i < n; ++i) params[i] = v[i] + 2.0 * v[n + i] / 3.0;  // K
+  }
+  rve_options o;
+  rve_default_options(&o);
+  o.precision = hd.precision;
+  o.tangent = hd.tangent;
+  o.residual = hd.residual;
+  o.max_newton = hd.max_newton;
+  o.max_cg = hd.max_cg;
+  o.mixed_refine = hd.mixed_refine;
+  o.cg_tol_floor = hd.cg_tol_floor;
+  o.cg_atol = hd.cg_atol;
+  if (opt) {
+    o.stream = opt->stream;
+    o.workspace = opt->workspace;
+    o.workspace_bytes = opt->workspace_bytes;
+  }
+  rve_t h = nullptr;
+  int rc = rve_create(&h, hd.nx, hd.ny, hd.nz, hd.model, nphase, hd.use_phase ? ph.data() : nullptr,
+                      hd.use_phase ? params.data() : nullptr, hd.use_phase ? nullptr : params.data(), &o);
+  if (rc) return rc;
+  for (const CkptBlock& b : ckpt_blocks(h)) {
+    auto it = blocks.find(b.tag);
+    if (it == blocks.end() || it->second.size() != b.bytes) {
+      rve_destroy(h);
+      return RVE_ERR_INVALID;
+    }
+    if (cudaMemcpyAsync(b.dev, it->second.data(), b.bytes, cudaMemcpyHostToDevice, h->s) != cudaSuccess ||
+        cudaStreamSynchronize(h->s) != cudaSuccess) {
+      rve_destroy(h);
+      return RVE_ERR_CUDA;
+    }
+  }
+  std::memcpy(h->Fbar, hd.Fbar, sizeof(hd.Fbar));
+  std::memcpy(h->Fbar_committed, hd.Fbar_committed, sizeof(hd.Fbar_committed));
+  std::array<int, 6> k;
+  for (int i = 0; i < 6; ++i) k[i] = hd.knobs[i];
+  apply_knobs(h, k);
+  h->knobs[6] = hd.knobs[6];
+  *out = h;
+  return RVE_OK;
+}
+
+int rve_grid(rve_t h, int dims[3]) {
+  if (!h || !dims) return RVE_ERR_INVALID;
+  dims[0] = h->g.nx;
+  dims[1] = h->g.ny;
+  dims[2] = h->g.nz;
+  return RVE_OK;
+}
+
 int rve_tuning(rve_t h, int knobs[7]) {
   if (!h || !knobs) return RVE_ERR_INVALID;
   for (int i = 0; i < 7; ++i) knobs[i] = h->knobs[i];

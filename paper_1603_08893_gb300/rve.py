@@ -9,6 +9,7 @@ the library as its workspace.
 from __future__ import annotations
 
 import ctypes as C
+import os
 
 import numpy as np
 
@@ -264,6 +265,19 @@ def rve_launch_count(h):
     return int(c.value)
 
 
+def rve_save(h, path):
+    """Checkpoint of the converged state of a handle."""
+    _check(lib.rve_save(h, os.fsencode(path)), h)
+
+
+def rve_load(path, stream=None):
+    """Handle created from a checkpoint file (library-allocated memory)."""
+    o = _options(stream=stream)
+    h = C.c_void_p()
+    _check(lib.rve_load(C.byref(h), os.fsencode(path), C.byref(o)), what=f"rve_load {path}")
+    return h
+
+
 TUNING_KNOBS = ("four_step_z", "z_blocks_per_sm", "four_step_y", "four_step_x",
                 "composite_radices", "staged_z", "autotuned")
 
@@ -364,6 +378,21 @@ class RVE:
 
     def tuning(self):
         return rve_tuning(self.h)
+
+    def save(self, path):
+        rve_save(self.h, path)
+
+    @classmethod
+    def load(cls, path, stream=None):
+        """A cell resumed from a checkpoint written by save()."""
+        self = cls.__new__(cls)
+        self.h = rve_load(path, stream)
+        dims = (C.c_int * 3)()
+        _check(lib.rve_grid(self.h, dims), self.h)
+        self.shape = tuple(int(d) for d in dims)
+        self.n = int(np.prod(self.shape))
+        self._keep = []
+        return self
 
 
 class RVEBatch:

@@ -55,3 +55,13 @@ def test_options_and_status_without_gpu(lib):
     m = ctypes.c_size_t(0)
     assert _lib.lib.rve_workspace_size(125, 125, 125, 0, ctypes.byref(o), ctypes.byref(m)) == 0
     assert 0 < m.value < 2 * n.value
+
+
+def test_load_rejects_malformed_checkpoint(lib, tmp_path):
+    import ctypes
+    from paper_1603_08893_gb300 import _lib
+    bad = tmp_path / "bad.ckpt"
+    bad.write_bytes(b"not a checkpoint" * 4)
+    h = ctypes.c_void_p()
+    assert _lib.lib.rve_load(ctypes.byref(h), str(bad).encode(), None) == -1
+    assert _lib.lib.rve_load(ctypes.byref(h), str(tmp_path / "missing").encode(), None) == -1
