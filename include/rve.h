@@ -71,9 +71,12 @@ extern "C" {
                        reductions in float64 (Newton acts as iterative refinement) */
 
 /* storage of the tangent used by the CG operator */
-#define RVE_TAN_AUTO 0      /* library choice (RECOMPUTE for SVK) */
+#define RVE_TAN_AUTO 0      /* library choice (RECOMPUTE for SVK, SYM45 for J2) */
 #define RVE_TAN_FULL81 1    /* K_ijkl stored, 81 reals per voxel */
 #define RVE_TAN_RECOMPUTE 2 /* SVK: dP = dF.S + F.dS recomputed from F (and S) */
+#define RVE_TAN_SYM45 3     /* K stored as the upper triangle of the symmetric 9x9 matrix
+                               dP_ij/dF_kl (major symmetry K_ijkl = K_lkji of both
+                               models), 45 reals per voxel */
 
 /* arithmetic of the mixed path's float64-accuracy transforms */
 #define RVE_RES_FLOATFLOAT 0 /* float-float on the float32 pipe: hi + lo float pairs,

@@ -30,6 +30,7 @@ RVE_MIXED = 1
 RVE_TAN_AUTO = 0
 RVE_TAN_FULL81 = 1
 RVE_TAN_RECOMPUTE = 2
+RVE_TAN_SYM45 = 3
 RVE_MAX_NEWTON_LOG = 64
 
 

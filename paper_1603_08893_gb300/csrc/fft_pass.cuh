@@ -98,6 +98,14 @@ RVE_DEV void tangent_post(const TangentView<R>& T, size_t v, size_t n, const Tan
         for (int kl = 0; kl < 9; ++kl) s = fma(__ldg(T.K4 + (size_t)((b * 3 + a) * 9 + kl) * n + v), in[kl], s);
         out[3 * a + b] = s;
       }
+  } else if constexpr (TAN == TAN_SYM45) {
+#pragma unroll
+    for (int r = 0; r < 9; ++r) {
+      R s = 0;
+#pragma unroll
+      for (int c = 0; c < 9; ++c) s = fma(__ldg(T.K4 + (size_t)sym45_index(r, c) * n + v), in[c], s);
+      out[r] = s;
+    }
   } else if constexpr (TAN == TAN_SVK) {
     const R* F = q.F;
     const R lam = q.lam, mu = q.mu;

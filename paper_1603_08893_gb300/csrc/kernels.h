@@ -9,7 +9,15 @@
 #include "fft.cuh"
 
 // tangent storage modes
-enum { TAN_FULL81 = 1, TAN_SVK = 2 };
+enum { TAN_FULL81 = 1, TAN_SVK = 2, TAN_SYM45 = 3 };
+
+// Packed symmetric tangent: the 9x9 matrix M[r][c] = dP_r / dF_c
+// (r = 3i + j for P_ij, c = 3k + l for F_kl) is symmetric for the
+// hyperelastic SVK law and the J2 update with frozen history (major symmetry
+// K_ijkl = K_lkji); its upper triangle r <= c is stored row by row.
+__host__ __device__ constexpr int sym45_index(int r, int c) {
+  return r <= c ? r * 9 - r * (r - 1) / 2 + (c - r) : c * 9 - c * (c - 1) / 2 + (r - c);
+}
 // sources of the forward pass input
 // SRC_CGPX: fused CG iteration front: p = r + beta p, lagged x += alpha p,
 // and p.(K:p) (= p.Ap for compatible p, G being an orthogonal projector)
@@ -118,8 +126,8 @@ inline int fs_split_n1(int n) {
 
 template <typename R>
 struct TangentView {
-  int mode;           // TAN_FULL81 / TAN_SVK / 0 (plain copy)
-  const R* K4;        // [81][n]
+  int mode;           // TAN_FULL81 / TAN_SYM45 / TAN_SVK / 0 (plain copy)
+  const R* K4;        // [81][n] (FULL81) or [45][n] (SYM45)
   const R* Fop;       // [9][n]
   const R* Sop;       // [6][n] or null (compute S from F)
   MatView<R> mat;     // lambda, mu
@@ -200,7 +208,8 @@ void launch_adjoint_grad(const double* F, const double* lam, const double W[9], 
 // ---- finite-strain J2 (kernels_j2.cu) ----
 template <typename RO>
 void launch_j2_constitutive(const double* F, size_t n, MatView<double> mat, const double* hc,
-                            double* ht, double* P, RO* K4, SolverState* st, cudaStream_t s);
+                            double* ht, double* P, RO* K4, SolverState* st, cudaStream_t s,
+                            int sym45 = 0);
 void launch_j2_k4_full(const double* F, size_t v0, size_t count, size_t n, MatView<double> mat,
                        const double* hc, double* dst, cudaStream_t s);
 size_t vec_max_blocks();

@@ -369,16 +369,20 @@ void launch_zfwd(const GridGeom& g, int src, const TangentView<R>& tan, const R*
   const int tm = tan.mode;
   if (src == SRC_FIELD) {
     if (tm == TAN_FULL81) ZF(SRC_FIELD, TAN_FULL81);
+    else if (tm == TAN_SYM45) ZF(SRC_FIELD, TAN_SYM45);
     else if (tm == TAN_SVK) ZF(SRC_FIELD, TAN_SVK);
     else ZF(SRC_FIELD, 0);
   } else if (src == SRC_CGP) {
     if (tm == TAN_FULL81) ZF(SRC_CGP, TAN_FULL81);
+    else if (tm == TAN_SYM45) ZF(SRC_CGP, TAN_SYM45);
     else ZF(SRC_CGP, TAN_SVK);
   } else if (src == SRC_CGPX) {
     if (tm == TAN_FULL81) ZF(SRC_CGPX, TAN_FULL81);
+    else if (tm == TAN_SYM45) ZF(SRC_CGPX, TAN_SYM45);
     else ZF(SRC_CGPX, TAN_SVK);
   } else {
     if (tm == TAN_FULL81) ZF(SRC_UNIFORM, TAN_FULL81);
+    else if (tm == TAN_SYM45) ZF(SRC_UNIFORM, TAN_SYM45);
     else ZF(SRC_UNIFORM, TAN_SVK);
   }
 #undef ZF
@@ -486,6 +490,10 @@ static void init_r() {
   allow_big_smem(k_zfwd<R, SRC_CGPX, TAN_SVK>);
   allow_big_smem(k_zfwd<R, SRC_UNIFORM, TAN_FULL81>);
   allow_big_smem(k_zfwd<R, SRC_UNIFORM, TAN_SVK>);
+  allow_big_smem(k_zfwd<R, SRC_FIELD, TAN_SYM45>);
+  allow_big_smem(k_zfwd<R, SRC_CGP, TAN_SYM45>);
+  allow_big_smem(k_zfwd<R, SRC_CGPX, TAN_SYM45>);
+  allow_big_smem(k_zfwd<R, SRC_UNIFORM, TAN_SYM45>);
   allow_big_smem(k_fft_y<R, true>);
   allow_big_smem(k_fft_y<R, false>);
   allow_big_smem(k_fft_x_proj<R>);

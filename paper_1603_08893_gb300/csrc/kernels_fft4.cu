@@ -669,11 +669,12 @@ void launch_zfwd4(const ZfwdParams<float>& P0, cudaStream_t s) {
   // persistent: as many thread blocks as are resident at once
   const int grid = std::min((nlines + P.lz - 1) / P.lz, std::max(1, g.zblk) * sm_count());
   const size_t sm = z4_smem(g, false);
-  const bool full = P.tan.mode == TAN_FULL81;
+  const int tm = P.tan.mode;
   switch (g.nz) {
 #define RVE_FS_ZF(N, A, B)                                                                    \
   case N:                                                                                     \
-    if (full) k_zfwd4<float, SRC_CGPX, TAN_FULL81, A, B><<<grid, FFT_THREADS, sm, s>>>(P);    \
+    if (tm == TAN_FULL81) k_zfwd4<float, SRC_CGPX, TAN_FULL81, A, B><<<grid, FFT_THREADS, sm, s>>>(P); \
+    else if (tm == TAN_SYM45) k_zfwd4<float, SRC_CGPX, TAN_SYM45, A, B><<<grid, FFT_THREADS, sm, s>>>(P); \
     else k_zfwd4<float, SRC_CGPX, TAN_SVK, A, B><<<grid, FFT_THREADS, sm, s>>>(P);            \
     break;
     RVE_FS_SIZES(RVE_FS_ZF)
@@ -710,6 +711,7 @@ cudaError_t fft4_kernels_init() {
   allow_smem(k_fft_x4<float, A, B>);                        \
   allow_smem(k_zfwd4<float, SRC_CGPX, TAN_FULL81, A, B>);   \
   allow_smem(k_zfwd4<float, SRC_CGPX, TAN_SVK, A, B>);      \
+  allow_smem(k_zfwd4<float, SRC_CGPX, TAN_SYM45, A, B>);    \
   allow_smem(k_zinv4_cgr<float, A, B>);                     \
   allow_smem(k_zfwd4p<A, B>);
   RVE_FS_SIZES(RVE_FS_INIT)

@@ -79,7 +79,7 @@ __global__ void __launch_bounds__(J2_THREADS) k_j2(const double* __restrict__ F,
                                                    const double* __restrict__ hc,
                                                    double* __restrict__ ht, double* __restrict__ P,
                                                    RO* __restrict__ K4, double* __restrict__ K64,
-                                                   SolverState* st) {
+                                                   SolverState* st, int sym45) {
   int flags = 0;
   const size_t stride = (size_t)gridDim.x * blockDim.x;
   for (size_t u = (size_t)blockIdx.x * blockDim.x + threadIdx.x; u < cnt; u += stride) {
@@ -258,9 +258,12 @@ __global__ void __launch_bounds__(J2_THREADS) k_j2(const double* __restrict__ F,
 #pragma unroll
           for (int j = 0; j < 3; ++j) {
             const double dP = dT[i][0] * Fi[j][0] + dT[i][1] * Fi[j][1] + dT[i][2] * Fi[j][2] - Pm[i][l] * Fi[j][k];
-            // K_jikl = dP_ij
+            // K_jikl = dP_ij, i.e. M[3i + j][3k + l]
             const size_t comp = (size_t)((j * 3 + i) * 3 + k) * 3 + l;
-            if (K4) K4[comp * n + v] = (RO)dP;
+            if (K4) {
+              if (!sym45) K4[comp * n + v] = (RO)dP;
+              else if (3 * i + j <= 3 * k + l) K4[(size_t)sym45_index(3 * i + j, 3 * k + l) * n + v] = (RO)dP;
+            }
             if (K64) K64[comp * cnt + u] = dP;
           }
       }
@@ -270,11 +273,12 @@ __global__ void __launch_bounds__(J2_THREADS) k_j2(const double* __restrict__ F,
 
 template <typename RO>
 void launch_j2_constitutive(const double* F, size_t n, MatView<double> mat, const double* hc,
-                            double* ht, double* P, RO* K4, SolverState* st, cudaStream_t s) {
+                            double* ht, double* P, RO* K4, SolverState* st, cudaStream_t s,
+                            int sym45) {
   size_t b = (n + J2_THREADS - 1) / J2_THREADS;
   if (b > 4864) b = 4864;
   if (b < 1) b = 1;
-  k_j2<RO><<<(unsigned)b, J2_THREADS, 0, s>>>(F, n, 0, n, mat, hc, ht, P, K4, nullptr, st);
+  k_j2<RO><<<(unsigned)b, J2_THREADS, 0, s>>>(F, n, 0, n, mat, hc, ht, P, K4, nullptr, st, sym45);
 }
 
 void launch_j2_k4_full(const double* F, size_t v0, size_t count, size_t n, MatView<double> mat,
@@ -283,11 +287,12 @@ void launch_j2_k4_full(const double* F, size_t v0, size_t count, size_t n, MatVi
   if (b > 4864) b = 4864;
   if (b < 1) b = 1;
   k_j2<double><<<(unsigned)b, J2_THREADS, 0, s>>>(F, n, v0, count, mat, hc, nullptr, nullptr,
-                                                   nullptr, dst, nullptr);
+                                                   nullptr, dst, nullptr, 0);
 }
 
 template void launch_j2_constitutive<float>(const double*, size_t, MatView<double>, const double*,
-                                            double*, double*, float*, SolverState*, cudaStream_t);
+                                            double*, double*, float*, SolverState*, cudaStream_t,
+                                            int);
 template void launch_j2_constitutive<double>(const double*, size_t, MatView<double>,
                                              const double*, double*, double*, double*,
-                                             SolverState*, cudaStream_t);
+                                             SolverState*, cudaStream_t, int);

@@ -187,6 +187,28 @@ __global__ void __launch_bounds__(VEC_THREADS) k_svk(const double* __restrict__ 
               if (i == l) kv += mu * B[j][k];
               K4[(size_t)(((i * 3 + j) * 3 + k) * 3 + l) * n + v] = (RO)kv;
             }
+    } else if (tan_mode == TAN_SYM45) {
+      double B[3][3];  // F F^T
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b)
+          B[a][b] = f[3 * a] * f[3 * b] + f[3 * a + 1] * f[3 * b + 1] + f[3 * a + 2] * f[3 * b + 2];
+      // K_ijkl is M[r][c] with r = 3j + i, c = 3k + l; upper triangle only
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+#pragma unroll
+          for (int k = 0; k < 3; ++k)
+#pragma unroll
+            for (int l = 0; l < 3; ++l) {
+              if (3 * j + i > 3 * k + l) continue;
+              double kv = lam * f[3 * j + i] * f[3 * k + l] + mu * f[3 * j + l] * f[3 * k + i];
+              if (j == k) kv += S[l][i];
+              if (i == l) kv += mu * B[j][k];
+              K4[(size_t)sym45_index(3 * j + i, 3 * k + l) * n + v] = (RO)kv;
+            }
     } else if (tan_mode == TAN_SVK) {
       if (Fop) {
 #pragma unroll

@@ -462,11 +462,13 @@ int enqueue_constitutive(rve_t h) {
   MatView<double> m = mat_view<double>(h);
   cudaMemsetAsync(&h->st->err_flags, 0, sizeof(int), h->s);  // flags of this evaluation only
   if (h->model == RVE_J2) {
+    const int sym = h->tan == TAN_SYM45;
     if (h->mixed)
-      launch_j2_constitutive<float>(h->F, h->n, m, h->hc, h->ht, h->P, as<float>(h->K4), h->st, h->s);
+      launch_j2_constitutive<float>(h->F, h->n, m, h->hc, h->ht, h->P, as<float>(h->K4), h->st, h->s,
+                                    sym);
     else
       launch_j2_constitutive<double>(h->F, h->n, m, h->hc, h->ht, h->P, as<double>(h->K4), h->st,
-                                     h->s);
+                                     h->s, sym);
     h->launches += 1;
     return RVE_OK;
   }
@@ -571,6 +573,8 @@ size_t layout(rve_t h, Arena& a) {
   h->Sop = nullptr;
   if (h->tan == TAN_FULL81) {
     h->K4 = a.take<char>(81 * n * ro);
+  } else if (h->tan == TAN_SYM45) {
+    h->K4 = a.take<char>(45 * n * ro);
   } else {
     if (h->mixed) h->Fop = a.take<char>(n9 * ro);
     else h->Sop = a.take<char>(6 * n * ro);
@@ -772,10 +776,13 @@ static int resolve_options(const rve_options* in, rve_options* out, int model, i
   if (model == RVE_SVK) {
     if (out->tangent == RVE_TAN_AUTO || out->tangent == RVE_TAN_RECOMPUTE) *tan = TAN_SVK;
     else if (out->tangent == RVE_TAN_FULL81) *tan = TAN_FULL81;
+    else if (out->tangent == RVE_TAN_SYM45) *tan = TAN_SYM45;
     else return RVE_ERR_INVALID;
   } else if (model == RVE_J2) {
-    // the J2 tangent is stored (81 values per voxel)
-    if (out->tangent == RVE_TAN_AUTO || out->tangent == RVE_TAN_FULL81) *tan = TAN_FULL81;
+    // the J2 tangent is stored: packed symmetric (45 values per voxel) by
+    // default, or all 81
+    if (out->tangent == RVE_TAN_AUTO || out->tangent == RVE_TAN_SYM45) *tan = TAN_SYM45;
+    else if (out->tangent == RVE_TAN_FULL81) *tan = TAN_FULL81;
     else return RVE_ERR_INVALID;
   } else {
     return RVE_ERR_INVALID;
@@ -988,7 +995,7 @@ struct CkptBlock {
 static std::vector<CkptBlock> ckpt_blocks(rve_t h) {
   const size_t n = h->n, ro = h->mixed ? 4 : 8;
   std::vector<CkptBlock> b = {{"F", h->F, 9 * n * 8}, {"Ft", h->Ft, 9 * n * 8}, {"P", h->P, 9 * n * 8}};
-  if (h->K4) b.push_back({"K4", h->K4, 81 * n * ro});
+  if (h->K4) b.push_back({"K4", h->K4, (h->tan == TAN_SYM45 ? 45 : 81) * n * ro});
   if (h->Fop && h->Fop != (void*)h->F) b.push_back({"Fop", h->Fop, 9 * n * ro});
   if (h->Sop) b.push_back({"Sop", h->Sop, 6 * n * ro});
   if (h->hc) b.push_back({"hc", h->hc, 7 * n * 8});
@@ -1019,7 +1026,7 @@ int rve_save(rve_t h, const char* path) {
   hd.nparam = h->nparam;
   hd.use_phase = h->phase != nullptr;
   hd.precision = h->opt.precision;
-  hd.tangent = h->tan == TAN_FULL81 ? RVE_TAN_FULL81 : RVE_TAN_RECOMPUTE;
+  hd.tangent = h->tan == TAN_FULL81 ? RVE_TAN_FULL81 : (h->tan == TAN_SYM45 ? RVE_TAN_SYM45 : RVE_TAN_RECOMPUTE);
   hd.residual = h->opt.residual;
   hd.max_newton = h->opt.max_newton;
   hd.max_cg = h->opt.max_cg;

@@ -24,7 +24,7 @@ except Exception:  # pragma: no cover
 _MODELS = {"svk": _lib.RVE_SVK, "j2": _lib.RVE_J2}
 _PREC = {"fp64": _lib.RVE_FP64, "mixed": _lib.RVE_MIXED}
 _TAN = {"auto": _lib.RVE_TAN_AUTO, "full81": _lib.RVE_TAN_FULL81,
-        "recompute": _lib.RVE_TAN_RECOMPUTE}
+        "recompute": _lib.RVE_TAN_RECOMPUTE, "sym45": _lib.RVE_TAN_SYM45}
 
 
 class RVEError(RuntimeError):

@@ -74,10 +74,11 @@ def j2_schedule_oracle():
     return ph, sched, out
 
 
-def test_j2_fp64_schedule_matches_oracle(j2_schedule_oracle):
+@pytest.mark.parametrize("tangent", ["sym45", "full81"])
+def test_j2_fp64_schedule_matches_oracle(j2_schedule_oracle, tangent):
     ph, sched, ref = j2_schedule_oracle
     r = RVE(ph.shape, model="j2", phase=ph, phase_params=PARAMS, precision="fp64",
-            cg_atol=1e-12)
+            cg_atol=1e-12, tangent=tangent)
     for k, Fb in enumerate(sched):
         r.set_macro_F(Fb)
         r.solve_increment(**TIGHT)

@@ -70,7 +70,7 @@ def test_projection_matches_oracle(shape):
 
 
 @pytest.mark.parametrize("shape", SHAPES)
-@pytest.mark.parametrize("tangent", ["recompute", "full81"])
+@pytest.mark.parametrize("tangent", ["recompute", "full81", "sym45"])
 def test_operator_fp64_matches_oracle(shape, tangent):
     r, F, K, mu, rng = _random_problem(shape, 3, "fp64", tangent)
     _, K4 = svk.constitutive(F, K, mu)
@@ -87,7 +87,7 @@ def test_operator_fp64_matches_oracle(shape, tangent):
 @pytest.mark.parametrize("shape", [(9, 11, 13), (31, 31, 31), (63, 63, 63), (27, 3, 125),
                                    (81, 75, 7), (7, 5, 225), (15, 21, 125), (45, 63, 27),
                                    (16, 20, 24), (15, 16, 17), (125, 16, 32)])
-@pytest.mark.parametrize("tangent", ["recompute", "full81"])
+@pytest.mark.parametrize("tangent", ["recompute", "full81", "sym45"])
 def test_operator_mixed_matches_oracle(shape, tangent):
     r, F, K, mu, rng = _random_problem(shape, 4, "mixed", tangent)
     _, K4 = svk.constitutive(F, K, mu)
