@@ -76,7 +76,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
     with cf.ThreadPoolExecutor(workers) as ex:
         list(ex.map(run, cmds))
     tmp = LIB + ".tmp"
-    run([nvcc, *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *objs])
+    run([nvcc, *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *objs, "-ldl"])
     os.replace(tmp, LIB)
     return LIB
 

@@ -13,6 +13,8 @@
 #include <type_traits>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/rve.h"
 #include "kernels.h"
 
@@ -216,6 +218,13 @@ struct rve_s {
 };
 
 namespace {
+
+// NVTX range for the solver phases (visible in Nsight timelines; no cost
+// without an attached tool)
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+};
 
 int fail(rve_t h, int code, const std::string& msg) {
   if (h) h->err = msg;
@@ -459,6 +468,7 @@ void enqueue_predictor(rve_t h) {
 }
 
 int enqueue_constitutive(rve_t h) {
+  NvtxRange nv("rve constitutive");
   MatView<double> m = mat_view<double>(h);
   cudaMemsetAsync(&h->st->err_flags, 0, sizeof(int), h->s);  // flags of this evaluation only
   if (h->model == RVE_J2) {
@@ -497,6 +507,7 @@ int push_state(rve_t h) {
 // convergence return at once (device flag), so overshoot costs launches only.
 template <typename R>
 int cg_solve(rve_t h, int* iters) {
+  NvtxRange nv("rve cg_solve");
   int launched = 0;
   int chunk = 4;
   h->solve_id++;
@@ -681,6 +692,7 @@ double time_cg_iteration(rve_t h) {
 }
 
 int autotune(rve_t h) {
+  NvtxRange nv("rve autotune");
   int dev = 0;
   cudaGetDevice(&dev);
   const TuneKey key{h->g.nx, h->g.ny, h->g.nz, dev, h->tan};
@@ -1012,6 +1024,7 @@ static std::vector<CkptBlock> ckpt_blocks(rve_t h) {
 }
 
 int rve_save(rve_t h, const char* path) {
+  NvtxRange nv("rve save");
   if (!h || !path) return RVE_ERR_INVALID;
   FILE* f = std::fopen(path, "wb");
   if (!f) return fail(h, RVE_ERR_INVALID, std::string("cannot open ") + path);
@@ -1057,6 +1070,7 @@ int rve_save(rve_t h, const char* path) {
 }
 
 int rve_load(rve_t* out, const char* path, const rve_options* opt) {
+  NvtxRange nv("rve load");
   if (!out || !path) return RVE_ERR_INVALID;
   *out = nullptr;
   FILE* f = std::fopen(path, "rb");
@@ -1192,6 +1206,7 @@ int rve_set_macro_F(rve_t h, const double Fbar[9]) {
 
 template <typename R>
 static int solve_increment_t(rve_t h, double tol_newton, double tol_cg, rve_stats* st) {
+  NvtxRange nv("rve solve_increment");
   const size_t n9 = 9 * h->n;
   CK(cudaEventRecord(h->e0, h->s));
   // device state for this increment
@@ -1331,6 +1346,7 @@ int rve_solve_increment(rve_t h, double tol_newton, double tol_cg, rve_stats* st
 
 int rve_solve_step(rve_t h, const double Fbar[9], double tol_newton, double tol_cg, int max_cuts,
                    rve_stats* st) {
+  NvtxRange nv("rve solve_step");
   if (!h || !Fbar || max_cuts < 0) return RVE_ERR_INVALID;
   for (int c = 0; c < 9; ++c)
     if (!std::isfinite(Fbar[c])) return fail(h, RVE_ERR_INVALID, "non-finite F-bar");
@@ -1465,6 +1481,7 @@ int rve_adjoint_grad_mu(rve_t h, const double W[9], double tol_cg, double* grad,
 
 int rve_adjoint_grad(rve_t h, const double W[9], double tol_cg, double* grad_K, double* grad_mu,
                      int on_device, int* cg_iters) {
+  NvtxRange nv("rve adjoint_grad");
   if (!h || !W || !(grad_K || grad_mu) || !(tol_cg > 0.0)) return RVE_ERR_INVALID;
   if (h->model != RVE_SVK) return fail(h, RVE_ERR_UNSUPPORTED, "adjoint: SVK only");
   int rc = sync_state(h);
@@ -1960,6 +1977,7 @@ int rve_batch_solve(rve_batch_t b, const double* Fbar, double tol_newton, double
 
 int rve_batch_solve_step(rve_batch_t b, const double* Fbar, double tol_newton, double tol_cg,
                          int max_cuts, rve_stats* stats) {
+  NvtxRange nv("rve batch_solve_step");
   if (!b || !Fbar || !(tol_newton > 0.0) || !(tol_cg > 0.0) || max_cuts < 0)
     return RVE_ERR_INVALID;
   b->err.clear();
