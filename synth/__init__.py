@@ -166,6 +166,16 @@ def uniaxial(eps: float) -> np.ndarray:
     return np.diag([1.0 + eps, 1.0, 1.0])
 
 
+# Mixed control masks: True where the P-bar component (3i+j) is prescribed
+# and F-bar is free; False where F-bar is prescribed.
+def uniaxial_stress_mask() -> np.ndarray:
+    """Uniaxial stress along x: F11 prescribed, F21 = F31 = F32 prescribed
+    (they fix the rotation), P12, P13, P22, P23, P33 prescribed."""
+    m = np.zeros(9, dtype=bool)
+    m[[1, 2, 4, 5, 8]] = True
+    return m
+
+
 def ramp(final: np.ndarray, nincr: int) -> list[np.ndarray]:
     """Equal increments from I to ``final``: ``I + (k/m)(final - I)``."""
     final = np.asarray(final, dtype=np.float64)
