@@ -123,8 +123,12 @@ typedef struct {
   double elapsed_ms;                       /* device time of the increment (CUDA events) */
   int substeps;                            /* rve_solve_step: increments solved */
   int cuts;                                /* rve_solve_step: halvings after a failure */
-  double substep_to[RVE_MAX_NEWTON_LOG];   /* rve_solve_step: fraction of the step reached
-                                              after each solved increment */
+  double substep_to[RVE_MAX_NEWTON_LOG];   /* rve_solve_step / rve_solve_mixed: fraction of
+                                              the step reached after each solved increment */
+  int macro_iters;                         /* rve_solve_mixed: increments solved as iterates
+                                              of the Newton loop on the free F-bar components */
+  int tangent_solves;                      /* rve_solve_mixed: linear solves for columns of
+                                              the homogenised tangent */
 } rve_stats;
 
 /* Fills *opt with the defaults listed above. */
@@ -144,7 +148,7 @@ int rve_workspace_size(int nx, int ny, int nz, int model, const rve_options* opt
  *  voxel_params : [nparam][n] float64 (host) per-voxel parameters, used
  *                 when phase is NULL
  *  opt          : may be NULL (defaults)
- * Errors: RVE_ERR_INVALID (even or non-positive sizes, bad model, phase index
+ * Errors: RVE_ERR_INVALID (non-positive sizes, bad model, phase index
  * >= nphase, missing parameters), RVE_ERR_NOMEM, RVE_ERR_CUDA. */
 int rve_create(rve_t* out, int nx, int ny, int nz, int model, int nphase, const uint8_t* phase,
                const double* phase_params, const double* voxel_params, const rve_options* opt);
@@ -181,6 +185,41 @@ int rve_solve_increment(rve_t h, double tol_newton, double tol_cg, rve_stats* st
  * yield point by far. */
 int rve_solve_step(rve_t h, const double Fbar[9], double tol_newton, double tol_cg, int max_cuts,
                    rve_stats* st);
+
+/* A load step under mixed macroscopic control.  mask[c] != 0 (c = 3i+j)
+ * prescribes P-bar_ij = Pbar[c] and leaves F-bar_ij free; mask[c] == 0
+ * prescribes F-bar_ij = Fbar[c] (Fbar and Pbar row-major, host; entries
+ * that are not prescribed are ignored).  Not in the paper, which prescribes
+ * the full F-bar (Sec. 3.1) and leaves other boundary conditions to the
+ * literature.  Each increment seeks the equilibrium G:P(F) = 0 from the
+ * committed state with <F>_c = F-bar_c on the strain-controlled and
+ * <P>_c = P*_c on the stress-controlled components, by Newton on the free
+ * F-bar components (starting at their committed values): every iterate is an
+ * increment as in rve_solve_increment (not committed in between), and the
+ * Jacobian is the homogenised tangent
+ *   dP-bar_a/dF-bar_b = <K : (E_b + dF_b)>_a,  G:K:dF_b = -G:K:E_b
+ * (Eq. bc:lin with dF-bar = E_b, the uniform unit tensor of component b;
+ * one CG solve per stress-controlled component), evaluated at the first
+ * iterate and whenever the stress residual fell by less than 4x, with
+ * Broyden's rank-one update otherwise.  The increment has converged when
+ * ||P-bar_S - P*_S|| <= tol_stress ||P-bar|| after an iterate (Frobenius
+ * norms over the stress-controlled, resp. all, components); at most 30
+ * iterates.  Sub-stepping as in rve_solve_step: the prescribed values move
+ * on the straight path from the committed F-bar and P-bar, and a failed
+ * increment is retried with half the step, at most max_cuts times in a row
+ * (max_cuts = 0: one increment).  Without stress-controlled components the
+ * call is rve_solve_step.  st (may be NULL): accumulated iterations,
+ * macro_iters, tangent_solves, substeps, cuts; elapsed_ms is the wall time
+ * of the call.  Errors as rve_solve_increment, plus RVE_ERR_INVALID for
+ * non-finite prescribed values or a homogenised tangent that is singular on
+ * the stress-controlled components (e.g. a rotation left free at zero
+ * stress); the state is then the last committed one. */
+int rve_solve_mixed(rve_t h, const double Fbar[9], const double Pbar[9], const int mask[9],
+                    double tol_stress, double tol_newton, double tol_cg, int max_cuts,
+                    rve_stats* st);
+
+/* F-bar of the last committed state (row-major, host). */
+int rve_macro_F(rve_t h, double Fbar[9]);
 
 /* Copies F, P (each [9][n] float64) or the tangent K ([81][n] float64,
  * evaluated in float64 at the current F) to dst (host or device). */

@@ -14,6 +14,7 @@ _EXPORTS = ("RVE", "RVEBatch", "RVEError", "rve_adjoint_grad", "rve_adjoint_grad
             "rve_get_F", "rve_get_K4", "rve_get_P", "rve_get_history", "rve_homogenized_P",
             "rve_kernel_time", "rve_kernel_timing", "rve_launch_count", "rve_tuning", "rve_save", "rve_load",
             "rve_project", "rve_project_noalloc", "rve_set_F", "rve_set_macro_F", "rve_solve_increment", "rve_solve_step",
+            "rve_solve_mixed", "rve_macro_F",
             "rve_workspace_size", "KERNEL_FAMILIES")
 
 __all__ = list(_EXPORTS)

@@ -52,7 +52,8 @@ class rve_stats(C.Structure):
                 ("residual", C.c_double * RVE_MAX_NEWTON_LOG),
                 ("elapsed_ms", C.c_double), ("substeps", C.c_int),
                 ("cuts", C.c_int),
-                ("substep_to", C.c_double * RVE_MAX_NEWTON_LOG)]
+                ("substep_to", C.c_double * RVE_MAX_NEWTON_LOG),
+                ("macro_iters", C.c_int), ("tangent_solves", C.c_int)]
 
 
 _H = C.c_void_p
@@ -69,6 +70,9 @@ _SIGS = {
                                       C.POINTER(rve_stats)]),
     "rve_solve_step": (C.c_int, [_H, _P, C.c_double, C.c_double, C.c_int,
                                  C.POINTER(rve_stats)]),
+    "rve_solve_mixed": (C.c_int, [_H, _P, _P, _P, C.c_double, C.c_double, C.c_double,
+                                  C.c_int, C.POINTER(rve_stats)]),
+    "rve_macro_F": (C.c_int, [_H, _P]),
     "rve_get_F": (C.c_int, [_H, _P, C.c_int]),
     "rve_get_P": (C.c_int, [_H, _P, C.c_int]),
     "rve_get_K4": (C.c_int, [_H, _P, C.c_int]),

@@ -59,6 +59,7 @@ struct SolverState {
   double Pbar[9];
   double meanF[9];
   double adjW[9];   // W / n of the adjoint right-hand side G : (K : W) / n
+  double Kmean[9];  // <K : (U + x)> of the homogenised-tangent column
   int err_flags;    // bit 0: det F <= 0, bit 1: non-finite value
   int dev_timeout;  // set by a thread block whose bounded wait on its own copies gave up
   // reduction counters (one per reducing kernel family)

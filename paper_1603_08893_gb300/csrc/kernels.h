@@ -171,6 +171,12 @@ void launch_G_df(const GridGeom& g, const double* in, double scale, int out_mode
                  float* r_out, float* x_out, SolverState* st, double* partials, cplx<dfl>* spec,
                  const Twiddles<dfl>& tw, cudaStream_t s);
 
+// out9 = < K : (U + x) > over the voxels, U a uniform tensor (device, 9
+// doubles), x a [9][n] field or null; K applied as in the first z pass
+template <typename R>
+void launch_tangent_mean(const TangentView<R>& tan, const R* x, const double* U, size_t n,
+                         double* out9, double* partials, unsigned int* counter, cudaStream_t s);
+
 cudaError_t fft_kernels_init();  // opt-in to large dynamic shared memory
 size_t fft_max_blocks(const GridGeom& g);
 

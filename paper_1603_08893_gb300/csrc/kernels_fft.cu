@@ -567,7 +567,57 @@ cudaError_t fft_kernels_init() {
   return g_init_err;
 }
 
+// Column of the homogenised tangent: < K : (U + x) > over the voxels, the
+// tangent applied exactly as in the first z pass (same storage modes), the
+// sums in float64 with the deterministic last-block reduction.
+template <typename R, int TAN>
+__global__ void __launch_bounds__(256) k_tangent_mean(TangentView<R> T, const R* __restrict__ x,
+                                                      const double* __restrict__ U, size_t n,
+                                                      double* out9, double* partials,
+                                                      unsigned int* counter) {
+  double s[9];
+  R u[9];
+#pragma unroll
+  for (int c = 0; c < 9; ++c) {
+    s[c] = 0.0;
+    u[c] = (R)U[c];
+  }
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+    TanPre<R> q;
+    tangent_pre<R, TAN>(T, v, n, q);
+    R in[9], out[9];
+#pragma unroll
+    for (int c = 0; c < 9; ++c) in[c] = x ? u[c] + x[(size_t)c * n + v] : u[c];
+    tangent_post<R, TAN>(T, v, n, q, in, out);
+#pragma unroll
+    for (int c = 0; c < 9; ++c) s[c] += (double)out[c];
+  }
+  double tot[9];
+  if (last_block_sum<9>(s, partials, counter, tot) && threadIdx.x == 0)
+#pragma unroll
+    for (int c = 0; c < 9; ++c) out9[c] = tot[c] / (double)n;
+}
+
+template <typename R>
+void launch_tangent_mean(const TangentView<R>& tan, const R* x, const double* U, size_t n,
+                         double* out9, double* partials, unsigned int* counter, cudaStream_t s) {
+  const size_t blocks = std::min<size_t>((n + 255) / 256, vec_max_blocks());
+  const dim3 grid((unsigned)std::max<size_t>(blocks, 1));
+  if (tan.mode == TAN_FULL81)
+    k_tangent_mean<R, TAN_FULL81><<<grid, 256, 0, s>>>(tan, x, U, n, out9, partials, counter);
+  else if (tan.mode == TAN_SYM45)
+    k_tangent_mean<R, TAN_SYM45><<<grid, 256, 0, s>>>(tan, x, U, n, out9, partials, counter);
+  else
+    k_tangent_mean<R, TAN_SVK><<<grid, 256, 0, s>>>(tan, x, U, n, out9, partials, counter);
+}
+
 // explicit instantiations
+template void launch_tangent_mean<float>(const TangentView<float>&, const float*, const double*,
+                                         size_t, double*, double*, unsigned int*, cudaStream_t);
+template void launch_tangent_mean<double>(const TangentView<double>&, const double*,
+                                          const double*, size_t, double*, double*, unsigned int*,
+                                          cudaStream_t);
 template void launch_zfwd<float>(const GridGeom&, int, const TangentView<float>&, const float*,
                                  const float*, float*, const double*, SolverState*, const int*,
                                  cplx<float>*, const Twiddles<float>&, cudaStream_t, float*,

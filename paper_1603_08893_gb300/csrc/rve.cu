@@ -2,6 +2,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <tuple>
 #include <mutex>
 #include <map>
@@ -24,6 +25,8 @@ const double kDivergedUpdate = 0.5;  // ||dF||/||F|| above this ends Newton as d
 // float32 CG stops after this many iterations without a 10% drop of ||r||
 // (its accuracy limit on high-contrast cells); float64 CG never does
 const int kMixedStagnation = 200;
+const int kMaxMacro = 30;            // Newton iterations on the free F-bar components
+const double kSingularPivot = 1e-10; // relative pivot of a singular homogenised tangent
 
 struct TimedLaunch {
   cudaEvent_t a, b;
@@ -450,13 +453,18 @@ void enqueue_operator64(rve_t h, int src, const double* in, const double* unif, 
 
 // predictor right-hand side b = -G:(K_(0) : dFbar) (Eq. bc:lin) in the
 // operator precision; dFbar = Fbar - <F> computed on the device.
+// With from_mean false the uniform field is the dFbar already in the device
+// state (a column of the homogenised tangent).
 template <typename R>
-void enqueue_predictor(rve_t h) {
+void enqueue_predictor(rve_t h, bool from_mean = true) {
   const GridGeom& g = h->g;
   const Twiddles<R>& tw = twiddles<R>(h);
   cplx<R>* spec = as<cplx<R>>(h->spec_op);
-  launch_mean9<double>(h->F, h->n, nullptr, h->partials, &h->st->counter[SLOT_MEAN], MEAN_DFBAR,
-                       h->st, h->s);
+  if (from_mean) {
+    launch_mean9<double>(h->F, h->n, nullptr, h->partials, &h->st->counter[SLOT_MEAN], MEAN_DFBAR,
+                         h->st, h->s);
+    h->launches += 1;
+  }
   launch_zfwd<R>(g, SRC_UNIFORM, tangent_view<R>(h), nullptr, nullptr, nullptr, h->st->dFbar,
                  h->st, nullptr, spec, tw, h->s);
   launch_fft_y<R>(g, false, spec, nullptr, tw, h->s);
@@ -464,7 +472,7 @@ void enqueue_predictor(rve_t h) {
   launch_fft_y<R>(g, true, spec, nullptr, tw, h->s);
   launch_zinv<R, R>(g, OUT_RESID, spec, nullptr, as<R>(h->r), as<R>(h->x), nullptr, h->st,
                     h->partials, nullptr, tw, h->s);
-  h->launches += 6;
+  h->launches += 5;
 }
 
 int enqueue_constitutive(rve_t h) {
@@ -1204,8 +1212,32 @@ int rve_set_macro_F(rve_t h, const double Fbar[9]) {
 
 }  // extern "C"
 
+// Stores the converged state of an increment: F, F-bar, P-bar and (J2) the
+// trial history of the last constitutive evaluation, after which the
+// constitutive response is re-evaluated with it (Algorithm 1, i = 0 of the
+// next increment).
+static int commit_state(rve_t h) {
+  CK(cudaMemcpyAsync(h->Ft, h->F, 9 * h->n * 8, cudaMemcpyDeviceToDevice, h->s));
+  std::memcpy(h->Fbar_committed, h->Fbar, sizeof(h->Fbar));
+  launch_mean9<double>(h->P, h->n, nullptr, h->partials, &h->st->counter[SLOT_MEAN], MEAN_PBAR,
+                       h->st, h->s);
+  h->launches += 1;
+  if (h->model == RVE_J2) {
+    std::swap(h->hc, h->ht);
+    enqueue_constitutive(h);
+  }
+  return RVE_OK;
+}
+
+// One increment to h->Fbar.  commit = false leaves a converged state
+// uncommitted: F, P and the J2 trial history stay those of the converged
+// iterate while the committed state (Ft, history) is kept, so that a later
+// increment still starts the return map from the committed history (the
+// iterates of mixed control).  A failure always rolls back to the
+// committed state.
 template <typename R>
-static int solve_increment_t(rve_t h, double tol_newton, double tol_cg, rve_stats* st) {
+static int solve_increment_t(rve_t h, double tol_newton, double tol_cg, rve_stats* st,
+                             bool commit = true) {
   NvtxRange nv("rve solve_increment");
   const size_t n9 = 9 * h->n;
   CK(cudaEventRecord(h->e0, h->s));
@@ -1300,18 +1332,9 @@ static int solve_increment_t(rve_t h, double tol_newton, double tol_cg, rve_stat
   if (result == RVE_OK && !converged)
     result = fail(h, RVE_ERR_NEWTON_MAXIT, "Newton did not converge");
   if (result == RVE_OK) {
-    // commit: store the converged state and history, homogenised stress
-    CK(cudaMemcpyAsync(h->Ft, h->F, n9 * 8, cudaMemcpyDeviceToDevice, h->s));
-    std::memcpy(h->Fbar_committed, h->Fbar, sizeof(h->Fbar));
-    launch_mean9<double>(h->P, h->n, nullptr, h->partials, &h->st->counter[SLOT_MEAN], MEAN_PBAR,
-                         h->st, h->s);
-    h->launches += 1;
-    if (h->model == RVE_J2) {
-      // the trial history of the converged iterate becomes the committed
-      // one; the next increment starts from the constitutive response at F
-      // with it (Algorithm 1, i = 0)
-      std::swap(h->hc, h->ht);
-      enqueue_constitutive(h);
+    if (commit) {
+      rc = commit_state(h);
+      if (rc) return rc;
     }
   } else {
     // roll back to the last committed state
@@ -1402,6 +1425,256 @@ int rve_solve_step(rve_t h, const double Fbar[9], double tol_newton, double tol_
     st->cuts = cuts;
   }
   return result;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Mixed macroscopic control.  Not in the paper: Sec. 3.1 prescribes the full
+// F-bar and leaves other boundary conditions to the literature.  The
+// stress-controlled components S have P-bar_S prescribed and F-bar_S free;
+// the state sought is the equilibrium of one increment from the committed
+// state with <F> = F-bar and <P>_S = P*_S.  Newton on F-bar_S: every iterate
+// is an ordinary (uncommitted) increment; the Jacobian is the homogenised
+// tangent dP-bar_a/dF-bar_b = <K : (E_b + dF_b)>_a, where dF_b solves the
+// predictor system G:K:dF_b = -G:K:E_b (Eq. bc:lin with dF-bar = E_b), taken
+// exactly at the first iterate and again whenever the stress residual fell
+// by less than 4x, with Broyden's rank-one update in between.
+// ---------------------------------------------------------------------------
+
+// Solves A u = b in place (m x m row-major, m <= 9) by Gaussian elimination
+// with partial pivoting; false if a pivot is below rel * max |A_ij|.
+static bool small_solve(int m, double* A, double* b, double rel) {
+  double amax = 0.0;
+  for (int i = 0; i < m * m; ++i) amax = std::max(amax, std::fabs(A[i]));
+  if (!(amax > 0.0)) return false;
+  for (int k = 0; k < m; ++k) {
+    int piv = k;
+    for (int i = k + 1; i < m; ++i)
+      if (std::fabs(A[i * m + k]) > std::fabs(A[piv * m + k])) piv = i;
+    if (!(std::fabs(A[piv * m + k]) > rel * amax)) return false;
+    if (piv != k) {
+      for (int j = 0; j < m; ++j) std::swap(A[k * m + j], A[piv * m + j]);
+      std::swap(b[k], b[piv]);
+    }
+    for (int i = k + 1; i < m; ++i) {
+      const double f = A[i * m + k] / A[k * m + k];
+      for (int j = k; j < m; ++j) A[i * m + j] -= f * A[k * m + j];
+      b[i] -= f * b[k];
+    }
+  }
+  for (int k = m - 1; k >= 0; --k) {
+    double v = b[k];
+    for (int j = k + 1; j < m; ++j) v -= A[k * m + j] * b[j];
+    b[k] = v / A[k * m + k];
+  }
+  return true;
+}
+
+static int rollback_state(rve_t h) {
+  CK(cudaMemcpyAsync(h->F, h->Ft, 9 * h->n * 8, cudaMemcpyDeviceToDevice, h->s));
+  enqueue_constitutive(h);
+  return sync_state(h);
+}
+
+// Columns cols[0..ncol) of dP-bar/dF-bar at the current converged state into
+// C[a * ncol + k] (a = component of P-bar), one CG solve each.
+template <typename R>
+static int homogenized_tangent_t(rve_t h, const int* cols, int ncol, double tol_cg, double* C,
+                                 int* cg_iters) {
+  NvtxRange nv("rve homogenized_tangent");
+  SolverState* hs = h->hst;
+  for (int k = 0; k < ncol; ++k) {
+    std::memset(hs, 0, sizeof(SolverState));
+    hs->cg_tol = h->mixed ? std::max(tol_cg, h->opt.cg_tol_floor) : tol_cg;
+    hs->cg_atol = h->opt.cg_atol;
+    hs->maxit = h->opt.max_cg;
+    hs->stag = h->mixed ? kMixedStagnation : 0;
+    hs->dFbar[cols[k]] = 1.0;
+    int rc = push_state(h);
+    if (rc) return rc;
+    enqueue_predictor<R>(h, false);
+    int its = 0;
+    rc = cg_solve<R>(h, &its);
+    *cg_iters += its;
+    if (rc) return fail(h, rc, std::string("homogenised tangent solve: ") + rve_status_string(rc));
+    launch_tangent_mean<R>(tangent_view<R>(h), as<R>(h->x), h->st->dFbar, h->n, h->st->Kmean,
+                           h->partials, &h->st->counter[SLOT_MISC], h->s);
+    h->launches += 1;
+    CK(cudaGetLastError());
+    rc = sync_state(h);
+    if (rc) return rc;
+    for (int a = 0; a < 9; ++a) C[a * ncol + k] = hs->Kmean[a];
+  }
+  return RVE_OK;
+}
+
+// P-bar of the current F into Pb (device P-bar slot and host copy)
+static int current_Pbar(rve_t h, double Pb[9]) {
+  launch_mean9<double>(h->P, h->n, nullptr, h->partials, &h->st->counter[SLOT_MEAN], MEAN_PBAR,
+                       h->st, h->s);
+  h->launches += 1;
+  const int rc = sync_state(h);
+  if (rc) return rc;
+  std::memcpy(Pb, h->hst->Pbar, 9 * sizeof(double));
+  return RVE_OK;
+}
+
+// One increment under mixed control to (Fb_in on the strain-controlled
+// components, Pt on S); commits on success, rolls back on failure.
+template <typename R>
+static int mixed_increment_t(rve_t h, const double Fb_in[9], const double Pt[9], const int* S,
+                             int ns, double tol_stress, double tol_newton, double tol_cg,
+                             rve_stats* acc) {
+  NvtxRange nv("rve mixed_increment");
+  double Fb[9];
+  std::memcpy(Fb, Fb_in, sizeof(Fb));
+  for (int k = 0; k < ns; ++k) Fb[S[k]] = h->Fbar_committed[S[k]];
+  double J[81], Rprev[9], dprev[9], rprev = 0.0;
+  bool have_J = false;
+  for (int m = 1; m <= kMaxMacro; ++m) {
+    std::memcpy(h->Fbar, Fb, sizeof(Fb));
+    rve_stats s1;
+    std::memset(&s1, 0, sizeof(s1));
+    int rc = solve_increment_t<R>(h, tol_newton, tol_cg, &s1, false);
+    acc->newton_iters += s1.newton_iters;
+    acc->cg_iters_total += s1.cg_iters_total;
+    acc->macro_iters += 1;
+    if (rc) return rc;  // rolled back to the committed state
+    double Pb[9];
+    rc = current_Pbar(h, Pb);
+    if (rc) return rc;
+    double Rs[9], rn = 0.0, pn = 0.0;
+    for (int c = 0; c < 9; ++c) pn += Pb[c] * Pb[c];
+    for (int k = 0; k < ns; ++k) {
+      Rs[k] = Pb[S[k]] - Pt[S[k]];
+      rn += Rs[k] * Rs[k];
+    }
+    rn = std::sqrt(rn);
+    if (!std::isfinite(rn)) {
+      rollback_state(h);
+      return fail(h, RVE_ERR_NONFINITE, "mixed control: non-finite P-bar");
+    }
+    if (ns == 0 || rn <= tol_stress * std::sqrt(pn)) return commit_state(h);
+    if (m == kMaxMacro) break;
+    if (!have_J || rn > 0.25 * rprev) {
+      double Cfull[81];
+      int its = 0;
+      rc = homogenized_tangent_t<R>(h, S, ns, tol_cg, Cfull, &its);
+      acc->cg_iters_total += its;
+      acc->tangent_solves += ns;
+      if (rc) {
+        rollback_state(h);
+        return rc;
+      }
+      for (int i = 0; i < ns; ++i)
+        for (int j = 0; j < ns; ++j) J[i * ns + j] = Cfull[S[i] * ns + j];
+      have_J = true;
+    } else {
+      // Broyden: J += ((R - R_prev) - J d) d^T / (d.d)
+      double dd = 0.0;
+      for (int j = 0; j < ns; ++j) dd += dprev[j] * dprev[j];
+      for (int i = 0; i < ns; ++i) {
+        double y = Rs[i] - Rprev[i];
+        for (int j = 0; j < ns; ++j) y -= J[i * ns + j] * dprev[j];
+        for (int j = 0; j < ns; ++j) J[i * ns + j] += y * dprev[j] / dd;
+      }
+    }
+    double A[81], d[9];
+    std::memcpy(A, J, sizeof(double) * ns * ns);
+    for (int k = 0; k < ns; ++k) d[k] = -Rs[k];
+    if (!small_solve(ns, A, d, kSingularPivot)) {
+      rollback_state(h);
+      return fail(h, RVE_ERR_INVALID,
+                  "mixed control: homogenised tangent singular on the stress-controlled "
+                  "components (leave a rotation-fixing set of F-bar components prescribed)");
+    }
+    for (int k = 0; k < ns; ++k) {
+      Fb[S[k]] += d[k];
+      Rprev[k] = Rs[k];
+      dprev[k] = d[k];
+    }
+    rprev = rn;
+  }
+  rollback_state(h);
+  return fail(h, RVE_ERR_NEWTON_MAXIT, "mixed control: macroscopic Newton did not converge");
+}
+
+extern "C" {
+
+int rve_solve_mixed(rve_t h, const double Fbar[9], const double Pbar[9], const int mask[9],
+                    double tol_stress, double tol_newton, double tol_cg, int max_cuts,
+                    rve_stats* st) {
+  NvtxRange nv("rve solve_mixed");
+  if (!h || !Fbar || !Pbar || !mask || max_cuts < 0) return RVE_ERR_INVALID;
+  if (!(tol_stress > 0.0) || !(tol_newton > 0.0) || !(tol_cg > 0.0))
+    return fail(h, RVE_ERR_INVALID, "tolerances must be > 0");
+  int S[9], ns = 0;
+  for (int c = 0; c < 9; ++c) {
+    if (mask[c]) S[ns++] = c;
+    if ((!mask[c] && !std::isfinite(Fbar[c])) || (mask[c] && !std::isfinite(Pbar[c])))
+      return fail(h, RVE_ERR_INVALID, "non-finite prescribed component");
+  }
+  h->err.clear();
+  const auto t0 = std::chrono::steady_clock::now();
+  // the path starts at the committed state: its F-bar and P-bar
+  double F0[9], P0[9];
+  std::memcpy(F0, h->Fbar_committed, sizeof(F0));
+  int rc = current_Pbar(h, P0);
+  if (rc) return rc;
+  rve_stats acc;
+  std::memset(&acc, 0, sizeof(acc));
+  double done = 0.0, step = 1.0;
+  const double min_step = std::ldexp(1.0, -max_cuts);
+  int cuts = 0, sub = 0, streak = 0, result = RVE_OK;
+  while (done < 1.0) {
+    const double to = std::min(1.0, done + step);
+    double Fb[9], Pt[9];
+    for (int c = 0; c < 9; ++c) {
+      Fb[c] = to >= 1.0 ? Fbar[c] : F0[c] + to * (Fbar[c] - F0[c]);
+      Pt[c] = to >= 1.0 ? Pbar[c] : P0[c] + to * (Pbar[c] - P0[c]);
+    }
+    h->err.clear();
+    rc = h->mixed ? mixed_increment_t<float>(h, Fb, Pt, S, ns, tol_stress, tol_newton, tol_cg, &acc)
+                  : mixed_increment_t<double>(h, Fb, Pt, S, ns, tol_stress, tol_newton, tol_cg,
+                                              &acc);
+    if (rc == RVE_OK) {
+      done = to;
+      if (sub < RVE_MAX_NEWTON_LOG) acc.substep_to[sub] = to;
+      ++sub;
+      if (++streak >= 2) {
+        step = std::min(2.0 * step, 1.0);
+        streak = 0;
+      }
+    } else if (rc == RVE_ERR_NEWTON_MAXIT || rc == RVE_ERR_CG_MAXIT || rc == RVE_ERR_NONFINITE ||
+               rc == RVE_ERR_DETF || rc == RVE_ERR_CG_BREAKDOWN) {
+      ++cuts;
+      streak = 0;
+      step *= 0.5;
+      if (step < min_step) {
+        result = rc;
+        break;
+      }
+    } else {
+      result = rc;
+      break;
+    }
+  }
+  if (st) {
+    *st = acc;
+    st->status = result;
+    st->substeps = sub;
+    st->cuts = cuts;
+    st->elapsed_ms =
+        std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  }
+  return result;
+}
+
+int rve_macro_F(rve_t h, double Fbar[9]) {
+  if (!h || !Fbar) return RVE_ERR_INVALID;
+  std::memcpy(Fbar, h->Fbar_committed, 9 * sizeof(double));
+  return RVE_OK;
 }
 
 int rve_get_F(rve_t h, double* dst, int on_device) {

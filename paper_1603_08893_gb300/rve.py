@@ -155,6 +155,34 @@ def rve_solve_step(h, Fbar, tol_newton=1e-5, tol_cg=1e-8, max_cuts=8, check=True
     return out
 
 
+def rve_solve_mixed(h, Fbar, Pbar, mask, tol_stress=1e-8, tol_newton=1e-5, tol_cg=1e-8,
+                    max_cuts=0, check=True):
+    """Load step under mixed control: mask[c] (c = 3i+j) true prescribes
+    P-bar_ij = Pbar[c] and frees F-bar_ij, false prescribes F-bar_ij = Fbar[c]."""
+    F = np.ascontiguousarray(Fbar, dtype=np.float64).reshape(9)
+    P = np.ascontiguousarray(Pbar, dtype=np.float64).reshape(9)
+    M = np.ascontiguousarray(np.asarray(mask).reshape(9) != 0, dtype=np.int32)
+    st = _lib.rve_stats()
+    code = lib.rve_solve_mixed(h, F.ctypes.data_as(C.c_void_p), P.ctypes.data_as(C.c_void_p),
+                               M.ctypes.data_as(C.c_void_p), float(tol_stress),
+                               float(tol_newton), float(tol_cg), int(max_cuts), C.byref(st))
+    out = dict(status=code, newton_iters=st.newton_iters,
+               cg_iters_total=st.cg_iters_total, substeps=st.substeps,
+               cuts=st.cuts, elapsed_ms=st.elapsed_ms, macro_iters=st.macro_iters,
+               tangent_solves=st.tangent_solves,
+               substep_to=list(st.substep_to[:min(st.substeps, _lib.RVE_MAX_NEWTON_LOG)]))
+    if check:
+        _check(code, h)
+    return out
+
+
+def rve_macro_F(h):
+    """F-bar of the last committed state, 3x3."""
+    F = np.empty(9, dtype=np.float64)
+    _check(lib.rve_macro_F(h, F.ctypes.data_as(C.c_void_p)), h)
+    return F.reshape(3, 3)
+
+
 def _get(fn, h, ncomp, n, out):
     if out is not None and _is_torch_cuda(out):
         if out.dtype != torch.float64 or not out.is_contiguous() or out.numel() != ncomp * n:
@@ -337,6 +365,14 @@ class RVE:
 
     def solve_step(self, Fbar, tol_newton=1e-5, tol_cg=1e-8, max_cuts=8, check=True):
         return rve_solve_step(self.h, Fbar, tol_newton, tol_cg, max_cuts, check)
+
+    def solve_mixed(self, Fbar, Pbar, mask, tol_stress=1e-8, tol_newton=1e-5, tol_cg=1e-8,
+                    max_cuts=0, check=True):
+        return rve_solve_mixed(self.h, Fbar, Pbar, mask, tol_stress, tol_newton, tol_cg,
+                               max_cuts, check)
+
+    def macro_F(self):
+        return rve_macro_F(self.h)
 
     def get_F(self, out=None):
         return self._shape9(rve_get_F(self.h, self.n, out))
