@@ -447,6 +447,41 @@ def bench_tangent125(args, torch, RVE):
                                        "full81": 253.3 - 37 + 324})
 
 
+def bench_mixed125(args, torch, RVE):
+    """Mixed macroscopic control on the 125^3 spheres, mixed precision:
+    uniaxial stress along x (F11 = 1.01 prescribed, the lateral and shear
+    P-bar components zero) against the uniaxial-strain increment to the same
+    F11, both as one increment from F = I."""
+    cfg = workload()
+    n = int(np.prod(cfg["shape"]))
+    kw = dict(phase=cfg["phase"], phase_params=cfg["phase_params"], precision="mixed")
+    Fb = synth.uniaxial(0.01)
+    res = {}
+    for mode in ("strain", "stress"):
+        r = RVE(cfg["shape"], **kw)
+        e0, e1, s = _events(torch)
+        torch.cuda.synchronize()
+        e0.record(s)
+        if mode == "strain":
+            r.set_macro_F(Fb)
+            st = r.solve_increment(cfg["tol_newton"], cfg["tol_cg"])
+        else:
+            st = r.solve_mixed(Fb, np.zeros(9), synth.uniaxial_stress_mask(), tol_stress=1e-6,
+                               tol_newton=cfg["tol_newton"], tol_cg=cfg["tol_cg"])
+        e1.record(s)
+        torch.cuda.synchronize()
+        res[mode] = (e0.elapsed_time(e1), st, r.homogenized_P(), r.macro_F())
+        r.close()
+    ms, st, Pb, Fm = res["stress"]
+    ms_e, st_e, Pb_e, _ = res["strain"]
+    _line("svk125_spheres_uniaxial_stress_mixed", METRIC, n * st["cg_iters_total"] / (ms / 1e3),
+          UNIT, dtype="f32/f64", ms=ms, cg_iters=st["cg_iters_total"],
+          macro_iters=st["macro_iters"], tangent_solves=st["tangent_solves"],
+          newton_iters=st["newton_iters"], lateral_F=float(Fm[1, 1]), P11=float(Pb[0, 0]),
+          strain_control_ms=ms_e, strain_control_cg_iters=st_e["cg_iters_total"],
+          strain_control_P11=float(Pb_e[0, 0]), time_ratio=ms / ms_e)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -462,7 +497,8 @@ def main():
     ap.add_argument("--j2-steps", type=int, default=2,
                     help="increments of the 315^3 J2 ramp timed by --workload j2_315")
     ap.add_argument("--workload", default="svk125",
-                    choices=["svk125", "cube31", "j2_315", "batch256", "adjoint243", "tangent125"],
+                    choices=["svk125", "cube31", "j2_315", "batch256", "adjoint243", "tangent125",
+                             "mixed125"],
                     help="svk125 (default) is the headline; the others print one line each")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -474,7 +510,8 @@ def main():
               "j2_315": lambda: bench_j2_315(args, torch, RVE),
               "batch256": lambda: bench_batch256(args, torch),
               "adjoint243": lambda: bench_adjoint243(args, torch, RVE),
-              "tangent125": lambda: bench_tangent125(args, torch, RVE)}[args.workload]
+              "tangent125": lambda: bench_tangent125(args, torch, RVE),
+              "mixed125": lambda: bench_mixed125(args, torch, RVE)}[args.workload]
         fn()
         return None
 

@@ -268,8 +268,10 @@ int rve_set_F(rve_t h, const double* F, int src_on_device);
  * [9][n] float64, both on the host or both on the device. */
 int rve_apply_operator(rve_t h, const double* dF, double* out, int on_device);
 
-/* out = G : A in float64 (Eq. weak:discr:FFT-intermediate).  A and out are
- * [9][n] float64, both on the host or both on the device. */
+/* out = G : A in float64 (Eq. weak:discr:FFT-intermediate): hardware
+ * float64, or for MIXED handles the arithmetic of rve_options.residual (the
+ * transform the mixed path applies to its residual).  A and out are [9][n]
+ * float64, both on the host or both on the device. */
 int rve_project(rve_t h, const double* A, double* out, int on_device);
 
 /* ---------------------------------------------------------------------------

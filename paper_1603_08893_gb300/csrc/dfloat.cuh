@@ -1,6 +1,6 @@
 // Float-float arithmetic: a value is the unevaluated sum hi + lo of two
-// floats with |lo| <= ulp(hi) / 2, about 48 significant bits (relative
-// rounding ~ 2^-47 per operation).  Built on the error-free transformations
+// floats with |lo| <= ulp(hi) / 2, about 48 significant bits (rounding
+// ~ 2^-47 per operation, relative to the operands).  Built on the error-free transformations
 // of Knuth (two-sum), Dekker (fast two-sum, |a| >= |b|) and the FMA
 // two-product.  GB300 issues float32 at 64x its float64 rate, so the
 // float64-accuracy transforms of the mixed path (residual G:P and the
@@ -41,13 +41,15 @@ RVE_DEV dfl fast_two_sum(float a, float b) {
   return {s, b - (s - a)};
 }
 
+// Sum with an absolute error of a few 2^-48 (|a| + |b|): the high parts are
+// added exactly, the low parts in one rounding, then renormalised.  Under
+// cancellation the result's relative error can grow, its absolute error does
+// not -- the bound that a linear transform (DFT, projection) needs, whose
+// error analysis is in absolute terms relative to the input's norm.  About
+// half the operations of the variant that also adds the low parts exactly.
 RVE_DEV dfl operator+(dfl a, dfl b) {
-  dfl s = two_sum(a.hi, b.hi);
-  const dfl t = two_sum(a.lo, b.lo);
-  s.lo += t.hi;
-  s = fast_two_sum(s.hi, s.lo);
-  s.lo += t.lo;
-  return fast_two_sum(s.hi, s.lo);
+  const dfl s = two_sum(a.hi, b.hi);
+  return fast_two_sum(s.hi, s.lo + (a.lo + b.lo));
 }
 
 RVE_DEV dfl operator-(dfl a) { return {-a.hi, -a.lo}; }

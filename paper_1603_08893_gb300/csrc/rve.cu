@@ -1865,7 +1865,7 @@ int rve_project(rve_t h, const double* A, double* out, int on_device) {
   const size_t n9 = 9 * h->n;
   int rc = copy_in(h, h->tmp64, A, n9 * 8, on_device);
   if (rc) return rc;
-  enqueue_project_fp64(h, h->tmp64, false);
+  enqueue_project_fp64(h, h->tmp64);
   CK(cudaGetLastError());
   return copy_out(h, out, h->tmp64, n9 * 8, on_device);
 }
