@@ -482,6 +482,36 @@ def bench_mixed125(args, torch, RVE):
           strain_control_P11=float(Pb_e[0, 0]), time_ratio=ms / ms_e)
 
 
+def bench_precond125(args, torch, RVE):
+    """Reference-medium preconditioned float32 CG against plain CG on the
+    125^3 spheres (contrast 100): the first 4 increments of the uniaxial ramp,
+    mixed precision, solve time and CG iterations of each, P-bar agreement."""
+    cfg = workload()
+    n = int(np.prod(cfg["shape"]))
+    k = 4
+    res = {}
+    for pc in ("none", "reference"):
+        r = RVE(cfg["shape"], phase=cfg["phase"], phase_params=cfg["phase_params"],
+                precision="mixed", precond=pc)
+        e0, e1, s = _events(torch)
+        cg = 0
+        torch.cuda.synchronize()
+        e0.record(s)
+        for Fb in cfg["schedule"][:k]:
+            r.set_macro_F(Fb)
+            cg += r.solve_increment(cfg["tol_newton"], cfg["tol_cg"])["cg_iters_total"]
+        e1.record(s)
+        torch.cuda.synchronize()
+        res[pc] = (e0.elapsed_time(e1), cg, r.homogenized_P())
+        r.close()
+    ms, cg, Pb = res["reference"]
+    ms0, cg0, Pb0 = res["none"]
+    _line("svk125_spheres_uniaxial_precond_mixed", METRIC, n * cg / (ms / 1e3), UNIT,
+          dtype="f32/f64", increments=k, solve_ms=ms, cg_iters=cg, plain_solve_ms=ms0,
+          plain_cg_iters=cg0, plain_value=n * cg0 / (ms0 / 1e3), solve_time_ratio=ms0 / ms,
+          pbar_rel_diff=float(np.abs(Pb - Pb0).max() / np.abs(Pb0).max()))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -498,7 +528,7 @@ def main():
                     help="increments of the 315^3 J2 ramp timed by --workload j2_315")
     ap.add_argument("--workload", default="svk125",
                     choices=["svk125", "cube31", "j2_315", "batch256", "adjoint243", "tangent125",
-                             "mixed125"],
+                             "mixed125", "precond125"],
                     help="svk125 (default) is the headline; the others print one line each")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -511,7 +541,8 @@ def main():
               "batch256": lambda: bench_batch256(args, torch),
               "adjoint243": lambda: bench_adjoint243(args, torch, RVE),
               "tangent125": lambda: bench_tangent125(args, torch, RVE),
-              "mixed125": lambda: bench_mixed125(args, torch, RVE)}[args.workload]
+              "mixed125": lambda: bench_mixed125(args, torch, RVE),
+              "precond125": lambda: bench_precond125(args, torch, RVE)}[args.workload]
         fn()
         return None
 

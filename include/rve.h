@@ -78,6 +78,14 @@ extern "C" {
                                dP_ij/dF_kl (major symmetry K_ijkl = K_lkji of both
                                models), 45 reals per voxel */
 
+/* CG preconditioner (not in the paper, which uses plain CG) */
+#define RVE_PRECOND_NONE 0      /* plain CG (Algorithm 1) */
+#define RVE_PRECOND_REFERENCE 1 /* reference-medium preconditioner M = G:K0:G, K0 isotropic
+                                   with the voxel averages of the Lame parameters; applied as
+                                   the inverse acoustic tensor of K0 per frequency in the x
+                                   pass; MIXED precision and x lengths with a four-step DFT
+                                   kernel (15, 21, 27, 33, 45, 63, 125, 243, 315) only */
+
 /* arithmetic of the mixed path's float64-accuracy transforms */
 #define RVE_RES_FLOATFLOAT 0 /* float-float on the float32 pipe: hi + lo float pairs,
                                 ~48-bit significand, float64 inputs and outputs */
@@ -106,6 +114,14 @@ typedef struct {
                            rve_create on this grid and keep the fastest; the choice
                            is cached per (grid, device, tangent) for the process;
                            default 0 */
+  int precond;          /* RVE_PRECOND_* (default NONE).  REFERENCE: every CG solve
+                           (Newton, predictor, adjoint, homogenised tangent) runs the
+                           preconditioned recurrence z = M^+ r with one transform round
+                           trip per iteration, as plain CG; it stops at
+                           sqrt(r.z) <= max(tol sqrt(r0.z0), cg_atol), the M^-1-norm of
+                           the residual instead of its 2-norm.  The converged Newton
+                           state is the same; CG needs fewer iterations as the phase
+                           contrast grows */
   void* stream;         /* cudaStream_t; NULL = legacy default stream */
   void* workspace;      /* optional caller-owned device memory (see rve_workspace_size) */
   size_t workspace_bytes;

@@ -31,6 +31,8 @@ RVE_TAN_AUTO = 0
 RVE_TAN_FULL81 = 1
 RVE_TAN_RECOMPUTE = 2
 RVE_TAN_SYM45 = 3
+RVE_PRECOND_NONE = 0
+RVE_PRECOND_REFERENCE = 1
 RVE_MAX_NEWTON_LOG = 64
 
 
@@ -39,7 +41,7 @@ class rve_options(C.Structure):
                 ("max_newton", C.c_int), ("max_cg", C.c_int),
                 ("cg_tol_floor", C.c_double), ("cg_atol", C.c_double),
                 ("mixed_refine", C.c_int), ("residual", C.c_int),
-                ("autotune", C.c_int),
+                ("autotune", C.c_int), ("precond", C.c_int),
                 ("stream", C.c_void_p), ("workspace", C.c_void_p),
                 ("workspace_bytes", C.c_size_t)]
 

@@ -304,7 +304,20 @@ struct ZinvParams {
   double* partials;
   const int* done;
   const cplx<R>* tw;
+  float mn_ell;  // >= 0: reduce z.(K0:z) with lambda0/mu0 = mn_ell (mu0 = 1), else z.z
 };
+
+// z.(K0:z) for the reference medium K0:z = ell tr(z) I + z + z^T (mu0 = 1):
+// the squared norm the preconditioned CG monitors (z = M^+ r, r.z = z.(K0:z)
+// for compatible z)
+template <typename R>
+RVE_DEV R mnorm_k0(const R (&z)[9], R ell) {
+  const R tr = z[0] + z[4] + z[8];
+  const R d2 = z[0] * z[0] + z[4] * z[4] + z[8] * z[8];
+  const R o2 = z[1] * z[1] + z[3] * z[3] + z[2] * z[2] + z[6] * z[6] + z[5] * z[5] + z[7] * z[7];
+  const R x2 = z[1] * z[3] + z[2] * z[6] + z[5] * z[7];
+  return ell * tr * tr + R(2) * d2 + o2 + R(2) * x2;
+}
 
 // Four-step float z passes of the fused CG iteration (kernels_fft4.cu),
 // used when the z length has a compiled split (g.fsz_n1 != 0).

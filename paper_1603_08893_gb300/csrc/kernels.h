@@ -48,6 +48,9 @@ struct GridGeom {
                // a candidate of the autotuner
   int fsy_t, fsy_grp, fsx_t, fsz_lz, fszf_lz;
   FastDiv f_fsy_ntk, f_fsx_ntk, f_fsy_L, f_fsx_L, f_fsz_L, f_fsz_lz;
+  // reference medium of the preconditioned CG (lambda0 / mu0 and
+  // (lambda0 + mu0) / (lambda0 + 2 mu0), with mu0 scaled to 1)
+  float pc_ell, pc_c;
 };
 
 // Axis lengths with compiled four-step kernels: X(N, N1, N2), N = N1 N2.
@@ -70,6 +73,12 @@ constexpr int fs_x_t(int n) {
   return 8 * 3 * n * 16 <= 65536 ? 16 : (8 * 3 * n * 8 <= 65536 ? 8 : 4);
 }
 // first z pass: tiles of about 32 KB (larger tiles measured slower)
+// x pass of the preconditioned iteration: all nine components per tile
+// (the reference-medium operator couples the tensor rows), tiles of at most
+// 96 KB
+constexpr int fs_x_t_g0(int n) {
+  return 72 * n * 16 <= 98304 ? 16 : (72 * n * 8 <= 98304 ? 8 : (72 * n * 4 <= 98304 ? 4 : 2));
+}
 constexpr int fs_zf_lz(int n) {
   return (32768 / (8 * n) - 1) / 5 < 1 ? 1 : ((32768 / (8 * n) - 1) / 5 > 64 ? 64 : (32768 / (8 * n) - 1) / 5);
 }
@@ -148,20 +157,24 @@ void launch_zfwd(const GridGeom& g, int src, const TangentView<R>& tan, const R*
 template <typename R>
 void launch_fft_y(const GridGeom& g, bool inverse, cplx<R>* spec, const int* done,
                   const Twiddles<R>& tw, cudaStream_t s);
+// gamma0: the reference-medium Green operator (preconditioned CG, float
+// four-step x lengths only) in place of G-hat
 template <typename R>
 void launch_fft_x_proj(const GridGeom& g, double scale, cplx<R>* spec, const int* done,
-                       const Twiddles<R>& tw, cudaStream_t s);
+                       const Twiddles<R>& tw, cudaStream_t s, bool gamma0 = false);
 // Inverse z transform and output stage.
+// mnorm: the CG reductions of OUT_CGR / OUT_RESID take the reference-medium
+// norm z.(K0:z) instead of z.z (preconditioned CG)
 template <typename R, typename RC>
 void launch_zinv(const GridGeom& g, int out, const cplx<R>* spec, R* dst, RC* r_out, RC* x_out,
                  const RC* p_in, SolverState* st, double* partials, const int* done,
-                 const Twiddles<R>& tw, cudaStream_t s);
+                 const Twiddles<R>& tw, cudaStream_t s, bool mnorm = false);
 
 // four-step float kernels (kernels_fft4.cu); used when g.fsy_n1 / g.fsx_n1
 void launch_fft_y4(const GridGeom& g, bool inverse, cplx<float>* spec, const int* done,
                    const cplx<float>* tw, cudaStream_t s);
 void launch_fft_x4(const GridGeom& g, double scale, cplx<float>* spec, const int* done,
-                   const cplx<float>* tw, cudaStream_t s);
+                   const cplx<float>* tw, cudaStream_t s, bool gamma0 = false);
 cudaError_t fft4_kernels_init();
 
 // G : in in float-float arithmetic on the float32 pipe (float64 in and out):

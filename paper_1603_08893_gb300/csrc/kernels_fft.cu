@@ -265,10 +265,12 @@ __global__ void FFT_BOUNDS(R) k_zinv(const ZinvParams<R, RC> P) {
       R s = 0;
 #pragma unroll
       for (int c = 0; c < 9; ++c) {
-        const R rn = fma(-alpha, out[c], rv[c]);
-        P.r_out[(size_t)c * n + v] = (RC)rn;
-        s = fma(rn, rn, s);
+        rv[c] = fma(-alpha, out[c], rv[c]);
+        P.r_out[(size_t)c * n + v] = (RC)rv[c];
+        s = fma(rv[c], rv[c], s);
       }
+      if constexpr (!is_dfl<R>::value)
+        if (P.mn_ell >= 0.f) s = mnorm_k0<R>(rv, (R)P.mn_ell);
       acc += (double)s;
     } else if constexpr (OUT == OUT_CGAP) {
       R pv[9];
@@ -289,6 +291,8 @@ __global__ void FFT_BOUNDS(R) k_zinv(const ZinvParams<R, RC> P) {
         P.x_out[(size_t)c * n + v] = (RC)0;
         s = fma(out[c], out[c], s);
       }
+      if constexpr (!is_dfl<R>::value)
+        if (P.mn_ell >= 0.f) s = mnorm_k0<R>(out, (R)P.mn_ell);
       acc += (double)s;
     }
   }
@@ -412,10 +416,10 @@ void launch_fft_y(const GridGeom& g, bool inverse, cplx<R>* spec, const int* don
 
 template <typename R>
 void launch_fft_x_proj(const GridGeom& g, double scale, cplx<R>* spec, const int* done,
-                       const Twiddles<R>& tw, cudaStream_t s) {
-  if (sizeof(R) == 4 && g.fsx_n1) {
+                       const Twiddles<R>& tw, cudaStream_t s, bool gamma0) {
+  if (sizeof(R) == 4 && (g.fsx_n1 || gamma0)) {
     launch_fft_x4(g, scale, reinterpret_cast<cplx<float>*>(spec), done,
-                  reinterpret_cast<const cplx<float>*>(tw.x), s);
+                  reinterpret_cast<const cplx<float>*>(tw.x), s, gamma0);
     return;
   }
   LineParams<R> P{};
@@ -434,9 +438,10 @@ void launch_fft_x_proj(const GridGeom& g, double scale, cplx<R>* spec, const int
 template <typename R, typename RC>
 void launch_zinv(const GridGeom& g, int out, const cplx<R>* spec, R* dst, RC* r_out, RC* x_out,
                  const RC* p_in, SolverState* st, double* partials, const int* done,
-                 const Twiddles<R>& tw, cudaStream_t s) {
+                 const Twiddles<R>& tw, cudaStream_t s, bool mnorm) {
   ZinvParams<R, RC> P{};
   P.g = g;
+  P.mn_ell = mnorm ? g.pc_ell : -1.f;
   P.lz = lz_of<R>(g);
   P.spec = spec;
   P.dst = dst;
@@ -631,19 +636,19 @@ template void launch_fft_y<float>(const GridGeom&, bool, cplx<float>*, const int
 template void launch_fft_y<double>(const GridGeom&, bool, cplx<double>*, const int*,
                                    const Twiddles<double>&, cudaStream_t);
 template void launch_fft_x_proj<float>(const GridGeom&, double, cplx<float>*, const int*,
-                                       const Twiddles<float>&, cudaStream_t);
+                                       const Twiddles<float>&, cudaStream_t, bool);
 template void launch_fft_x_proj<double>(const GridGeom&, double, cplx<double>*, const int*,
-                                        const Twiddles<double>&, cudaStream_t);
+                                        const Twiddles<double>&, cudaStream_t, bool);
 template void launch_zinv<double, double>(const GridGeom&, int, const cplx<double>*, double*,
                                           double*, double*, const double*, SolverState*, double*,
-                                          const int*, const Twiddles<double>&, cudaStream_t);
+                                          const int*, const Twiddles<double>&, cudaStream_t, bool);
 template void launch_zinv<double, float>(const GridGeom&, int, const cplx<double>*, double*,
                                          float*, float*, const float*, SolverState*, double*,
-                                         const int*, const Twiddles<double>&, cudaStream_t);
+                                         const int*, const Twiddles<double>&, cudaStream_t, bool);
 template void launch_zinv<float, float>(const GridGeom&, int, const cplx<float>*, float*, float*,
                                         float*, const float*, SolverState*, double*, const int*,
-                                        const Twiddles<float>&, cudaStream_t);
+                                        const Twiddles<float>&, cudaStream_t, bool);
 template void launch_fft_y<dfl>(const GridGeom&, bool, cplx<dfl>*, const int*,
                                 const Twiddles<dfl>&, cudaStream_t);
 template void launch_fft_x_proj<dfl>(const GridGeom&, double, cplx<dfl>*, const int*,
-                                     const Twiddles<dfl>&, cudaStream_t);
+                                     const Twiddles<dfl>&, cudaStream_t, bool);

@@ -142,6 +142,81 @@ __global__ void __launch_bounds__(FFT_THREADS, (Fs4Occ<R, N1, N2>::value))
   fs_phase_a_s2g<R, N1, N2, LM>(buf, tw2, gl);
 }
 
+// x pass of the preconditioned CG iteration: as k_fft_x4, with the
+// reference-medium Green operator Gamma0 = pinv(G K0 G) G in place of G-hat.
+// Per frequency, with a_i = sum_l A_il xi_l / |xi|^2 (the coefficient of
+// Eq. G_red) and d = xi . a / |xi|^2, the inverse acoustic tensor of the
+// isotropic K0 (mu0 = 1) gives C_ij = (a_i - c xi_i d) xi_j,
+// c = (lambda0 + mu0) / (lambda0 + 2 mu0).  d couples the three tensor rows,
+// so a tile holds all nine components: (9 components) x nx x (T kz), one ky.
+template <typename R, int N1, int N2>
+__global__ void __launch_bounds__(FFT_THREADS, 2) k_fft_x4_g0(const LineParams<R> P) {
+  constexpr int N = N1 * N2;
+  constexpr int T = fs_x_t_g0(N);
+  using LM = FsLayout<T, N * T, 1, T, 9 * T>;
+  if (P.done && *P.done) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cplx<R>* tw2 = reinterpret_cast<cplx<R>*>(smem_raw);
+  cplx<R>* buf = tw2 + ((N + 1) & ~1);
+  const int ny = P.g.ny;
+  const int hz = P.g.hz, hzp = P.g.hzp;
+  const int ntk = (hz + T - 1) / T;
+  const size_t rs = (size_t)ny * hzp;  // stride of spectrum rows (c*nx + x)
+  const int tile = blockIdx.x;
+  const int y = tile / ntk;
+  const int k0 = (tile - y * ntk) * T;
+  cplx<R>* gbase = P.spec + (size_t)y * hzp + k0;
+  // line l = (component l / T, kz k0 + l % T): rows x at stride rs
+  auto gl = [&](int l) {
+    const int c = l / T, t = l - (l / T) * T;
+    return GLine<R>{gbase + (size_t)c * N * rs + t, rs, k0 + t < hz, k0 + t < hz};
+  };
+  fs_twiddles<R, N1, N2>(tw2, P.tw);
+  __syncthreads();
+  fs_phase_a_g2s<R, N1, N2, LM>(buf, tw2, gl);
+  __syncthreads();
+  fs_phase_b<R, N1, N2, false, LM>(buf);
+  const R qy = signed_freq<R>(y, ny) / (R)ny;
+  const R sc = (R)P.scale;
+  const R cc = (R)P.g.pc_c;
+  R* qxs = reinterpret_cast<R*>(buf + 9 * N * T);  // [N]
+  R* qzs = qxs + N;                                // [T]
+  for (int i = threadIdx.x; i < N + T; i += blockDim.x) {
+    if (i < N) qxs[i] = signed_freq<R>(fs_freq<N1, N2>(i), N) / (R)N;
+    else qzs[i - N] = (R)(k0 + i - N) / (R)P.g.nz;
+  }
+  __syncthreads();
+  const bool nyq_y = (ny % 2 == 0) && (2 * y == ny);
+  const int kz_nyq = (P.g.nz % 2 == 0) ? P.g.nz / 2 : -1;
+  constexpr int NT = N * T;
+  for (int i = threadIdx.x; i < NT; i += blockDim.x) {
+    const R q[3] = {qxs[i / T], qy, qzs[i % T]};
+    const R q2 = q[0] * q[0] + q[1] * q[1] + q[2] * q[2];
+    const bool nyq = nyq_y || (k0 + i % T == kz_nyq);
+    const R inv = (q2 > R(0) && !nyq) ? __frcp_rn(q2) : R(0);
+    R ax[3], ay[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      const cplx<R> A0 = buf[(3 * r) * NT + i], A1 = buf[(3 * r + 1) * NT + i],
+                    A2 = buf[(3 * r + 2) * NT + i];
+      ax[r] = sc * inv * (q[0] * A0.x + q[1] * A1.x + q[2] * A2.x);
+      ay[r] = sc * inv * (q[0] * A0.y + q[1] * A1.y + q[2] * A2.y);
+    }
+    const R dx = cc * inv * (q[0] * ax[0] + q[1] * ax[1] + q[2] * ax[2]);
+    const R dy = cc * inv * (q[0] * ay[0] + q[1] * ay[1] + q[2] * ay[2]);
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      const R bx = ax[r] - q[r] * dx, by = ay[r] - q[r] * dy;
+#pragma unroll
+      for (int j = 0; j < 3; ++j) buf[(3 * r + j) * NT + i] = {bx * q[j], by * q[j]};
+    }
+  }
+  __syncthreads();
+  fs_phase_b<R, N1, N2, true, LM>(buf);
+  __syncthreads();
+  fs_phase_a_s2g<R, N1, N2, LM>(buf, tw2, gl);
+}
+
 // L2 prefetch of the first-pass inputs of a tile (r and F, after the first
 // iteration p and x, the phase bytes): every 128-byte line of each
 // component's range, addresses clamped into the range.
@@ -474,6 +549,7 @@ __global__ void __launch_bounds__(FFT_THREADS, (Fs4Occ<R, N1, N2>::value))
   if (threadIdx.x == 0) mbar_init(&bar, 1);
   fs_twiddles<R, N1, N2>(tw2, P.tw);
   const R alpha = (R)P.st->alpha;
+  const R mn_ell = (R)P.mn_ell;
   __syncthreads();
   double acc = 0.0;
   unsigned parity = 0;
@@ -546,10 +622,11 @@ __global__ void __launch_bounds__(FFT_THREADS, (Fs4Occ<R, N1, N2>::value))
       R s = 0;
 #pragma unroll
       for (int c = 0; c < 9; ++c) {
-        const R rn = fma(-alpha, out[c], rt[c * SP + rofs[c] + i]);
-        P.r_out[(size_t)c * n + v0 + i] = rn;
-        s = fma(rn, rn, s);
+        out[c] = fma(-alpha, out[c], rt[c * SP + rofs[c] + i]);
+        P.r_out[(size_t)c * n + v0 + i] = out[c];
+        s = fma(out[c], out[c], s);
       }
+      if (mn_ell >= R(0)) s = mnorm_k0<R>(out, mn_ell);
       acc += (double)s;
     }
     __syncthreads();  // buffer, r copy and rofs are refilled by the next tile
@@ -601,9 +678,25 @@ void launch_fft_y4(const GridGeom& g, bool inverse, cplx<float>* spec, const int
 }
 
 void launch_fft_x4(const GridGeom& g, double scale, cplx<float>* spec, const int* done,
-                   const cplx<float>* tw, cudaStream_t s) {
+                   const cplx<float>* tw, cudaStream_t s, bool gamma0) {
   LineParams<float> P;
   P.g = g;
+  if (gamma0) {
+    P.t = 0;
+    P.grp = 1;
+    P.scale = scale;
+    P.spec = spec;
+    P.done = done;
+    P.tw = tw;
+    switch (g.nx) {
+#define RVE_FS_XG(N, A, B)                                                                      case N: {                                                                                       constexpr int T = fs_x_t_g0(N);                                                               const int ntiles = g.ny * ((g.hz + T - 1) / T);                                               const size_t sm = sizeof(cplx<float>) * ((size_t)((N + 1) & ~1) + 9 * (size_t)N * T) +                          sizeof(float) * ((size_t)N + T);                                            k_fft_x4_g0<float, A, B><<<ntiles, FFT_THREADS, sm, s>>>(P);                                  break;                                                                                      }
+      RVE_FS_SIZES(RVE_FS_XG)
+#undef RVE_FS_XG
+      default:
+        break;
+    }
+    return;
+  }
   P.t = g.fsx_t;
   P.grp = 1;
   P.scale = scale;
@@ -709,6 +802,7 @@ cudaError_t fft4_kernels_init() {
   allow_smem(k_fft_y4<float, A, B, true>);                  \
   allow_smem(k_fft_y4<float, A, B, false>);                 \
   allow_smem(k_fft_x4<float, A, B>);                        \
+  allow_smem(k_fft_x4_g0<float, A, B>);                     \
   allow_smem(k_zfwd4<float, SRC_CGPX, TAN_FULL81, A, B>);   \
   allow_smem(k_zfwd4<float, SRC_CGPX, TAN_SVK, A, B>);      \
   allow_smem(k_zfwd4<float, SRC_CGPX, TAN_SYM45, A, B>);    \

@@ -202,6 +202,7 @@ struct rve_s {
   Twiddles<double> twd{};
   Twiddles<dfl> twdf{};
   bool floatfloat = false;  // mixed: float64-accuracy transforms in float-float
+  bool precond = false;     // reference-medium preconditioned float32 CG
   int knobs[7] = {1, 3, 1, 1, 1, 0, 0};  // kernel variants (rve_tuning)
   double Fbar[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
   double Fbar_committed[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};  // F-bar of the last committed state
@@ -339,7 +340,7 @@ void enqueue_cg_iteration(rve_t h, int iter) {
   }
   {
     FamilyTimer t(h, 2, iter);
-    launch_fft_x_proj<R>(g, 1.0 / (double)h->n, spec, done, tw, h->s);
+    launch_fft_x_proj<R>(g, 1.0 / (double)h->n, spec, done, tw, h->s, fused && h->precond);
   }
   {
     FamilyTimer t(h, 3, iter);
@@ -348,7 +349,7 @@ void enqueue_cg_iteration(rve_t h, int iter) {
   if (fused) {
     FamilyTimer t(h, 4, iter);
     launch_zinv<R, R>(g, OUT_CGR, spec, nullptr, as<R>(h->r), nullptr, nullptr, h->st,
-                      h->partials, done, tw, h->s);
+                      h->partials, done, tw, h->s, h->precond);
     h->launches += 5;
     return;
   }
@@ -363,6 +364,28 @@ void enqueue_cg_iteration(rve_t h, int iter) {
                         h->partials, h->s);
   }
   h->launches += 6;
+}
+
+// Preconditioned CG (reference medium, float32 path): the residual r of
+// the right-hand side just set up is replaced by z = Gamma0 r (the inverse
+// acoustic tensor of K0 applied in Fourier space, in the x pass) and the CG
+// state restarts on it with the norm z.(K0:z) = r.z.  The iteration then
+// updates z instead of r: z -= alpha Gamma0 (K:p), one transform round trip
+// per iteration as without preconditioning; p.Ap = p.(K:p) as before.
+void enqueue_precondition(rve_t h) {
+  const GridGeom& g = h->g;
+  const Twiddles<float>& tw = h->twf;
+  cplx<float>* spec = as<cplx<float>>(h->spec_op);
+  TangentView<float> plain{};
+  plain.mode = 0;
+  launch_zfwd<float>(g, SRC_FIELD, plain, as<float>(h->r), nullptr, nullptr, nullptr, h->st,
+                     nullptr, spec, tw, h->s);
+  launch_fft_y<float>(g, false, spec, nullptr, tw, h->s);
+  launch_fft_x_proj<float>(g, 1.0 / (double)h->n, spec, nullptr, tw, h->s, true);
+  launch_fft_y<float>(g, true, spec, nullptr, tw, h->s);
+  launch_zinv<float, float>(g, OUT_RESID, spec, nullptr, as<float>(h->r), as<float>(h->x), nullptr,
+                            h->st, h->partials, nullptr, tw, h->s, true);
+  h->launches += 5;
 }
 
 // The last lagged step x += alpha p of a float32 CG solve.
@@ -519,6 +542,7 @@ int cg_solve(rve_t h, int* iters) {
   int launched = 0;
   int chunk = 4;
   h->solve_id++;
+  if (std::is_same<R, float>::value && h->precond) enqueue_precondition(h);
   int rc = sync_state(h);
   if (rc) return rc;
   while (!h->hst->done) {
@@ -703,7 +727,7 @@ int autotune(rve_t h) {
   NvtxRange nv("rve autotune");
   int dev = 0;
   cudaGetDevice(&dev);
-  const TuneKey key{h->g.nx, h->g.ny, h->g.nz, dev, h->tan};
+  const TuneKey key{h->g.nx, h->g.ny, h->g.nz, dev, h->tan + 16 * (int)h->precond};
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune_cache.find(key);
@@ -758,6 +782,7 @@ void rve_default_options(rve_options* o) {
   o->mixed_refine = 0;
   o->residual = RVE_RES_FLOATFLOAT;
   o->autotune = 0;
+  o->precond = RVE_PRECOND_NONE;
 }
 
 const char* rve_status_string(int code) {
@@ -793,6 +818,10 @@ static int resolve_options(const rve_options* in, rve_options* out, int model, i
   if (out->mixed_refine < 0 || out->mixed_refine > 8) return RVE_ERR_INVALID;
   if (out->residual != RVE_RES_FLOATFLOAT && out->residual != RVE_RES_FP64) return RVE_ERR_INVALID;
   if (out->autotune != 0 && out->autotune != 1) return RVE_ERR_INVALID;
+  if (out->precond != RVE_PRECOND_NONE && out->precond != RVE_PRECOND_REFERENCE)
+    return RVE_ERR_INVALID;
+  if (out->precond == RVE_PRECOND_REFERENCE && out->precision != RVE_MIXED)
+    return RVE_ERR_UNSUPPORTED;
   if (model == RVE_SVK) {
     if (out->tangent == RVE_TAN_AUTO || out->tangent == RVE_TAN_RECOMPUTE) *tan = TAN_SVK;
     else if (out->tangent == RVE_TAN_FULL81) *tan = TAN_FULL81;
@@ -853,6 +882,9 @@ int rve_create(rve_t* out, int nx, int ny, int nz, int model, int nphase, const 
   h->n = h->g.n;
   h->mixed = h->opt.precision == RVE_MIXED;
   h->floatfloat = h->mixed && h->opt.residual == RVE_RES_FLOATFLOAT;
+  h->precond = h->opt.precond == RVE_PRECOND_REFERENCE;
+  if (h->precond && !fs_split_n1(nx))
+    return bail(RVE_ERR_UNSUPPORTED, "preconditioned CG needs an x length with a four-step DFT kernel");
   h->tan = tan;
   h->nparam = (model == RVE_J2) ? 4 : 2;
   h->s = (cudaStream_t)h->opt.stream;
@@ -957,6 +989,30 @@ int rve_create(rve_t* out, int nx, int ny, int nz, int model, int nphase, const 
     ok &= ck(cudaStreamSynchronize(h->s));
   }
   if (!ok) return bail(RVE_ERR_CUDA, std::string("initial copies failed: ") + cudaGetErrorString(first_err));
+  {
+    // reference medium of the preconditioner: voxel averages of the Lame
+    // parameters (only lambda0 / mu0 matters)
+    double lam0 = 0.0, mu0 = 0.0;
+    if (phase) {
+      std::vector<size_t> cnt(256, 0);
+      for (size_t v = 0; v < h->n; ++v) cnt[phase[v]]++;
+      for (int k = 0; k < nphase; ++k) {
+        const double K = phase_params[k * h->nparam], mu = phase_params[k * h->nparam + 1];
+        lam0 += (double)cnt[k] * (K - 2.0 * mu / 3.0);
+        mu0 += (double)cnt[k] * mu;
+      }
+    } else {
+      for (size_t v = 0; v < h->n; ++v) {
+        lam0 += voxel_params[v] - 2.0 * voxel_params[h->n + v] / 3.0;
+        mu0 += voxel_params[h->n + v];
+      }
+    }
+    if (h->precond && !(mu0 > 0.0 && lam0 + 2.0 * mu0 / 3.0 > 0.0))
+      return bail(RVE_ERR_INVALID, "reference medium needs positive average moduli");
+    const double ell = mu0 > 0.0 ? lam0 / mu0 : 0.0;
+    h->g.pc_ell = (float)ell;
+    h->g.pc_c = (float)((ell + 1.0) / (ell + 2.0));
+  }
   // F = I, evaluate the material there
   {
     std::vector<double> I(9 * h->n, 0.0);
@@ -1003,6 +1059,7 @@ struct CkptHeader {
   int max_newton, max_cg, mixed_refine;
   double cg_tol_floor, cg_atol;
   int knobs[7];
+  int precond;
   double Fbar[9], Fbar_committed[9];
 };
 
@@ -1039,7 +1096,7 @@ int rve_save(rve_t h, const char* path) {
   CkptHeader hd;
   std::memset(&hd, 0, sizeof(hd));
   std::memcpy(hd.magic, "RVECKPT1", 8);
-  hd.version = 1;
+  hd.version = 2;
   hd.nx = h->g.nx;
   hd.ny = h->g.ny;
   hd.nz = h->g.nz;
@@ -1054,6 +1111,7 @@ int rve_save(rve_t h, const char* path) {
   hd.mixed_refine = h->opt.mixed_refine;
   hd.cg_tol_floor = h->opt.cg_tol_floor;
   hd.cg_atol = h->opt.cg_atol;
+  hd.precond = h->opt.precond;
   std::memcpy(hd.knobs, h->knobs, sizeof(hd.knobs));
   std::memcpy(hd.Fbar, h->Fbar, sizeof(hd.Fbar));
   std::memcpy(hd.Fbar_committed, h->Fbar_committed, sizeof(hd.Fbar_committed));
@@ -1085,7 +1143,7 @@ int rve_load(rve_t* out, const char* path, const rve_options* opt) {
   if (!f) return RVE_ERR_INVALID;
   CkptHeader hd;
   if (std::fread(&hd, sizeof(hd), 1, f) != 1 || std::memcmp(hd.magic, "RVECKPT1", 8) != 0 ||
-      hd.version != 1) {
+      hd.version != 2) {
     std::fclose(f);
     return RVE_ERR_INVALID;
   }
@@ -1141,6 +1199,7 @@ int rve_load(rve_t* out, const char* path, const rve_options* opt) {
   o.mixed_refine = hd.mixed_refine;
   o.cg_tol_floor = hd.cg_tol_floor;
   o.cg_atol = hd.cg_atol;
+  o.precond = hd.precond;
   if (opt) {
     o.stream = opt->stream;
     o.workspace = opt->workspace;
@@ -2013,6 +2072,8 @@ int batch_cg_phase(rve_batch_t b, const std::vector<int>& active, std::vector<in
     int rc = batch_capture<R>(b, active);
     if (rc) return bfail(b, rc, "graph capture of the batched CG iteration failed");
   }
+  for (int c : active)
+    if (b->rv[c]->precond) enqueue_precondition(b->rv[c]);
   batch_sync_all(b);
   long long guard = 0;
   const long long max_launch = (long long)b->rv[active[0]]->opt.max_cg / kGraphIters + 4096;

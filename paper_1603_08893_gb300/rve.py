@@ -59,7 +59,7 @@ def _in_ptr(a, n):
 
 def _options(precision="fp64", tangent="auto", max_newton=50, max_cg=10000,
              cg_tol_floor=1e-5, cg_atol=0.0, mixed_refine=0, residual="floatfloat",
-             autotune=False, stream=None):
+             autotune=False, precond="none", stream=None):
     o = _lib.rve_options()
     lib.rve_default_options(C.byref(o))
     o.precision = _PREC[precision]
@@ -71,6 +71,7 @@ def _options(precision="fp64", tangent="auto", max_newton=50, max_cg=10000,
     o.mixed_refine = int(mixed_refine)
     o.residual = {"floatfloat": 0, "fp64": 1}[residual]
     o.autotune = 1 if autotune else 0
+    o.precond = {"none": 0, "reference": 1}[precond]
     if stream is None and torch is not None and torch.cuda.is_available():
         stream = torch.cuda.current_stream().cuda_stream
     o.stream = C.c_void_p(int(stream)) if stream else None
