@@ -107,8 +107,8 @@ def test_preconditioned_batch_equals_individual_solves():
     cells = []
     for n in (15, 21, 27, 15):
         ph, _ = synth.spheres(n, 0.3, 4.0, 10.0, rng)
-        cells.append(((n, n, n), ph, synth.two_phase_params(rng.uniform(2, 100)),
-                      np.eye(3) + rng.uniform(-0.05, 0.05, (3, 3))))
+        cells.append(((n, n, n), ph, synth.two_phase_params(rng.uniform(2, 20)),
+                      np.eye(3) + rng.uniform(-0.02, 0.02, (3, 3))))
     b = RVEBatch([c[0] for c in cells], [c[1] for c in cells], [c[2] for c in cells],
                  precision="mixed", precond="reference")
     st = b.solve(np.stack([c[3] for c in cells]))
