@@ -512,6 +512,56 @@ def bench_precond125(args, torch, RVE):
           pbar_rel_diff=float(np.abs(Pb - Pb0).max() / np.abs(Pb0).max()))
 
 
+def bench_contrast63(args, torch, RVE):
+    """Phase-contrast sweep of the paper's Sec. 5.5 experiment on a synthetic
+    stand-in (the micrograph is not available): 63^3 periodic Voronoi cell
+    (64 cells, half hard), J2 with E = 1, nu = 0.3, soft tau_y0 = 0.003 and
+    H = 0.01, hard ones chi times larger, chi in {sqrt 2, 2, 4, 8}; pure shear
+    F-bar = diag(l, 1/l, 1) to l = 1.2 in --contrast-increments increments
+    (250 in the paper), mixed precision with load-step cutting, plain and
+    reference-preconditioned CG.  Cumulative Newton and CG iterations and
+    device time per chi, also at equivalent strains 0.05 / 0.1 / 0.2."""
+    n = 63
+    ph, _ = synth.voronoi(n, 64, np.random.default_rng(2))
+    K, mu = 1.0 / 1.2, 1.0 / 2.6
+    m = args.contrast_increments
+    lams = [1.0 + 0.2 * (k + 1) / m for k in range(m)]
+    marks = (0.05, 0.1, 0.2)
+    out = {}
+    for pc in ("none", "reference"):
+        for chi in (np.sqrt(2.0), 2.0, 4.0, 8.0):
+            params = np.array([[K, mu, 0.003, 0.01], [K, mu, 0.003 * chi, 0.01 * chi]])
+            r = RVE((n, n, n), model="j2", phase=ph, phase_params=params, precision="mixed",
+                    precond=pc)
+            e0, e1, s = _events(torch)
+            newton = cg = cuts = 0
+            at = {}
+            torch.cuda.synchronize()
+            e0.record(s)
+            for lam in lams:
+                st = r.solve_step(np.diag([lam, 1.0 / lam, 1.0]), 1e-5, 1e-8, max_cuts=10)
+                newton += st["newton_iters"]
+                cg += st["cg_iters_total"]
+                cuts += st["cuts"]
+                eq = 2.0 / np.sqrt(3.0) * np.log(lam)
+                for mk in marks:
+                    if eq >= mk and mk not in at:
+                        at[mk] = (newton, cg)
+            e1.record(s)
+            torch.cuda.synchronize()
+            out[f"{pc}/chi={chi:.3g}"] = {
+                "newton_iters": newton, "cg_iters": cg, "cuts": cuts,
+                "solve_ms": e0.elapsed_time(e1),
+                "at_eq_strain": {str(k): {"newton": v[0], "cg": v[1]} for k, v in at.items()},
+                "pbar_xx": float(r.homogenized_P()[0, 0]),
+                "max_eps_p": float(r.get_history()[6].max())}
+            r.close()
+    tot_cg = sum(v["cg_iters"] for v in out.values())
+    tot_ms = sum(v["solve_ms"] for v in out.values())
+    _line("j2_63_voronoi_pure_shear_contrast_sweep", METRIC, n ** 3 * tot_cg / (tot_ms / 1e3),
+          UNIT, dtype="f32/f64", increments=m, sweep=out)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -526,9 +576,11 @@ def main():
                          "used for profiler captures")
     ap.add_argument("--j2-steps", type=int, default=2,
                     help="increments of the 315^3 J2 ramp timed by --workload j2_315")
+    ap.add_argument("--contrast-increments", type=int, default=250,
+                    help="increments of the pure-shear ramp of --workload contrast63")
     ap.add_argument("--workload", default="svk125",
                     choices=["svk125", "cube31", "j2_315", "batch256", "adjoint243", "tangent125",
-                             "mixed125", "precond125"],
+                             "mixed125", "precond125", "contrast63"],
                     help="svk125 (default) is the headline; the others print one line each")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -542,7 +594,8 @@ def main():
               "adjoint243": lambda: bench_adjoint243(args, torch, RVE),
               "tangent125": lambda: bench_tangent125(args, torch, RVE),
               "mixed125": lambda: bench_mixed125(args, torch, RVE),
-              "precond125": lambda: bench_precond125(args, torch, RVE)}[args.workload]
+              "precond125": lambda: bench_precond125(args, torch, RVE),
+              "contrast63": lambda: bench_contrast63(args, torch, RVE)}[args.workload]
         fn()
         return None
 
