@@ -1,5 +1,7 @@
 """Gradient of a homogenised-stress functional with respect to per-voxel
-shear and bulk moduli, Saint Venant-Kirchhoff (Sec. 4), by one adjoint solve.
+material parameters by one adjoint solve: shear and bulk moduli for Saint
+Venant-Kirchhoff (Sec. 4), and K, mu, tau_y0, H for J2 (Sec. 5) with the
+history at the start of the increment held fixed (below).
 
 Not in the paper; derived from its equilibrium equations.  With
 F = Fbar + w (w compatible, zero mean) the converged state satisfies
@@ -21,7 +23,7 @@ and in the same way, with the same lambda, for the bulk moduli
 """
 import numpy as np
 
-from . import fourier, solver, svk, tensor as t
+from . import fourier, j2, solver, svk, tensor as t
 
 
 def dP_dmu(F):
@@ -88,3 +90,61 @@ def localization(problem, W, tol_cg=1e-12, cg_atol=0.0):
     U = t.uniform(W, grid)
     dF, _, _ = solver.cg(op, -op(U), tol_cg, atol=cg_atol)
     return U + dF
+
+
+# ---------------------------------------------------------------------------
+# J2 (Sec. 5).  Reading: the derivative is taken for the last increment with
+# the committed history at its start (Cp^-1_n, eps_p,n) held fixed -- the
+# exact total derivative for a path of one increment from the virgin state.
+# The consistent tangent of the increment is symmetric (major symmetry), so
+# the adjoint system is the SVK one with the J2 tangent.  At fixed F and
+# history the eigenbasis of be = F Cp^-1 F^T does not depend on the
+# parameters; in it, with e the principal deviatoric log strain,
+# q = sqrt(3/2 e.e), tau_eq = 2 mu q, tau_y = tau_y0 + H eps_p,n,
+# dgamma = (tau_eq - tau_y)/(3 mu + H) on the plastic branch:
+#   tau_p = K tr(eps) + s_p,   s_p = 2 mu e - 3 mu dgamma e / q,
+#   d tau_p / dK      = tr(eps),
+#   d s_p / dmu       = 2 e - 3 (dgamma + mu d dgamma/dmu) e / q,
+#                       d dgamma/dmu = (2 q H + 3 tau_y) / (3 mu + H)^2,
+#   d s_p / dtau_y0   = 3 mu / (3 mu + H) e / q,
+#   d s_p / dH        = 3 mu (eps_p,n + dgamma) / (3 mu + H) e / q,
+# (elastic branch: 2 e for mu, 0 for tau_y0 and H), and dP = d tau F^-T.
+# ---------------------------------------------------------------------------
+def j2_dP_dparams(F, Cpi, ep, K, mu, ty0, H):
+    """(dP/dK, dP/dmu, dP/dtau_y0, dP/dH) for voxels: F, Cpi [n,3,3]; ep and
+    the parameters [n].  Returns [4, n, 3, 3]."""
+    st = j2.return_map(F, Cpi, ep, K, mu, ty0, H)
+    Q, e, tr = st["Q"], st["dev"], st["tr"]
+    plastic, dg, teq = st["plastic"], st["dg"], st["teq"]
+    q = np.where(plastic, teq / (2.0 * mu), 1.0)
+    den = 3.0 * mu + H
+    ty = ty0 + H * ep
+    ddg_dmu = (2.0 * q * H + 3.0 * ty) / den ** 2
+    eq = e / q[:, None]
+    d = np.zeros((4,) + e.shape)
+    d[0] = tr[:, None]
+    d[1] = 2.0 * e - np.where(plastic, 3.0 * (dg + mu * ddg_dmu), 0.0)[:, None] * eq
+    d[2] = np.where(plastic, 3.0 * mu / den, 0.0)[:, None] * eq
+    d[3] = np.where(plastic, 3.0 * mu * (ep + dg) / den, 0.0)[:, None] * eq
+    dtau = np.einsum("nab,knb,ncb->knac", Q, d, Q)
+    return np.einsum("knac,nbc->knab", dtau, st["Finv"])
+
+
+def j2_grad_params(F, Cpi, ep, K, mu, ty0, H, W, tol_cg=1e-12, cg_atol=0.0):
+    """dJ/d(K, mu, tau_y0, H) per voxel, [4, *grid], for J = W : P-bar at a
+    converged J2 increment: F [3,3,*grid], the history at the start of the
+    increment (Cpi [n,3,3], ep [n]) and the parameters ([n] each)."""
+    W = np.asarray(W, dtype=np.float64)
+    grid = F.shape[-3:]
+    n = int(np.prod(grid))
+    Fv = np.moveaxis(F.reshape(3, 3, -1), -1, 0)
+    st = j2.return_map(Fv, Cpi, ep, K, mu, ty0, H)
+    K4v = j2.tangent(Fv, Cpi, K, mu, H, st)
+    K4 = np.moveaxis(K4v, 0, -1).reshape((3, 3, 3, 3) + tuple(grid))
+    op = solver.tangent_operator(K4)
+    b = fourier.G(svk.tangent_apply(K4, t.uniform(W, grid)) / n)
+    lam, _, _ = solver.cg(op, b, tol_cg, atol=cg_atol)
+    lamv = np.moveaxis(lam.reshape(3, 3, -1), -1, 0)
+    dP = j2_dP_dparams(Fv, Cpi, ep, K, mu, ty0, H)
+    g = np.einsum("ab,knab->kn", W, dP) / n - np.einsum("nab,knab->kn", lamv, dP)
+    return g.reshape((4,) + tuple(grid))

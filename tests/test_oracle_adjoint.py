@@ -1,10 +1,15 @@
-"""Pins of the oracle's adjoint gradient dJ/dmu (CPU only).
+"""Pins of the oracle's adjoint gradients (CPU only).
 
 Against central finite differences of the converged P-bar with respect to
 single-voxel shear moduli, the independent forward (localisation) formula,
 and the envelope identity for the mean strain energy,
 dW-bar/dmu_k = (1/n) devE_k : devE_k at fixed F-bar (the fluctuation
-derivative vanishes at equilibrium).
+derivative vanishes at equilibrium).  J2: the stress derivatives with
+respect to K, mu, tau_y0, H against central differences of the return map
+(from a plastic committed history, elastic and plastic branches); the
+adjoint gradient summed over a phase against central differences of P-bar
+over re-solved increments from the virgin state; Euler's identity for a
+stress homogeneous of degree one in the parameters.
 """
 import numpy as np
 import pytest
@@ -123,3 +128,82 @@ def test_bulk_envelope_identity(state):
             vals.append(np.mean(svk.energy(q.F, q.K, q.mu)))
         fd = (vals[0] - vals[1]) / (2 * h)
         assert abs(fd - expected[idx]) < 1e-6 * np.abs(expected).max() + 1e-14
+
+
+# ---------------------------------------------------------------------------
+# J2: derivative at fixed start-of-increment history
+# ---------------------------------------------------------------------------
+J2_PARAMS = np.array([[1 / 1.2, 1 / 2.6, 0.003, 0.01], [1 / 1.2, 1 / 2.6, 0.006, 0.01]])
+
+
+def test_j2_stress_parameter_derivatives_match_finite_differences():
+    from oracle import j2
+    rng = np.random.default_rng(11)
+    m = 64
+    K = np.full(m, 1 / 1.2)
+    mu = np.full(m, 1 / 2.6)
+    ty0 = rng.uniform(0.002, 0.006, m)
+    H = rng.uniform(0.005, 0.05, m)
+    # a committed history from an earlier plastic step, then a further step
+    F0 = np.moveaxis(synth.random_F((m,), rng, 0.01), -1, 0)
+    st0 = j2.return_map(F0, np.broadcast_to(np.eye(3), (m, 3, 3)).copy(), np.zeros(m), K, mu,
+                        ty0, H)
+    Cpi, ep = st0["Cpi_new"], st0["ep_new"]
+    # partly unloading (elastic), partly loading further (plastic)
+    sc = rng.uniform(0.5, 1.5, m)[:, None, None]
+    F = np.eye(3) + sc * (F0 - np.eye(3)) + np.moveaxis(rng.uniform(-1e-3, 1e-3, (3, 3, m)), -1, 0)
+    d = adjoint.j2_dP_dparams(F, Cpi, ep, K, mu, ty0, H)
+    st = j2.return_map(F, Cpi, ep, K, mu, ty0, H)
+    assert 0.2 < st["plastic"].mean() < 1.0 and ep.max() > 0.0
+    args = [K, mu, ty0, H]
+    for k in range(4):
+        h = 1e-6 * args[k]
+        a_p = [a.copy() for a in args]
+        a_m = [a.copy() for a in args]
+        a_p[k] = args[k] + h
+        a_m[k] = args[k] - h
+        fd = (j2.return_map(F, Cpi, ep, *a_p)["P"] - j2.return_map(F, Cpi, ep, *a_m)["P"]) \
+            / (2 * h)[:, None, None]
+        assert np.abs(d[k] - fd).max() < 1e-6 * np.abs(fd).max() + 1e-12, k
+
+
+def _j2_cell():
+    rng = np.random.default_rng(13)
+    shape = (7, 5, 9)
+    ph = (rng.uniform(size=shape) < 0.5).astype(np.uint8)
+    return shape, ph
+
+
+def _j2_Pbar(shape, ph, params, Fbar):
+    prob = solver.J2Problem.from_phase(ph, params)
+    prob.increment(Fbar, **TIGHT)
+    return prob
+
+
+def test_j2_adjoint_gradient_matches_phase_finite_differences_and_euler():
+    shape, ph = _j2_cell()
+    Fbar = synth.simple_shear(0.006)
+    W = np.zeros((3, 3))
+    W[0, 1] = 1.0
+    prob = _j2_Pbar(shape, ph, J2_PARAMS, Fbar)
+    n = ph.size
+    assert prob.mat.ep.max() > 1e-4
+    p = J2_PARAMS[ph.reshape(-1)]
+    g = adjoint.j2_grad_params(prob.F, np.broadcast_to(np.eye(3), (n, 3, 3)).copy(), np.zeros(n),
+                               p[:, 0], p[:, 1], p[:, 2], p[:, 3], W, 1e-13, 1e-15)
+    J = float(np.sum(W * prob.homogenized_P()))
+    # Euler: P-bar is homogeneous of degree one in (K, mu, tau_y0, H)
+    euler = sum(float(np.sum(p[:, k] * g[k].reshape(-1))) for k in range(4))
+    assert abs(euler - J) < 1e-9 * abs(J)
+    for phase in (0, 1):
+        for k in range(4):
+            h = 1e-6 * J2_PARAMS[phase, k]
+            Jpm = []
+            for sgn in (1.0, -1.0):
+                q = J2_PARAMS.copy()
+                q[phase, k] += sgn * h
+                Jpm.append(float(np.sum(W * _j2_Pbar(shape, ph, q, Fbar).homogenized_P())))
+            fd = (Jpm[0] - Jpm[1]) / (2 * h)
+            adj = float(g[k][ph == phase].sum())
+            assert abs(adj - fd) < 1e-5 * max(abs(fd), 1e-3 * abs(J) / J2_PARAMS[phase, k]), \
+                (phase, k, adj, fd)
