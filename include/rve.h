@@ -259,7 +259,7 @@ int rve_get_history(rve_t h, double* dst, int dst_on_device);
  * The linear solve stops at ||r|| <= tol_cg ||b|| (float32 handles refine
  * float32 CG solutions against the float64 residual).  grad: [n] float64
  * (host or device).  cg_iters (may be NULL) receives the CG iterations.
- * RVE_ERR_UNSUPPORTED for the J2 model (path-dependent; not built). */
+ * J2: see rve_adjoint_grad_params. */
 int rve_adjoint_grad_mu(rve_t h, const double W[9], double tol_cg, double* grad, int grad_on_device,
                         int* cg_iters);
 
@@ -270,6 +270,27 @@ int rve_adjoint_grad_mu(rve_t h, const double W[9], double tol_cg, double* grad,
  * grad_K, grad_mu: [n] float64 each (host or device), either may be NULL. */
 int rve_adjoint_grad(rve_t h, const double W[9], double tol_cg, double* grad_K, double* grad_mu,
                      int grads_on_device, int* cg_iters);
+
+/* Gradient of J = W : P-bar with respect to every per-voxel material
+ * parameter, from one adjoint field: grads [nparam][n] float64 (host or
+ * device) in the order of rve_create's parameters -- SVK: K, mu (as
+ * rve_adjoint_grad); J2: K, mu, tau_y0, H.  Not in the paper.  J2 (Sec. 5)
+ * is path dependent: the derivative is that of the last committed increment
+ * with the history at its start held fixed -- the adjoint system uses the
+ * consistent tangent of that increment (symmetric), and at fixed F and
+ * history
+ *   dtau/dK = tr(eps) I,  ds/dmu = 2 e - 3 (dgamma + mu (2 q H + 3 tau_y)/(3 mu + H)^2) e/q,
+ *   ds/dtau_y0 = 3 mu/(3 mu + H) e/q,  ds/dH = 3 mu (eps_p + dgamma)/(3 mu + H) e/q
+ * in the principal basis of the trial elastic strain (e its deviator,
+ * q = sqrt(3/2 e:e), tau_y = tau_y0 + H eps_p; elastic voxels: 2 e for mu,
+ * 0 for tau_y0, H), dP = dtau F^-T.  Exact for a path of one increment from
+ * the virgin state; for longer paths the contribution of the last increment
+ * only (the adjoint through the history of earlier increments is not built).
+ * MIXED J2 handles solve the adjoint system in float32 without float64
+ * refinement (their tangent is stored in float32), relative accuracy about
+ * the CG tolerance floor. */
+int rve_adjoint_grad_params(rve_t h, const double W[9], double tol_cg, double* grads,
+                            int grads_on_device, int* cg_iters);
 
 /* Homogenised first Piola-Kirchhoff stress P-bar = <P> (voxel average),
  * row-major, host. */
@@ -344,6 +365,10 @@ const char* rve_status_string(int code);
  * unreadable or malformed files. */
 int rve_save(rve_t h, const char* path);
 int rve_load(rve_t* out, const char* path, const rve_options* opt);
+
+/* The handle's constitutive model (RVE_SVK, RVE_J2), or RVE_ERR_INVALID
+ * for a null handle. */
+int rve_model(rve_t h);
 
 /* Grid sizes of a handle. */
 int rve_grid(rve_t h, int dims[3]);

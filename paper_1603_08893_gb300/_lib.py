@@ -83,6 +83,8 @@ _SIGS = {
                                       C.POINTER(C.c_int)]),
     "rve_adjoint_grad": (C.c_int, [_H, _P, C.c_double, _P, _P, C.c_int,
                                    C.POINTER(C.c_int)]),
+    "rve_adjoint_grad_params": (C.c_int, [_H, _P, C.c_double, _P, C.c_int,
+                                          C.POINTER(C.c_int)]),
     "rve_homogenized_P": (C.c_int, [_H, _P]),
     "rve_set_F": (C.c_int, [_H, _P, C.c_int]),
     "rve_apply_operator": (C.c_int, [_H, _P, _P, C.c_int]),
@@ -94,6 +96,7 @@ _SIGS = {
     "rve_save": (C.c_int, [_H, C.c_char_p]),
     "rve_load": (C.c_int, [C.POINTER(_H), C.c_char_p, C.POINTER(rve_options)]),
     "rve_grid": (C.c_int, [_H, C.POINTER(C.c_int)]),
+    "rve_model": (C.c_int, [_H]),
     "rve_kernel_timing": (C.c_int, [_H, C.c_int, C.c_int]),
     "rve_kernel_time": (C.c_int, [_H, C.POINTER(C.c_double),
                                   C.POINTER(C.c_longlong)]),

@@ -133,6 +133,11 @@ inline int fs_split_n1(int n) {
   }
 }
 
+// a 3x3 tensor passed by value to a kernel (row-major)
+struct W9 {
+  double w[9];
+};
+
 template <typename R>
 struct TangentView {
   int mode;           // TAN_FULL81 / TAN_SYM45 / TAN_SVK / 0 (plain copy)
@@ -231,6 +236,9 @@ void launch_j2_constitutive(const double* F, size_t n, MatView<double> mat, cons
                             int sym45 = 0);
 void launch_j2_k4_full(const double* F, size_t v0, size_t count, size_t n, MatView<double> mat,
                        const double* hc, double* dst, cudaStream_t s);
+// out[4][n]: dJ/d(K, mu, tau_y0, H) per voxel, J = W : P-bar, history hs fixed
+void launch_j2_adjoint_grad(const double* F, size_t n, MatView<double> mat, const double* hs,
+                            const double* lam, const double W[9], double* out, cudaStream_t s);
 size_t vec_max_blocks();
 
 // mean9 post-processing modes

@@ -7,6 +7,8 @@
 // exact derivative dP/dF of this update (committed history frozen), with the
 // derivative of the matrix logarithm from divided differences of ln in the
 // eigenbasis of be.  Stored as K_ijkl = dP_ji / dF_kl (Eq. iter:varP).
+#include <algorithm>
+
 #include "kernels.h"
 
 #define J2_THREADS 128
@@ -271,6 +273,120 @@ __global__ void __launch_bounds__(J2_THREADS) k_j2(const double* __restrict__ F,
   if (flags && st) atomicOr(&st->err_flags, flags);
 }
 
+// Adjoint gradient of J = W : P-bar with respect to the per-voxel
+// parameters (K, mu, tau_y0, H) at fixed F and fixed history hs (the one at
+// the start of the increment): out[k][v] = (1/n) W : dP/dp_k - lambda : dP/dp_k.
+// At fixed F and history the eigenbasis of be is fixed; with e the
+// principal deviatoric log strain, q = sqrt(3/2 e.e), tau_y = tau_y0 + H eps_p
+// and dgamma = (2 mu q - tau_y) / (3 mu + H) on the plastic branch,
+// s = 2 mu e - 3 mu dgamma e / q and
+//   d tau_p/dK = tr(eps),  d s/dmu = 2 e - 3 (dgamma + mu (2 q H + 3 tau_y)/(3 mu + H)^2) e/q,
+//   d s/dtau_y0 = 3 mu/(3 mu + H) e/q,  d s/dH = 3 mu (eps_p + dgamma)/(3 mu + H) e/q
+// (elastic: 2 e for mu, 0 for tau_y0 and H); dP = d tau F^-T.
+__global__ void __launch_bounds__(J2_THREADS) k_j2_adjoint_grad(
+    const double* __restrict__ F, size_t n, MatView<double> mat, const double* __restrict__ hs,
+    const double* __restrict__ lam, W9 w, double* __restrict__ out) {
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  const double inv_n = 1.0 / (double)n;
+  for (size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+    double f[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) f[i][j] = F[(size_t)(3 * i + j) * n + v];
+    double C[3][3];
+    C[0][0] = hs[v];
+    C[1][1] = hs[n + v];
+    C[2][2] = hs[2 * n + v];
+    C[0][1] = C[1][0] = hs[3 * n + v];
+    C[0][2] = C[2][0] = hs[4 * n + v];
+    C[1][2] = C[2][1] = hs[5 * n + v];
+    const double ep = hs[6 * n + v];
+    const double mu = mat.get(v, 1), ty0 = mat.get(v, 2), H = mat.get(v, 3);
+    double FC[3][3], be[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) FC[i][j] = f[i][0] * C[0][j] + f[i][1] * C[1][j] + f[i][2] * C[2][j];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) be[i][j] = FC[i][0] * f[j][0] + FC[i][1] * f[j][1] + FC[i][2] * f[j][2];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = i + 1; j < 3; ++j) be[i][j] = be[j][i] = 0.5 * (be[i][j] + be[j][i]);
+    double Q[3][3];
+    jacobi3(be, Q);
+    double eps[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) eps[a] = 0.5 * log(be[a][a]);
+    const double tr = eps[0] + eps[1] + eps[2];
+    double e[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) e[a] = eps[a] - tr / 3.0;
+    const double q = sqrt(1.5 * (e[0] * e[0] + e[1] * e[1] + e[2] * e[2]));
+    const double teq = 2.0 * mu * q;
+    const double ty = ty0 + H * ep;
+    const double phi = teq - ty;
+    const bool plastic = phi > 0.0;
+    const double den = 3.0 * mu + H;
+    const double dg = plastic ? phi / den : 0.0;
+    // principal derivatives of tau for (K, mu, tau_y0, H)
+    double d[4][3];
+    const double iq = plastic ? 1.0 / q : 0.0;
+    const double cmu = plastic ? 3.0 * (dg + mu * (2.0 * q * H + 3.0 * ty) / (den * den)) : 0.0;
+    const double cty = plastic ? 3.0 * mu / den : 0.0;
+    const double cH = plastic ? 3.0 * mu * (ep + dg) / den : 0.0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      d[0][a] = tr;
+      d[1][a] = 2.0 * e[a] - cmu * e[a] * iq;
+      d[2][a] = cty * e[a] * iq;
+      d[3][a] = cH * e[a] * iq;
+    }
+    const double det = f[0][0] * (f[1][1] * f[2][2] - f[1][2] * f[2][1]) -
+                       f[0][1] * (f[1][0] * f[2][2] - f[1][2] * f[2][0]) +
+                       f[0][2] * (f[1][0] * f[2][1] - f[1][1] * f[2][0]);
+    const double id = 1.0 / det;
+    double Fi[3][3];
+    Fi[0][0] = (f[1][1] * f[2][2] - f[1][2] * f[2][1]) * id;
+    Fi[0][1] = (f[0][2] * f[2][1] - f[0][1] * f[2][2]) * id;
+    Fi[0][2] = (f[0][1] * f[1][2] - f[0][2] * f[1][1]) * id;
+    Fi[1][0] = (f[1][2] * f[2][0] - f[1][0] * f[2][2]) * id;
+    Fi[1][1] = (f[0][0] * f[2][2] - f[0][2] * f[2][0]) * id;
+    Fi[1][2] = (f[0][2] * f[1][0] - f[0][0] * f[1][2]) * id;
+    Fi[2][0] = (f[1][0] * f[2][1] - f[1][1] * f[2][0]) * id;
+    Fi[2][1] = (f[0][1] * f[2][0] - f[0][0] * f[2][1]) * id;
+    Fi[2][2] = (f[0][0] * f[1][1] - f[0][1] * f[1][0]) * id;
+    // c_ab = (1/n) W_ab - lambda_ab; g_k = sum_ab c_ab (d tau_k F^-T)_ab
+    double c[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) c[i][j] = inv_n * w.w[3 * i + j] - lam[(size_t)(3 * i + j) * n + v];
+    // sum_ab c_ab tau_ac Fi_bc = sum_ac tau_ac (c Fi)_ac with (c Fi)_ac = sum_b c_ab Fi_bc
+    double cF[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int k = 0; k < 3; ++k) cF[i][k] = c[i][0] * Fi[0][k] + c[i][1] * Fi[1][k] + c[i][2] * Fi[2][k];
+    // tau = Q diag(t) Q^T: sum_ac Q_a p t_p Q_c p cF_ac = sum_p t_p (Q^T cF Q)_pp
+    double m[3];
+#pragma unroll
+    for (int p = 0; p < 3; ++p) {
+      double acc = 0.0;
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) acc += Q[i][p] * cF[i][k] * Q[k][p];
+      m[p] = acc;
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) out[(size_t)k * n + v] = d[k][0] * m[0] + d[k][1] * m[1] + d[k][2] * m[2];
+  }
+}
+
 template <typename RO>
 void launch_j2_constitutive(const double* F, size_t n, MatView<double> mat, const double* hc,
                             double* ht, double* P, RO* K4, SolverState* st, cudaStream_t s,
@@ -288,6 +404,14 @@ void launch_j2_k4_full(const double* F, size_t v0, size_t count, size_t n, MatVi
   if (b < 1) b = 1;
   k_j2<double><<<(unsigned)b, J2_THREADS, 0, s>>>(F, n, v0, count, mat, hc, nullptr, nullptr,
                                                    nullptr, dst, nullptr, 0);
+}
+
+void launch_j2_adjoint_grad(const double* F, size_t n, MatView<double> mat, const double* hs,
+                           const double* lam, const double W[9], double* out, cudaStream_t s) {
+  W9 w;
+  for (int c = 0; c < 9; ++c) w.w[c] = W[c];
+  const size_t b = std::min<size_t>((n + J2_THREADS - 1) / J2_THREADS, 65535);
+  k_j2_adjoint_grad<<<(unsigned)std::max<size_t>(b, 1), J2_THREADS, 0, s>>>(F, n, mat, hs, lam, w, out);
 }
 
 template void launch_j2_constitutive<float>(const double*, size_t, MatView<double>, const double*,

@@ -310,9 +310,6 @@ __global__ void __launch_bounds__(VEC_THREADS) k_accumulate(size_t n9, double* _
 // dJ/dmu_k = (1/n) W : (dP/dmu)_k - lambda_k : (dP/dmu)_k with
 // dP/dmu = F . (2 dev E) at fixed bulk modulus (S = lambda tr(E) I + 2 mu E,
 // lambda = K - 2 mu / 3).
-struct W9 {
-  double w[9];
-};
 // dJ/dmu (g) and, when gK != null, dJ/dK per voxel from the adjoint field:
 // (W/n - lambda) : dP/dq with dP/dmu = F . (2 dev E), dP/dK = F . (tr(E) I).
 __global__ void __launch_bounds__(VEC_THREADS) k_adjoint_grad(const double* __restrict__ F,

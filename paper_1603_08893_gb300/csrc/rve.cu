@@ -208,8 +208,9 @@ struct rve_s {
   double Fbar_committed[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};  // F-bar of the last committed state
   double* adj_b = nullptr;  // adjoint right-hand side [9][n] (SVK)
   double* adj_l = nullptr;  // adjoint solution [9][n] (SVK)
-  double* hc = nullptr;  // J2 history, committed [7][n]
-  double* ht = nullptr;  // J2 history, trial [7][n]
+  double* hc = nullptr;     // J2 history, committed [7][n]
+  double* ht = nullptr;     // J2 history, trial [7][n]
+  double* hprev = nullptr;  // J2 history at the start of the last committed increment
   std::string err;
   long long launches = 0;
   // instrumentation
@@ -628,12 +629,12 @@ size_t layout(rve_t h, Arena& a) {
   if (h->model == RVE_J2) {
     h->hc = a.take<double>(7 * n);
     h->ht = a.take<double>(7 * n);
-    h->adj_b = h->adj_l = nullptr;
+    h->hprev = a.take<double>(7 * n);
   } else {
-    h->hc = h->ht = nullptr;
-    h->adj_b = a.take<double>(n9);
-    h->adj_l = a.take<double>(n9);
+    h->hc = h->ht = h->hprev = nullptr;
   }
+  h->adj_b = a.take<double>(n9);
+  h->adj_l = a.take<double>(n9);
   h->table64 = a.take<double>(256 * 4);
   h->table32 = a.take<float>(256 * 4);
   h->vox64 = nullptr;
@@ -1029,6 +1030,7 @@ int rve_create(rve_t* out, int nx, int ny, int nz, int model, int nphase, const 
       for (size_t v = 0; v < h->n; ++v) H0[c * h->n + v] = 1.0;
     ok &= ck(cudaMemcpyAsync(h->hc, H0.data(), H0.size() * 8, cudaMemcpyHostToDevice, h->s));
     ok &= ck(cudaMemcpyAsync(h->ht, H0.data(), H0.size() * 8, cudaMemcpyHostToDevice, h->s));
+    ok &= ck(cudaMemcpyAsync(h->hprev, H0.data(), H0.size() * 8, cudaMemcpyHostToDevice, h->s));
     ok &= ck(cudaStreamSynchronize(h->s));
   }
   if (h->tan == TAN_SVK && !h->mixed) h->Fop = h->F;  // FP64 recompute reads F itself
@@ -1077,6 +1079,7 @@ static std::vector<CkptBlock> ckpt_blocks(rve_t h) {
   if (h->Sop) b.push_back({"Sop", h->Sop, 6 * n * ro});
   if (h->hc) b.push_back({"hc", h->hc, 7 * n * 8});
   if (h->ht) b.push_back({"ht", h->ht, 7 * n * 8});
+  if (h->hprev) b.push_back({"hprev", h->hprev, 7 * n * 8});
   if (h->phase) {
     b.push_back({"phase", h->phase, n});
     b.push_back({"t64", h->table64, 256 * 4 * 8});
@@ -1231,6 +1234,8 @@ int rve_load(rve_t* out, const char* path, const rve_options* opt) {
   return RVE_OK;
 }
 
+int rve_model(rve_t h) { return h ? h->model : RVE_ERR_INVALID; }
+
 int rve_grid(rve_t h, int dims[3]) {
   if (!h || !dims) return RVE_ERR_INVALID;
   dims[0] = h->g.nx;
@@ -1282,7 +1287,12 @@ static int commit_state(rve_t h) {
                        h->st, h->s);
   h->launches += 1;
   if (h->model == RVE_J2) {
-    std::swap(h->hc, h->ht);
+    // the trial history becomes the committed one; the former committed
+    // one is kept as the start of this increment (for the adjoint)
+    double* start = h->hc;
+    h->hc = h->ht;
+    h->ht = h->hprev;
+    h->hprev = start;
     enqueue_constitutive(h);
   }
   return RVE_OK;
@@ -1773,6 +1783,30 @@ int rve_get_K4(rve_t h, double* dst, int on_device) {
 template <typename RC>
 static int adjoint_solve(rve_t h, double tol, int* total_iters) {
   const size_t n9 = 9 * h->n;
+  if (std::is_same<RC, float>::value && h->model == RVE_J2) {
+    // a mixed J2 handle keeps its tangent in float32 only: one float32 solve
+    // of the adjoint system (no float64 refinement), then the float64
+    // projection onto compatible fields
+    const GridGeom& g = h->g;
+    const Twiddles<float>& tw = h->twf;
+    cplx<float>* spec = as<cplx<float>>(h->spec_op);
+    launch_zfwd<float>(g, SRC_UNIFORM, tangent_view<float>(h), nullptr, nullptr, nullptr,
+                       h->st->adjW, h->st, nullptr, spec, tw, h->s);
+    launch_fft_y<float>(g, false, spec, nullptr, tw, h->s);
+    launch_fft_x_proj<float>(g, 1.0 / (double)h->n, spec, nullptr, tw, h->s);
+    launch_fft_y<float>(g, true, spec, nullptr, tw, h->s);
+    launch_zinv<float, float>(g, OUT_RESID, spec, nullptr, as<float>(h->r), as<float>(h->x),
+                              nullptr, h->st, h->partials, nullptr, tw, h->s);
+    h->launches += 5;
+    int its = 0;
+    const int rc = cg_solve<float>(h, &its);
+    if (rc) return fail(h, rc, std::string("adjoint solve: ") + rve_status_string(rc));
+    launch_convert<float, double>(as<float>(h->x), h->adj_l, n9, h->s);
+    enqueue_project_fp64(h, h->adj_l);
+    h->launches += 1;
+    *total_iters = its;
+    return RVE_OK;
+  }
   // b = G : (K : W/n) in float64
   enqueue_operator64(h, SRC_UNIFORM, nullptr, h->st->adjW, h->adj_b);
   CK(cudaMemsetAsync(h->adj_l, 0, n9 * sizeof(double), h->s));
@@ -1811,11 +1845,13 @@ int rve_adjoint_grad_mu(rve_t h, const double W[9], double tol_cg, double* grad,
   return rve_adjoint_grad(h, W, tol_cg, nullptr, grad, on_device, cg_iters);
 }
 
-int rve_adjoint_grad(rve_t h, const double W[9], double tol_cg, double* grad_K, double* grad_mu,
-                     int on_device, int* cg_iters) {
-  NvtxRange nv("rve adjoint_grad");
-  if (!h || !W || !(grad_K || grad_mu) || !(tol_cg > 0.0)) return RVE_ERR_INVALID;
-  if (h->model != RVE_SVK) return fail(h, RVE_ERR_UNSUPPORTED, "adjoint: SVK only");
+}  // extern "C"
+
+// Adjoint gradients of J = W : P-bar for every per-voxel parameter, into
+// h->tmp64 as [nparam][n] in the order of rve_create (K, mu[, tau_y0, H]).
+// J2: the tangent and the parameter derivatives are those of the last
+// committed increment, i.e. with the history at its start (h->hprev).
+static int adjoint_grads(rve_t h, const double W[9], double tol_cg, int* cg_iters) {
   int rc = sync_state(h);
   if (rc) return rc;
   SolverState* hs = h->hst;
@@ -1828,19 +1864,66 @@ int rve_adjoint_grad(rve_t h, const double W[9], double tol_cg, double* grad_K, 
   hs->done = 0;
   rc = push_state(h);
   if (rc) return rc;
+  MatView<double> m = mat_view<double>(h);
+  const int sym = h->tan == TAN_SYM45;
+  if (h->model == RVE_J2) {
+    // the consistent tangent of the increment: F with its starting history
+    if (h->mixed)
+      launch_j2_constitutive<float>(h->F, h->n, m, h->hprev, nullptr, nullptr, as<float>(h->K4),
+                                    h->st, h->s, sym);
+    else
+      launch_j2_constitutive<double>(h->F, h->n, m, h->hprev, nullptr, nullptr,
+                                     as<double>(h->K4), h->st, h->s, sym);
+    h->launches += 1;
+  }
   int its = 0;
   rc = h->mixed ? adjoint_solve<float>(h, tol_cg, &its) : adjoint_solve<double>(h, tol_cg, &its);
+  if (h->model == RVE_J2) {
+    // back to the tangent of the committed state
+    if (h->mixed)
+      launch_j2_constitutive<float>(h->F, h->n, m, h->hc, nullptr, nullptr, as<float>(h->K4),
+                                    h->st, h->s, sym);
+    else
+      launch_j2_constitutive<double>(h->F, h->n, m, h->hc, nullptr, nullptr, as<double>(h->K4),
+                                     h->st, h->s, sym);
+    h->launches += 1;
+  }
   if (rc) return rc;
   if (cg_iters) *cg_iters = its;
-  launch_adjoint_grad(h->F, h->adj_l, W, h->n, h->tmp64, h->tmp64 + h->n, h->s);
+  if (h->model == RVE_J2) {
+    launch_j2_adjoint_grad(h->F, h->n, m, h->hprev, h->adj_l, W, h->tmp64, h->s);
+  } else {
+    // [K][n] then [mu][n]
+    launch_adjoint_grad(h->F, h->adj_l, W, h->n, h->tmp64 + h->n, h->tmp64, h->s);
+  }
   h->launches += 1;
   CK(cudaGetLastError());
+  return RVE_OK;
+}
+
+extern "C" {
+
+int rve_adjoint_grad(rve_t h, const double W[9], double tol_cg, double* grad_K, double* grad_mu,
+                     int on_device, int* cg_iters) {
+  NvtxRange nv("rve adjoint_grad");
+  if (!h || !W || !(grad_K || grad_mu) || !(tol_cg > 0.0)) return RVE_ERR_INVALID;
+  int rc = adjoint_grads(h, W, tol_cg, cg_iters);
+  if (rc) return rc;
   if (grad_mu) {
-    rc = copy_out(h, grad_mu, h->tmp64, h->n * sizeof(double), on_device);
+    rc = copy_out(h, grad_mu, h->tmp64 + h->n, h->n * sizeof(double), on_device);
     if (rc) return rc;
   }
-  if (grad_K) return copy_out(h, grad_K, h->tmp64 + h->n, h->n * sizeof(double), on_device);
+  if (grad_K) return copy_out(h, grad_K, h->tmp64, h->n * sizeof(double), on_device);
   return RVE_OK;
+}
+
+int rve_adjoint_grad_params(rve_t h, const double W[9], double tol_cg, double* grads,
+                            int on_device, int* cg_iters) {
+  NvtxRange nv("rve adjoint_grad_params");
+  if (!h || !W || !grads || !(tol_cg > 0.0)) return RVE_ERR_INVALID;
+  const int rc = adjoint_grads(h, W, tol_cg, cg_iters);
+  if (rc) return rc;
+  return copy_out(h, grads, h->tmp64, (size_t)h->nparam * h->n * sizeof(double), on_device);
 }
 
 int rve_get_history(rve_t h, double* dst, int on_device) {
@@ -1873,6 +1956,8 @@ int rve_set_F(rve_t h, const double* F, int on_device) {
     std::memcpy(h->Fbar_committed, h->hst->Pbar, sizeof(h->Fbar_committed));
   }
   CK(cudaMemcpyAsync(h->Ft, h->F, 9 * h->n * 8, cudaMemcpyDeviceToDevice, h->s));
+  if (h->hprev)  // no increment since: the committed history is its own start
+    CK(cudaMemcpyAsync(h->hprev, h->hc, 7 * h->n * 8, cudaMemcpyDeviceToDevice, h->s));
   std::memset(h->hst, 0, sizeof(SolverState));
   rc = push_state(h);
   if (rc) return rc;
@@ -2199,10 +2284,7 @@ int batch_solve_t(rve_batch_t b, const double* Fbar, double tol_newton, double t
     rve_t h = b->rv[c];
     const size_t n9 = 9 * h->n;
     if (result[c] == RVE_OK) {
-      cudaMemcpyAsync(h->Ft, h->F, n9 * 8, cudaMemcpyDeviceToDevice, h->s);
-      std::memcpy(h->Fbar_committed, h->Fbar, sizeof(h->Fbar));
-      launch_mean9<double>(h->P, h->n, nullptr, h->partials, &h->st->counter[SLOT_MEAN],
-                           MEAN_PBAR, h->st, h->s);
+      commit_state(h);
     } else {
       cudaMemcpyAsync(h->F, h->Ft, n9 * 8, cudaMemcpyDeviceToDevice, h->s);
       enqueue_constitutive(h);

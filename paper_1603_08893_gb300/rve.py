@@ -242,6 +242,18 @@ def rve_adjoint_grad(h, W, n, tol_cg=1e-12):
     return gK, gm, its.value
 
 
+def rve_adjoint_grad_params(h, W, n, nparam, tol_cg=1e-12):
+    """dJ/d(parameters) per voxel, [nparam, n], for J = W : P-bar (SVK: K, mu;
+    J2: K, mu, tau_y0, H at the history of the last increment's start), and
+    the CG iterations."""
+    Wc = np.ascontiguousarray(W, dtype=np.float64).reshape(9)
+    its = C.c_int(0)
+    g = np.empty(nparam * n, dtype=np.float64)
+    _check(lib.rve_adjoint_grad_params(h, Wc.ctypes.data_as(C.c_void_p), float(tol_cg),
+                                       g.ctypes.data_as(C.c_void_p), 0, C.byref(its)), h)
+    return g.reshape(nparam, n), its.value
+
+
 def rve_homogenized_P(h):
     P = np.empty(9, dtype=np.float64)
     _check(lib.rve_homogenized_P(h, P.ctypes.data_as(C.c_void_p)), h)
@@ -396,6 +408,12 @@ class RVE:
         """(dJ/dK, dJ/dmu), each [*shape], for J = W : P-bar, and the CG iterations."""
         gK, gm, its = rve_adjoint_grad(self.h, W, self.n, tol_cg)
         return gK.reshape(self.shape), gm.reshape(self.shape), its
+
+    def adjoint_grad_params(self, W, tol_cg=1e-12):
+        """dJ/d(K, mu[, tau_y0, H]) per voxel, [nparam, *shape], and the CG iterations."""
+        nparam = 4 if lib.rve_model(self.h) == _MODELS["j2"] else 2
+        g, its = rve_adjoint_grad_params(self.h, W, self.n, nparam, tol_cg)
+        return g.reshape((nparam,) + self.shape), its
 
     def get_history(self):
         """J2: committed (Cp^-1 [6 symmetric components], eps_p) per voxel, [7, *shape]."""

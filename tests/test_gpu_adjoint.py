@@ -1,5 +1,6 @@
 """GPU adjoint gradient of the homogenised stress with respect to per-voxel
-shear moduli (SVK), through the C ABI and torch.autograd.
+shear moduli (SVK), through the C ABI and torch.autograd; J2 gradients with
+respect to K, mu, tau_y0, H at the history of the last increment's start.
 
 Checks: against the oracle's adjoint gradient (1e-9), against central finite
 differences of GPU solves at 64 random voxels of a 31^3 lognormal cell
@@ -144,3 +145,68 @@ def test_autograd_bulk_and_shear():
     r.close()
     assert np.abs(gmu.cpu().numpy() - gmu_ref).max() < 1e-10 * np.abs(gmu_ref).max()
     assert np.abs(gK.cpu().numpy() - gK_ref).max() < 1e-10 * np.abs(gK_ref).max()
+
+
+# ---------------------------------------------------------------------------
+# J2: gradient with respect to K, mu, tau_y0, H at the history of the last
+# increment's start (rve_adjoint_grad_params)
+# ---------------------------------------------------------------------------
+J2_PARAMS = np.array([[1 / 1.2, 1 / 2.6, 0.003, 0.01], [1 / 1.2, 1 / 2.6, 0.006, 0.01]])
+
+
+def _j2_cell():
+    rng = np.random.default_rng(13)
+    shape = (7, 5, 9)
+    return shape, (rng.uniform(size=shape) < 0.5).astype(np.uint8)
+
+
+def _j2_oracle_grad(prob_F, Cpi, ep, ph):
+    p = J2_PARAMS[ph.reshape(-1)]
+    return oadj.j2_grad_params(prob_F, Cpi, ep, p[:, 0], p[:, 1], p[:, 2], p[:, 3], WXY,
+                               1e-13, 1e-15)
+
+
+def test_j2_adjoint_matches_oracle_over_two_increments():
+    """Increment 1 from the virgin state (exact derivative), increment 2 with
+    the history committed by increment 1 held fixed."""
+    shape, ph = _j2_cell()
+    n = ph.size
+    prob = solver.J2Problem.from_phase(ph, J2_PARAMS)
+    r = RVE(shape, model="j2", phase=ph, phase_params=J2_PARAMS, precision="fp64",
+            cg_atol=1e-14)
+    for k, Fb in enumerate((synth.simple_shear(0.004), synth.simple_shear(0.008))):
+        Cpi0, ep0 = prob.mat.Cpi.copy(), prob.mat.ep.copy()
+        prob.increment(Fb, tol_newton=1e-11, tol_cg=1e-13, cg_atol=1e-14)
+        r.set_macro_F(Fb)
+        r.solve_increment(**TIGHT)
+        ref = _j2_oracle_grad(prob.F, Cpi0, ep0, ph)
+        got, _ = r.adjoint_grad_params(WXY, tol_cg=1e-13)
+        for q in range(4):
+            assert np.abs(got[q] - ref[q]).max() < 1e-8 * np.abs(ref[q]).max(), (k, q)
+        gK, gmu = r.adjoint_grad(WXY, tol_cg=1e-13)[:2]
+        assert np.array_equal(gK, got[0]) and np.array_equal(gmu, got[1])
+    assert prob.mat.ep.max() > 1e-4
+    # Euler's identity holds for the first increment only (virgin history)
+    r.close()
+
+
+def test_j2_adjoint_euler_identity_and_mixed():
+    shape, ph = _j2_cell()
+    Fb = synth.simple_shear(0.006)
+    p = J2_PARAMS[ph]
+    out = {}
+    for prec in ("fp64", "mixed"):
+        r = RVE(shape, model="j2", phase=ph, phase_params=J2_PARAMS, precision=prec,
+                cg_atol=1e-14)
+        r.set_macro_F(Fb)
+        r.solve_increment(**TIGHT)
+        g, _ = r.adjoint_grad_params(WXY, tol_cg=1e-12)
+        J = float(r.homogenized_P()[0, 1])
+        euler = float(sum(np.sum(p[..., k] * g[k]) for k in range(4)))
+        out[prec] = (g, J, euler)
+        r.close()
+    g64, J, euler = out["fp64"]
+    assert abs(euler - J) < 1e-9 * abs(J)
+    gmx = out["mixed"][0]
+    for q in range(4):
+        assert np.abs(gmx[q] - g64[q]).max() < 1e-4 * np.abs(g64[q]).max()

@@ -57,3 +57,32 @@ def test_batch_cell_matches_oracle():
     F = batch.get_F(2)
     assert np.linalg.norm(F - prob.F) / np.linalg.norm(prob.F) < 1e-10
     batch.close()
+
+
+def test_j2_batch_commits_history_like_individual_solves():
+    """J2 cells: the batch commits each cell's history as a single cell does
+    (two increments, the second starting from the first's plastic state)."""
+    params = np.array([[1 / 1.2, 1 / 2.6, 0.003, 0.01], [1 / 1.2, 1 / 2.6, 0.006, 0.01]])
+    cells = []
+    for n, seed in ((9, 1), (15, 2), (9, 3)):
+        ph, _ = synth.voronoi(n, 6, np.random.default_rng(seed))
+        cells.append(((n, n, n), ph))
+    b = RVEBatch([c[0] for c in cells], [c[1] for c in cells], [params] * len(cells),
+                 model="j2", precision="mixed")
+    singles = [RVE(c[0], model="j2", phase=c[1], phase_params=params, precision="mixed")
+               for c in cells]
+    for gamma in (0.004, 0.008):
+        Fb = synth.simple_shear(gamma)
+        st = b.solve(np.stack([Fb] * len(cells)))
+        assert all(s["status"] == 0 for s in st)
+        for i, r in enumerate(singles):
+            r.set_macro_F(Fb)
+            r.solve_increment()
+            assert np.array_equal(r.get_F(), b.get_F(i))
+    from paper_1603_08893_gb300 import rve as api
+    for i, r in enumerate(singles):
+        hb = api.rve_get_history(api.lib.rve_batch_cell(b.h, i), r.n)
+        assert np.array_equal(r.get_history().reshape(-1), hb)
+        assert r.get_history().reshape(7, -1)[6].max() > 0.0
+        r.close()
+    b.close()
