@@ -174,15 +174,21 @@ def test_j2_adjoint_matches_oracle_over_two_increments():
     prob = solver.J2Problem.from_phase(ph, J2_PARAMS)
     r = RVE(shape, model="j2", phase=ph, phase_params=J2_PARAMS, precision="fp64",
             cg_atol=1e-14)
-    for k, Fb in enumerate((synth.simple_shear(0.004), synth.simple_shear(0.008))):
+    # shear with some stretch (simple shear alone is isochoric and, with equal
+    # elastic phases, leaves dJ/dK at round-off level)
+    for k, Fb in enumerate((synth.simple_shear(0.004) + np.diag([0.002, 0, 0]),
+                            synth.simple_shear(0.008) + np.diag([0.004, 0, 0]))):
         Cpi0, ep0 = prob.mat.Cpi.copy(), prob.mat.ep.copy()
         prob.increment(Fb, tol_newton=1e-11, tol_cg=1e-13, cg_atol=1e-14)
         r.set_macro_F(Fb)
         r.solve_increment(**TIGHT)
         ref = _j2_oracle_grad(prob.F, Cpi0, ep0, ph)
         got, _ = r.adjoint_grad_params(WXY, tol_cg=1e-13)
+        # compared as parameter x derivative (the units of J)
+        th = np.moveaxis(J2_PARAMS[ph], -1, 0)
+        scale = np.abs(th * ref).max()
         for q in range(4):
-            assert np.abs(got[q] - ref[q]).max() < 1e-8 * np.abs(ref[q]).max(), (k, q)
+            assert np.abs(th[q] * (got[q] - ref[q])).max() < 1e-9 * scale, (k, q)
         gK, gmu = r.adjoint_grad(WXY, tol_cg=1e-13)[:2]
         assert np.array_equal(gK, got[0]) and np.array_equal(gmu, got[1])
     assert prob.mat.ep.max() > 1e-4
@@ -192,7 +198,7 @@ def test_j2_adjoint_matches_oracle_over_two_increments():
 
 def test_j2_adjoint_euler_identity_and_mixed():
     shape, ph = _j2_cell()
-    Fb = synth.simple_shear(0.006)
+    Fb = synth.simple_shear(0.006) + np.diag([0.003, 0, 0])
     p = J2_PARAMS[ph]
     out = {}
     for prec in ("fp64", "mixed"):
@@ -208,5 +214,7 @@ def test_j2_adjoint_euler_identity_and_mixed():
     g64, J, euler = out["fp64"]
     assert abs(euler - J) < 1e-9 * abs(J)
     gmx = out["mixed"][0]
+    th = np.moveaxis(p, -1, 0)
+    scale = np.abs(th * g64).max()
     for q in range(4):
-        assert np.abs(gmx[q] - g64[q]).max() < 1e-4 * np.abs(g64[q]).max()
+        assert np.abs(th[q] * (gmx[q] - g64[q])).max() < 1e-4 * scale

@@ -182,7 +182,9 @@ def _j2_Pbar(shape, ph, params, Fbar):
 
 def test_j2_adjoint_gradient_matches_phase_finite_differences_and_euler():
     shape, ph = _j2_cell()
-    Fbar = synth.simple_shear(0.006)
+    # shear with some stretch: simple shear alone is isochoric and, with the
+    # phases' equal elastic moduli, leaves dJ/dK at round-off level
+    Fbar = synth.simple_shear(0.006) + np.diag([0.003, 0.0, 0.0])
     W = np.zeros((3, 3))
     W[0, 1] = 1.0
     prob = _j2_Pbar(shape, ph, J2_PARAMS, Fbar)
