@@ -1,10 +1,13 @@
-"""torch.autograd wrapper: homogenised stress of an SVK cell as a
-differentiable function of its per-voxel shear and bulk moduli.
+"""torch.autograd wrappers: homogenised stress of an SVK cell as a
+differentiable function of its per-voxel shear and bulk moduli, and of a J2
+cell after one increment from the virgin state as a function of its
+per-voxel K, mu, tau_y0 and H.
 
 forward solves the cell (Newton-CG through the C ABI) for the macroscopic
 deformation; backward is one adjoint CG solve with the same operator
-followed by the per-voxel sensitivity kernel (rve_adjoint_grad), which
-gives both gradients from the same adjoint field.
+followed by the per-voxel sensitivity kernel (rve_adjoint_grad /
+rve_adjoint_grad_params), which gives every gradient from the same adjoint
+field.
 """
 from __future__ import annotations
 
@@ -56,3 +59,49 @@ def homogenized_stress(mu, K, Fbar, **kw):
     if kw:
         raise TypeError(f"unknown arguments {sorted(kw)}")
     return HomogenizedStress.apply(mu, K, Fbar, *args)
+
+
+class J2HomogenizedStress(torch.autograd.Function):
+    """P-bar(K, mu, tau_y0, H) of a J2 cell after ONE increment from the
+    virgin state to F-bar: the case where the library's derivative (taken at
+    the history at the increment's start) is the exact total derivative.
+    Each parameter is a tensor of the cell's shape (or a scalar)."""
+
+    @staticmethod
+    def forward(ctx, K, mu, ty0, H, Fbar, tol_newton=1e-5, tol_cg=1e-8, precision="fp64",
+                adjoint_tol=1e-10, cg_atol=0.0):
+        ref = next(t for t in (K, mu, ty0, H) if isinstance(t, torch.Tensor) and t.dim() == 3)
+        shape = tuple(ref.shape)
+        vals = []
+        for t in (K, mu, ty0, H):
+            a = t.detach().cpu().numpy() if isinstance(t, torch.Tensor) else np.asarray(t)
+            vals.append(np.broadcast_to(a.astype(np.float64), shape))
+        r = RVE(shape, model="j2", voxel_params=np.stack(vals), precision=precision,
+                cg_atol=cg_atol)
+        r.set_macro_F(np.asarray(Fbar, dtype=np.float64))
+        r.solve_increment(tol_newton, tol_cg)
+        ctx.rve = r
+        ctx.adjoint_tol = adjoint_tol
+        ctx.device = ref.device
+        ctx.is_tensor = [isinstance(t, torch.Tensor) for t in (K, mu, ty0, H)]
+        return torch.from_numpy(r.homogenized_P()).to(ref.device)
+
+    @staticmethod
+    def backward(ctx, grad_P):
+        W = grad_P.detach().cpu().numpy().astype(np.float64)
+        g, _ = ctx.rve.adjoint_grad_params(W, ctx.adjoint_tol)
+        ctx.rve.close()
+        out = [torch.from_numpy(np.ascontiguousarray(g[k])).to(ctx.device) if ctx.is_tensor[k]
+               else None for k in range(4)]
+        return tuple(out) + (None,) * 6
+
+
+def j2_homogenized_stress(K, mu, tau_y0, H, Fbar, **kw):
+    """Differentiable P-bar (3x3 float64) of a J2 cell with per-voxel
+    parameters after one increment from the virgin state to `Fbar`."""
+    args = [kw.pop(k, d) for k, d in (("tol_newton", 1e-5), ("tol_cg", 1e-8),
+                                       ("precision", "fp64"), ("adjoint_tol", 1e-10),
+                                       ("cg_atol", 0.0))]
+    if kw:
+        raise TypeError(f"unknown arguments {sorted(kw)}")
+    return J2HomogenizedStress.apply(K, mu, tau_y0, H, Fbar, *args)

@@ -218,3 +218,27 @@ def test_j2_adjoint_euler_identity_and_mixed():
     scale = np.abs(th * g64).max()
     for q in range(4):
         assert np.abs(th[q] * (gmx[q] - g64[q])).max() < 1e-4 * scale
+
+
+def test_j2_autograd_one_increment():
+    from paper_1603_08893_gb300.autograd import j2_homogenized_stress
+    shape, ph = _j2_cell()
+    p = J2_PARAMS[ph]
+    ts = [torch.tensor(np.ascontiguousarray(p[..., k]), dtype=torch.float64, requires_grad=True)
+          for k in range(4)]
+    Fb = synth.simple_shear(0.006) + np.diag([0.003, 0, 0])
+    Pbar = j2_homogenized_stress(*ts, Fb, tol_newton=1e-11, tol_cg=1e-13, cg_atol=1e-14,
+                                 adjoint_tol=1e-13)
+    J = Pbar[0, 1]
+    grads = torch.autograd.grad(J, ts)
+    r = RVE(shape, model="j2", phase=ph, phase_params=J2_PARAMS, precision="fp64",
+            cg_atol=1e-14)
+    r.set_macro_F(Fb)
+    r.solve_increment(**TIGHT)
+    ref, _ = r.adjoint_grad_params(WXY, tol_cg=1e-13)
+    r.close()
+    scale = max(float(np.abs(p[..., k] * ref[k]).max()) for k in range(4))
+    for k in range(4):
+        assert np.abs(p[..., k] * (grads[k].numpy() - ref[k])).max() < 1e-9 * scale
+    euler = float(sum((t.detach() * g).sum() for t, g in zip(ts, grads)))
+    assert abs(euler - float(J)) < 1e-9 * abs(float(J))
