@@ -290,7 +290,7 @@ def reference_arm(args):
 def _line(workload, metric, value, unit, **extra):
     d = {"workload": workload, "metric": metric, "value": value, "unit": unit,
          "n_gpus": 1, "data": "synthetic"}
-    d.update(extra)
+    d.update(extra)  # may override n_gpus
     print(json.dumps(d), flush=True)
 
 
@@ -359,28 +359,41 @@ def bench_j2_315(args, torch, RVE):
 
 def bench_batch256(args, torch):
     """256 SVK cells of uneven size, one increment each, CUDA graph, autotuned
-    kernels, mixed path with per-cell increment cutting (config 4)."""
+    kernels, mixed path with per-cell increment cutting (config 4).  Under
+    torchrun the cells are sharded over the ranks (largest first to the least
+    loaded rank, no data-path collective); value = all ranks' units / the
+    slowest rank's time (strong scaling: the batch is fixed)."""
     from paper_1603_08893_gb300 import RVEBatch
-    cells = synth.config_batch()
+    from paper_1603_08893_gb300.shard import partition_cells
+    rank, world, dist = dist_setup(args.gpus)
+    all_cells = synth.config_batch()
+    mine = partition_cells([c["shape"] for c in all_cells], world)[rank]
+    cells = [all_cells[i] for i in mine]
     shapes = [c["shape"] for c in cells]
     t0 = time.perf_counter()
     b = RVEBatch(shapes, [c["phase"] for c in cells], [c["phase_params"] for c in cells],
                  precision="mixed", autotune=True)
     setup_s = time.perf_counter() - t0
     F = np.stack([c["Fbar"] for c in cells])
-    e0, e1, s = _events(torch)
     torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
     t0 = time.perf_counter()
     stats = b.solve(F, 1e-5, 1e-8, check=False, max_cuts=4)
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
     units = sum(int(np.prod(sh)) * st["cg_iters_total"] for sh, st in zip(shapes, stats))
     failed = sum(1 for st in stats if st["status"] != 0)
-    _line("svk_batch256_uneven_mixed", METRIC, units / wall, UNIT, dtype="f32/f64",
-          cells=len(cells), voxels=int(sum(int(np.prod(sh)) for sh in shapes)),
-          failed_cells=failed, solve_s=wall, setup_and_autotune_s=setup_s,
-          cg_iters=int(sum(st["cg_iters_total"] for st in stats)),
-          timing="host wall clock around the batch solve (its calls return when idle)")
+    wall_max, units_all = reduce_max_sum(dist, wall, float(units))
+    _, failed_all = reduce_max_sum(dist, 0.0, float(failed))
+    if rank == 0:
+        _line("svk_batch256_uneven_mixed", METRIC, units_all / wall_max, UNIT, dtype="f32/f64",
+              n_gpus=world, scaling="strong", cells=len(all_cells),
+              voxels=int(sum(int(np.prod(c["shape"])) for c in all_cells)),
+              failed_cells=int(failed_all), solve_s=wall_max, setup_and_autotune_s=setup_s,
+              cg_iters_rank0=int(sum(st["cg_iters_total"] for st in stats)),
+              timing="host wall clock around the batch solve (its calls return when "
+                     "idle), max over ranks")
     b.close()
 
 
