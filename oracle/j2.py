@@ -13,7 +13,15 @@ algorithmic tangent to Simo (1992) and Geers (2004); the readings used here
   I and 0;
 * trial: be = F Cp^-1 F^T, eps_tr = (1/2) ln be (principal logarithm),
   tau_tr = K tr(eps_tr) I + 2 mu dev(eps_tr);
-* tau_eq = sqrt(3/2 dev(tau):dev(tau)); plastic iff phi_tr > 0 (strictly);
+* tau_eq = sqrt(3/2 dev(tau):dev(tau)); the plastic branch is taken when
+  phi_tr > -1e-10 tau_y, i.e. also ON the yield surface, where dgamma =
+  max(phi_tr, 0) / (3 mu + H) = 0 leaves the stress elastic and the tangent
+  is the elasto-plastic one.  A state that yielded in the last increment
+  starts the next one exactly on the surface (phi = 0 up to round-off), and
+  Algorithm 1 evaluates the predictor tangent there; Sec. 5.3 says the
+  discrete switch affects the convergence only around the yield point and
+  Sec. 5.5 reports two Newton iterations per increment in the plastic
+  regime, which the elastic tangent on the surface would not give;
 * radial return in logarithmic strain: dgamma = phi_tr / (3 mu + H),
   dev(tau) = beta dev(tau_tr), beta = 1 - 3 mu dgamma / tau_eq_tr,
   eps_p += dgamma, elastic strain eps_e = tr(eps_tr)/3 I + beta dev(eps_tr),
@@ -72,8 +80,8 @@ def return_map(F, Cpi, ep, K, mu, ty0, H):
     s_tr = 2.0 * mu[:, None] * dev                        # principal deviatoric trial stress
     teq = np.sqrt(1.5 * (s_tr * s_tr).sum(-1))
     phi = teq - (ty0 + H * ep)
-    plastic = phi > 0.0
-    dg = np.where(plastic, phi / (3.0 * mu + H), 0.0)
+    plastic = phi > -1e-10 * (ty0 + H * ep)
+    dg = np.where(plastic, np.maximum(phi, 0.0) / (3.0 * mu + H), 0.0)
     with np.errstate(invalid="ignore", divide="ignore"):
         beta = np.where(plastic, 1.0 - 3.0 * mu * dg / np.where(teq > 0, teq, 1.0), 1.0)
     tau_p = K[:, None] * tr[:, None] + beta[:, None] * s_tr   # principal Kirchhoff stress
