@@ -2,6 +2,8 @@
 // be = F Cp^-1 F^T, eps = ln(be)/2 (principal), Kirchhoff stress
 // tau = K tr(eps) I + 2 mu dev(eps) (Eq. elas:C acting on the logarithmic
 // strain), von Mises yield phi = tau_eq - (tau_y0 + H eps_p) (Eq. simo:flow),
+// plastic branch for phi > -1e-10 tau_y (on the yield surface too, with
+// dgamma = max(phi, 0)/(3 mu + H) = 0 there: elasto-plastic tangent),
 // radial return in principal logarithmic strains, P = tau F^-T (pull-back),
 // trial history Cp^-1 = F^-1 be F^-T, eps_p += dgamma.  The tangent is the
 // exact derivative dP/dF of this update (committed history frozen), with the
@@ -12,6 +14,10 @@
 #include "kernels.h"
 
 #define J2_THREADS 128
+
+// relative margin below the yield stress within which a state counts as on
+// the yield surface (round-off of the return map's consistency phi = 0)
+constexpr double kYieldSurfaceTol = 1e-10;
 
 namespace {
 
@@ -132,8 +138,10 @@ __global__ void __launch_bounds__(J2_THREADS) k_j2(const double* __restrict__ F,
     }
     const double teq = sqrt(1.5 * (s[0] * s[0] + s[1] * s[1] + s[2] * s[2]));
     const double phi = teq - (ty0 + H * ep);
-    const bool plastic = phi > 0.0;
-    const double dg = plastic ? phi / (3.0 * mu + H) : 0.0;
+    // plastic branch also on the yield surface (a state that yielded in the
+    // last increment): dgamma = 0 there, elasto-plastic tangent
+    const bool plastic = phi > -kYieldSurfaceTol * (ty0 + H * ep);
+    const double dg = plastic ? fmax(phi, 0.0) / (3.0 * mu + H) : 0.0;
     const double beta = plastic ? 1.0 - 3.0 * mu * dg / teq : 1.0;
     double taup[3];
 #pragma unroll
@@ -329,9 +337,9 @@ __global__ void __launch_bounds__(J2_THREADS) k_j2_adjoint_grad(
     const double teq = 2.0 * mu * q;
     const double ty = ty0 + H * ep;
     const double phi = teq - ty;
-    const bool plastic = phi > 0.0;
+    const bool plastic = phi > -kYieldSurfaceTol * ty;
     const double den = 3.0 * mu + H;
-    const double dg = plastic ? phi / den : 0.0;
+    const double dg = plastic ? fmax(phi, 0.0) / den : 0.0;
     // principal derivatives of tau for (K, mu, tau_y0, H)
     double d[4][3];
     const double iq = plastic ? 1.0 / q : 0.0;

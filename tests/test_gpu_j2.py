@@ -5,12 +5,10 @@ converged float64 schedules 1e-9 (relative 2-norm of F and P); the mixed
 path's P-bar 1e-8 of the float64 path.
 
 Schedules are solved to tight tolerances (eta_NW = 1e-10, eta_CG = 1e-12):
-voxels that yielded in the previous increment start the next one exactly on
-the yield surface, so the elastic/plastic choice of the predictor tangent
-(phi > 0, Sec. 5.3) is decided by round-off and the two implementations
-take different Newton paths to the same equilibrium; only tightly converged
-states are comparable (at eta_NW = 1e-5 they differ by ~1e-10 relative, and
-the history carries that forward).
+the two implementations may take different Newton paths to the same
+equilibrium (voxels near the yield surface switch branches on round-off), so
+only tightly converged states are comparable (at eta_NW = 1e-5 they differ
+by ~1e-10 relative, and the history carries that forward).
 """
 import numpy as np
 import pytest
