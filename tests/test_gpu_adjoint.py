@@ -243,3 +243,13 @@ def test_j2_autograd_one_increment():
     euler = float(sum((t.detach() * g).sum() for t, g in zip(ts, grads)))
     Jv = float(J.detach())
     assert abs(euler - Jv) < 1e-9 * abs(Jv)
+
+
+def test_svk_adjoint_grad_params_equals_adjoint_grad():
+    mu, K, _ = _cell(9)
+    r = _solve(mu, K, synth.simple_shear(0.05))
+    g, _ = r.adjoint_grad_params(WXY, tol_cg=1e-12)
+    gK, gmu, _ = r.adjoint_grad(WXY, tol_cg=1e-12)
+    assert g.shape == (2,) + mu.shape
+    assert np.array_equal(g[0], gK) and np.array_equal(g[1], gmu)
+    r.close()

@@ -175,3 +175,36 @@ def test_singular_stress_control_fails_and_rolls_back():
     assert np.array_equal(r.get_F(), eye)
     assert np.array_equal(r.macro_F(), np.eye(3))
     r.close()
+
+
+def test_invalid_mixed_control_arguments():
+    shape = (5, 5, 5)
+    r = RVE(shape, phase=np.zeros(shape, np.uint8), phase_params=[[0.833, 0.386]])
+    Fb = np.eye(3)
+    st = r.solve_mixed(Fb, np.zeros(9), MASK, tol_stress=0.0, check=False)
+    assert st["status"] == -1
+    P = np.zeros(9)
+    P[4] = np.nan                      # a prescribed stress component
+    st = r.solve_mixed(Fb, P, MASK, check=False)
+    assert st["status"] == -1
+    F = np.eye(3)
+    F[1, 1] = np.nan                   # a free component: ignored
+    st = r.solve_mixed(F, np.zeros(9), MASK, tol_stress=1e-10)
+    assert st["status"] == 0 and np.isfinite(r.macro_F()).all()
+    r.close()
+
+
+def test_mixed_control_with_preconditioned_cg(svk_oracle):
+    _, params, Fb, Pt, _, _, _ = svk_oracle
+    shape = (15, 11, 13)   # x length with a four-step kernel (preconditioned x pass)
+    rng = np.random.default_rng(11)
+    ph = (rng.uniform(size=shape) < 0.35).astype(np.uint8)
+    prob = solver.SVKProblem.from_phase(ph, params)
+    Fs, _, _ = mixed.solve_mixed(prob, Fb, Pt, MASK, tol_stress=1e-12, cg_atol=1e-13, **TIGHT)
+    r = RVE(shape, phase=ph, phase_params=params, precision="mixed", precond="reference",
+            cg_atol=1e-13)
+    r.solve_mixed(Fb, Pt, MASK, tol_stress=1e-12, **TIGHT)
+    assert np.abs(r.macro_F() - Fs).max() < 1e-8
+    assert maxrel(r.homogenized_P(), prob.homogenized_P()) < 1e-8
+    assert rel(r.get_F(), prob.F) < 1e-7
+    r.close()
