@@ -151,3 +151,24 @@ def test_objectivity_and_tangent_symmetry():
     K4T = np.einsum("nijkl->nlkji", K4)
     # the return map derives from an incremental potential: major symmetry
     assert np.abs(K4 - K4T).max() < 1e-10 * np.abs(K4).max()
+
+
+def test_two_newton_iterations_per_increment_in_the_plastic_regime():
+    """Sec. 5.5: about two Newton iterations per increment once the cell
+    deforms plastically (more only around the yield point): the predictor
+    tangent at a state on the yield surface is the elasto-plastic one.
+    Pure shear diag(l, 1/l, 1) in steps of 0.2/250 on a two-phase Voronoi
+    cell with the contrast chi = 2 of the example."""
+    import synth
+    from oracle import solver
+    ph, _ = synth.voronoi(9, 8, np.random.default_rng(2))
+    K, mu = 1 / 1.2, 1 / 2.6
+    params = np.array([[K, mu, 0.003, 0.01], [K, mu, 0.006, 0.02]])
+    prob = solver.J2Problem.from_phase(ph, params)
+    counts = []
+    for k in range(50):
+        lam = 1.0 + 0.2 * (k + 1) / 250
+        counts.append(prob.increment(np.diag([lam, 1 / lam, 1.0]), 1e-5, 1e-8).newton_iters)
+    assert prob.mat.ep.max() > 0.01 and (prob.mat.ep > 0).mean() > 0.5
+    assert max(counts[:15]) >= 3                 # around the yield point
+    assert np.mean(counts[-10:]) <= 2.3          # plastic regime
