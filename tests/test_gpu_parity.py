@@ -104,7 +104,8 @@ def test_operator_fp64_matches_oracle(shape, tangent):
 
 @pytest.mark.parametrize("shape", [(9, 11, 13), (31, 31, 31), (63, 63, 63), (27, 3, 125),
                                    (81, 75, 7), (7, 5, 225), (15, 21, 125), (45, 63, 27),
-                                   (16, 20, 24), (15, 16, 17), (125, 16, 32)])
+                                   (16, 20, 24), (15, 16, 17), (125, 16, 32),
+                                   (243, 7, 5), (5, 243, 3), (315, 5, 3), (3, 315, 5)])
 @pytest.mark.parametrize("tangent", ["recompute", "full81", "sym45"])
 def test_operator_mixed_matches_oracle(shape, tangent):
     r, F, K, mu, rng = _random_problem(shape, 4, "mixed", tangent)
@@ -171,7 +172,8 @@ def test_cube31_mixed_schedule_matches_tight_oracle():
     r.close()
 
 
-@pytest.mark.parametrize("shape", [(15, 21, 125), (27, 33, 45), (16, 18, 20)])
+@pytest.mark.parametrize("shape", [(15, 21, 125), (27, 33, 45), (16, 18, 20), (7, 5, 243),
+                                   (5, 3, 315), (243, 5, 3), (3, 315, 5)])
 def test_mixed_solve_matches_tight_oracle(shape):
     """Converged mixed solve on axis lengths served by the four-step kernels
     (the fused float CG iteration on every pass) against the tightly
