@@ -148,3 +148,110 @@ def j2_grad_params(F, Cpi, ep, K, mu, ty0, H, W, tol_cg=1e-12, cg_atol=0.0):
     dP = j2_dP_dparams(Fv, Cpi, ep, K, mu, ty0, H)
     g = np.einsum("ab,knab->kn", W, dP) / n - np.einsum("nab,knab->kn", lamv, dP)
     return g.reshape((4,) + tuple(grid))
+
+
+# ---------------------------------------------------------------------------
+# J2 through the history of a path of increments (reverse sweep).  With
+# h_m = H(F_m, h_{m-1}) the history after increment m, F_m in equilibrium
+# G:P(F_m, h_{m-1}) = 0 at <F_m> = F-bar_m, and J = W : P-bar after the last
+# increment M, a backward sweep over m = M..1 carries a_m = dJ/dh_m
+# (a_M = 0):
+#   g_m      = (1/n) K_M W [m = M] + (dH/dF)^T a_m          (dJ/dF_m),
+#   lambda_m : G K_m G lambda_m = G g_m                     (K_m symmetric),
+#   c_m      = (1/n) W [m = M] - lambda_m,
+#   dJ/dp   += c_m : dP/dp + (dH/dp)^T a_m,
+#   a_{m-1}  = c_m : dP/dh + (dH/dh)^T a_m,
+# all local derivatives at (F_m, h_{m-1}).  Here the history derivatives of
+# the return map are central differences per voxel (a reference for a
+# kernel of the derivative formulas); the parameter derivative of P is the
+# closed form above.
+# ---------------------------------------------------------------------------
+def _hist_pack(Cpi, ep):
+    return np.stack([Cpi[:, 0, 0], Cpi[:, 1, 1], Cpi[:, 2, 2], Cpi[:, 0, 1], Cpi[:, 0, 2],
+                     Cpi[:, 1, 2], ep], axis=1)
+
+
+def _hist_unpack(h):
+    C = np.empty((h.shape[0], 3, 3))
+    for k, (i, j) in enumerate(((0, 0), (1, 1), (2, 2), (0, 1), (0, 2), (1, 2))):
+        C[:, i, j] = h[:, k]
+        C[:, j, i] = h[:, k]
+    return C, h[:, 6].copy()
+
+
+def j2_local_jacobians(F, Cpi, ep, K, mu, ty0, H, step=1e-7):
+    """Central differences of the return map per voxel at (F, history) --
+    step 1e-7: the truncation error of the logarithm / exponential of nearly
+    equal eigenvalues (small strains) is still visible at 1e-6:
+    dP/dh [n,9,7], dH/dF [n,7,9], dH/dh [n,7,7], dH/dp [n,7,4], with
+    h = (Cp^-1_00, _11, _22, _01, _02, _12, eps_p) and p = (K, mu, tau_y0, H)."""
+    n = F.shape[0]
+    h0 = _hist_pack(Cpi, ep)
+    prm = [K, mu, ty0, H]
+
+    def run(Fx, hx, px):
+        C, e = _hist_unpack(hx)
+        st = j2.return_map(Fx, C, e, *px)
+        return st["P"].reshape(n, 9), _hist_pack(st["Cpi_new"], st["ep_new"])
+
+    dPdh = np.zeros((n, 9, 7))
+    dHdh = np.zeros((n, 7, 7))
+    for k in range(7):
+        d = np.zeros_like(h0)
+        d[:, k] = step
+        Pp, Hp = run(F, h0 + d, prm)
+        Pm, Hm = run(F, h0 - d, prm)
+        dPdh[:, :, k] = (Pp - Pm) / (2 * step)
+        dHdh[:, :, k] = (Hp - Hm) / (2 * step)
+    dHdF = np.zeros((n, 7, 9))
+    for a in range(9):
+        d = np.zeros_like(F)
+        d[:, a // 3, a % 3] = step
+        _, Hp = run(F + d, h0, prm)
+        _, Hm = run(F - d, h0, prm)
+        dHdF[:, :, a] = (Hp - Hm) / (2 * step)
+    dHdp = np.zeros((n, 7, 4))
+    for t in range(4):
+        s = step * np.abs(prm[t])
+        pp = [q.copy() for q in prm]
+        pm = [q.copy() for q in prm]
+        pp[t] = prm[t] + s
+        pm[t] = prm[t] - s
+        _, Hp = run(F, h0, pp)
+        _, Hm = run(F, h0, pm)
+        dHdp[:, :, t] = (Hp - Hm) / (2 * s)[:, None]
+    return dPdh, dHdF, dHdh, dHdp
+
+
+def j2_path_grad_params(states, K, mu, ty0, H, W, tol_cg=1e-12, cg_atol=0.0):
+    """dJ/d(K, mu, tau_y0, H) per voxel, [4, *grid], for J = W : P-bar after
+    a path of increments.  ``states``: per increment, in order, (F_m
+    [3,3,*grid] converged, Cpi_{m-1} [n,3,3], ep_{m-1} [n]) -- the field
+    and the history at the increment's start."""
+    W = np.asarray(W, dtype=np.float64)
+    grid = states[0][0].shape[-3:]
+    n = int(np.prod(grid))
+    prm = (K, mu, ty0, H)
+    a = np.zeros((n, 7))
+    g = np.zeros((4, n))
+    last = len(states) - 1
+    for m in range(last, -1, -1):
+        F, Cpi, ep = states[m]
+        Fv = np.moveaxis(F.reshape(3, 3, -1), -1, 0)
+        st = j2.return_map(Fv, Cpi, ep, *prm)
+        K4v = j2.tangent(Fv, Cpi, K, mu, H, st)
+        K4 = np.moveaxis(K4v, 0, -1).reshape((3, 3, 3, 3) + tuple(grid))
+        dPdh, dHdF, dHdh, dHdp = j2_local_jacobians(Fv, Cpi, ep, *prm)
+        gF = np.einsum("nka,nk->na", dHdF, a)
+        gfield = np.moveaxis(gF, 0, -1).reshape((3, 3) + tuple(grid))
+        if m == last:
+            gfield = gfield + svk.tangent_apply(K4, t.uniform(W, grid)) / n
+        op = solver.tangent_operator(K4)
+        lam, _, _ = solver.cg(op, fourier.G(gfield), tol_cg, atol=cg_atol)
+        c = -np.moveaxis(lam.reshape(3, 3, -1), -1, 0).reshape(n, 9)
+        if m == last:
+            c = c + W.reshape(9) / n
+        dPdp = j2_dP_dparams(Fv, Cpi, ep, *prm).reshape(4, n, 9)
+        g += np.einsum("na,tna->tn", c, dPdp) + np.einsum("nk,nkt->tn", a, dHdp)
+        a = np.einsum("na,nak->nk", c, dPdh) + np.einsum("nk,nkj->nj", a, dHdh)
+    return g.reshape((4,) + tuple(grid))

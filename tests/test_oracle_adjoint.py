@@ -209,3 +209,54 @@ def test_j2_adjoint_gradient_matches_phase_finite_differences_and_euler():
             adj = float(g[k][ph == phase].sum())
             assert abs(adj - fd) < 1e-5 * max(abs(fd), 1e-3 * abs(J) / J2_PARAMS[phase, k]), \
                 (phase, k, adj, fd)
+
+
+def _j2_path(shape, ph, params, ramp):
+    prob = solver.J2Problem.from_phase(ph, params)
+    states = []
+    for Fb in ramp:
+        Cpi0, ep0 = prob.mat.Cpi.copy(), prob.mat.ep.copy()
+        prob.increment(Fb, **TIGHT)
+        states.append((prob.F.copy(), Cpi0, ep0))
+    return prob, states
+
+
+def test_j2_path_adjoint_matches_finite_differences_over_the_path():
+    shape, ph = _j2_cell()
+    # loading, reversal and reloading: the history of earlier increments
+    # shapes the last one (the reverse sweep through dH/dh is exercised)
+    ramp = [synth.simple_shear(g) + np.diag([g / 2, 0.0, 0.0]) for g in (0.004, 0.008, -0.002, 0.006)]
+    W = np.zeros((3, 3))
+    W[0, 1] = 1.0
+    prob, states = _j2_path(shape, ph, J2_PARAMS, ramp)
+    n = ph.size
+    p = J2_PARAMS[ph.reshape(-1)]
+    assert prob.mat.ep.max() > 1e-3
+    g = adjoint.j2_path_grad_params(states, p[:, 0], p[:, 1], p[:, 2], p[:, 3], W, 1e-13, 1e-15)
+    # one increment: the fixed-history gradient
+    g1 = adjoint.j2_path_grad_params(states[:1], p[:, 0], p[:, 1], p[:, 2], p[:, 3], W,
+                                     1e-13, 1e-15)
+    F1, C0, e0 = states[0]
+    ref1 = adjoint.j2_grad_params(F1, C0, e0, p[:, 0], p[:, 1], p[:, 2], p[:, 3], W, 1e-13, 1e-15)
+    assert np.abs(g1 - ref1).max() < 1e-8 * np.abs(ref1).max()
+    J = float(np.sum(W * prob.homogenized_P()))
+    for phase in (0, 1):
+        for k in range(4):
+            h = 1e-6 * J2_PARAMS[phase, k]
+            Jpm = []
+            for sgn in (1.0, -1.0):
+                q = J2_PARAMS.copy()
+                q[phase, k] += sgn * h
+                Jpm.append(float(np.sum(W * _j2_path(shape, ph, q, ramp)[0].homogenized_P())))
+            fd = (Jpm[0] - Jpm[1]) / (2 * h)
+            adj = float(g[k][ph == phase].sum())
+            # floor: the finite difference of J (converged to ~1e-11) over a
+            # 1e-6 step resolves p dJ/dp to ~1e-7 |J|
+            assert abs(adj - fd) < 1e-5 * max(abs(fd), 1e-2 * abs(J) / J2_PARAMS[phase, k]), \
+                (phase, k, adj, fd)
+    # the history matters: the last-increment derivative alone misses it
+    F3, C2, e2 = states[-1]
+    last = adjoint.j2_grad_params(F3, C2, e2, p[:, 0], p[:, 1], p[:, 2], p[:, 3], W, 1e-13,
+                                  1e-15)
+    assert abs(float(last[2][ph == 0].sum()) - float(g[2][ph == 0].sum())) > \
+        1e-3 * abs(float(g[2][ph == 0].sum()))
