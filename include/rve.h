@@ -292,6 +292,31 @@ int rve_adjoint_grad(rve_t h, const double W[9], double tol_cg, double* grad_K, 
 int rve_adjoint_grad_params(rve_t h, const double W[9], double tol_cg, double* grads,
                             int grads_on_device, int* cg_iters);
 
+/* Path tape of a J2 handle (not in the paper): enable != 0 starts recording,
+ * at every committed increment, its converged F and the history at its
+ * start (16 float64 per voxel per increment, device memory allocated per
+ * increment); 0 stops and frees it.  Any call clears the previous tape, as
+ * does rve_set_F.  RVE_ERR_UNSUPPORTED for SVK (path independent).
+ * rve_tape_length returns the increments recorded. */
+int rve_tape(rve_t h, int enable);
+int rve_tape_length(rve_t h);
+
+/* Gradient of J = W : P-bar after the taped path with respect to the
+ * per-voxel J2 parameters K, mu, tau_y0, H, through the history of every
+ * taped increment (grads [4][n], host or device): a reverse sweep over the
+ * increments m = M..1 with a_m = dJ/dh_m (a_M = 0) --
+ *   G K_m G lambda_m = G ((1/n) K_M W [m = M] + (dH/dF)^T a_m),
+ *   c_m = (1/n) W [m = M] - lambda_m,
+ *   dJ/dp += c_m : dP/dp + (dH/dp)^T a_m,   a_{m-1} = c_m : dP/dh + (dH/dh)^T a_m,
+ * K_m, P and the new history H at (F_m, h_{m-1}); the return map's
+ * derivatives by central differences per voxel (step 1e-7).  The taped path
+ * must start at the state the parameters act from (the virgin state, or
+ * the state of rve_set_F, which clears the tape) and end at the current
+ * state.  Float64 J2 handles only (RVE_ERR_UNSUPPORTED otherwise);
+ * RVE_ERR_INVALID for an empty tape. */
+int rve_adjoint_grad_path(rve_t h, const double W[9], double tol_cg, double* grads,
+                          int grads_on_device, int* cg_iters);
+
 /* Homogenised first Piola-Kirchhoff stress P-bar = <P> (voxel average),
  * row-major, host. */
 int rve_homogenized_P(rve_t h, double Pbar[9]);

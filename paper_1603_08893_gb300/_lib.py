@@ -85,6 +85,9 @@ _SIGS = {
                                    C.POINTER(C.c_int)]),
     "rve_adjoint_grad_params": (C.c_int, [_H, _P, C.c_double, _P, C.c_int,
                                           C.POINTER(C.c_int)]),
+    "rve_tape": (C.c_int, [_H, C.c_int]),
+    "rve_tape_length": (C.c_int, [_H]),
+    "rve_adjoint_grad_path": (C.c_int, [_H, _P, C.c_double, _P, C.c_int, C.POINTER(C.c_int)]),
     "rve_homogenized_P": (C.c_int, [_H, _P]),
     "rve_set_F": (C.c_int, [_H, _P, C.c_int]),
     "rve_apply_operator": (C.c_int, [_H, _P, _P, C.c_int]),

@@ -236,6 +236,14 @@ void launch_j2_constitutive(const double* F, size_t n, MatView<double> mat, cons
                             int sym45 = 0);
 void launch_j2_k4_full(const double* F, size_t v0, size_t count, size_t n, MatView<double> mat,
                        const double* hc, double* dst, cudaStream_t s);
+// reverse sweep of the J2 adjoint through the history of a path (central
+// differences of the return map): gF = (dH/dF)^T a; one backward step with
+// c = W/n [last] - lambda: g += c : dP/dp + a . dH/dp, a_out = c : dP/dh + a . dH/dh
+void launch_j2_path_gF(const double* F, size_t n, MatView<double> mat, const double* hs,
+                       const double* a, double* gF, cudaStream_t s);
+void launch_j2_path_step(const double* F, size_t n, MatView<double> mat, const double* hs,
+                         const double* lam, const double W[9], int last, const double* a_in,
+                         double* a_out, double* g, cudaStream_t s);
 // out[4][n]: dJ/d(K, mu, tau_y0, H) per voxel, J = W : P-bar, history hs fixed
 void launch_j2_adjoint_grad(const double* F, size_t n, MatView<double> mat, const double* hs,
                             const double* lam, const double W[9], double* out, cudaStream_t s);

@@ -395,6 +395,176 @@ __global__ void __launch_bounds__(J2_THREADS) k_j2_adjoint_grad(
   }
 }
 
+// ---------------------------------------------------------------------------
+// Adjoint through the history of a path of increments (reverse sweep): the
+// return map's derivatives with respect to the history h = (Cp^-1_00, _11,
+// _22, _01, _02, _12, eps_p), to F and to the parameters, by central
+// differences of one voxel's return map (step 1e-7; relative for the
+// parameters).
+// ---------------------------------------------------------------------------
+
+// One voxel: P (row-major 9) and the new history (7) from F (row-major 9),
+// the history at the increment's start and the parameters (bulk modulus).
+RVE_DEV void j2_eval(const double (&Fv)[9], const double (&hs)[7], double Kb, double mu,
+                     double ty0, double H, double (&P)[9], double (&hn)[7]) {
+  double f[3][3], C[3][3];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) f[i][j] = Fv[3 * i + j];
+  C[0][0] = hs[0];
+  C[1][1] = hs[1];
+  C[2][2] = hs[2];
+  C[0][1] = C[1][0] = hs[3];
+  C[0][2] = C[2][0] = hs[4];
+  C[1][2] = C[2][1] = hs[5];
+  const double ep = hs[6];
+  double FC[3][3], be[3][3];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) FC[i][j] = f[i][0] * C[0][j] + f[i][1] * C[1][j] + f[i][2] * C[2][j];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) be[i][j] = FC[i][0] * f[j][0] + FC[i][1] * f[j][1] + FC[i][2] * f[j][2];
+  for (int i = 0; i < 3; ++i)
+    for (int j = i + 1; j < 3; ++j) be[i][j] = be[j][i] = 0.5 * (be[i][j] + be[j][i]);
+  double Q[3][3];
+  jacobi3(be, Q);
+  double eps[3];
+  for (int a = 0; a < 3; ++a) eps[a] = 0.5 * log(be[a][a]);
+  const double tr = eps[0] + eps[1] + eps[2];
+  double dev[3], sp[3];
+  for (int a = 0; a < 3; ++a) {
+    dev[a] = eps[a] - tr / 3.0;
+    sp[a] = 2.0 * mu * dev[a];
+  }
+  const double teq = sqrt(1.5 * (sp[0] * sp[0] + sp[1] * sp[1] + sp[2] * sp[2]));
+  const double phi = teq - (ty0 + H * ep);
+  const bool plastic = phi > -kYieldSurfaceTol * (ty0 + H * ep);
+  const double dg = plastic ? fmax(phi, 0.0) / (3.0 * mu + H) : 0.0;
+  const double beta = plastic ? 1.0 - 3.0 * mu * dg / teq : 1.0;
+  double taup[3];
+  for (int a = 0; a < 3; ++a) taup[a] = Kb * tr + beta * sp[a];
+  const double det = f[0][0] * (f[1][1] * f[2][2] - f[1][2] * f[2][1]) -
+                     f[0][1] * (f[1][0] * f[2][2] - f[1][2] * f[2][0]) +
+                     f[0][2] * (f[1][0] * f[2][1] - f[1][1] * f[2][0]);
+  const double id = 1.0 / det;
+  double Fi[3][3];
+  Fi[0][0] = (f[1][1] * f[2][2] - f[1][2] * f[2][1]) * id;
+  Fi[0][1] = (f[0][2] * f[2][1] - f[0][1] * f[2][2]) * id;
+  Fi[0][2] = (f[0][1] * f[1][2] - f[0][2] * f[1][1]) * id;
+  Fi[1][0] = (f[1][2] * f[2][0] - f[1][0] * f[2][2]) * id;
+  Fi[1][1] = (f[0][0] * f[2][2] - f[0][2] * f[2][0]) * id;
+  Fi[1][2] = (f[0][2] * f[1][0] - f[0][0] * f[1][2]) * id;
+  Fi[2][0] = (f[1][0] * f[2][1] - f[1][1] * f[2][0]) * id;
+  Fi[2][1] = (f[0][1] * f[2][0] - f[0][0] * f[2][1]) * id;
+  Fi[2][2] = (f[0][0] * f[1][1] - f[0][1] * f[1][0]) * id;
+  // P = Q diag(taup) Q^T F^-T ; G = F^-1 Q
+  double QF[3][3];  // (Q^T F^-T)_a j = sum_k Q_ka Fi_jk
+  for (int a = 0; a < 3; ++a)
+    for (int j = 0; j < 3; ++j) QF[a][j] = Q[0][a] * Fi[j][0] + Q[1][a] * Fi[j][1] + Q[2][a] * Fi[j][2];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j)
+      P[3 * i + j] = Q[i][0] * taup[0] * QF[0][j] + Q[i][1] * taup[1] * QF[1][j] +
+                     Q[i][2] * taup[2] * QF[2][j];
+  double bn[3], G[3][3], Cn[3][3];
+  for (int a = 0; a < 3; ++a) bn[a] = exp(2.0 * (tr / 3.0 + beta * dev[a]));
+  for (int i = 0; i < 3; ++i)
+    for (int a = 0; a < 3; ++a) G[i][a] = Fi[i][0] * Q[0][a] + Fi[i][1] * Q[1][a] + Fi[i][2] * Q[2][a];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) Cn[i][j] = G[i][0] * bn[0] * G[j][0] + G[i][1] * bn[1] * G[j][1] + G[i][2] * bn[2] * G[j][2];
+  hn[0] = Cn[0][0];
+  hn[1] = Cn[1][1];
+  hn[2] = Cn[2][2];
+  hn[3] = 0.5 * (Cn[0][1] + Cn[1][0]);
+  hn[4] = 0.5 * (Cn[0][2] + Cn[2][0]);
+  hn[5] = 0.5 * (Cn[1][2] + Cn[2][1]);
+  hn[6] = ep + dg;
+}
+
+constexpr double kPathStep = 1e-7;
+
+// gF[c][v] = sum_k a_k dH_k/dF_c (the functional's sensitivity to F_m
+// through the history h_m)
+__global__ void __launch_bounds__(J2_THREADS) k_j2_path_gF(const double* __restrict__ F, size_t n,
+                                                         MatView<double> mat,
+                                                         const double* __restrict__ hs,
+                                                         const double* __restrict__ a,
+                                                         double* __restrict__ gF) {
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+    double Fv[9], h[7], av[7];
+    for (int c = 0; c < 9; ++c) Fv[c] = F[(size_t)c * n + v];
+    for (int k = 0; k < 7; ++k) {
+      h[k] = hs[(size_t)k * n + v];
+      av[k] = a[(size_t)k * n + v];
+    }
+    const double mu = mat.get(v, 1), ty0 = mat.get(v, 2), H = mat.get(v, 3);
+    const double Kb = mat.get(v, 0) + 2.0 * mu / 3.0;
+    double Pp[9], Pm[9], hp[7], hm[7];
+    for (int c = 0; c < 9; ++c) {
+      const double f0 = Fv[c];
+      Fv[c] = f0 + kPathStep;
+      j2_eval(Fv, h, Kb, mu, ty0, H, Pp, hp);
+      Fv[c] = f0 - kPathStep;
+      j2_eval(Fv, h, Kb, mu, ty0, H, Pm, hm);
+      Fv[c] = f0;
+      double s = 0.0;
+      for (int k = 0; k < 7; ++k) s += av[k] * (hp[k] - hm[k]);
+      gF[(size_t)c * n + v] = s / (2.0 * kPathStep);
+    }
+  }
+}
+
+// One backward step at (F_m, h_{m-1}): with c = (1/n) W [last] - lambda,
+//   g[p][v]     += c : dP/dp + a . dH/dp          (p = K, mu, tau_y0, H),
+//   a_out[k][v]  = c : dP/dh_k + a . dH/dh_k.
+__global__ void __launch_bounds__(J2_THREADS) k_j2_path_step(
+    const double* __restrict__ F, size_t n, MatView<double> mat, const double* __restrict__ hs,
+    const double* __restrict__ lam, W9 w, int last, const double* __restrict__ a_in,
+    double* __restrict__ a_out, double* __restrict__ g) {
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  const double inv_n = 1.0 / (double)n;
+  for (size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+    double Fv[9], h[7], av[7], c[9];
+    for (int q = 0; q < 9; ++q) {
+      Fv[q] = F[(size_t)q * n + v];
+      c[q] = (last ? inv_n * w.w[q] : 0.0) - lam[(size_t)q * n + v];
+    }
+    for (int k = 0; k < 7; ++k) {
+      h[k] = hs[(size_t)k * n + v];
+      av[k] = a_in ? a_in[(size_t)k * n + v] : 0.0;
+    }
+    double p[4];
+    p[1] = mat.get(v, 1);
+    p[0] = mat.get(v, 0) + 2.0 * p[1] / 3.0;
+    p[2] = mat.get(v, 2);
+    p[3] = mat.get(v, 3);
+    double Pp[9], Pm[9], hp[7], hm[7];
+    for (int k = 0; k < 7; ++k) {
+      const double h0 = h[k];
+      h[k] = h0 + kPathStep;
+      j2_eval(Fv, h, p[0], p[1], p[2], p[3], Pp, hp);
+      h[k] = h0 - kPathStep;
+      j2_eval(Fv, h, p[0], p[1], p[2], p[3], Pm, hm);
+      h[k] = h0;
+      double s = 0.0;
+      for (int q = 0; q < 9; ++q) s += c[q] * (Pp[q] - Pm[q]);
+      for (int j = 0; j < 7; ++j) s += av[j] * (hp[j] - hm[j]);
+      a_out[(size_t)k * n + v] = s / (2.0 * kPathStep);
+    }
+    for (int t = 0; t < 4; ++t) {
+      const double p0 = p[t];
+      const double st = kPathStep * fabs(p0);
+      p[t] = p0 + st;
+      j2_eval(Fv, h, p[0], p[1], p[2], p[3], Pp, hp);
+      p[t] = p0 - st;
+      j2_eval(Fv, h, p[0], p[1], p[2], p[3], Pm, hm);
+      p[t] = p0;
+      double s = 0.0;
+      for (int q = 0; q < 9; ++q) s += c[q] * (Pp[q] - Pm[q]);
+      for (int j = 0; j < 7; ++j) s += av[j] * (hp[j] - hm[j]);
+      g[(size_t)t * n + v] += s / (2.0 * st);
+    }
+  }
+}
+
 template <typename RO>
 void launch_j2_constitutive(const double* F, size_t n, MatView<double> mat, const double* hc,
                             double* ht, double* P, RO* K4, SolverState* st, cudaStream_t s,
@@ -420,6 +590,22 @@ void launch_j2_adjoint_grad(const double* F, size_t n, MatView<double> mat, cons
   for (int c = 0; c < 9; ++c) w.w[c] = W[c];
   const size_t b = std::min<size_t>((n + J2_THREADS - 1) / J2_THREADS, 65535);
   k_j2_adjoint_grad<<<(unsigned)std::max<size_t>(b, 1), J2_THREADS, 0, s>>>(F, n, mat, hs, lam, w, out);
+}
+
+void launch_j2_path_gF(const double* F, size_t n, MatView<double> mat, const double* hs,
+                       const double* a, double* gF, cudaStream_t s) {
+  const size_t b = std::min<size_t>((n + J2_THREADS - 1) / J2_THREADS, 65535);
+  k_j2_path_gF<<<(unsigned)std::max<size_t>(b, 1), J2_THREADS, 0, s>>>(F, n, mat, hs, a, gF);
+}
+
+void launch_j2_path_step(const double* F, size_t n, MatView<double> mat, const double* hs,
+                         const double* lam, const double W[9], int last, const double* a_in,
+                         double* a_out, double* g, cudaStream_t s) {
+  W9 w;
+  for (int c = 0; c < 9; ++c) w.w[c] = W[c];
+  const size_t b = std::min<size_t>((n + J2_THREADS - 1) / J2_THREADS, 65535);
+  k_j2_path_step<<<(unsigned)std::max<size_t>(b, 1), J2_THREADS, 0, s>>>(F, n, mat, hs, lam, w,
+                                                                          last, a_in, a_out, g);
 }
 
 template void launch_j2_constitutive<float>(const double*, size_t, MatView<double>, const double*,

@@ -211,6 +211,9 @@ struct rve_s {
   double* hc = nullptr;     // J2 history, committed [7][n]
   double* ht = nullptr;     // J2 history, trial [7][n]
   double* hprev = nullptr;  // J2 history at the start of the last committed increment
+  // J2 path tape (rve_tape): per committed increment its F and starting history
+  bool tape_on = false;
+  std::vector<double*> tape_F, tape_h;
   std::string err;
   long long launches = 0;
   // instrumentation
@@ -221,6 +224,8 @@ struct rve_s {
   std::vector<std::pair<long long, int>> solve_iters;  // (solve id, effective iterations)
   cudaEvent_t e0 = nullptr, e1 = nullptr;
 };
+
+static void tape_clear(rve_t h);
 
 namespace {
 
@@ -1251,6 +1256,7 @@ int rve_tuning(rve_t h, int knobs[7]) {
 }
 
 void rve_destroy(rve_t h) {
+  if (h) tape_clear(h);
   if (!h) return;
   if (h->s) cudaStreamSynchronize(h->s);
   else cudaDeviceSynchronize();
@@ -1293,9 +1299,28 @@ static int commit_state(rve_t h) {
     h->hc = h->ht;
     h->ht = h->hprev;
     h->hprev = start;
+    if (h->tape_on) {
+      double *tf = nullptr, *th = nullptr;
+      if (cudaMalloc(&tf, 9 * h->n * 8) != cudaSuccess || cudaMalloc(&th, 7 * h->n * 8) != cudaSuccess) {
+        cudaFree(tf);
+        return fail(h, RVE_ERR_NOMEM, "tape: allocation failed");
+      }
+      CK(cudaMemcpyAsync(tf, h->F, 9 * h->n * 8, cudaMemcpyDeviceToDevice, h->s));
+      CK(cudaMemcpyAsync(th, h->hprev, 7 * h->n * 8, cudaMemcpyDeviceToDevice, h->s));
+      h->tape_F.push_back(tf);
+      h->tape_h.push_back(th);
+    }
     enqueue_constitutive(h);
   }
   return RVE_OK;
+}
+
+static void tape_clear(rve_t h) {
+  if (!h->tape_F.empty() || !h->tape_h.empty()) cudaStreamSynchronize(h->s);
+  for (double* p : h->tape_F) cudaFree(p);
+  for (double* p : h->tape_h) cudaFree(p);
+  h->tape_F.clear();
+  h->tape_h.clear();
 }
 
 // One increment to h->Fbar.  commit = false leaves a converged state
@@ -1926,6 +1951,96 @@ int rve_adjoint_grad_params(rve_t h, const double W[9], double tol_cg, double* g
   return copy_out(h, grads, h->tmp64, (size_t)h->nparam * h->n * sizeof(double), on_device);
 }
 
+int rve_tape(rve_t h, int enable) {
+  if (!h) return RVE_ERR_INVALID;
+  if (h->model != RVE_J2) return fail(h, RVE_ERR_UNSUPPORTED, "tape: J2 only");
+  tape_clear(h);
+  h->tape_on = enable != 0;
+  return RVE_OK;
+}
+
+int rve_tape_length(rve_t h) { return h ? (int)h->tape_F.size() : RVE_ERR_INVALID; }
+
+// Reverse sweep over the taped increments (J2, float64 handles): per
+// increment m = M..1 the tangent at (F_m, h_{m-1}), the adjoint field of
+// G K G lambda = G g with g = (1/n) K W [m = M] + (dH/dF)^T a, then the
+// parameter gradient and a = dJ/dh_{m-1}; finally the state's tangent and
+// trial history are evaluated again at the current F.
+int rve_adjoint_grad_path(rve_t h, const double W[9], double tol_cg, double* grads,
+                          int on_device, int* cg_iters) {
+  NvtxRange nv("rve adjoint_grad_path");
+  if (!h || !W || !grads || !(tol_cg > 0.0)) return RVE_ERR_INVALID;
+  if (h->model != RVE_J2 || h->mixed)
+    return fail(h, RVE_ERR_UNSUPPORTED, "path adjoint: float64 J2 handles only");
+  const int M = (int)h->tape_F.size();
+  if (M < 1) return fail(h, RVE_ERR_INVALID, "path adjoint: empty tape (rve_tape before the increments)");
+  const size_t n = h->n, n9 = 9 * n;
+  int rc = sync_state(h);
+  if (rc) return rc;
+  SolverState* hs = h->hst;
+  std::memset(hs->counter, 0, sizeof(hs->counter));
+  for (int c = 0; c < 9; ++c) hs->adjW[c] = W[c] / (double)n;
+  hs->cg_tol = tol_cg;
+  hs->cg_atol = h->opt.cg_atol;
+  hs->maxit = h->opt.max_cg;
+  hs->stag = 0;
+  hs->done = 0;
+  rc = push_state(h);
+  if (rc) return rc;
+  MatView<double> m = mat_view<double>(h);
+  const int sym = h->tan == TAN_SYM45;
+  // scratch: g in tmp64 [4][n]; a = dJ/dh in ht and Ft (both rebuilt below)
+  double* g = h->tmp64;
+  double* a_cur = h->ht;
+  double* a_next = h->Ft;
+  CK(cudaMemsetAsync(g, 0, 4 * n * sizeof(double), h->s));
+  int its_total = 0;
+  for (int k = M - 1; k >= 0; --k) {
+    const bool last = k == M - 1;
+    const double* Fk = h->tape_F[k];
+    const double* hk = h->tape_h[k];
+    launch_j2_constitutive<double>(Fk, n, m, hk, nullptr, nullptr, as<double>(h->K4), h->st, h->s,
+                                   sym);
+    h->launches += 1;
+    // right-hand side G g
+    if (last) {
+      enqueue_operator64(h, SRC_UNIFORM, nullptr, h->st->adjW, h->adj_b);
+    } else {
+      launch_j2_path_gF(Fk, n, m, hk, a_cur, h->adj_b, h->s);
+      enqueue_project_fp64(h, h->adj_b);
+      h->launches += 1;
+    }
+    launch_cg_init<double>(n9, h->adj_b, nullptr, as<double>(h->r), as<double>(h->x), h->st,
+                           h->partials, h->s);
+    h->launches += 1;
+    rc = sync_state(h);
+    if (rc) return rc;
+    int its = 0;
+    rc = cg_solve<double>(h, &its);
+    its_total += its;
+    if (rc) {
+      fail(h, rc, std::string("path adjoint solve: ") + rve_status_string(rc));
+      break;
+    }
+    launch_j2_path_step(Fk, n, m, hk, as<double>(h->x), W, last ? 1 : 0, last ? nullptr : a_cur,
+                        a_next, g, h->s);
+    h->launches += 1;
+    std::swap(a_cur, a_next);
+  }
+  // back to the committed state: tangent and trial history at (F, hc), Ft = F
+  launch_j2_constitutive<double>(h->F, n, m, h->hc, h->ht, nullptr, as<double>(h->K4), h->st,
+                                 h->s, sym);
+  h->launches += 1;
+  CK(cudaMemcpyAsync(h->Ft, h->F, n9 * 8, cudaMemcpyDeviceToDevice, h->s));
+  if (rc) {
+    sync_state(h);
+    return rc;
+  }
+  CK(cudaGetLastError());
+  if (cg_iters) *cg_iters = its_total;
+  return copy_out(h, grads, g, 4 * n * sizeof(double), on_device);
+}
+
 int rve_get_history(rve_t h, double* dst, int on_device) {
   if (!h || !dst || h->model != RVE_J2) return RVE_ERR_INVALID;
   return copy_out(h, dst, h->hc, 7 * h->n * 8, on_device);
@@ -1958,6 +2073,7 @@ int rve_set_F(rve_t h, const double* F, int on_device) {
   CK(cudaMemcpyAsync(h->Ft, h->F, 9 * h->n * 8, cudaMemcpyDeviceToDevice, h->s));
   if (h->hprev)  // no increment since: the committed history is its own start
     CK(cudaMemcpyAsync(h->hprev, h->hc, 7 * h->n * 8, cudaMemcpyDeviceToDevice, h->s));
+  tape_clear(h);  // a new path starts here
   std::memset(h->hst, 0, sizeof(SolverState));
   rc = push_state(h);
   if (rc) return rc;

@@ -415,6 +415,23 @@ class RVE:
         g, its = rve_adjoint_grad_params(self.h, W, self.n, nparam, tol_cg)
         return g.reshape((nparam,) + self.shape), its
 
+    def tape(self, enable=True):
+        """J2: record (or stop recording) the path for adjoint_grad_path."""
+        _check(lib.rve_tape(self.h, 1 if enable else 0), self.h)
+
+    def tape_length(self):
+        return int(lib.rve_tape_length(self.h))
+
+    def adjoint_grad_path(self, W, tol_cg=1e-12):
+        """J2: dJ/d(K, mu, tau_y0, H) per voxel, [4, *shape], for J = W : P-bar
+        after the taped path (through the history), and the CG iterations."""
+        Wc = np.ascontiguousarray(W, dtype=np.float64).reshape(9)
+        its = C.c_int(0)
+        g = np.empty(4 * self.n, dtype=np.float64)
+        _check(lib.rve_adjoint_grad_path(self.h, Wc.ctypes.data_as(C.c_void_p), float(tol_cg),
+                                         g.ctypes.data_as(C.c_void_p), 0, C.byref(its)), self.h)
+        return g.reshape((4,) + self.shape), its.value
+
     def get_history(self):
         """J2: committed (Cp^-1 [6 symmetric components], eps_p) per voxel, [7, *shape]."""
         return rve_get_history(self.h, self.n).reshape((7,) + self.shape)

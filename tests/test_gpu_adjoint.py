@@ -253,3 +253,41 @@ def test_svk_adjoint_grad_params_equals_adjoint_grad():
     assert g.shape == (2,) + mu.shape
     assert np.array_equal(g[0], gK) and np.array_equal(g[1], gmu)
     r.close()
+
+
+def test_j2_path_adjoint_matches_oracle():
+    """Through the history of a loading-reversal-reloading path (reverse
+    sweep over the taped increments) against the oracle's reverse sweep."""
+    shape, ph = _j2_cell()
+    ramp = [synth.simple_shear(g) + np.diag([g / 2, 0.0, 0.0]) for g in (0.004, 0.008, -0.002, 0.006)]
+    prob = solver.J2Problem.from_phase(ph, J2_PARAMS)
+    states = []
+    r = RVE(shape, model="j2", phase=ph, phase_params=J2_PARAMS, precision="fp64",
+            cg_atol=1e-14)
+    r.tape(True)
+    for k, Fb in enumerate(ramp):
+        Cpi0, ep0 = prob.mat.Cpi.copy(), prob.mat.ep.copy()
+        prob.increment(Fb, tol_newton=1e-11, tol_cg=1e-13, cg_atol=1e-14)
+        states.append((prob.F.copy(), Cpi0, ep0))
+        r.set_macro_F(Fb)
+        r.solve_increment(**TIGHT)
+        if k == 0:
+            # one increment: the fixed-history derivative in closed form
+            g1, _ = r.adjoint_grad_path(WXY, tol_cg=1e-13)
+            ref1, _ = r.adjoint_grad_params(WXY, tol_cg=1e-13)
+            th = np.moveaxis(J2_PARAMS[ph], -1, 0)
+            assert np.abs(th * (g1 - ref1)).max() < 1e-6 * np.abs(th * ref1).max()
+    assert r.tape_length() == len(ramp)
+    before = (r.get_F(), r.get_P(), r.get_history(), r.get_K4())
+    g, _ = r.adjoint_grad_path(WXY, tol_cg=1e-13)
+    after = (r.get_F(), r.get_P(), r.get_history(), r.get_K4())
+    assert all(np.array_equal(x, y) for x, y in zip(before, after))   # state untouched
+    p = J2_PARAMS[ph.reshape(-1)]
+    ref = oadj.j2_path_grad_params(states, p[:, 0], p[:, 1], p[:, 2], p[:, 3], WXY, 1e-13, 1e-15)
+    th = np.moveaxis(J2_PARAMS[ph], -1, 0)
+    scale = np.abs(th * ref).max()
+    for q in range(4):
+        assert np.abs(th[q] * (g[q] - ref[q])).max() < 1e-6 * scale, q
+    r.set_F(r.get_F())          # a new path starts: the tape is cleared
+    assert r.tape_length() == 0
+    r.close()
