@@ -1,6 +1,6 @@
 """torch.autograd wrappers: homogenised stress of an SVK cell as a
 differentiable function of its per-voxel shear and bulk moduli, and of a J2
-cell after one increment from the virgin state as a function of its
+cell after a path of increments from the virgin state as a function of its
 per-voxel K, mu, tau_y0 and H.
 
 forward solves the cell (Newton-CG through the C ABI) for the macroscopic
@@ -62,10 +62,12 @@ def homogenized_stress(mu, K, Fbar, **kw):
 
 
 class J2HomogenizedStress(torch.autograd.Function):
-    """P-bar(K, mu, tau_y0, H) of a J2 cell after ONE increment from the
-    virgin state to F-bar: the case where the library's derivative (taken at
-    the history at the increment's start) is the exact total derivative.
-    Each parameter is a tensor of the cell's shape (or a scalar)."""
+    """P-bar(K, mu, tau_y0, H) of a J2 cell after increments from the virgin
+    state to the F-bar of each (Fbar: one 3x3 tensor, or a sequence of them
+    for a path).  One increment: backward by rve_adjoint_grad_params; a path
+    (float64 handles): recorded with rve_tape and differentiated through the
+    history by rve_adjoint_grad_path.  Each parameter is a tensor of the
+    cell's shape (or a scalar)."""
 
     @staticmethod
     def forward(ctx, K, mu, ty0, H, Fbar, tol_newton=1e-5, tol_cg=1e-8, precision="fp64",
@@ -78,8 +80,13 @@ class J2HomogenizedStress(torch.autograd.Function):
             vals.append(np.broadcast_to(a.astype(np.float64), shape))
         r = RVE(shape, model="j2", voxel_params=np.stack(vals), precision=precision,
                 cg_atol=cg_atol)
-        r.set_macro_F(np.asarray(Fbar, dtype=np.float64))
-        r.solve_increment(tol_newton, tol_cg)
+        ramp = np.asarray(Fbar, dtype=np.float64).reshape(-1, 3, 3)
+        ctx.path = len(ramp) > 1
+        if ctx.path:
+            r.tape(True)
+        for Fb in ramp:
+            r.set_macro_F(Fb)
+            r.solve_increment(tol_newton, tol_cg)
         ctx.rve = r
         ctx.adjoint_tol = adjoint_tol
         ctx.device = ref.device
@@ -89,7 +96,10 @@ class J2HomogenizedStress(torch.autograd.Function):
     @staticmethod
     def backward(ctx, grad_P):
         W = grad_P.detach().cpu().numpy().astype(np.float64)
-        g, _ = ctx.rve.adjoint_grad_params(W, ctx.adjoint_tol)
+        if ctx.path:
+            g, _ = ctx.rve.adjoint_grad_path(W, ctx.adjoint_tol)
+        else:
+            g, _ = ctx.rve.adjoint_grad_params(W, ctx.adjoint_tol)
         ctx.rve.close()
         out = [torch.from_numpy(np.ascontiguousarray(g[k])).to(ctx.device) if ctx.is_tensor[k]
                else None for k in range(4)]
@@ -98,7 +108,8 @@ class J2HomogenizedStress(torch.autograd.Function):
 
 def j2_homogenized_stress(K, mu, tau_y0, H, Fbar, **kw):
     """Differentiable P-bar (3x3 float64) of a J2 cell with per-voxel
-    parameters after one increment from the virgin state to `Fbar`."""
+    parameters after the increments to `Fbar` (a 3x3 F-bar, or a sequence
+    of them) from the virgin state."""
     args = [kw.pop(k, d) for k, d in (("tol_newton", 1e-5), ("tol_cg", 1e-8),
                                        ("precision", "fp64"), ("adjoint_tol", 1e-10),
                                        ("cg_atol", 0.0))]

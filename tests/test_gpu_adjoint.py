@@ -291,3 +291,28 @@ def test_j2_path_adjoint_matches_oracle():
     r.set_F(r.get_F())          # a new path starts: the tape is cleared
     assert r.tape_length() == 0
     r.close()
+
+
+def test_j2_autograd_along_a_path():
+    from paper_1603_08893_gb300.autograd import j2_homogenized_stress
+    shape, ph = _j2_cell()
+    p = J2_PARAMS[ph]
+    ts = [torch.tensor(np.ascontiguousarray(p[..., k]), dtype=torch.float64, requires_grad=True)
+          for k in range(4)]
+    ramp = np.stack([synth.simple_shear(g) + np.diag([g / 2, 0.0, 0.0])
+                     for g in (0.004, 0.008, -0.002, 0.006)])
+    Pbar = j2_homogenized_stress(*ts, ramp, tol_newton=1e-11, tol_cg=1e-13, cg_atol=1e-14,
+                                 adjoint_tol=1e-13)
+    grads = torch.autograd.grad(Pbar[0, 1], ts)
+    r = RVE(shape, model="j2", phase=ph, phase_params=J2_PARAMS, precision="fp64",
+            cg_atol=1e-14)
+    r.tape(True)
+    for Fb in ramp:
+        r.set_macro_F(Fb)
+        r.solve_increment(**TIGHT)
+    ref, _ = r.adjoint_grad_path(WXY, tol_cg=1e-13)
+    r.close()
+    th = np.moveaxis(p, -1, 0)
+    scale = np.abs(th * ref).max()
+    for k in range(4):
+        assert np.abs(th[k] * (grads[k].numpy() - ref[k])).max() < 1e-9 * scale
