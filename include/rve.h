@@ -386,8 +386,9 @@ const char* rve_status_string(int code);
  * rve_load creates a new handle from such a file: every solver option comes
  * from the file; opt (may be NULL) supplies only stream and workspace (NULL
  * workspace: the library allocates).  Continuing from a loaded handle gives
- * bit-identical results to continuing the saved one.  RVE_ERR_INVALID for
- * unreadable or malformed files. */
+ * bit-identical results to continuing the saved one.  The J2 path tape
+ * (rve_tape) is not saved: a loaded handle starts without one.
+ * RVE_ERR_INVALID for unreadable or malformed files. */
 int rve_save(rve_t h, const char* path);
 int rve_load(rve_t* out, const char* path, const rve_options* opt);
 
