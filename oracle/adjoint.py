@@ -161,10 +161,9 @@ def j2_grad_params(F, Cpi, ep, K, mu, ty0, H, W, tol_cg=1e-12, cg_atol=0.0):
 #   c_m      = (1/n) W [m = M] - lambda_m,
 #   dJ/dp   += c_m : dP/dp + (dH/dp)^T a_m,
 #   a_{m-1}  = c_m : dP/dh + (dH/dh)^T a_m,
-# all local derivatives at (F_m, h_{m-1}).  Here the history derivatives of
-# the return map are central differences per voxel (a reference for a
-# kernel of the derivative formulas); the parameter derivative of P is the
-# closed form above.
+# all local derivatives at (F_m, h_{m-1}): in closed form (the return map
+# linearised step by step, below) or by central differences per voxel; the
+# parameter derivative of P is the closed form above.
 # ---------------------------------------------------------------------------
 def _hist_pack(Cpi, ep):
     return np.stack([Cpi[:, 0, 0], Cpi[:, 1, 1], Cpi[:, 2, 2], Cpi[:, 0, 1], Cpi[:, 0, 2],
@@ -223,11 +222,12 @@ def j2_local_jacobians(F, Cpi, ep, K, mu, ty0, H, step=1e-7):
     return dPdh, dHdF, dHdh, dHdp
 
 
-def j2_path_grad_params(states, K, mu, ty0, H, W, tol_cg=1e-12, cg_atol=0.0):
+def j2_path_grad_params(states, K, mu, ty0, H, W, tol_cg=1e-12, cg_atol=0.0, local="closed"):
     """dJ/d(K, mu, tau_y0, H) per voxel, [4, *grid], for J = W : P-bar after
     a path of increments.  ``states``: per increment, in order, (F_m
     [3,3,*grid] converged, Cpi_{m-1} [n,3,3], ep_{m-1} [n]) -- the field
-    and the history at the increment's start."""
+    and the history at the increment's start.  ``local``: the return map's
+    derivatives in closed form ("closed") or by central differences ("fd")."""
     W = np.asarray(W, dtype=np.float64)
     grid = states[0][0].shape[-3:]
     n = int(np.prod(grid))
@@ -241,7 +241,8 @@ def j2_path_grad_params(states, K, mu, ty0, H, W, tol_cg=1e-12, cg_atol=0.0):
         st = j2.return_map(Fv, Cpi, ep, *prm)
         K4v = j2.tangent(Fv, Cpi, K, mu, H, st)
         K4 = np.moveaxis(K4v, 0, -1).reshape((3, 3, 3, 3) + tuple(grid))
-        dPdh, dHdF, dHdh, dHdp = j2_local_jacobians(Fv, Cpi, ep, *prm)
+        jac = j2_local_jacobians_closed if local == "closed" else j2_local_jacobians
+        dPdh, dHdF, dHdh, dHdp = jac(Fv, Cpi, ep, *prm)
         gF = np.einsum("nka,nk->na", dHdF, a)
         gfield = np.moveaxis(gF, 0, -1).reshape((3, 3) + tuple(grid))
         if m == last:
@@ -255,3 +256,92 @@ def j2_path_grad_params(states, K, mu, ty0, H, W, tol_cg=1e-12, cg_atol=0.0):
         g += np.einsum("na,tna->tn", c, dPdp) + np.einsum("nk,nkt->tn", a, dHdp)
         a = np.einsum("na,nak->nk", c, dPdh) + np.einsum("nk,nkj->nj", a, dHdh)
     return g.reshape((4,) + tuple(grid))
+
+
+def _sinhc(x):
+    """sinh(x)/x, 1 at x = 0."""
+    with np.errstate(invalid="ignore", divide="ignore"):
+        return np.where(np.abs(x) < 1e-8, 1.0 + x * x / 6.0, np.sinh(x) / np.where(x == 0, 1.0, x))
+
+
+def j2_return_map_directional(F, Cpi, ep, K, mu, ty0, H, dF=None, dC=None, dep=None, dprm=None):
+    """Directional derivative of the J2 return map per voxel, in closed form:
+    (dP [n,3,3], dh_new [n,7]) for perturbations dF [n,3,3], dC [n,3,3]
+    (symmetric), dep [n] and dprm [4, n] of (K, mu, tau_y0, H).  Each step
+    of ``j2.return_map`` linearised: the logarithm by the Daleckii-Krein
+    divided differences of ln, the radial return, the exponential of the
+    elastic log strain by those of exp(2 x), the pull-backs with
+    d(F^-1) = -F^-1 dF F^-1."""
+    n = F.shape[0]
+    Z = np.zeros((n, 3, 3))
+    dF = Z if dF is None else dF
+    dC = Z if dC is None else dC
+    dep = np.zeros(n) if dep is None else dep
+    dK, dmu, dty, dH = (np.zeros((4, n)) if dprm is None else dprm)
+    st = j2.return_map(F, Cpi, ep, K, mu, ty0, H)
+    Q, lam, plastic = st["Q"], st["lam"], st["plastic"]
+    teq, dg, beta, tr = st["teq"], st["dg"], st["beta"], st["tr"]
+    Finv = st["Finv"]
+    FT = np.swapaxes(F, -1, -2)
+    QT = np.swapaxes(Q, -1, -2)
+    I = np.eye(3)
+    # trial log strain
+    dbe = dF @ Cpi @ FT + F @ Cpi @ np.swapaxes(dF, -1, -2) + F @ dC @ FT
+    deps = Q @ (0.5 * j2._f1(lam) * (QT @ dbe @ Q)) @ QT
+    dtr = np.trace(deps, axis1=-2, axis2=-1)
+    Ed = np.einsum("nab,nb,ncb->nac", Q, st["dev"], Q)             # deviatoric log strain
+    dEd = deps - dtr[:, None, None] * I / 3.0
+    s_tr = 2.0 * mu[:, None, None] * Ed
+    ds_tr = 2.0 * mu[:, None, None] * dEd + 2.0 * dmu[:, None, None] * Ed
+    den = 3.0 * mu + H
+    tsafe = np.where(teq > 0, teq, 1.0)
+    dteq = np.where(plastic, 1.5 * (s_tr * ds_tr).sum((-2, -1)) / tsafe, 0.0)
+    dphi = dteq - dty - dH * ep - H * dep
+    ddg = np.where(plastic, (dphi - dg * (3.0 * dmu + dH)) / den, 0.0)
+    dbeta = np.where(plastic, -3.0 * (dmu * dg + mu * ddg) / tsafe
+                     + 3.0 * mu * dg * dteq / tsafe ** 2, 0.0)
+    tau = st["tau"]
+    dtau = ((dK * tr + K * dtr)[:, None, None] * I + dbeta[:, None, None] * s_tr
+            + beta[:, None, None] * ds_tr)
+    dFinv = -Finv @ dF @ Finv
+    dP = dtau @ st["FinvT"] + tau @ np.swapaxes(dFinv, -1, -2)
+    # new history
+    x = tr[:, None] / 3.0 + beta[:, None] * st["dev"]                 # principal elastic log strain
+    deps_e = dtr[:, None, None] * I / 3.0 + dbeta[:, None, None] * Ed + beta[:, None, None] * dEd
+    xa, xb = x[:, :, None], x[:, None, :]
+    g1 = 2.0 * np.exp(xa + xb) * _sinhc(xa - xb)                     # divided differences of exp(2x)
+    dbn = Q @ (g1 * (QT @ deps_e @ Q)) @ QT
+    bn = np.einsum("nab,nb,ncb->nac", Q, np.exp(2.0 * x), Q)
+    dCn = dFinv @ bn @ st["FinvT"] + Finv @ dbn @ st["FinvT"] + Finv @ bn @ np.swapaxes(dFinv, -1, -2)
+    dCn = 0.5 * (dCn + np.swapaxes(dCn, -1, -2))
+    dh = _hist_pack(dCn, dep + ddg)
+    return dP, dh
+
+
+def j2_local_jacobians_closed(F, Cpi, ep, K, mu, ty0, H):
+    """Same outputs as ``j2_local_jacobians`` from the closed-form
+    directional derivatives."""
+    n = F.shape[0]
+    prm = (K, mu, ty0, H)
+    dPdh = np.zeros((n, 9, 7))
+    dHdh = np.zeros((n, 7, 7))
+    for k in range(7):
+        e = np.zeros((n, 7))
+        e[:, k] = 1.0
+        dC, dep = _hist_unpack(e)
+        dP, dh = j2_return_map_directional(F, Cpi, ep, *prm, dC=dC, dep=dep)
+        dPdh[:, :, k] = dP.reshape(n, 9)
+        dHdh[:, :, k] = dh
+    dHdF = np.zeros((n, 7, 9))
+    for a in range(9):
+        dF = np.zeros((n, 3, 3))
+        dF[:, a // 3, a % 3] = 1.0
+        _, dh = j2_return_map_directional(F, Cpi, ep, *prm, dF=dF)
+        dHdF[:, :, a] = dh
+    dHdp = np.zeros((n, 7, 4))
+    for t in range(4):
+        d = np.zeros((4, n))
+        d[t] = 1.0
+        _, dh = j2_return_map_directional(F, Cpi, ep, *prm, dprm=d)
+        dHdp[:, :, t] = dh
+    return dPdh, dHdF, dHdh, dHdp

@@ -260,3 +260,33 @@ def test_j2_path_adjoint_matches_finite_differences_over_the_path():
                                   1e-15)
     assert abs(float(last[2][ph == 0].sum()) - float(g[2][ph == 0].sum())) > \
         1e-3 * abs(float(g[2][ph == 0].sum()))
+
+
+def test_j2_return_map_closed_form_derivatives():
+    """The return map linearised step by step (Daleckii-Krein for ln and
+    exp, radial return, pull-backs) against central differences, and its F
+    derivative against the consistent tangent."""
+    from oracle import j2
+    rng = np.random.default_rng(11)
+    m = 64
+    K, mu = np.full(m, 1 / 1.2), np.full(m, 1 / 2.6)
+    ty0, H = rng.uniform(0.002, 0.006, m), rng.uniform(0.005, 0.05, m)
+    F0 = np.moveaxis(synth.random_F((m,), rng, 0.01), -1, 0)
+    st0 = j2.return_map(F0, np.broadcast_to(np.eye(3), (m, 3, 3)).copy(), np.zeros(m), K, mu,
+                        ty0, H)
+    Cpi, ep = st0["Cpi_new"], st0["ep_new"]
+    sc = rng.uniform(0.5, 1.5, m)[:, None, None]
+    F = np.eye(3) + sc * (F0 - np.eye(3)) + np.moveaxis(rng.uniform(-1e-3, 1e-3, (3, 3, m)), -1, 0)
+    closed = adjoint.j2_local_jacobians_closed(F, Cpi, ep, K, mu, ty0, H)
+    fd = adjoint.j2_local_jacobians(F, Cpi, ep, K, mu, ty0, H, step=1e-6)
+    for a, b in zip(closed, fd):
+        assert np.abs(a - b).max() < 1e-6 * np.abs(b).max()
+    st = j2.return_map(F, Cpi, ep, K, mu, ty0, H)
+    K4 = j2.tangent(F, Cpi, K, mu, H, st)
+    assert 0.2 < st["plastic"].mean() < 1.0
+    for a in range(9):
+        dF = np.zeros((m, 3, 3))
+        dF[:, a // 3, a % 3] = 1.0
+        dP, _ = adjoint.j2_return_map_directional(F, Cpi, ep, K, mu, ty0, H, dF=dF)
+        ref = np.swapaxes(K4[:, :, :, a // 3, a % 3], -1, -2)   # K_ijkl = dP_ji/dF_kl
+        assert np.abs(dP - ref).max() < 1e-13 * np.abs(ref).max()
