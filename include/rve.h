@@ -59,7 +59,7 @@ extern "C" {
 #define RVE_ERR_NONFINITE (-7)    /* NaN or Inf in a residual, norm or stress */
 #define RVE_ERR_DETF (-8)         /* det F <= 0 in some voxel of a converged state */
 #define RVE_ERR_TIMEOUT (-9)      /* a bounded device wait gave up */
-#define RVE_ERR_UNSUPPORTED (-10) /* valid request this build does not implement */
+#define RVE_ERR_UNSUPPORTED (-10) /* valid request the library does not implement */
 
 /* constitutive models */
 #define RVE_SVK 0 /* Saint Venant-Kirchhoff (Sec. 4); params per phase: K, mu */

@@ -883,7 +883,7 @@ int rve_create(rve_t* out, int nx, int ny, int nz, int model, int nphase, const 
     return bail(RVE_ERR_INVALID, "grid sizes must be positive and supported by the DFT plan");
   int tan = 0;
   int rc = resolve_options(opt, &h->opt, model, &tan);
-  if (rc) return bail(rc, rc == RVE_ERR_UNSUPPORTED ? "model not available in this build"
+  if (rc) return bail(rc, rc == RVE_ERR_UNSUPPORTED ? "option combination not supported"
                                                     : "invalid options");
   h->n = h->g.n;
   h->mixed = h->opt.precision == RVE_MIXED;
