@@ -290,3 +290,24 @@ def test_j2_return_map_closed_form_derivatives():
         dP, _ = adjoint.j2_return_map_directional(F, Cpi, ep, K, mu, ty0, H, dF=dF)
         ref = np.swapaxes(K4[:, :, :, a // 3, a % 3], -1, -2)   # K_ijkl = dP_ji/dF_kl
         assert np.abs(dP - ref).max() < 1e-13 * np.abs(ref).max()
+
+
+def test_j2_parameter_derivatives_two_derivations_agree():
+    """dP/d(K, mu, tau_y0, H) from the principal-basis formulas and from the
+    step-by-step linearisation of the return map."""
+    from oracle import j2
+    rng = np.random.default_rng(5)
+    m = 48
+    K, mu = np.full(m, 1 / 1.2), np.full(m, 1 / 2.6)
+    ty0, H = rng.uniform(0.002, 0.006, m), rng.uniform(0.005, 0.05, m)
+    F0 = np.moveaxis(synth.random_F((m,), rng, 0.012), -1, 0)
+    st0 = j2.return_map(F0, np.broadcast_to(np.eye(3), (m, 3, 3)).copy(), np.zeros(m), K, mu,
+                        ty0, H)
+    F = F0 + np.moveaxis(rng.uniform(-2e-3, 2e-3, (3, 3, m)), -1, 0)
+    a = adjoint.j2_dP_dparams(F, st0["Cpi_new"], st0["ep_new"], K, mu, ty0, H)
+    for t in range(4):
+        d = np.zeros((4, m))
+        d[t] = 1.0
+        dP, _ = adjoint.j2_return_map_directional(F, st0["Cpi_new"], st0["ep_new"], K, mu, ty0, H,
+                                                  dprm=d)
+        assert np.abs(dP - a[t]).max() < 1e-12 * max(np.abs(a[t]).max(), 1e-30), t
