@@ -311,3 +311,20 @@ def test_j2_parameter_derivatives_two_derivations_agree():
         dP, _ = adjoint.j2_return_map_directional(F, st0["Cpi_new"], st0["ep_new"], K, mu, ty0, H,
                                                   dprm=d)
         assert np.abs(dP - a[t]).max() < 1e-12 * max(np.abs(a[t]).max(), 1e-30), t
+
+
+@pytest.mark.parametrize("F0", [np.eye(3), np.diag([1.01, 1.0, 1.0]), np.diag([1.02, 0.99, 0.99])])
+def test_j2_closed_form_derivatives_at_repeated_eigenvalues(F0):
+    """Repeated eigenvalues of be (the virgin state, uniaxial stretches):
+    the divided differences take their limits and still equal central
+    differences."""
+    m = 2
+    K, mu = np.full(m, 1 / 1.2), np.full(m, 1 / 2.6)
+    ty0, H = np.array([0.003, 0.001]), np.full(m, 0.01)
+    F = np.broadcast_to(F0, (m, 3, 3)).copy()
+    Cpi = np.broadcast_to(np.eye(3), (m, 3, 3)).copy()
+    ep = np.zeros(m)
+    closed = adjoint.j2_local_jacobians_closed(F, Cpi, ep, K, mu, ty0, H)
+    fd = adjoint.j2_local_jacobians(F, Cpi, ep, K, mu, ty0, H, step=1e-6)
+    for a, b in zip(closed, fd):
+        assert np.abs(a - b).max() < 1e-6 * max(np.abs(b).max(), 1.0)
