@@ -476,7 +476,11 @@ size_t fft_max_blocks(const GridGeom& g) {
 // Dynamic shared memory of these kernels stays below 200 KB (checked when the
 // grid geometry is built); the opt-in limit leaves room for static shared
 // memory (reduction scratch) within the 227 KB per block.
+// g_init_err is shared by every caller of fft_kernels_init, which holds
+// g_init_mu for the whole set-up so that host threads creating handles and
+// the allocation-free entry point can set it up at the same time.
 static cudaError_t g_init_err = cudaSuccess;
+static std::mutex g_init_mu;
 
 template <typename K>
 static void allow_big_smem(K kernel) {
@@ -550,6 +554,7 @@ void launch_G_df(const GridGeom& g, const double* in, double scale, int out_mode
 }
 
 cudaError_t fft_kernels_init() {
+  std::lock_guard<std::mutex> lock(g_init_mu);
   g_init_err = cudaSuccess;
   init_r<float>();
   init_r<double>();

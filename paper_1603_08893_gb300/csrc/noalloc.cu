@@ -1,14 +1,14 @@
 // rve_project_noalloc: the float64 projection G : A for callers that cannot
 // allocate device memory.
 //
-// Some callers cannot call cudaMalloc at all: code that runs while a CUDA
-// graph is being captured, plugins of host programs that own every device
-// allocation themselves, or real-time paths where an allocation (and the
-// implicit synchronisation it may bring) is not allowed.  For them this file
-// keeps the scratch of the projection -- the float64 half spectrum of the
-// nine components and the twiddle tables -- in one fixed device array that
-// lives as long as the library is loaded.  Every GPU that loads the library
-// holds RVE_NOALLOC_SCRATCH_BYTES of it until the process exits.
+// Some callers cannot call cudaMalloc at all: plugins of host programs that
+// own every device allocation themselves and hand out only their own
+// buffers, or real-time paths where an allocation (and the implicit device
+// synchronisation it may bring) is not allowed.  For them this file keeps
+// the scratch of the projection -- the float64 half spectrum of the nine
+// components and the twiddle tables -- in one fixed device array that lives
+// as long as the library is loaded.  Every GPU that loads the library holds
+// RVE_NOALLOC_SCRATCH_BYTES of it until the process exits.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -26,11 +26,14 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[RVE_NOALLOC_SCR
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 void* g_scratch_addr[kMaxDevices] = {};
+bool g_kernels_ready[kMaxDevices] = {};
 
-// Device address of the scratch array on the current device.  In host code
-// the array's name only stands for a host-side shadow, so its device address
-// is looked up once per device (with that device current).
-int scratch_address(void** out) {
+// Per-device set-up, done once per device with that device current and under
+// the lock: the device address of the scratch array (in host code the array's
+// name only stands for a host-side shadow, so the address is looked up with
+// cudaGetSymbolAddress) and the shared-memory attributes of the transform
+// kernels.  Later calls only read the cached address.
+int device_setup(void** out) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return RVE_ERR_CUDA;
   if (dev < 0 || dev >= kMaxDevices) return RVE_ERR_UNSUPPORTED;
@@ -39,6 +42,10 @@ int scratch_address(void** out) {
     void* p = nullptr;
     if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return RVE_ERR_CUDA;
     g_scratch_addr[dev] = p;
+  }
+  if (!g_kernels_ready[dev]) {
+    if (fft_kernels_init() != cudaSuccess) return RVE_ERR_CUDA;
+    g_kernels_ready[dev] = true;
   }
   *out = g_scratch_addr[dev];
   return RVE_OK;
@@ -76,9 +83,8 @@ extern "C" int rve_project_noalloc(int nx, int ny, int nz, const double* A, doub
   const size_t spec_bytes = sizeof(cplx<double>) * 9 * g.sstride;
   if (tw_bytes + spec_bytes > (size_t)RVE_NOALLOC_SCRATCH_BYTES) return RVE_ERR_NOMEM;
   void* base = nullptr;
-  int rc = scratch_address(&base);
+  int rc = device_setup(&base);
   if (rc) return rc;
-  if (fft_kernels_init() != cudaSuccess) return RVE_ERR_CUDA;
   cudaStream_t s = (cudaStream_t)stream;
   cplx<double>* tw = reinterpret_cast<cplx<double>*>(base);
   cplx<double>* spec = reinterpret_cast<cplx<double>*>(reinterpret_cast<char*>(base) + tw_bytes);

@@ -286,18 +286,30 @@ def rve_project(h, A, n, out=None):
 
 def rve_project_noalloc(shape, A, out, stream=None):
     """out = G : A (float64) without a handle and without any device
-    allocation; A and out are float64 CUDA tensors of 9*n values.  For
-    callers that cannot allocate device memory (the scratch lives in a fixed
-    array inside the library).  Enqueues on `stream` (default: torch's
-    current stream) and returns the status code."""
+    allocation, for callers that cannot allocate device memory (the scratch
+    lives in a fixed array inside the library).  A and out are contiguous
+    float64 CUDA tensors of 9*nx*ny*nz values on the current device (out may
+    be A).  Enqueues on `stream` (default: torch's current stream); raises
+    RVEError on a non-zero status."""
+    nx, ny, nz = (int(s) for s in shape)
     if not (_is_torch_cuda(A) and _is_torch_cuda(out)):
         raise ValueError("A and out must be CUDA tensors")
+    dev = torch.cuda.current_device()
+    for name, t in (("A", A), ("out", out)):
+        if t.dtype != torch.float64:
+            raise ValueError(f"{name} must be float64")
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+        if t.numel() != 9 * nx * ny * nz:
+            raise ValueError(f"{name} must hold 9*nx*ny*nz values")
+        if t.device.index != dev:
+            raise ValueError(f"{name} must be on the current device")
     if stream is None:
         stream = torch.cuda.current_stream().cuda_stream
-    nx, ny, nz = (int(s) for s in shape)
-    return lib.rve_project_noalloc(nx, ny, nz, C.c_void_p(A.data_ptr()),
+    code = lib.rve_project_noalloc(nx, ny, nz, C.c_void_p(A.data_ptr()),
                                    C.c_void_p(out.data_ptr()),
                                    C.c_void_p(int(stream)) if stream else None)
+    _check(code, None, "rve_project_noalloc")
 
 
 def rve_launch_count(h):
@@ -332,6 +344,12 @@ def rve_tuning(h):
 
 def rve_kernel_timing(h, family, enable=True):
     _check(lib.rve_kernel_timing(h, int(family), int(bool(enable))), h)
+
+
+def rve_set_wait_polls(h, polls):
+    """Failure-test setting: polls of a bounded device wait before it gives
+    up and the call reports RVE_ERR_TIMEOUT (default 1 << 20)."""
+    _check(lib.rve_set_wait_polls(h, int(polls)), h)
 
 
 def rve_kernel_time(h):
