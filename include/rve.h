@@ -417,31 +417,50 @@ int rve_launch_count(rve_t h, long long* count);
 int rve_kernel_timing(rve_t h, int family, int enable);
 int rve_kernel_time(rve_t h, double* total_ms, long long* launches);
 
+/* Failure-test setting (the paper has no counterpart): the number of polls a
+ * thread block's bounded wait on its own asynchronous (TMA) copies makes
+ * before it gives up, marks the solver state and lets the call end with
+ * RVE_ERR_TIMEOUT after rolling back to the committed state.  The default
+ * is 1 << 20 polls (far longer than a copy takes); 0 makes every first wait
+ * give up at once, which exercises the timeout path without a fault: after
+ * giving up a block still waits (bounded) for its copies to land before it
+ * touches the staged data again.  Applies to the handle's later calls.
+ * Returns RVE_OK, or RVE_ERR_INVALID for a null handle. */
+int rve_set_wait_polls(rve_t h, unsigned polls);
+
 /* ---------------------------------------------------------------------------
  * Allocation-free projection.  (The paper has no counterpart: this entry
  * point exists for callers of this library that cannot allocate device
- * memory -- code running while a CUDA graph is captured, plugins whose host
- * program owns all device allocations, real-time paths that must not
- * allocate.)
+ * memory -- plugins of a host program that owns every device allocation
+ * itself and hands out only its own buffers, and real-time paths where an
+ * allocation, with the implicit device synchronisation it may bring, is not
+ * allowed.)
  *
  * out = G : A in float64, the same operation as rve_project, without a
  * handle and without allocating anything: its scratch (the float64 half
  * spectrum, 9*nx*ny*(nz/2+1 rounded up to a multiple of 4) complex values,
  * plus the twiddle tables) lives in one fixed device array of
  * RVE_NOALLOC_SCRATCH_BYTES that the library reserves on every GPU that
- * loads it, for the life of the process.
+ * loads it, for the life of the process.  Odd and even sizes are accepted
+ * (even axes take G-hat = 0 at their Nyquist frequency, Appendix C).
  *  A, out : [9][n] float64 in device memory of the current device; out may
- *           equal A.  The caller owns both.
+ *           equal A.  The caller owns both; the library cannot check their
+ *           lengths, so each must hold 9*nx*ny*nz values.
  *  stream : cudaStream_t (NULL = legacy default stream).  The call only
  *           enqueues work; synchronise the stream before reading out.
- * The first call on a device looks up the array's device address (one
- * cudaGetSymbolAddress); make that first call before any stream capture.
+ * The first call on a device does the set-up for that device, with it
+ * current: one cudaGetSymbolAddress for the array's device address (cached
+ * for the process) and the kernels' shared-memory attributes.  Make that
+ * first call before any stream capture.  cudaDeviceReset invalidates the
+ * cached address: do not use this entry point after resetting a device.
  * All calls on a device share the one array and it keeps the last call's
- * contents: calls whose work overlaps on the GPU (different streams without
- * ordering, or concurrent host threads) race on it.
- * Errors: RVE_ERR_INVALID (null pointer, even or unsupported sizes),
+ * contents (each call rewrites everything it reads, so nothing is cleared):
+ * calls whose work overlaps on the GPU (different streams without ordering,
+ * or concurrent host threads) race on it.
+ * Errors: RVE_ERR_INVALID (null pointer, a size below 1 or above 2047, or
+ * a line too long for the transform kernels' shared-memory tiles),
  * RVE_ERR_NOMEM (the grid's scratch exceeds RVE_NOALLOC_SCRATCH_BYTES, e.g.
- * 63^3), RVE_ERR_CUDA. */
+ * 63^3), RVE_ERR_UNSUPPORTED (device ordinal 64 or above), RVE_ERR_CUDA. */
 #define RVE_NOALLOC_SCRATCH_BYTES (16u * 1024u * 1024u)
 int rve_project_noalloc(int nx, int ny, int nz, const double* A, double* out, void* stream);
 

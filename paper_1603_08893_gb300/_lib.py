@@ -101,6 +101,7 @@ _SIGS = {
     "rve_grid": (C.c_int, [_H, C.POINTER(C.c_int)]),
     "rve_model": (C.c_int, [_H]),
     "rve_kernel_timing": (C.c_int, [_H, C.c_int, C.c_int]),
+    "rve_set_wait_polls": (C.c_int, [_H, C.c_uint]),
     "rve_kernel_time": (C.c_int, [_H, C.POINTER(C.c_double),
                                   C.POINTER(C.c_longlong)]),
     "rve_project_noalloc": (C.c_int, [C.c_int, C.c_int, C.c_int, _P, _P, _P]),

@@ -51,7 +51,13 @@ struct GridGeom {
   // reference medium of the preconditioned CG (lambda0 / mu0 and
   // (lambda0 + mu0) / (lambda0 + 2 mu0), with mu0 scaled to 1)
   float pc_ell, pc_c;
+  // polls of a thread block's bounded wait on its own asynchronous copies
+  // before it gives up and reports a timeout (kDefaultWaitPolls; 0 in the
+  // failure tests: every first wait gives up at once)
+  unsigned wait_polls;
 };
+
+constexpr unsigned kDefaultWaitPolls = 1u << 20;
 
 // Axis lengths with compiled four-step kernels: X(N, N1, N2), N = N1 N2.
 #define RVE_FS_SIZES(X) \

@@ -418,9 +418,9 @@ __global__ void __launch_bounds__(FFT_THREADS, 3) k_zfwd4p(const ZfwdParams<floa
     const int nl = min(lz, nlines - l0);
     const int nvox = nl * N;
     const size_t v0 = (size_t)l0 * N;
-    if (!mbar_wait_bounded(&bar, parity, 1u << 20)) {
+    if (!mbar_wait_bounded(&bar, parity, P.g.wait_polls)) {
       atomicOr(&P.st->dev_timeout, 1);
-      mbar_wait_bounded(&bar, parity, 1u << 20);  // let the copies land before going on
+      mbar_wait_bounded(&bar, parity, kDefaultWaitPolls);  // let the copies land before going on
     }
     parity ^= 1u;
     const int pofs = soffs[narr];
@@ -604,9 +604,9 @@ __global__ void __launch_bounds__(FFT_THREADS, (Fs4Occ<R, N1, N2>::value))
       zinv_prefetch_tile<R>(P, next * lz, nl2, (size_t)next * lz * N, nl2 * N);
     }
     fs_lines<R, N1, N2, true, LM>(buf, tw2);
-    if (!mbar_wait_bounded(&bar, parity, 1u << 20)) {
+    if (!mbar_wait_bounded(&bar, parity, P.g.wait_polls)) {
       atomicOr(&P.st->dev_timeout, 1);
-      mbar_wait_bounded(&bar, parity, 1u << 20);  // let the copies land before going on
+      mbar_wait_bounded(&bar, parity, kDefaultWaitPolls);  // let the copies land before going on
     }
     parity ^= 1u;
     for (int i = threadIdx.x; i < nvox; i += blockDim.x) {

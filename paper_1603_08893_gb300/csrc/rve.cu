@@ -105,6 +105,7 @@ bool make_geom(int nx, int ny, int nz, GridGeom* g) {
   g->hzp = (g->hz + 3) & ~3;
   g->n = (size_t)nx * ny * nz;
   g->sstride = (size_t)nx * ny * g->hzp;
+  g->wait_polls = kDefaultWaitPolls;
   if (!factor_plan(nx, &g->px) || !factor_plan(ny, &g->py) || !factor_plan(nz, &g->pz)) return false;
   if (!factor_plan(nx, &g->pxs, false) || !factor_plan(ny, &g->pys, false) ||
       !factor_plan(nz, &g->pzs, false))
@@ -2146,6 +2147,12 @@ int rve_kernel_timing(rve_t h, int family, int enable) {
   h->timed.clear();
   h->solve_iters.clear();
   h->timing_family = enable ? family : -1;
+  return RVE_OK;
+}
+
+int rve_set_wait_polls(rve_t h, unsigned polls) {
+  if (!h) return RVE_ERR_INVALID;
+  h->g.wait_polls = polls;
   return RVE_OK;
 }
 

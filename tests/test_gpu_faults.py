@@ -71,3 +71,39 @@ def test_workspace_too_small_is_reported():
     code = _lib.lib.rve_create(ctypes.byref(h), *SHAPE, 0, 1, ph.ctypes.data_as(ctypes.c_void_p),
                                pp.ctypes.data_as(ctypes.c_void_p), None, ctypes.byref(o))
     assert code == -3 and not h.value
+
+
+def test_device_wait_timeout_is_reported_and_rolled_back():
+    """The last pass of the fused float32 CG iteration waits, bounded, on its
+    own TMA copies.  With the poll count set to 0 every first wait gives up
+    at once (the block then waits, bounded, for its copies to land, so
+    nothing faults and nothing hangs): the increment ends with
+    RVE_ERR_TIMEOUT and the committed state stays in place; with the default
+    poll count restored the same increment solves to the result of a handle
+    that never timed out."""
+    from paper_1603_08893_gb300 import rve_set_wait_polls
+
+    shape = (45, 45, 45)  # four-step lengths: the TMA-staged last z pass
+    rng = np.random.default_rng(32)
+    ph = (rng.uniform(size=shape) < 0.3).astype(np.uint8)
+    kw = dict(phase=ph, phase_params=synth.two_phase_params(20.0), precision="mixed")
+    steps = [synth.simple_shear(0.01), synth.simple_shear(0.02)]
+    r = RVE(shape, **kw)
+    r.set_macro_F(steps[0])
+    r.solve_increment()
+    F1 = r.get_F()
+    rve_set_wait_polls(r.h, 0)
+    r.set_macro_F(steps[1])
+    st = r.solve_increment(check=False)
+    assert st["status"] == _lib.RVE_ERR_TIMEOUT
+    assert np.array_equal(r.get_F(), F1)
+    rve_set_wait_polls(r.h, 1 << 20)
+    st = r.solve_increment(check=False)
+    assert st["status"] == 0
+    ref = RVE(shape, **kw)
+    for Fb in steps:
+        ref.set_macro_F(Fb)
+        ref.solve_increment()
+    assert np.array_equal(r.get_F(), ref.get_F())
+    r.close()
+    ref.close()
