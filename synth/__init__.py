@@ -128,18 +128,22 @@ def voronoi(n: int, ncells: int, rng: np.random.Generator,
     cell_phase[perm[:nhard]] = 1
     cell = np.empty((n, n, n), dtype=np.int32)
     coords = np.arange(n, dtype=np.float64)
-    yy, zz = np.meshgrid(coords, coords, indexing="ij")
+    # squared periodic offsets per seed and axis; d2 = (dx^2 + dy^2) + dz^2
+    # in the same order of operations for every voxel
+    dx2 = np.stack([_periodic_delta(coords - seeds[s, 0], n) ** 2 for s in range(ncells)])
+    dy2 = np.stack([_periodic_delta(coords - seeds[s, 1], n) ** 2 for s in range(ncells)])
+    dz2 = np.stack([_periodic_delta(coords - seeds[s, 2], n) ** 2 for s in range(ncells)])
+    best = np.empty((n, n))
+    d2 = np.empty((n, n))
+    better = np.empty((n, n), dtype=bool)
     for x in range(n):
-        best = np.full((n, n), np.inf)
+        best.fill(np.inf)
         arg = np.zeros((n, n), dtype=np.int32)
         for s in range(ncells):
-            dx = _periodic_delta(x - seeds[s, 0], n)
-            dy = _periodic_delta(yy - seeds[s, 1], n)
-            dz = _periodic_delta(zz - seeds[s, 2], n)
-            d2 = dx * dx + dy * dy + dz * dz
-            better = d2 < best
-            best = np.where(better, d2, best)
-            arg = np.where(better, s, arg)
+            np.add((dx2[s, x] + dy2[s])[:, None], dz2[s][None, :], out=d2)
+            np.less(d2, best, out=better)
+            np.copyto(best, d2, where=better)
+            arg[better] = s
         cell[x] = arg
     return cell_phase[cell], cell
 
