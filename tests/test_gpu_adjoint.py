@@ -4,7 +4,8 @@ respect to K, mu, tau_y0, H at the history of the last increment's start.
 
 Checks: against the oracle's adjoint gradient (1e-9), against central finite
 differences of GPU solves at 64 random voxels of a 31^3 lognormal cell
-(1e-5 relative to the largest gradient entry), mixed vs float64.
+(1e-5 relative per entry, with an absolute floor of 1e-8 of the largest
+entry for the round-off of the difference quotient), mixed vs float64.
 """
 import numpy as np
 import pytest
@@ -71,7 +72,9 @@ def test_adjoint_matches_finite_differences_31():
             vals.append(q.homogenized_P()[0, 1])
             q.close()
         fd = (vals[0] - vals[1]) / (2 * h)
-        assert abs(g[idx] - fd) < 1e-5 * gmax
+        # per entry: the difference quotient carries O((h/mu)^2) = 1e-8
+        # truncation and ~1e-17 / (2h) round-off of the two P-bar values
+        assert abs(g[idx] - fd) <= 1e-5 * abs(fd) + 1e-8 * gmax, (idx, g[idx], fd)
 
 
 def test_mixed_adjoint_matches_fp64():
@@ -129,7 +132,7 @@ def test_bulk_gradient_matches_oracle_and_fd():
             vals.append(q.homogenized_P()[0, 1])
             q.close()
         fd = (vals[0] - vals[1]) / (2 * h)
-        assert abs(gK[idx] - fd) < 1e-5 * np.abs(gK).max()
+        assert abs(gK[idx] - fd) <= 1e-5 * abs(fd) + 1e-8 * np.abs(gK).max(), (idx, gK[idx], fd)
 
 
 def test_autograd_bulk_and_shear():
