@@ -1,8 +1,10 @@
 """GPU parity of the finite-strain J2 path (Sec. 5) against the FP64 oracle.
 
 Tolerances: constitutive response and tangent 1e-12 of the largest entry;
-converged float64 schedules 1e-9 (relative 2-norm of F and P); the mixed
-path's P-bar 1e-8 of the float64 path.
+converged float64 schedules 1e-10 (relative 2-norm of F and P, the float64
+bar); the mixed path against the same tight oracle: fields F and P 1e-7
+(relative 2-norm), P-bar 1e-8, on a 9^3 cell (Stockham kernels) and a 15^3
+cell (15 = 3 x 5: the four-step kernels of the fused float32 iteration).
 
 Schedules are solved to tight tolerances (eta_NW = 1e-10, eta_CG = 1e-12):
 the two implementations may take different Newton paths to the same
@@ -60,15 +62,21 @@ def test_j2_constitutive_matches_oracle(amp):
 TIGHT = dict(tol_newton=1e-10, tol_cg=1e-12)
 
 
-@pytest.fixture(scope="module")
-def j2_schedule_oracle():
-    ph = _voronoi(9, 8)
+@pytest.fixture(scope="module", params=[9, 15])
+def j2_schedule_oracle(request):
+    """The ramp solved by the oracle to tight tolerances, and the P field of
+    the oracle's own solve at the benchmark's tolerances (eta_NW = 1e-5,
+    eta_CG = 1e-8): the Newton truncation error of that tolerance."""
+    ph = _voronoi(request.param, 8)
     prob = solver.J2Problem.from_phase(ph, PARAMS)
+    loose = solver.J2Problem.from_phase(ph, PARAMS)
     sched = synth.ramp(synth.simple_shear(0.012), 12)
     out = []
     for Fb in sched:
         prob.increment(Fb, cg_atol=1e-12, **TIGHT)
-        out.append((prob.F.copy(), prob.P.copy(), prob.mat.ep.copy()))
+        loose.increment(Fb, tol_newton=1e-5, tol_cg=1e-8)
+        out.append((prob.F.copy(), prob.P.copy(), prob.mat.ep.copy(), prob.homogenized_P(),
+                    loose.P.copy(), loose.homogenized_P()))
     return ph, sched, out
 
 
@@ -80,12 +88,41 @@ def test_j2_fp64_schedule_matches_oracle(j2_schedule_oracle, tangent):
     for k, Fb in enumerate(sched):
         r.set_macro_F(Fb)
         r.solve_increment(**TIGHT)
-        F_ref, P_ref, ep_ref = ref[k]
-        assert rel(r.get_F(), F_ref) < 1e-9, k
-        assert rel(r.get_P(), P_ref) < 1e-9, k
+        F_ref, P_ref, ep_ref = ref[k][:3]
+        assert rel(r.get_F(), F_ref) < 1e-10, k
+        assert rel(r.get_P(), P_ref) < 1e-10, k
         ep = r.get_history()[6].reshape(-1)
-        assert np.abs(ep - ep_ref).max() < 1e-9 * max(ep_ref.max(), 1e-3), k
+        assert np.abs(ep - ep_ref).max() < 1e-10 * max(ep_ref.max(), 1e-3), k
     assert ref[-1][2].max() > 1e-3  # the schedule does reach the plastic range
+    r.close()
+
+
+@pytest.mark.parametrize("tol_newton", [1e-10, 1e-5])
+def test_j2_mixed_schedule_matches_tight_oracle(j2_schedule_oracle, tol_newton):
+    """Mixed precision (float32 CG operator with the stored SYM45 tangent,
+    float64 residual and return map) along the whole ramp, against the
+    tightly converged float64 oracle, at a tight Newton tolerance and at the
+    benchmark's (1e-5): the history carries each increment's error forward,
+    so the bar holds over the path, not only per increment.  F meets 1e-7
+    at both tolerances; P and P-bar meet 1e-7 and 1e-8 at the tight one,
+    and at eta_NW = 1e-5 stay within twice the oracle's own distance from
+    its tight solution at that tolerance (Newton truncation, the same in
+    float64: the last update is only below 1e-5 of ||F||, which is mostly
+    the identity, and around the yield point the oracle's own P-bar at
+    that tolerance is ~1e-6 away from the tight one)."""
+    ph, sched, ref = j2_schedule_oracle
+    r = RVE(ph.shape, model="j2", phase=ph, phase_params=PARAMS, precision="mixed",
+            cg_atol=1e-12)
+    for k, Fb in enumerate(sched):
+        r.set_macro_F(Fb)
+        r.solve_increment(tol_newton, 1e-8)
+        F_ref, P_ref, _, pb_ref, P_loose, pb_loose = ref[k]
+        assert rel(r.get_F(), F_ref) < 1e-7, k
+        tight = tol_newton < 1e-9
+        bar = 1e-7 if tight else max(1e-7, 2 * rel(P_loose, P_ref))
+        assert rel(r.get_P(), P_ref) < bar, k
+        bar = 1e-8 if tight else max(1e-8, 2 * maxrel(pb_loose, pb_ref))
+        assert maxrel(r.homogenized_P(), pb_ref) < bar, k
     r.close()
 
 
