@@ -25,6 +25,7 @@ import argparse
 import json
 import os
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -80,11 +81,10 @@ class ClockSampler:
     def __init__(self, gpu_index=0):
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        self.path = os.path.join(tempfile.mkdtemp(prefix="rve_clocks_"), "clocks.csv")
 
     def start(self):
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
@@ -210,31 +210,97 @@ def kernel_profile(RVE, cfg, torch, families, steps=1):
     return res
 
 
-def cpu_baseline_sample(cfg, iters=4):
-    """The FP64 oracle, as it stands, on a bounded sample of the workload:
-    `iters` CG iterations of the first increment's predictor solve."""
-    from oracle import solver as osolver
-    from oracle import tensor as otensor
-    prob = osolver.SVKProblem.from_phase(cfg["phase"], cfg["phase_params"])
-    t0 = time.perf_counter()
-    _, K4 = prob.constitutive(prob.F)
-    t_const = time.perf_counter() - t0
-    op = osolver.tangent_operator(K4)
-    dFbar = otensor.uniform(cfg["schedule"][0] - np.eye(3), prob.shape)
-    b = -op(dFbar)
-    t0 = time.perf_counter()
+def host_cores():
     try:
-        osolver.cg(op, b, cfg["tol_cg"], maxiter=iters)
-    except osolver.SolverError:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:  # pragma: no cover
+        return os.cpu_count() or 1
+
+
+def cpu_model():
+    """CPU model name of the host (x86 'model name', or lscpu's 'Model name'
+    on Arm hosts whose /proc/cpuinfo has none)."""
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
         pass
-    t_cg = time.perf_counter() - t0
-    n = int(np.prod(cfg["shape"]))
-    return dict(value=n * iters / t_cg, unit=UNIT, cores=1, kind="oracle",
-                sample=(f"{iters} CG iterations (operator G:(K:p) + vector updates) of the "
-                        f"first increment's predictor solve on the 125^3 cell, numpy FFT "
-                        f"backend, single thread; constitutive evaluation "
-                        f"({t_const:.1f} s) not counted"),
-                seconds=t_cg + t_const)
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.machine()
+
+
+class OracleSample:
+    """The FP64 oracle, as it stands, on the host cores: the scipy.fft
+    backend with one worker per core for its DFTs (its other steps are
+    numpy as written), the tangent of the first increment's predictor and
+    CG iterations of that predictor solve on the same cell."""
+
+    def __init__(self, cfg):
+        from oracle import fourier
+        from oracle import solver as osolver
+        from oracle import tensor as otensor
+        self.cores = host_cores()
+        self.cpu = cpu_model()
+        self.fourier, self.osolver = fourier, osolver
+        self.old = fourier.get_backend()
+        fourier.set_backend("scipy", workers=self.cores)
+        self.cfg = cfg
+        self.n = int(np.prod(cfg["shape"]))
+        prob = osolver.SVKProblem.from_phase(cfg["phase"], cfg["phase_params"])
+        t0 = time.perf_counter()
+        _, K4 = prob.constitutive(prob.F)
+        self.t_const = time.perf_counter() - t0
+        self.op = osolver.tangent_operator(K4)
+        self.b = -self.op(otensor.uniform(cfg["schedule"][0] - np.eye(3), prob.shape))
+
+    def iterate(self, k):
+        """Seconds for k CG iterations (operator G:(K:p) + vector updates)."""
+        t0 = time.perf_counter()
+        try:
+            self.osolver.cg(self.op, self.b, self.cfg["tol_cg"], maxiter=k)
+        except self.osolver.SolverError:
+            pass
+        return time.perf_counter() - t0
+
+    def close(self):
+        self.fourier.set_backend(self.old["name"], self.old["workers"])
+
+    def describe(self, iters, what):
+        return (f"{what} CG iterations of the first increment's predictor solve on the "
+                f"{self.cfg['shape'][0]}^3 cell, oracle with the scipy.fft backend on "
+                f"{self.cores} workers (DFTs; its other steps single-threaded numpy), "
+                f"{self.cpu}")
+
+
+def cpu_baseline_sample(cfg, gpu_cg_iters=None, gpu_newton_iters=None, iters=10):
+    """The oracle on a bounded sample of the workload (`iters` CG iterations
+    plus the constitutive evaluation they need), with the full run
+    extrapolated from the GPU run's CG and Newton counts (labelled as such:
+    the oracle's own counts differ slightly)."""
+    o = OracleSample(cfg)
+    try:
+        o.iterate(1)  # plans and page faults
+        t_cg = o.iterate(iters)
+    finally:
+        o.close()
+    out = dict(value=o.n * iters / t_cg, unit=UNIT, cores=o.cores, kind="oracle",
+               sample=o.describe(iters, iters) +
+               f"; one constitutive evaluation (tangent) {o.t_const:.1f} s",
+               cpu_model=o.cpu, seconds=t_cg + o.t_const)
+    if gpu_cg_iters:
+        out["extrapolated_full_run_s"] = round(
+            gpu_cg_iters * t_cg / iters + (gpu_newton_iters or 0) * o.t_const, 1)
+        out["extrapolation"] = ("per-iteration CG time x the GPU run's CG iterations + one "
+                                "constitutive evaluation per Newton iteration of the GPU run")
+    return out
 
 
 def reference_arm(args):
@@ -245,38 +311,26 @@ def reference_arm(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    from oracle import solver as osolver
-    from oracle import tensor as otensor
     cfg = workload()
-    prob = osolver.SVKProblem.from_phase(cfg["phase"], cfg["phase_params"])
-    _, K4 = prob.constitutive(prob.F)
-    op = osolver.tangent_operator(K4)
-    b = -op(otensor.uniform(cfg["schedule"][0] - np.eye(3), prob.shape))
-
-    def iterate(k):
-        try:
-            osolver.cg(op, b, cfg["tol_cg"], maxiter=k)
-        except osolver.SolverError:
-            pass
-
-    if args.warmup > 0:
-        iterate(args.warmup)
-    t0 = time.perf_counter()
-    iterate(args.steps)
-    dt = time.perf_counter() - t0
-    n = int(np.prod(cfg["shape"]))
-    v = n * args.steps / dt
-    sample = (f"{args.steps} CG iterations of the first increment's predictor solve on the "
-              f"125^3 cell (after {args.warmup} warm-up iterations), numpy FFT backend, "
-              f"single thread; constitutive evaluation and right-hand side untimed")
+    o = OracleSample(cfg)
+    try:
+        if args.warmup > 0:
+            o.iterate(args.warmup)
+        dt = o.iterate(args.steps)
+    finally:
+        o.close()
+    v = o.n * args.steps / dt
+    sample = (o.describe(args.steps, args.steps) +
+              f", after {args.warmup} warm-up iterations; constitutive evaluation and "
+              f"right-hand side untimed")
     out = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT,
            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": 1e3 * dt / max(args.steps, 1),
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
            "dtype": "f64", "data": "synthetic",
            "config": {"workload": cfg["workload"], "grid": 125},
-           "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                            "sample": sample},
+           "cpu_baseline": {"value": v, "unit": UNIT, "cores": o.cores, "kind": "oracle",
+                            "sample": sample, "cpu_model": o.cpu},
            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0,
                    "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
@@ -350,10 +404,20 @@ def bench_j2_315(args, torch, RVE):
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
     ep = r.get_history()[6]
-    _line("j2_315_voronoi_shear_mixed", METRIC, n * cg / (ms / 1e3), UNIT, dtype="f32/f64",
+    value = n * cg / (ms / 1e3)
+    # algorithmic bytes of one float32 CG iteration with the stored SYM45
+    # tangent: the first pass reads 45 tangent reals instead of F and phase
+    spec = 9 * 2 * 4.0 * (cfg["shape"][2] // 2 + 1) / cfg["shape"][2]
+    b_iter = (9 * 4 * 5 + 45 * 4 + spec) + 3 * 2 * spec + (spec + 9 * 4 * 2)
+    peak, peak_kind = load_peaks()
+    _line("j2_315_voronoi_shear_mixed", METRIC, value, UNIT, dtype="f32/f64",
           increments=steps, substeps=subs, cuts=cuts, cg_iters=cg, newton_iters=newton,
           solve_ms=ms, pbar_xy=float(r.homogenized_P()[0, 1]), max_eps_p=float(ep.max()),
-          plastic_fraction=float((ep > 0).mean()))
+          plastic_fraction=float((ep > 0).mean()),
+          cg_iteration_bytes_per_voxel=round(b_iter, 1),
+          hbm_frac_whole_step=round(value * b_iter / 1e9 / peak, 4), peak_kind=peak_kind,
+          note="hbm_frac_whole_step counts only CG-iteration bytes against the time of "
+               "whole increments (return maps, residuals and cut attempts included)")
     r.close()
 
 
@@ -671,7 +735,21 @@ def main():
                     "traffic": NCU_TRAFFIC_BYTES.get(fam), "peak_kind": peak_kind,
                     "algorithmic_bytes_per_launch": bpl,
                     "avg_launch_ms": prof[fam]["avg_ms"]}
-        cpu = None if args.no_cpu_baseline else cpu_baseline_sample(cfg)
+            # every family against the same peak, and the whole five-pass
+            # iteration (algorithmic bytes of one iteration / its kernel time)
+            per = {}
+            tot_b = tot_ms = 0.0
+            for f, v in prof.items():
+                b_f = family_bytes_per_voxel(cfg["shape"][2], f) * n
+                per[f] = round(b_f / (v["avg_ms"] / 1e3) / 1e9 / peak, 4)
+                tot_b += b_f
+                tot_ms += v["avg_ms"]
+            roof["per_family_frac"] = per
+            roof["iteration"] = {"bytes": tot_b, "ms": round(tot_ms, 5),
+                                 "achieved": round(tot_b / (tot_ms / 1e3) / 1e9, 1),
+                                 "frac": round(tot_b / (tot_ms / 1e3) / 1e9 / peak, 4)}
+        cpu = (None if args.no_cpu_baseline else
+               cpu_baseline_sample(cfg, mixed["cg"], mixed["newton"]))
         result = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup,
@@ -695,7 +773,9 @@ def main():
             "roofline": roof,
             "kernel_profile_ms": ({k: round(v["avg_ms"], 5) for k, v in prof.items()}
                                   if prof else None),
-            "cpu_baseline": ({k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")}
+            "cpu_baseline": ({k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample",
+                                                  "cpu_model", "extrapolated_full_run_s",
+                                                  "extrapolation") if k in cpu}
                              if cpu else None),
             "e2e": {"value": u_e2e / t_e2e, "unit": UNIT, "h2d_bytes_per_step": 72,
                     "d2h_bytes_per_step": 9 * n * 8 + 72},
