@@ -14,10 +14,18 @@
 // two-point butterfly; other primes use a direct sum, one output per thread.
 // Stages alternate between two shared-memory buffers.
 #pragma once
+#include <type_traits>
+
 #include "common.cuh"
 #include "dfloat.cuh"
 
 #define RVE_MAX_STAGES 16
+// Threads per block of every kernel that runs the four-step line DFTs below;
+// their work loops stride by this constant, not by blockDim.x, so that the
+// compiler can fold the index arithmetic of each unrolled round.
+#ifndef FFT_THREADS
+#define FFT_THREADS 256
+#endif
 
 // Unsigned division by a run-time constant d through one 64-bit multiply:
 // q = (a * ceil(2^40 / d)) >> 40, exact whenever a * d < 2^40 (all indices
@@ -121,8 +129,88 @@ struct Roots {
   }
 };
 
-template <typename R, int RAD, bool INV>
+// Packed float pairs (one 64-bit register pair holding re, im) and the
+// sm_100+ two-wide float instructions on them.
+namespace f2 {
+typedef unsigned long long u64;
+RVE_DEV u64 pk(float lo, float hi) {
+  u64 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+RVE_DEV float2 up(u64 r) {
+  float2 f;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(f.x), "=f"(f.y) : "l"(r));
+  return f;
+}
+RVE_DEV u64 add(u64 a, u64 b) {
+  u64 d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+RVE_DEV u64 sub(u64 a, u64 b) {
+  u64 d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+RVE_DEV u64 fma(u64 a, u64 b, u64 c) {
+  u64 d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+RVE_DEV u64 mul(u64 a, u64 b) {
+  u64 d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+}  // namespace f2
+
+// The symmetric odd-length DFT on packed pairs: the sums and differences of
+// x_r, x_(R-r) and the accumulation over the roots take one two-wide
+// instruction per complex value instead of two.
+template <int RAD, bool INV>
+RVE_DEV void dft_odd_f2(cplx<float> (&v)[RAD], const float (&cs)[RAD], const float (&sn)[RAD]) {
+  constexpr int H = (RAD - 1) / 2;
+  f2::u64 a[H], b[H];
+#pragma unroll
+  for (int r = 1; r <= H; ++r) {
+    const f2::u64 p = f2::pk(v[r].x, v[r].y), q = f2::pk(v[RAD - r].x, v[RAD - r].y);
+    a[r - 1] = f2::add(p, q);
+    b[r - 1] = f2::sub(p, q);
+  }
+  const f2::u64 x0 = f2::pk(v[0].x, v[0].y);
+  f2::u64 s = x0;
+#pragma unroll
+  for (int r = 0; r < H; ++r) s = f2::add(s, a[r]);
+#pragma unroll
+  for (int k = 1; k <= H; ++k) {
+    f2::u64 re = x0, im;
+#pragma unroll
+    for (int r = 1; r <= H; ++r) {
+      const int m = (r * k) % RAD;
+      re = f2::fma(f2::pk(cs[m], cs[m]), a[r - 1], re);
+      im = (r == 1) ? f2::mul(f2::pk(sn[m], sn[m]), b[r - 1])
+                    : f2::fma(f2::pk(sn[m], sn[m]), b[r - 1], im);
+    }
+    const float2 e = f2::up(re), o = f2::up(im);
+    if (!INV) {
+      v[k] = {e.x + o.y, e.y - o.x};
+      v[RAD - k] = {e.x - o.y, e.y + o.x};
+    } else {
+      v[k] = {e.x - o.y, e.y + o.x};
+      v[RAD - k] = {e.x + o.y, e.y - o.x};
+    }
+  }
+  const float2 s0 = f2::up(s);
+  v[0] = {s0.x, s0.y};
+}
+
+template <typename R, int RAD, bool INV, bool PK = true>
 RVE_DEV void dft_odd(cplx<R> (&v)[RAD], const R (&cs)[RAD], const R (&sn)[RAD]) {
+  if constexpr (PK && std::is_same<R, float>::value) {
+    dft_odd_f2<RAD, INV>(v, cs, sn);
+    return;
+  }
   constexpr int H = (RAD - 1) / 2;
   cplx<R> a[H], b[H];
 #pragma unroll
@@ -208,7 +296,7 @@ RVE_DEV void stage_pp(const cplx<R>* __restrict__ src, cplx<R>* __restrict__ dst
 
 // R-point DFT with compile-time roots (cs[m] = cos(2 pi m/R), sn[m] =
 // sin(2 pi m/R); the forward transform multiplies by exp(-2 pi i m/R)).
-template <typename R, int RAD, bool INV>
+template <typename R, int RAD, bool INV, bool PK = true>
 RVE_DEV void dft_const(cplx<R> (&v)[RAD]) {
   constexpr Roots<RAD> T{};
   R cs[RAD], sn[RAD];
@@ -217,7 +305,7 @@ RVE_DEV void dft_const(cplx<R> (&v)[RAD]) {
     cs[m] = (R)T.c[m];
     sn[m] = (R)T.s[m];
   }
-  dft_odd<R, RAD, INV>(v, cs, sn);
+  dft_odd<R, RAD, INV, PK>(v, cs, sn);
 }
 
 constexpr int smallest_factor(int m) {
@@ -226,14 +314,14 @@ constexpr int smallest_factor(int m) {
   return m;
 }
 
-template <typename R, int M, bool INV>
+template <typename R, int M, bool INV, bool PK = true>
 RVE_DEV void dft_reg(cplx<R> (&v)[M]);
 
 // M = R1 R2 point DFT in registers, natural order in and out, by one
 // Cooley-Tukey split: with r = R2 a + b and k = k1 + R1 k2,
 //   X_k = sum_b w_R2^(b k2) [w_M^(b k1) sum_a w_R1^(a k1) x_(R2 a + b)]
 // (w_M = exp(-2 pi i / M) forward, its conjugate inverse).
-template <typename R, int R1, int R2, bool INV>
+template <typename R, int R1, int R2, bool INV, bool PK = true>
 RVE_DEV void dft_split(cplx<R> (&v)[R1 * R2]) {
   constexpr int M = R1 * R2;
   constexpr Roots<M> T{};
@@ -242,7 +330,7 @@ RVE_DEV void dft_split(cplx<R> (&v)[R1 * R2]) {
     cplx<R> t[R1];
 #pragma unroll
     for (int a = 0; a < R1; ++a) t[a] = v[R2 * a + b];
-    dft_reg<R, R1, INV>(t);
+    dft_reg<R, R1, INV, PK>(t);
 #pragma unroll
     for (int k1 = 0; k1 < R1; ++k1) {
       cplx<R> y = t[k1];
@@ -260,7 +348,7 @@ RVE_DEV void dft_split(cplx<R> (&v)[R1 * R2]) {
     cplx<R> t[R2];
 #pragma unroll
     for (int b = 0; b < R2; ++b) t[b] = v[R2 * k1 + b];
-    dft_reg<R, R2, INV>(t);
+    dft_reg<R, R2, INV, PK>(t);
 #pragma unroll
     for (int k2 = 0; k2 < R2; ++k2) o[k1 + R1 * k2] = t[k2];
   }
@@ -270,7 +358,7 @@ RVE_DEV void dft_split(cplx<R> (&v)[R1 * R2]) {
 
 // M-point DFT in registers: the two-point butterfly, the symmetric form for
 // an odd prime, otherwise split off the smallest prime factor.
-template <typename R, int M, bool INV>
+template <typename R, int M, bool INV, bool PK>
 RVE_DEV void dft_reg(cplx<R> (&v)[M]) {
   if constexpr (M == 1) {
     return;
@@ -279,9 +367,9 @@ RVE_DEV void dft_reg(cplx<R> (&v)[M]) {
     v[0] = c_add(a, v[1]);
     v[1] = c_sub(a, v[1]);
   } else if constexpr (smallest_factor(M) == M) {
-    dft_const<R, M, INV>(v);
+    dft_const<R, M, INV, PK>(v);
   } else {
-    dft_split<R, smallest_factor(M), M / smallest_factor(M), INV>(v);
+    dft_split<R, smallest_factor(M), M / smallest_factor(M), INV, PK>(v);
   }
 }
 
@@ -495,7 +583,7 @@ RVE_DEV int fs_pos(int k) { return N2 * (k % N1) + k / N1; }
 // tw2[n2 N1 + k1] = tw[n2 k1] (tw[k] = exp(-2 pi i k / N)), built by the block
 template <typename R, int N1, int N2>
 RVE_DEV void fs_twiddles(cplx<R>* tw2, const cplx<R>* tw) {
-  for (int j = threadIdx.x; j < N1 * N2; j += blockDim.x) {
+  for (int j = threadIdx.x; j < N1 * N2; j += FFT_THREADS) {
     const int n2 = j / N1, k1 = j - (j / N1) * N1;
     tw2[j] = tw[n2 * k1];
   }
@@ -504,7 +592,7 @@ RVE_DEV void fs_twiddles(cplx<R>* tw2, const cplx<R>* tw) {
 template <typename R, int N1, int N2, bool INV, typename LM>
 RVE_DEV void fs_phase_a(cplx<R>* buf, const cplx<R>* tw2) {
   constexpr int total = LM::L * N2;
-  for (int i = threadIdx.x; i < total; i += blockDim.x) {
+  for (int i = threadIdx.x; i < total; i += FFT_THREADS) {
     const int n2 = i / LM::L;
     const int l = i - n2 * LM::L;
     cplx<R>* line = buf + LM::base(l) + n2 * LM::ES;
@@ -526,17 +614,17 @@ RVE_DEV void fs_phase_a(cplx<R>* buf, const cplx<R>* tw2) {
   }
 }
 
-template <typename R, int N1, int N2, bool INV, typename LM>
+template <typename R, int N1, int N2, bool INV, typename LM, bool PK = true>
 RVE_DEV void fs_phase_b(cplx<R>* buf) {
   constexpr int total = LM::L * N1;
-  for (int i = threadIdx.x; i < total; i += blockDim.x) {
+  for (int i = threadIdx.x; i < total; i += FFT_THREADS) {
     const int k1 = i / LM::L;
     const int l = i - k1 * LM::L;
     cplx<R>* line = buf + LM::base(l) + N2 * k1 * LM::ES;
     cplx<R> u[N2];
 #pragma unroll
     for (int j = 0; j < N2; ++j) u[j] = line[j * LM::ES];
-    dft_reg<R, N2, INV>(u);
+    dft_reg<R, N2, INV, PK>(u);
 #pragma unroll
     for (int j = 0; j < N2; ++j) line[j * LM::ES] = u[j];
   }
@@ -575,10 +663,10 @@ struct GLine {
 };
 
 // forward phase A: natural order from global, result to shared memory
-template <typename R, int N1, int N2, typename LM, typename GL>
+template <typename R, int N1, int N2, typename LM, typename GL, bool PK = true>
 RVE_DEV void fs_phase_a_g2s(cplx<R>* buf, const cplx<R>* tw2, const GL& gl) {
   constexpr int total = LM::L * N2;
-  for (int i = threadIdx.x; i < total; i += blockDim.x) {
+  for (int i = threadIdx.x; i < total; i += FFT_THREADS) {
     const int n2 = i / LM::L;
     const int l = i - n2 * LM::L;
     const GLine<R> g = gl(l);
@@ -586,7 +674,7 @@ RVE_DEV void fs_phase_a_g2s(cplx<R>* buf, const cplx<R>* tw2, const GL& gl) {
 #pragma unroll
     for (int m = 0; m < N1; ++m)
       v[m] = g.rd ? g.p[(size_t)(N2 * m + n2) * g.stride] : cplx<R>{R(0), R(0)};
-    dft_reg<R, N1, false>(v);
+    dft_reg<R, N1, false, PK>(v);
     if (n2 != 0) {
       const cplx<R>* w = tw2 + n2 * N1;
 #pragma unroll
@@ -602,7 +690,7 @@ RVE_DEV void fs_phase_a_g2s(cplx<R>* buf, const cplx<R>* tw2, const GL& gl) {
 template <typename R, int N1, int N2, typename LM, typename GL>
 RVE_DEV void fs_phase_b_s2g(const cplx<R>* buf, const GL& gl) {
   constexpr int total = LM::L * N1;
-  for (int i = threadIdx.x; i < total; i += blockDim.x) {
+  for (int i = threadIdx.x; i < total; i += FFT_THREADS) {
     const int k1 = i / LM::L;
     const int l = i - k1 * LM::L;
     const cplx<R>* line = buf + LM::base(l) + N2 * k1 * LM::ES;
@@ -622,7 +710,7 @@ RVE_DEV void fs_phase_b_s2g(const cplx<R>* buf, const GL& gl) {
 template <typename R, int N1, int N2, typename LM, typename GL>
 RVE_DEV void fs_phase_b_g2s(cplx<R>* buf, const GL& gl) {
   constexpr int total = LM::L * N1;
-  for (int i = threadIdx.x; i < total; i += blockDim.x) {
+  for (int i = threadIdx.x; i < total; i += FFT_THREADS) {
     const int k1 = i / LM::L;
     const int l = i - k1 * LM::L;
     const GLine<R> g = gl(l);
@@ -641,7 +729,7 @@ RVE_DEV void fs_phase_b_g2s(cplx<R>* buf, const GL& gl) {
 template <typename R, int N1, int N2, typename LM, typename GL>
 RVE_DEV void fs_phase_a_s2g(const cplx<R>* buf, const cplx<R>* tw2, const GL& gl) {
   constexpr int total = LM::L * N2;
-  for (int i = threadIdx.x; i < total; i += blockDim.x) {
+  for (int i = threadIdx.x; i < total; i += FFT_THREADS) {
     const int n2 = i / LM::L;
     const int l = i - n2 * LM::L;
     const cplx<R>* line = buf + LM::base(l) + n2 * LM::ES;

@@ -2,7 +2,9 @@
 #pragma once
 #include "kernels.h"
 
+#ifndef FFT_THREADS
 #define FFT_THREADS 256
+#endif
 // float kernels: three CTAs per SM (<= 85 registers); double: two (<= 128)
 #define FFT_BOUNDS(R) __launch_bounds__(FFT_THREADS, sizeof(R) == 4 ? 3 : 2)
 
@@ -203,9 +205,9 @@ RVE_DEV ZfwdScalars<R> zfwd_scalars(const ZfwdParams<R>& P) {
 // direction p = r + beta p (SRC_CGPX also applies the previous step
 // x += alpha p and accumulates p.(K:p)), or a uniform tensor; then the
 // tangent.  Every global load of the voxel is issued before its stores.
-template <typename R, int SRC, int TAN>
+template <typename R, int SRC, int TAN, typename A>
 RVE_DEV void zfwd_voxel(const ZfwdParams<R>& P, const ZfwdScalars<R>& sc, size_t v, R (&out)[9],
-                        double& pkp) {
+                        A& pkp) {
   const size_t n = P.g.n;
   TanPre<R> q;
   tangent_pre<R, TAN>(P.tan, v, n, q);
@@ -256,7 +258,7 @@ RVE_DEV void zfwd_voxel(const ZfwdParams<R>& P, const ZfwdScalars<R>& sc, size_t
     R sp = 0;
 #pragma unroll
     for (int c = 0; c < 9; ++c) sp = fma(in[c], out[c], sp);
-    pkp += (double)sp;
+    pkp += (A)sp;
   }
 }
 

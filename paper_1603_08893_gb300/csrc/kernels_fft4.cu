@@ -53,7 +53,7 @@ __global__ void __launch_bounds__(FFT_THREADS, (Fs4Occ<R, N1, N2>::value) + (N1 
     constexpr int EPC = 16 / sizeof(cplx<R>);
     constexpr int CPR = T / EPC;  // 16-byte chunks per row
     const int nch = ng * N * CPR;
-    for (int c = threadIdx.x; c < nch; c += blockDim.x) {
+    for (int c = threadIdx.x; c < nch; c += FFT_THREADS) {
       const int row = c / CPR;
       const int t = (c - row * CPR) * EPC;
       const bool ok = (k0 + t) < hzp;
@@ -106,15 +106,15 @@ __global__ void __launch_bounds__(FFT_THREADS, (Fs4Occ<R, N1, N2>::value))
   };
   fs_twiddles<R, N1, N2>(tw2, P.tw);
   __syncthreads();
-  fs_phase_a_g2s<R, N1, N2, LM>(buf, tw2, gl);
+  fs_phase_a_g2s<R, N1, N2, LM, decltype(gl), false>(buf, tw2, gl);
   __syncthreads();
-  fs_phase_b<R, N1, N2, false, LM>(buf);
+  fs_phase_b<R, N1, N2, false, LM, false>(buf);
   const R qy = signed_freq<R>(y, ny) / (R)ny;
   const R sc = (R)P.scale;
   // xi_x of each transposed position and xi_z of each kz of the tile
   R* qxs = reinterpret_cast<R*>(buf + 3 * N * T);  // [N]
   R* qzs = qxs + N;                                // [T]
-  for (int i = threadIdx.x; i < N + T; i += blockDim.x) {
+  for (int i = threadIdx.x; i < N + T; i += FFT_THREADS) {
     if (i < N) qxs[i] = signed_freq<R>(fs_freq<N1, N2>(i), N) / (R)N;
     else qzs[i - N] = (R)(k0 + i - N) / (R)P.g.nz;
   }
@@ -123,7 +123,7 @@ __global__ void __launch_bounds__(FFT_THREADS, (Fs4Occ<R, N1, N2>::value))
   // this kernel's x length is odd)
   const bool nyq_y = (ny % 2 == 0) && (2 * y == ny);
   const int kz_nyq = (P.g.nz % 2 == 0) ? P.g.nz / 2 : -1;
-  for (int i = threadIdx.x; i < N * T; i += blockDim.x) {
+  for (int i = threadIdx.x; i < N * T; i += FFT_THREADS) {
     const R qx = qxs[i / T];
     const R qz = qzs[i % T];
     const R q2 = qx * qx + qy * qy + qz * qz;
@@ -133,13 +133,48 @@ __global__ void __launch_bounds__(FFT_THREADS, (Fs4Occ<R, N1, N2>::value))
     const R sx = f * (qx * A0.x + qy * A1.x + qz * A2.x);
     const R sy = f * (qx * A0.y + qy * A1.y + qz * A2.y);
     buf[i] = {sx * qx, sy * qx};
-    buf[N * T + i] = {sx * qy, sy * qy};
-    buf[2 * N * T + i] = {sx * qz, sy * qz};
+    buf[N * T + i] = {sx, sy};
   }
   __syncthreads();
-  fs_phase_b<R, N1, N2, true, LM>(buf);
+  // Row j of the projected tensor is s xi_j with s = xi.A_i / |xi|^2, and
+  // xi_y, xi_z are constant along an x line: the inverse x transforms of
+  // components 1 and 2 are xi_y and xi_z times the one of s.  Two inverse
+  // transforms per tensor row instead of three.
+  using LM2 = FsLayout<T, N * T, 1, T, 2 * T>;
+  fs_phase_b<R, N1, N2, true, LM2, false>(buf);
   __syncthreads();
-  fs_phase_a_s2g<R, N1, N2, LM>(buf, tw2, gl);
+  constexpr int total = 2 * T * N2;
+  for (int i = threadIdx.x; i < total; i += FFT_THREADS) {
+    const int n2 = i / (2 * T);
+    const int l = i - n2 * (2 * T);
+    const cplx<R>* line = buf + LM2::base(l) + n2 * LM2::ES;
+    cplx<R> v[N1];
+#pragma unroll
+    for (int k1 = 0; k1 < N1; ++k1) v[k1] = line[k1 * N2 * LM2::ES];
+    if (n2 != 0) {
+      const cplx<R>* w = tw2 + n2 * N1;
+#pragma unroll
+      for (int k1 = 1; k1 < N1; ++k1) v[k1] = c_mulc(v[k1], w[k1]);
+    }
+    dft_reg<R, N1, true, false>(v);
+    const int t = l % T;
+    if (k0 + t < hz) {
+      if (l < T) {
+        cplx<R>* g = gbase + t;
+#pragma unroll
+        for (int m = 0; m < N1; ++m) g[(size_t)(N2 * m + n2) * rs] = v[m];
+      } else {
+        const R qz = qzs[t];
+        cplx<R>* g1 = gbase + (size_t)N * rs + t;
+        cplx<R>* g2 = gbase + (size_t)(2 * N) * rs + t;
+#pragma unroll
+        for (int m = 0; m < N1; ++m) {
+          g1[(size_t)(N2 * m + n2) * rs] = {qy * v[m].x, qy * v[m].y};
+          g2[(size_t)(N2 * m + n2) * rs] = {qz * v[m].x, qz * v[m].y};
+        }
+      }
+    }
+  }
 }
 
 // x pass of the preconditioned CG iteration: as k_fft_x4, with the
@@ -181,7 +216,7 @@ __global__ void __launch_bounds__(FFT_THREADS, 2) k_fft_x4_g0(const LineParams<R
   const R cc = (R)P.g.pc_c;
   R* qxs = reinterpret_cast<R*>(buf + 9 * N * T);  // [N]
   R* qzs = qxs + N;                                // [T]
-  for (int i = threadIdx.x; i < N + T; i += blockDim.x) {
+  for (int i = threadIdx.x; i < N + T; i += FFT_THREADS) {
     if (i < N) qxs[i] = signed_freq<R>(fs_freq<N1, N2>(i), N) / (R)N;
     else qzs[i - N] = (R)(k0 + i - N) / (R)P.g.nz;
   }
@@ -189,7 +224,7 @@ __global__ void __launch_bounds__(FFT_THREADS, 2) k_fft_x4_g0(const LineParams<R
   const bool nyq_y = (ny % 2 == 0) && (2 * y == ny);
   const int kz_nyq = (P.g.nz % 2 == 0) ? P.g.nz / 2 : -1;
   constexpr int NT = N * T;
-  for (int i = threadIdx.x; i < NT; i += blockDim.x) {
+  for (int i = threadIdx.x; i < NT; i += FFT_THREADS) {
     const R q[3] = {qxs[i / T], qy, qzs[i % T]};
     const R q2 = q[0] * q[0] + q[1] * q[1] + q[2] * q[2];
     const bool nyq = nyq_y || (k0 + i % T == kz_nyq);
@@ -229,7 +264,7 @@ RVE_DEV void zfwd_prefetch_tile(const ZfwdParams<R>& P, const ZfwdScalars<R>& sc
     const int nf = sc.first ? 18 : 36;
     const int narr = nf + (ph ? 1 : 0);
     const int lpa = (int)(((size_t)nvox * sizeof(R)) / 128) + 2;  // lines per array (bound)
-    for (int j = threadIdx.x; j < narr * lpa; j += blockDim.x) {
+    for (int j = threadIdx.x; j < narr * lpa; j += FFT_THREADS) {
       const int a = j / lpa, q = j - a * lpa;
       const char* lo;
       size_t len;
@@ -275,10 +310,11 @@ __global__ void __launch_bounds__(FFT_THREADS, (Fs4Occ<R, N1, N2>::value))
     const int nl = min(lz, nlines - l0);
     const int nvox = nl * N;
     const size_t v0 = (size_t)l0 * N;
-    for (int i = threadIdx.x; i < lz * N; i += blockDim.x) {
+    R tpk = 0;  // this tile's share of p.(K:p): a few voxels per thread
+    for (int i = threadIdx.x; i < lz * N; i += FFT_THREADS) {
       R out[9];
       if (i < nvox) {
-        zfwd_voxel<R, SRC, TAN>(P, sc, v0 + i, out, pkp);
+        zfwd_voxel<R, SRC, TAN>(P, sc, v0 + i, out, tpk);
       } else {
 #pragma unroll
         for (int c = 0; c < 9; ++c) out[c] = 0;
@@ -288,6 +324,7 @@ __global__ void __launch_bounds__(FFT_THREADS, (Fs4Occ<R, N1, N2>::value))
 #pragma unroll
       for (int k = 0; k < 5; ++k) e[k * lz] = {out[2 * k], (2 * k + 1 < 9) ? out[2 * k + 1] : R(0)};
     }
+    pkp += (double)tpk;
     __syncthreads();
     const int next = tile + gridDim.x;
     if (next < ntiles) {
@@ -298,7 +335,7 @@ __global__ void __launch_bounds__(FFT_THREADS, (Fs4Occ<R, N1, N2>::value))
     // half spectrum, two kz per thread (16-byte stores); with hz odd the
     // last pair's second value lands in the row padding as zero
     constexpr int hz2 = (hz + 1) / 2;
-    for (int i = threadIdx.x; i < 5 * lz * hz2; i += blockDim.x) {
+    for (int i = threadIdx.x; i < 5 * lz * hz2; i += FFT_THREADS) {
       const int rest = i / hz2;
       const int kz = 2 * (i - rest * hz2);
       const int k = rest / lz;
@@ -424,7 +461,7 @@ __global__ void __launch_bounds__(FFT_THREADS, 3) k_zfwd4p(const ZfwdParams<floa
     }
     parity ^= 1u;
     const int pofs = soffs[narr];
-    for (int i = threadIdx.x; i < lz * N; i += blockDim.x) {
+    for (int i = threadIdx.x; i < lz * N; i += FFT_THREADS) {
       R out[9];
       if (i < nvox) {
         const size_t v = v0 + i;
@@ -468,7 +505,7 @@ __global__ void __launch_bounds__(FFT_THREADS, 3) k_zfwd4p(const ZfwdParams<floa
     __syncthreads();  // staged copy consumed: refill it with the next tile
     if (threadIdx.x == 0 && tile + (int)gridDim.x < ntiles) issue(tile + gridDim.x);
     fs_lines<R, N1, N2, false, LM>(buf, tw2);
-    for (int i = threadIdx.x; i < 5 * lz * hz; i += blockDim.x) {
+    for (int i = threadIdx.x; i < 5 * lz * hz; i += FFT_THREADS) {
       const int rest = i / hz;
       const int kz = i - rest * hz;
       const int k = rest / lz;
@@ -500,7 +537,7 @@ RVE_DEV void zinv_prefetch_tile(const ZinvParams<R, R>& P, int l0, int nl, size_
   const size_t slen = (size_t)nl * hzp * sizeof(cplx<R>);
   const size_t rlen = (size_t)nvox * sizeof(R);
   const int lps = (int)(slen / 128) + 2, lpr = (int)(rlen / 128) + 2;
-  for (int j = threadIdx.x; j < 9 * (lps + lpr); j += blockDim.x) {
+  for (int j = threadIdx.x; j < 9 * (lps + lpr); j += FFT_THREADS) {
     const int c = j / (lps + lpr), q = j - c * (lps + lpr);
     const char* lo;
     size_t len, off;
@@ -577,24 +614,43 @@ __global__ void __launch_bounds__(FFT_THREADS, (Fs4Occ<R, N1, N2>::value))
     // full z spectrum of the packed lines z = a + i b, written transposed;
     // item = (component pair k, line li, kz pair); a pair's second kz may
     // lie in the row padding (hz odd), where nothing is read or written
-    const int totl = 5 * lz * hz2;
-    for (int i = threadIdx.x; i < totl; i += blockDim.x) {
-      const int rest = i / hz2;
-      const int kz = 2 * (i - rest * hz2);
-      const int k = rest / lz;
-      const int li = rest - k * lz;
-      float4 A = {0.f, 0.f, 0.f, 0.f}, B = {0.f, 0.f, 0.f, 0.f};
-      if (li < nl) {
-        const size_t o = (size_t)(l0 + li) * hzp + kz;
-        A = *reinterpret_cast<const float4*>(P.spec + (size_t)(2 * k) * ss + o);
-        if (2 * k + 1 < 9) B = *reinterpret_cast<const float4*>(P.spec + (size_t)(2 * k + 1) * ss + o);
+    // two rounds of items per batch: both rounds' spectrum loads are in
+    // flight before the first round's stores
+    constexpr int totl = 5 * lz * hz2;
+    constexpr int NR = (totl + FFT_THREADS - 1) / FFT_THREADS;
+#pragma unroll
+    for (int r0 = 0; r0 < NR; r0 += 2) {
+      float4 A[2], B[2];
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int i = threadIdx.x + (r0 + u) * FFT_THREADS;
+        const int rest = i / hz2;
+        const int kz = 2 * (i - rest * hz2);
+        const int k = rest / lz;
+        const int li = rest - k * lz;
+        A[u] = B[u] = float4{0.f, 0.f, 0.f, 0.f};
+        if (r0 + u < NR && i < totl && li < nl) {
+          const size_t o = (size_t)(l0 + li) * hzp + kz;
+          A[u] = *reinterpret_cast<const float4*>(P.spec + (size_t)(2 * k) * ss + o);
+          if (2 * k + 1 < 9) B[u] = *reinterpret_cast<const float4*>(P.spec + (size_t)(2 * k + 1) * ss + o);
+        }
       }
-      const int l = k * lz + li;
-      buf[fs_pos<N1, N2>(kz) * LP + l] = {A.x - B.y, A.y + B.x};
-      if (kz > 0) buf[fs_pos<N1, N2>(N - kz) * LP + l] = {A.x + B.y, B.x - A.y};
-      if (kz + 1 < hz) {
-        buf[fs_pos<N1, N2>(kz + 1) * LP + l] = {A.z - B.w, A.w + B.z};
-        buf[fs_pos<N1, N2>(N - kz - 1) * LP + l] = {A.z + B.w, B.z - A.w};
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int i = threadIdx.x + (r0 + u) * FFT_THREADS;
+        if (r0 + u >= NR || i >= totl) continue;
+        const int rest = i / hz2;
+        const int kz = 2 * (i - rest * hz2);
+        const int k = rest / lz;
+        const int li = rest - k * lz;
+        const int l = k * lz + li;
+        const float4 a = A[u], b = B[u];
+        buf[fs_pos<N1, N2>(kz) * LP + l] = {a.x - b.y, a.y + b.x};
+        if (kz > 0) buf[fs_pos<N1, N2>(N - kz) * LP + l] = {a.x + b.y, b.x - a.y};
+        if (kz + 1 < hz) {
+          buf[fs_pos<N1, N2>(kz + 1) * LP + l] = {a.z - b.w, a.w + b.z};
+          buf[fs_pos<N1, N2>(N - kz - 1) * LP + l] = {a.z + b.w, b.z - a.w};
+        }
       }
     }
     __syncthreads();
@@ -609,7 +665,8 @@ __global__ void __launch_bounds__(FFT_THREADS, (Fs4Occ<R, N1, N2>::value))
       mbar_wait_bounded(&bar, parity, kDefaultWaitPolls);  // let the copies land before going on
     }
     parity ^= 1u;
-    for (int i = threadIdx.x; i < nvox; i += blockDim.x) {
+    R tacc = 0;  // this tile's share of r.r: a few voxels per thread
+    for (int i = threadIdx.x; i < nvox; i += FFT_THREADS) {
       const int li = i / N;
       const cplx<R>* e = buf + (i - li * N) * LP + li;
       R out[9];
@@ -627,8 +684,9 @@ __global__ void __launch_bounds__(FFT_THREADS, (Fs4Occ<R, N1, N2>::value))
         s = fma(out[c], out[c], s);
       }
       if (mn_ell >= R(0)) s = mnorm_k0<R>(out, mn_ell);
-      acc += (double)s;
+      tacc += s;
     }
+    acc += (double)tacc;
     __syncthreads();  // buffer, r copy and rofs are refilled by the next tile
   }
   double v1[1] = {acc}, tot[1];
