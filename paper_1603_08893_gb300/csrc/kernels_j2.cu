@@ -398,87 +398,231 @@ __global__ void __launch_bounds__(J2_THREADS) k_j2_adjoint_grad(
 // ---------------------------------------------------------------------------
 // Adjoint through the history of a path of increments (reverse sweep): the
 // return map's derivatives with respect to the history h = (Cp^-1_00, _11,
-// _22, _01, _02, _12, eps_p), to F and to the parameters, by central
-// differences of one voxel's return map (step 1e-7; relative for the
-// parameters).
+// _22, _01, _02, _12, eps_p), to F and to the parameters (K, mu, tau_y0, H),
+// in closed form: every step of the return map linearised (the matrix
+// logarithm and exponential by Daleckii-Krein divided differences in the
+// eigenbasis of be, the radial return, the pull-backs with
+// d(F^-1) = -F^-1 dF F^-1), one directional derivative per unit direction.
 // ---------------------------------------------------------------------------
 
-// One voxel: P (row-major 9) and the new history (7) from F (row-major 9),
-// the history at the increment's start and the parameters (bulk modulus).
-RVE_DEV void j2_eval(const double (&Fv)[9], const double (&hs)[7], double Kb, double mu,
-                     double ty0, double H, double (&P)[9], double (&hn)[7]) {
-  double f[3][3], C[3][3];
+// The return map of one voxel and the pieces its linearisation needs.
+struct J2State {
+  double f[3][3], C[3][3], ep;  // F, committed Cp^-1 and eps_p
+  double K, mu, ty0, H;         // bulk and shear moduli, yield stress, hardening
+  double Q[3][3];               // eigenvectors of be (columns)
+  double f1[3][3];              // divided differences of ln at the eigenvalues of be
+  double tr, dev[3];            // trace and principal deviator of the trial log strain
+  double teq, dg, beta;
+  bool plastic;
+  double Fi[3][3];              // F^-1
+  double tau[3][3];             // Kirchhoff stress
+  double g1[3][3];              // divided differences of exp(2 x), x the elastic log strain
+  double bn[3][3];              // new elastic be = exp(2 eps_e)
+};
+
+// sinh(x)/x, 1 + x^2/6 near 0
+RVE_DEV double sinhc(double x) { return fabs(x) < 1e-8 ? 1.0 + x * x / 6.0 : sinh(x) / x; }
+
+RVE_DEV void j2_state(const double (&Fv)[9], const double (&hs)[7], double Kb, double mu,
+                      double ty0, double H, J2State& S) {
   for (int i = 0; i < 3; ++i)
-    for (int j = 0; j < 3; ++j) f[i][j] = Fv[3 * i + j];
-  C[0][0] = hs[0];
-  C[1][1] = hs[1];
-  C[2][2] = hs[2];
-  C[0][1] = C[1][0] = hs[3];
-  C[0][2] = C[2][0] = hs[4];
-  C[1][2] = C[2][1] = hs[5];
-  const double ep = hs[6];
+    for (int j = 0; j < 3; ++j) S.f[i][j] = Fv[3 * i + j];
+  S.C[0][0] = hs[0];
+  S.C[1][1] = hs[1];
+  S.C[2][2] = hs[2];
+  S.C[0][1] = S.C[1][0] = hs[3];
+  S.C[0][2] = S.C[2][0] = hs[4];
+  S.C[1][2] = S.C[2][1] = hs[5];
+  S.ep = hs[6];
+  S.K = Kb;
+  S.mu = mu;
+  S.ty0 = ty0;
+  S.H = H;
   double FC[3][3], be[3][3];
   for (int i = 0; i < 3; ++i)
-    for (int j = 0; j < 3; ++j) FC[i][j] = f[i][0] * C[0][j] + f[i][1] * C[1][j] + f[i][2] * C[2][j];
+    for (int j = 0; j < 3; ++j)
+      FC[i][j] = S.f[i][0] * S.C[0][j] + S.f[i][1] * S.C[1][j] + S.f[i][2] * S.C[2][j];
   for (int i = 0; i < 3; ++i)
-    for (int j = 0; j < 3; ++j) be[i][j] = FC[i][0] * f[j][0] + FC[i][1] * f[j][1] + FC[i][2] * f[j][2];
+    for (int j = 0; j < 3; ++j)
+      be[i][j] = FC[i][0] * S.f[j][0] + FC[i][1] * S.f[j][1] + FC[i][2] * S.f[j][2];
   for (int i = 0; i < 3; ++i)
     for (int j = i + 1; j < 3; ++j) be[i][j] = be[j][i] = 0.5 * (be[i][j] + be[j][i]);
-  double Q[3][3];
-  jacobi3(be, Q);
-  double eps[3];
-  for (int a = 0; a < 3; ++a) eps[a] = 0.5 * log(be[a][a]);
-  const double tr = eps[0] + eps[1] + eps[2];
-  double dev[3], sp[3];
+  jacobi3(be, S.Q);
+  double lam[3], eps[3];
   for (int a = 0; a < 3; ++a) {
-    dev[a] = eps[a] - tr / 3.0;
-    sp[a] = 2.0 * mu * dev[a];
+    lam[a] = be[a][a];
+    eps[a] = 0.5 * log(lam[a]);
   }
-  const double teq = sqrt(1.5 * (sp[0] * sp[0] + sp[1] * sp[1] + sp[2] * sp[2]));
-  const double phi = teq - (ty0 + H * ep);
-  const bool plastic = phi > -kYieldSurfaceTol * (ty0 + H * ep);
-  const double dg = plastic ? fmax(phi, 0.0) / (3.0 * mu + H) : 0.0;
-  const double beta = plastic ? 1.0 - 3.0 * mu * dg / teq : 1.0;
-  double taup[3];
-  for (int a = 0; a < 3; ++a) taup[a] = Kb * tr + beta * sp[a];
+  for (int a = 0; a < 3; ++a)
+    for (int c = 0; c < 3; ++c) S.f1[a][c] = dd_log(lam[a], lam[c]);
+  S.tr = eps[0] + eps[1] + eps[2];
+  double sp[3];
+  for (int a = 0; a < 3; ++a) {
+    S.dev[a] = eps[a] - S.tr / 3.0;
+    sp[a] = 2.0 * mu * S.dev[a];
+  }
+  S.teq = sqrt(1.5 * (sp[0] * sp[0] + sp[1] * sp[1] + sp[2] * sp[2]));
+  const double phi = S.teq - (ty0 + H * S.ep);
+  S.plastic = phi > -kYieldSurfaceTol * (ty0 + H * S.ep);
+  S.dg = S.plastic ? fmax(phi, 0.0) / (3.0 * mu + H) : 0.0;
+  S.beta = S.plastic ? 1.0 - 3.0 * mu * S.dg / (S.teq > 0.0 ? S.teq : 1.0) : 1.0;
+  const double (&f)[3][3] = S.f;
   const double det = f[0][0] * (f[1][1] * f[2][2] - f[1][2] * f[2][1]) -
                      f[0][1] * (f[1][0] * f[2][2] - f[1][2] * f[2][0]) +
                      f[0][2] * (f[1][0] * f[2][1] - f[1][1] * f[2][0]);
   const double id = 1.0 / det;
-  double Fi[3][3];
-  Fi[0][0] = (f[1][1] * f[2][2] - f[1][2] * f[2][1]) * id;
-  Fi[0][1] = (f[0][2] * f[2][1] - f[0][1] * f[2][2]) * id;
-  Fi[0][2] = (f[0][1] * f[1][2] - f[0][2] * f[1][1]) * id;
-  Fi[1][0] = (f[1][2] * f[2][0] - f[1][0] * f[2][2]) * id;
-  Fi[1][1] = (f[0][0] * f[2][2] - f[0][2] * f[2][0]) * id;
-  Fi[1][2] = (f[0][2] * f[1][0] - f[0][0] * f[1][2]) * id;
-  Fi[2][0] = (f[1][0] * f[2][1] - f[1][1] * f[2][0]) * id;
-  Fi[2][1] = (f[0][1] * f[2][0] - f[0][0] * f[2][1]) * id;
-  Fi[2][2] = (f[0][0] * f[1][1] - f[0][1] * f[1][0]) * id;
-  // P = Q diag(taup) Q^T F^-T ; G = F^-1 Q
-  double QF[3][3];  // (Q^T F^-T)_a j = sum_k Q_ka Fi_jk
+  S.Fi[0][0] = (f[1][1] * f[2][2] - f[1][2] * f[2][1]) * id;
+  S.Fi[0][1] = (f[0][2] * f[2][1] - f[0][1] * f[2][2]) * id;
+  S.Fi[0][2] = (f[0][1] * f[1][2] - f[0][2] * f[1][1]) * id;
+  S.Fi[1][0] = (f[1][2] * f[2][0] - f[1][0] * f[2][2]) * id;
+  S.Fi[1][1] = (f[0][0] * f[2][2] - f[0][2] * f[2][0]) * id;
+  S.Fi[1][2] = (f[0][2] * f[1][0] - f[0][0] * f[1][2]) * id;
+  S.Fi[2][0] = (f[1][0] * f[2][1] - f[1][1] * f[2][0]) * id;
+  S.Fi[2][1] = (f[0][1] * f[2][0] - f[0][0] * f[2][1]) * id;
+  S.Fi[2][2] = (f[0][0] * f[1][1] - f[0][1] * f[1][0]) * id;
+  double taup[3], x[3], e2[3];
+  for (int a = 0; a < 3; ++a) {
+    taup[a] = Kb * S.tr + S.beta * sp[a];
+    x[a] = S.tr / 3.0 + S.beta * S.dev[a];
+    e2[a] = exp(2.0 * x[a]);
+  }
   for (int a = 0; a < 3; ++a)
-    for (int j = 0; j < 3; ++j) QF[a][j] = Q[0][a] * Fi[j][0] + Q[1][a] * Fi[j][1] + Q[2][a] * Fi[j][2];
+    for (int c = 0; c < 3; ++c) S.g1[a][c] = 2.0 * exp(x[a] + x[c]) * sinhc(x[a] - x[c]);
   for (int i = 0; i < 3; ++i)
-    for (int j = 0; j < 3; ++j)
-      P[3 * i + j] = Q[i][0] * taup[0] * QF[0][j] + Q[i][1] * taup[1] * QF[1][j] +
-                     Q[i][2] * taup[2] * QF[2][j];
-  double bn[3], G[3][3], Cn[3][3];
-  for (int a = 0; a < 3; ++a) bn[a] = exp(2.0 * (tr / 3.0 + beta * dev[a]));
-  for (int i = 0; i < 3; ++i)
-    for (int a = 0; a < 3; ++a) G[i][a] = Fi[i][0] * Q[0][a] + Fi[i][1] * Q[1][a] + Fi[i][2] * Q[2][a];
-  for (int i = 0; i < 3; ++i)
-    for (int j = 0; j < 3; ++j) Cn[i][j] = G[i][0] * bn[0] * G[j][0] + G[i][1] * bn[1] * G[j][1] + G[i][2] * bn[2] * G[j][2];
-  hn[0] = Cn[0][0];
-  hn[1] = Cn[1][1];
-  hn[2] = Cn[2][2];
-  hn[3] = 0.5 * (Cn[0][1] + Cn[1][0]);
-  hn[4] = 0.5 * (Cn[0][2] + Cn[2][0]);
-  hn[5] = 0.5 * (Cn[1][2] + Cn[2][1]);
-  hn[6] = ep + dg;
+    for (int j = 0; j < 3; ++j) {
+      double t = 0.0, b = 0.0;
+      for (int a = 0; a < 3; ++a) {
+        t += S.Q[i][a] * taup[a] * S.Q[j][a];
+        b += S.Q[i][a] * e2[a] * S.Q[j][a];
+      }
+      S.tau[i][j] = t;
+      S.bn[i][j] = b;
+    }
 }
 
-constexpr double kPathStep = 1e-7;
+// M <- Q (W o (Q^T A Q)) Q^T: a function's derivative in the eigenbasis Q
+// with divided differences W
+RVE_DEV void eig_apply(const double (&Q)[3][3], const double (&W)[3][3], const double (&A)[3][3],
+                       double (&M)[3][3]) {
+  double T[3][3], U[3][3];
+  for (int a = 0; a < 3; ++a)
+    for (int j = 0; j < 3; ++j) T[a][j] = Q[0][a] * A[0][j] + Q[1][a] * A[1][j] + Q[2][a] * A[2][j];
+  for (int a = 0; a < 3; ++a)
+    for (int c = 0; c < 3; ++c)
+      U[a][c] = W[a][c] * (T[a][0] * Q[0][c] + T[a][1] * Q[1][c] + T[a][2] * Q[2][c]);
+  for (int i = 0; i < 3; ++i)
+    for (int c = 0; c < 3; ++c) T[i][c] = Q[i][0] * U[0][c] + Q[i][1] * U[1][c] + Q[i][2] * U[2][c];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) M[i][j] = T[i][0] * Q[j][0] + T[i][1] * Q[j][1] + T[i][2] * Q[j][2];
+}
+
+RVE_DEV void mm3(const double (&A)[3][3], const double (&B)[3][3], double (&C)[3][3]) {
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) C[i][j] = A[i][0] * B[0][j] + A[i][1] * B[1][j] + A[i][2] * B[2][j];
+}
+
+// A B^T
+RVE_DEV void mmt3(const double (&A)[3][3], const double (&B)[3][3], double (&C)[3][3]) {
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) C[i][j] = A[i][0] * B[j][0] + A[i][1] * B[j][1] + A[i][2] * B[j][2];
+}
+
+// Directional derivative of the return map at S in the direction (dF, dC
+// (symmetric), dep, dp = (dK, dmu, dtau_y0, dH)): dP (row-major 9) and the
+// new history's dh (7).
+RVE_DEV void j2_dir(const J2State& S, const double (&dF)[3][3], const double (&dC)[3][3],
+                    double dep, const double (&dp)[4], double (&dP)[9], double (&dh)[7]) {
+  const double dK = dp[0], dmu = dp[1], dty = dp[2], dH = dp[3];
+  const double I[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+  // d(be) = dF C F^T + F C dF^T + F dC F^T
+  double A[3][3], B[3][3], dbe[3][3];
+  mm3(dF, S.C, A);
+  mmt3(A, S.f, dbe);
+  mm3(S.f, dC, B);
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      const double fcdf = (S.f[i][0] * S.C[0][0] + S.f[i][1] * S.C[1][0] + S.f[i][2] * S.C[2][0]) * dF[j][0] +
+                          (S.f[i][0] * S.C[0][1] + S.f[i][1] * S.C[1][1] + S.f[i][2] * S.C[2][1]) * dF[j][1] +
+                          (S.f[i][0] * S.C[0][2] + S.f[i][1] * S.C[1][2] + S.f[i][2] * S.C[2][2]) * dF[j][2];
+      const double fdcf = B[i][0] * S.f[j][0] + B[i][1] * S.f[j][1] + B[i][2] * S.f[j][2];
+      dbe[i][j] += fcdf + fdcf;
+    }
+  // trial log strain: d(eps) = (1/2) Dln(be)[d(be)]
+  double hf1[3][3], deps[3][3];
+  for (int a = 0; a < 3; ++a)
+    for (int c = 0; c < 3; ++c) hf1[a][c] = 0.5 * S.f1[a][c];
+  eig_apply(S.Q, hf1, dbe, deps);
+  const double dtr = deps[0][0] + deps[1][1] + deps[2][2];
+  double Ed[3][3], dEd[3][3], s_tr[3][3], ds_tr[3][3];
+  double ssum = 0.0;
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      Ed[i][j] = S.Q[i][0] * S.dev[0] * S.Q[j][0] + S.Q[i][1] * S.dev[1] * S.Q[j][1] +
+                 S.Q[i][2] * S.dev[2] * S.Q[j][2];
+      dEd[i][j] = deps[i][j] - dtr * I[i][j] / 3.0;
+      s_tr[i][j] = 2.0 * S.mu * Ed[i][j];
+      ds_tr[i][j] = 2.0 * S.mu * dEd[i][j] + 2.0 * dmu * Ed[i][j];
+      ssum += s_tr[i][j] * ds_tr[i][j];
+    }
+  // radial return
+  const double den = 3.0 * S.mu + S.H;
+  const double tsafe = S.teq > 0.0 ? S.teq : 1.0;
+  const double dteq = S.plastic ? 1.5 * ssum / tsafe : 0.0;
+  const double dphi = dteq - dty - dH * S.ep - S.H * dep;
+  const double ddg = S.plastic ? (dphi - S.dg * (3.0 * dmu + dH)) / den : 0.0;
+  const double dbeta = S.plastic ? -3.0 * (dmu * S.dg + S.mu * ddg) / tsafe +
+                                       3.0 * S.mu * S.dg * dteq / (tsafe * tsafe)
+                                 : 0.0;
+  // stress and its pull-back: dP = d(tau) F^-T + tau d(F^-1)^T
+  double dtau[3][3], dFi[3][3], deps_e[3][3];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      dtau[i][j] = (dK * S.tr + S.K * dtr) * I[i][j] + dbeta * s_tr[i][j] + S.beta * ds_tr[i][j];
+      deps_e[i][j] = dtr * I[i][j] / 3.0 + dbeta * Ed[i][j] + S.beta * dEd[i][j];
+    }
+  mm3(S.Fi, dF, A);
+  mm3(A, S.Fi, dFi);
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) dFi[i][j] = -dFi[i][j];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j)
+      dP[3 * i + j] = dtau[i][0] * S.Fi[j][0] + dtau[i][1] * S.Fi[j][1] + dtau[i][2] * S.Fi[j][2] +
+                      S.tau[i][0] * dFi[j][0] + S.tau[i][1] * dFi[j][1] + S.tau[i][2] * dFi[j][2];
+  // new history: d(be_new) = Dexp2(eps_e)[d(eps_e)], Cp^-1 = F^-1 be_new F^-T
+  double dbn[3][3], T1[3][3], dCn[3][3];
+  eig_apply(S.Q, S.g1, deps_e, dbn);
+  mm3(dFi, S.bn, A);
+  mmt3(A, S.Fi, dCn);       // dF^-1 be F^-T
+  mm3(S.Fi, dbn, A);
+  mmt3(A, S.Fi, T1);        // F^-1 dbe F^-T
+  mm3(S.Fi, S.bn, A);
+  mmt3(A, dFi, B);          // F^-1 be dF^-T
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) dCn[i][j] += T1[i][j] + B[i][j];
+  dh[0] = dCn[0][0];
+  dh[1] = dCn[1][1];
+  dh[2] = dCn[2][2];
+  dh[3] = 0.5 * (dCn[0][1] + dCn[1][0]);
+  dh[4] = 0.5 * (dCn[0][2] + dCn[2][0]);
+  dh[5] = 0.5 * (dCn[1][2] + dCn[2][1]);
+  dh[6] = dep + ddg;
+}
+
+// unit direction k of the history h = (C00, C11, C22, C01, C02, C12, eps_p)
+RVE_DEV void hist_unit(int k, double (&dC)[3][3], double& dep) {
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) dC[i][j] = 0.0;
+  dep = 0.0;
+  switch (k) {
+    case 0: dC[0][0] = 1.0; break;
+    case 1: dC[1][1] = 1.0; break;
+    case 2: dC[2][2] = 1.0; break;
+    case 3: dC[0][1] = dC[1][0] = 1.0; break;
+    case 4: dC[0][2] = dC[2][0] = 1.0; break;
+    case 5: dC[1][2] = dC[2][1] = 1.0; break;
+    default: dep = 1.0; break;
+  }
+}
 
 // gF[c][v] = sum_k a_k dH_k/dF_c (the functional's sensitivity to F_m
 // through the history h_m)
@@ -497,17 +641,18 @@ __global__ void __launch_bounds__(J2_THREADS) k_j2_path_gF(const double* __restr
     }
     const double mu = mat.get(v, 1), ty0 = mat.get(v, 2), H = mat.get(v, 3);
     const double Kb = mat.get(v, 0) + 2.0 * mu / 3.0;
-    double Pp[9], Pm[9], hp[7], hm[7];
+    J2State S;
+    j2_state(Fv, h, Kb, mu, ty0, H, S);
+    const double zC[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+    const double zp[4] = {0, 0, 0, 0};
+    double dF[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}}, dP[9], dh[7];
     for (int c = 0; c < 9; ++c) {
-      const double f0 = Fv[c];
-      Fv[c] = f0 + kPathStep;
-      j2_eval(Fv, h, Kb, mu, ty0, H, Pp, hp);
-      Fv[c] = f0 - kPathStep;
-      j2_eval(Fv, h, Kb, mu, ty0, H, Pm, hm);
-      Fv[c] = f0;
+      dF[c / 3][c % 3] = 1.0;
+      j2_dir(S, dF, zC, 0.0, zp, dP, dh);
+      dF[c / 3][c % 3] = 0.0;
       double s = 0.0;
-      for (int k = 0; k < 7; ++k) s += av[k] * (hp[k] - hm[k]);
-      gF[(size_t)c * n + v] = s / (2.0 * kPathStep);
+      for (int k = 0; k < 7; ++k) s += av[k] * dh[k];
+      gF[(size_t)c * n + v] = s;
     }
   }
 }
@@ -531,36 +676,30 @@ __global__ void __launch_bounds__(J2_THREADS) k_j2_path_step(
       h[k] = hs[(size_t)k * n + v];
       av[k] = a_in ? a_in[(size_t)k * n + v] : 0.0;
     }
-    double p[4];
-    p[1] = mat.get(v, 1);
-    p[0] = mat.get(v, 0) + 2.0 * p[1] / 3.0;
-    p[2] = mat.get(v, 2);
-    p[3] = mat.get(v, 3);
-    double Pp[9], Pm[9], hp[7], hm[7];
+    const double mu = mat.get(v, 1);
+    J2State S;
+    j2_state(Fv, h, mat.get(v, 0) + 2.0 * mu / 3.0, mu, mat.get(v, 2), mat.get(v, 3), S);
+    const double zF[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+    double dC[3][3], dep, dP[9], dh[7];
+    double dp[4] = {0, 0, 0, 0};
     for (int k = 0; k < 7; ++k) {
-      const double h0 = h[k];
-      h[k] = h0 + kPathStep;
-      j2_eval(Fv, h, p[0], p[1], p[2], p[3], Pp, hp);
-      h[k] = h0 - kPathStep;
-      j2_eval(Fv, h, p[0], p[1], p[2], p[3], Pm, hm);
-      h[k] = h0;
+      hist_unit(k, dC, dep);
+      j2_dir(S, zF, dC, dep, dp, dP, dh);
       double s = 0.0;
-      for (int q = 0; q < 9; ++q) s += c[q] * (Pp[q] - Pm[q]);
-      for (int j = 0; j < 7; ++j) s += av[j] * (hp[j] - hm[j]);
-      a_out[(size_t)k * n + v] = s / (2.0 * kPathStep);
+      for (int q = 0; q < 9; ++q) s += c[q] * dP[q];
+      for (int j = 0; j < 7; ++j) s += av[j] * dh[j];
+      a_out[(size_t)k * n + v] = s;
     }
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) dC[i][j] = 0.0;
     for (int t = 0; t < 4; ++t) {
-      const double p0 = p[t];
-      const double st = kPathStep * fabs(p0);
-      p[t] = p0 + st;
-      j2_eval(Fv, h, p[0], p[1], p[2], p[3], Pp, hp);
-      p[t] = p0 - st;
-      j2_eval(Fv, h, p[0], p[1], p[2], p[3], Pm, hm);
-      p[t] = p0;
+      dp[t] = 1.0;
+      j2_dir(S, zF, dC, 0.0, dp, dP, dh);
+      dp[t] = 0.0;
       double s = 0.0;
-      for (int q = 0; q < 9; ++q) s += c[q] * (Pp[q] - Pm[q]);
-      for (int j = 0; j < 7; ++j) s += av[j] * (hp[j] - hm[j]);
-      g[(size_t)t * n + v] += s / (2.0 * st);
+      for (int q = 0; q < 9; ++q) s += c[q] * dP[q];
+      for (int j = 0; j < 7; ++j) s += av[j] * dh[j];
+      g[(size_t)t * n + v] += s;
     }
   }
 }

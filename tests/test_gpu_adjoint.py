@@ -260,7 +260,9 @@ def test_svk_adjoint_grad_params_equals_adjoint_grad():
 
 def test_j2_path_adjoint_matches_oracle():
     """Through the history of a loading-reversal-reloading path (reverse
-    sweep over the taped increments) against the oracle's reverse sweep."""
+    sweep over the taped increments, the return map's derivatives in closed
+    form) against the oracle's reverse sweep, to 1e-9 of the largest
+    parameter-weighted gradient entry."""
     shape, ph = _j2_cell()
     ramp = [synth.simple_shear(g) + np.diag([g / 2, 0.0, 0.0]) for g in (0.004, 0.008, -0.002, 0.006)]
     prob = solver.J2Problem.from_phase(ph, J2_PARAMS)
@@ -279,7 +281,7 @@ def test_j2_path_adjoint_matches_oracle():
             g1, _ = r.adjoint_grad_path(WXY, tol_cg=1e-13)
             ref1, _ = r.adjoint_grad_params(WXY, tol_cg=1e-13)
             th = np.moveaxis(J2_PARAMS[ph], -1, 0)
-            assert np.abs(th * (g1 - ref1)).max() < 1e-6 * np.abs(th * ref1).max()
+            assert np.abs(th * (g1 - ref1)).max() < 1e-9 * np.abs(th * ref1).max()
     assert r.tape_length() == len(ramp)
     before = (r.get_F(), r.get_P(), r.get_history(), r.get_K4())
     g, _ = r.adjoint_grad_path(WXY, tol_cg=1e-13)
@@ -289,8 +291,9 @@ def test_j2_path_adjoint_matches_oracle():
     ref = oadj.j2_path_grad_params(states, p[:, 0], p[:, 1], p[:, 2], p[:, 3], WXY, 1e-13, 1e-15)
     th = np.moveaxis(J2_PARAMS[ph], -1, 0)
     scale = np.abs(th * ref).max()
-    for q in range(4):
-        assert np.abs(th[q] * (g[q] - ref[q])).max() < 1e-6 * scale, q
+    err = [float(np.abs(th[q] * (g[q] - ref[q])).max() / scale) for q in range(4)]
+    print("path adjoint vs oracle (units of the largest th * dJ/dth):", err)
+    assert max(err) < 1e-9, err
     r.set_F(r.get_F())          # a new path starts: the tape is cleared
     assert r.tape_length() == 0
     r.close()
