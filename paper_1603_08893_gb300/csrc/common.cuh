@@ -135,13 +135,13 @@ RVE_DEV void block_sum(double (&v)[NV]) {
 // Writes this block's NV partial sums to partials[block*NV + k]; the block
 // that finishes last sums all partials in a fixed order (deterministic,
 // independent of which block is last) into total[k] and returns true.
+// The reduction over `nblk` thread blocks that call it with their index
+// `bid` (a batched launch runs several such groups, one per cell).
 template <int NV>
-RVE_DEV bool last_block_sum(double (&v)[NV], double* partials, unsigned int* counter,
-                            double (&total)[NV]) {
+RVE_DEV bool last_block_sum_of(double (&v)[NV], double* partials, unsigned int* counter,
+                               double (&total)[NV], unsigned int bid, unsigned int nblk) {
   __shared__ bool am_last;
   block_sum<NV>(v);
-  const unsigned int nblk = gridDim.x * gridDim.y * gridDim.z;
-  const unsigned int bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
   if (threadIdx.x == 0) {
 #pragma unroll
     for (int k = 0; k < NV; ++k) partials[(size_t)bid * NV + k] = v[k];
@@ -163,6 +163,14 @@ RVE_DEV bool last_block_sum(double (&v)[NV], double* partials, unsigned int* cou
   for (int k = 0; k < NV; ++k) total[k] = s[k];
   if (threadIdx.x == 0) *counter = 0u;
   return true;
+}
+
+template <int NV>
+RVE_DEV bool last_block_sum(double (&v)[NV], double* partials, unsigned int* counter,
+                            double (&total)[NV]) {
+  return last_block_sum_of<NV>(v, partials, counter, total,
+                               blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z),
+                               gridDim.x * gridDim.y * gridDim.z);
 }
 
 // ---------------------------------------------------------------------------

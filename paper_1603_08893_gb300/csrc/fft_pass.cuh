@@ -268,9 +268,10 @@ RVE_DEV void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];
 // p.Ap = p.G(K p) = (G p).(K p) = p.(K p) for compatible p (G is an
 // orthogonal projector), so alpha is known before the inverse transforms.
 template <typename R>
-RVE_DEV void zfwd_step_length(const ZfwdParams<R>& P, double pkp) {
+RVE_DEV void zfwd_step_length(const ZfwdParams<R>& P, double pkp, unsigned bid, unsigned nblk) {
   double v1[1] = {pkp}, tot[1];
-  if (last_block_sum<1>(v1, P.partials, &P.st->counter[SLOT_PAP], tot) && threadIdx.x == 0) {
+  if (last_block_sum_of<1>(v1, P.partials, &P.st->counter[SLOT_PAP], tot, bid, nblk) &&
+      threadIdx.x == 0) {
     SolverState* st = P.st;
     const double pap = tot[0];
     st->pAp = pap;

@@ -188,6 +188,24 @@ void launch_fft_x4(const GridGeom& g, double scale, cplx<float>* spec, const int
                    const cplx<float>* tw, cudaStream_t s, bool gamma0 = false);
 cudaError_t fft4_kernels_init();
 
+// Batched passes of the fused float32 CG iteration (kernels_fft4.cu) for
+// cells whose three axes all have four-step kernels of the batch sizes
+// (15, 21, 27, 33, 45, 63).  While a batch records on this host thread, the
+// four-step launchers store each launch (parameters, grid, shared memory)
+// in it instead of launching; fs4_batch_launch then runs each of the five
+// passes of one CG iteration for every recorded cell in ONE launch, every
+// cell's blocks doing exactly what its own launch would (same tiles, same
+// block count, same reductions), so results are bit-identical to solving
+// the cell alone.
+struct Fs4Batch;
+Fs4Batch* fs4_batch_new();
+void fs4_batch_free(Fs4Batch* b);
+bool fs4_batch_eligible(const GridGeom& g, bool mixed, int tan_mode, bool precond);
+void fs4_batch_record(Fs4Batch* b);  // nullptr ends recording
+int fs4_batch_cells(const Fs4Batch* b);
+cudaError_t fs4_batch_upload(Fs4Batch* b);  // device copies of the launch tables
+void fs4_batch_launch(const Fs4Batch* b, cudaStream_t s);
+
 // G : in in float-float arithmetic on the float32 pipe (float64 in and out):
 // out_mode OUT_PLAIN writes out64 = scale * G:in; OUT_RESID writes
 // r_out = scale * G:in (float32), x_out = 0 and initialises the CG state.

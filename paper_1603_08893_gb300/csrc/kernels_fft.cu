@@ -72,7 +72,7 @@ __global__ void FFT_BOUNDS(R) k_zfwd(const ZfwdParams<R> P) {
       P.spec[(size_t)(2 * k + 1) * ss + o] = {dy, -dx};
     }
   }
-  if (SRC == SRC_CGPX) zfwd_step_length<R>(P, pkp);
+  if (SRC == SRC_CGPX) zfwd_step_length<R>(P, pkp, blockIdx.x, gridDim.x);
 }
 
 // Complex DFT along y (forward or inverse) on tiles of (grp component-x

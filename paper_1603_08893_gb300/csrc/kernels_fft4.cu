@@ -6,6 +6,7 @@
 // is undone in the addressing of the global stores (forward y), loads
 // (inverse y) or of the projection (x pass).
 #include <algorithm>
+#include <vector>
 
 #include "fft_pass.cuh"
 
@@ -24,8 +25,7 @@ struct Fs4Occ {
 // memory (N2 = 25 loads per thread in flight), so the transposed
 // intermediate order never leaves shared memory.
 template <typename R, int N1, int N2, bool INV>
-__global__ void __launch_bounds__(FFT_THREADS, (Fs4Occ<R, N1, N2>::value) + (N1 * N2 <= 125 ? 1 : 0))
-    k_fft_y4(const LineParams<R> P) {
+RVE_DEV void fft_y4_tile(const LineParams<R>& P, const int tile) {
   constexpr int N = N1 * N2;
   constexpr int T = fs_y_t(), GRP = fs_y_grp(N);
   using LM = FsLayout<T, N * T, 1, T, GRP * T>;
@@ -36,7 +36,6 @@ __global__ void __launch_bounds__(FFT_THREADS, (Fs4Occ<R, N1, N2>::value) + (N1 
   const int hz = P.g.hz, hzp = P.g.hzp;  // kz extent (z axis), not this axis
   const int ngroups = 9 * P.g.nx;
   const int ntk = (hz + T - 1) / T;
-  const int tile = blockIdx.x;
   const int tg = (int)P.g.f_fsy_ntk.div((unsigned)tile);
   const int k0 = (tile - tg * ntk) * T, g0 = tg * GRP;
   const int ng = min(GRP, ngroups - g0);
@@ -76,12 +75,17 @@ __global__ void __launch_bounds__(FFT_THREADS, (Fs4Occ<R, N1, N2>::value) + (N1 
   }
 }
 
+template <typename R, int N1, int N2, bool INV>
+__global__ void __launch_bounds__(FFT_THREADS, (Fs4Occ<R, N1, N2>::value) + (N1 * N2 <= 125 ? 1 : 0))
+    k_fft_y4(const LineParams<R> P) {
+  fft_y4_tile<R, N1, N2, INV>(P, blockIdx.x);
+}
+
 // Forward DFT along x, projection A_ij <- xi_j (sum_l xi_l A_il) / |xi|^2
 // (Eq. G_red) in the transposed order, inverse DFT along x; tile = (tensor
 // row i) x nx x (T kz) for one ky, T compile-time (fs_x_t).
 template <typename R, int N1, int N2>
-__global__ void __launch_bounds__(FFT_THREADS, (Fs4Occ<R, N1, N2>::value))
-    k_fft_x4(const LineParams<R> P) {
+RVE_DEV void fft_x4_tile(const LineParams<R>& P, const int tile) {
   constexpr int N = N1 * N2;
   constexpr int T = fs_x_t(N);
   using LM = FsLayout<T, N * T, 1, T, 3 * T>;
@@ -93,7 +97,6 @@ __global__ void __launch_bounds__(FFT_THREADS, (Fs4Occ<R, N1, N2>::value))
   const int hz = P.g.hz, hzp = P.g.hzp;
   const int ntk = (hz + T - 1) / T;
   const size_t rs = (size_t)ny * hzp;  // stride of spectrum rows (c*nx + x)
-  const int tile = blockIdx.x;
   const int q = (int)P.g.f_fsx_ntk.div((unsigned)tile);
   const int k0 = (tile - q * ntk) * T;
   const int irow = (int)P.g.f_ny.div((unsigned)q);
@@ -175,6 +178,12 @@ __global__ void __launch_bounds__(FFT_THREADS, (Fs4Occ<R, N1, N2>::value))
       }
     }
   }
+}
+
+template <typename R, int N1, int N2>
+__global__ void __launch_bounds__(FFT_THREADS, (Fs4Occ<R, N1, N2>::value))
+    k_fft_x4(const LineParams<R> P) {
+  fft_x4_tile<R, N1, N2>(P, blockIdx.x);
 }
 
 // x pass of the preconditioned CG iteration: as k_fft_x4, with the
@@ -289,8 +298,7 @@ RVE_DEV void zfwd_prefetch_tile(const ZfwdParams<R>& P, const ZfwdScalars<R>& sc
 // packed lines, half spectrum out -- and prefetches its next tile's inputs
 // into L2 before the DFT, so that they arrive while it computes.
 template <typename R, int SRC, int TAN, int N1, int N2>
-__global__ void __launch_bounds__(FFT_THREADS, (Fs4Occ<R, N1, N2>::value))
-    k_zfwd4(const ZfwdParams<R> P) {
+RVE_DEV void zfwd4_blocks(const ZfwdParams<R>& P, const int bid, const int nblk) {
   constexpr int N = N1 * N2;
   constexpr int lz = fs_zf_lz(N), LP = (5 * lz) | 1, hz = N / 2 + 1;
   using LM = FsLayout<5 * lz, 0, 1, LP, 5 * lz>;
@@ -305,7 +313,7 @@ __global__ void __launch_bounds__(FFT_THREADS, (Fs4Occ<R, N1, N2>::value))
   const int hzp = P.g.hzp;
   const size_t ss = P.g.sstride;
   double pkp = 0.0;
-  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+  for (int tile = bid; tile < ntiles; tile += nblk) {
     const int l0 = tile * lz;
     const int nl = min(lz, nlines - l0);
     const int nvox = nl * N;
@@ -326,7 +334,7 @@ __global__ void __launch_bounds__(FFT_THREADS, (Fs4Occ<R, N1, N2>::value))
     }
     pkp += (double)tpk;
     __syncthreads();
-    const int next = tile + gridDim.x;
+    const int next = tile + nblk;
     if (next < ntiles) {
       const int nl2 = min(lz, nlines - next * lz);
       zfwd_prefetch_tile<R, SRC, TAN>(P, sc, (size_t)next * lz * N, nl2 * N);
@@ -370,7 +378,13 @@ __global__ void __launch_bounds__(FFT_THREADS, (Fs4Occ<R, N1, N2>::value))
     }
     __syncthreads();  // the buffer is refilled by the next tile
   }
-  if (SRC == SRC_CGPX) zfwd_step_length<R>(P, pkp);
+  if (SRC == SRC_CGPX) zfwd_step_length<R>(P, pkp, bid, nblk);
+}
+
+template <typename R, int SRC, int TAN, int N1, int N2>
+__global__ void __launch_bounds__(FFT_THREADS, (Fs4Occ<R, N1, N2>::value))
+    k_zfwd4(const ZfwdParams<R> P) {
+  zfwd4_blocks<R, SRC, TAN, N1, N2>(P, blockIdx.x, gridDim.x);
 }
 
 // First pass of the fused float CG iteration for the SVK tangent with a
@@ -524,7 +538,7 @@ __global__ void __launch_bounds__(FFT_THREADS, 3) k_zfwd4p(const ZfwdParams<floa
     }
     __syncthreads();  // the DFT buffer is refilled by the next tile
   }
-  zfwd_step_length<R>(P, pkp);
+  zfwd_step_length<R>(P, pkp, blockIdx.x, gridDim.x);
 }
 
 // L2 prefetch of the last pass's inputs of a tile: the tile's half spectrum
@@ -563,8 +577,7 @@ RVE_DEV void zinv_prefetch_tile(const ZinvParams<R, R>& P, int l0, int nl, size_
 // then r -= alpha Ap in place and r.r.  The next tile's inputs are
 // prefetched into L2 before the DFT stage.
 template <typename R, int N1, int N2>
-__global__ void __launch_bounds__(FFT_THREADS, (Fs4Occ<R, N1, N2>::value))
-    k_zinv4_cgr(const ZinvParams<R, R> P) {
+RVE_DEV void zinv4_cgr_blocks(const ZinvParams<R, R>& P, const int bid, const int nblk) {
   static_assert(sizeof(R) == 4, "float32 CG iteration");
   constexpr int N = N1 * N2;
   constexpr int lz = fs_z_lz(N), LP = (5 * lz) | 1, hz = N / 2 + 1;
@@ -590,7 +603,7 @@ __global__ void __launch_bounds__(FFT_THREADS, (Fs4Occ<R, N1, N2>::value))
   __syncthreads();
   double acc = 0.0;
   unsigned parity = 0;
-  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+  for (int tile = bid; tile < ntiles; tile += nblk) {
     const int l0 = tile * lz;
     const int nl = min(lz, nlines - l0);
     const int nvox = nl * N;
@@ -654,7 +667,7 @@ __global__ void __launch_bounds__(FFT_THREADS, (Fs4Occ<R, N1, N2>::value))
       }
     }
     __syncthreads();
-    const int next = tile + gridDim.x;
+    const int next = tile + nblk;
     if (next < ntiles) {
       const int nl2 = min(lz, nlines - next * lz);
       zinv_prefetch_tile<R>(P, next * lz, nl2, (size_t)next * lz * N, nl2 * N);
@@ -690,7 +703,8 @@ __global__ void __launch_bounds__(FFT_THREADS, (Fs4Occ<R, N1, N2>::value))
     __syncthreads();  // buffer, r copy and rofs are refilled by the next tile
   }
   double v1[1] = {acc}, tot[1];
-  if (last_block_sum<1>(v1, P.partials, &P.st->counter[SLOT_RR], tot) && threadIdx.x == 0) {
+  if (last_block_sum_of<1>(v1, P.partials, &P.st->counter[SLOT_RR], tot, bid, nblk) &&
+      threadIdx.x == 0) {
     if (P.st->dev_timeout) {
       P.st->status = RVE_DEV_ERR_TIMEOUT;
       P.st->done = 1;
@@ -698,6 +712,12 @@ __global__ void __launch_bounds__(FFT_THREADS, (Fs4Occ<R, N1, N2>::value))
       cg_after_rr(P.st, tot[0]);
     }
   }
+}
+
+template <typename R, int N1, int N2>
+__global__ void __launch_bounds__(FFT_THREADS, (Fs4Occ<R, N1, N2>::value))
+    k_zinv4_cgr(const ZinvParams<R, R> P) {
+  zinv4_cgr_blocks<R, N1, N2>(P, blockIdx.x, gridDim.x);
 }
 
 cudaError_t g_err4 = cudaSuccess;
@@ -708,6 +728,49 @@ void allow_smem(K kernel) {
   if (e != cudaSuccess && g_err4 == cudaSuccess) g_err4 = e;
 }
 
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Recording of the four-step launches for batched passes (see kernels.h).
+// ---------------------------------------------------------------------------
+namespace {
+// one kind of pass (0 first z, 1 y forward, 2 x, 3 y inverse, 4 last z)
+// for every recorded cell
+struct Fs4Pass {
+  std::vector<char> params;  // per cell, one parameter struct of the kind
+  std::vector<int> axis, tan, nblk;
+  std::vector<int2> blk;     // per block of the batched launch: (cell, block)
+  size_t smem = 0;
+  char* d_params = nullptr;
+  int *d_axis = nullptr, *d_tan = nullptr, *d_nblk = nullptr;
+  int2* d_blk = nullptr;
+};
+thread_local Fs4Batch* t_rec = nullptr;
+
+constexpr bool fs4_batch_size(int n) {
+  return n == 15 || n == 21 || n == 27 || n == 33 || n == 45 || n == 63;
+}
+}  // namespace
+
+struct Fs4Batch {
+  Fs4Pass pass[5];
+  bool bad = false;  // a launch that cannot be batched was recorded
+};
+
+namespace {
+template <typename PT>
+void rec_add(int kind, const PT& P, int axis, int tan, int grid, size_t sm) {
+  Fs4Pass& p = t_rec->pass[kind];
+  if (!fs4_batch_size(axis)) t_rec->bad = true;
+  const int c = (int)p.axis.size();
+  const char* raw = reinterpret_cast<const char*>(&P);
+  p.params.insert(p.params.end(), raw, raw + sizeof(PT));
+  p.axis.push_back(axis);
+  p.tan.push_back(tan);
+  p.nblk.push_back(grid);
+  for (int b = 0; b < grid; ++b) p.blk.push_back(make_int2(c, b));
+  p.smem = std::max(p.smem, sm);
+}
 }  // namespace
 
 void launch_fft_y4(const GridGeom& g, bool inverse, cplx<float>* spec, const int* done,
@@ -722,6 +785,10 @@ void launch_fft_y4(const GridGeom& g, bool inverse, cplx<float>* spec, const int
   P.tw = tw;
   const int ntiles = ((g.hz + P.t - 1) / P.t) * ((9 * g.nx + P.grp - 1) / P.grp);
   const size_t sm = sizeof(cplx<float>) * ((size_t)((g.ny + 1) & ~1) + (size_t)P.grp * g.ny * P.t);
+  if (t_rec) {
+    rec_add(inverse ? 3 : 1, P, g.ny, 0, ntiles, sm);
+    return;
+  }
   switch (g.ny) {
 #define RVE_FS_Y(N, A, B)                                                   \
   case N:                                                                   \
@@ -739,6 +806,10 @@ void launch_fft_x4(const GridGeom& g, double scale, cplx<float>* spec, const int
                    const cplx<float>* tw, cudaStream_t s, bool gamma0) {
   LineParams<float> P;
   P.g = g;
+  if (gamma0 && t_rec) {
+    t_rec->bad = true;
+    return;
+  }
   if (gamma0) {
     P.t = 0;
     P.grp = 1;
@@ -764,6 +835,10 @@ void launch_fft_x4(const GridGeom& g, double scale, cplx<float>* spec, const int
   const int ntiles = 3 * g.ny * ((g.hz + P.t - 1) / P.t);
   const size_t sm = sizeof(cplx<float>) * ((size_t)((g.nx + 1) & ~1) + 3 * (size_t)g.nx * P.t) +
                     sizeof(float) * ((size_t)g.nx + P.t);
+  if (t_rec) {
+    rec_add(2, P, g.nx, 0, ntiles, sm);
+    return;
+  }
   switch (g.nx) {
 #define RVE_FS_X(N, A, B)                                       \
   case N:                                                       \
@@ -800,6 +875,10 @@ void launch_zfwd4(const ZfwdParams<float>& P0, cudaStream_t s) {
   ZfwdParams<float> P = P0;
   const GridGeom& g = P.g;
   if (g.zstage && P.tan.mode == TAN_SVK && P.tan.mat.phase && !P.tan.Sop && fs_zt_lz(g.nz) >= 1) {
+    if (t_rec) {
+      t_rec->bad = true;
+      return;
+    }
     const int lz = fs_zt_lz(g.nz);
     P.lz = lz;
     const int grid = std::min((g.nx * g.ny + lz - 1) / lz, std::max(1, g.zblk) * sm_count());
@@ -821,6 +900,11 @@ void launch_zfwd4(const ZfwdParams<float>& P0, cudaStream_t s) {
   const int grid = std::min((nlines + P.lz - 1) / P.lz, std::max(1, g.zblk) * sm_count());
   const size_t sm = z4_smem(g, false);
   const int tm = P.tan.mode;
+  if (t_rec) {
+    if (tm != TAN_SVK && tm != TAN_SYM45) t_rec->bad = true;
+    rec_add(0, P, g.nz, tm, grid, sm);
+    return;
+  }
   switch (g.nz) {
 #define RVE_FS_ZF(N, A, B)                                                                    \
   case N:                                                                                     \
@@ -842,6 +926,11 @@ void launch_zinv4(const ZinvParams<float, float>& P0, cudaStream_t s) {
   const int nlines = g.nx * g.ny;
   const int grid = std::min((nlines + P.lz - 1) / P.lz, std::max(1, g.zblk) * sm_count());
   const size_t sm = z4_smem(g, true);
+  if (t_rec) {
+    if (P.mn_ell >= 0.f) t_rec->bad = true;
+    rec_add(4, P, g.nz, 0, grid, sm);
+    return;
+  }
   switch (g.nz) {
 #define RVE_FS_ZI(N, A, B)                                          \
   case N:                                                           \
@@ -853,6 +942,96 @@ void launch_zinv4(const ZinvParams<float, float>& P0, cudaStream_t s) {
       break;
   }
 }
+
+// ---------------------------------------------------------------------------
+// Batched passes: block blockIdx.x runs block blk.y of cell blk.x's own
+// launch of that pass (its parameters, its block count), dispatched on the
+// cell's axis length.
+// ---------------------------------------------------------------------------
+#define RVE_FS_BATCH_SIZES(X) X(15, 5, 3) X(21, 7, 3) X(27, 9, 3) X(33, 11, 3) X(45, 9, 5) X(63, 9, 7)
+
+namespace {
+struct Fs4Tab {
+  const int2* blk;
+  const int* axis;
+  const int* tan;
+  const int* nblk;
+  const char* params;
+};
+
+// out of line: each size gets its own register allocation (inlined into one
+// switch, the six first-pass bodies spill heavily at the 80-register bound)
+template <int TAN, int N1, int N2>
+__device__ __noinline__ void zfwd4_blocks_call(const ZfwdParams<float>* P, int bid, int nblk) {
+  zfwd4_blocks<float, SRC_CGPX, TAN, N1, N2>(*P, bid, nblk);
+}
+
+__global__ void __launch_bounds__(FFT_THREADS, 3) k_fs4_batch_zfwd(const Fs4Tab T) {
+  const int2 b = T.blk[blockIdx.x];
+  const ZfwdParams<float>& P = reinterpret_cast<const ZfwdParams<float>*>(T.params)[b.x];
+  const int nb = T.nblk[b.x];
+  const bool sym = T.tan[b.x] == TAN_SYM45;
+  switch (T.axis[b.x]) {
+#define RVE_B_ZF(N, A, B)                                                  \
+  case N:                                                                  \
+    if (sym) zfwd4_blocks_call<TAN_SYM45, A, B>(&P, b.y, nb);              \
+    else zfwd4_blocks_call<TAN_SVK, A, B>(&P, b.y, nb);                    \
+    break;
+    RVE_FS_BATCH_SIZES(RVE_B_ZF)
+#undef RVE_B_ZF
+    default:
+      break;
+  }
+}
+
+template <bool INV>
+__global__ void __launch_bounds__(FFT_THREADS, 4) k_fs4_batch_y(const Fs4Tab T) {
+  const int2 b = T.blk[blockIdx.x];
+  const LineParams<float>& P = reinterpret_cast<const LineParams<float>*>(T.params)[b.x];
+  switch (T.axis[b.x]) {
+#define RVE_B_Y(N, A, B)                       \
+  case N:                                      \
+    fft_y4_tile<float, A, B, INV>(P, b.y);     \
+    break;
+    RVE_FS_BATCH_SIZES(RVE_B_Y)
+#undef RVE_B_Y
+    default:
+      break;
+  }
+}
+
+__global__ void __launch_bounds__(FFT_THREADS, 4) k_fs4_batch_x(const Fs4Tab T) {
+  const int2 b = T.blk[blockIdx.x];
+  const LineParams<float>& P = reinterpret_cast<const LineParams<float>*>(T.params)[b.x];
+  switch (T.axis[b.x]) {
+#define RVE_B_X(N, A, B)                  \
+  case N:                                 \
+    fft_x4_tile<float, A, B>(P, b.y);     \
+    break;
+    RVE_FS_BATCH_SIZES(RVE_B_X)
+#undef RVE_B_X
+    default:
+      break;
+  }
+}
+
+__global__ void __launch_bounds__(FFT_THREADS, 3) k_fs4_batch_zinv(const Fs4Tab T) {
+  const int2 b = T.blk[blockIdx.x];
+  const ZinvParams<float, float>& P =
+      reinterpret_cast<const ZinvParams<float, float>*>(T.params)[b.x];
+  const int nb = T.nblk[b.x];
+  switch (T.axis[b.x]) {
+#define RVE_B_ZI(N, A, B)                               \
+  case N:                                               \
+    zinv4_cgr_blocks<float, A, B>(P, b.y, nb);          \
+    break;
+    RVE_FS_BATCH_SIZES(RVE_B_ZI)
+#undef RVE_B_ZI
+    default:
+      break;
+  }
+}
+}  // namespace
 
 cudaError_t fft4_kernels_init() {
   g_err4 = cudaSuccess;
@@ -868,5 +1047,78 @@ cudaError_t fft4_kernels_init() {
   allow_smem(k_zfwd4p<A, B>);
   RVE_FS_SIZES(RVE_FS_INIT)
 #undef RVE_FS_INIT
+  allow_smem(k_fs4_batch_zfwd);
+  allow_smem(k_fs4_batch_y<false>);
+  allow_smem(k_fs4_batch_y<true>);
+  allow_smem(k_fs4_batch_x);
+  allow_smem(k_fs4_batch_zinv);
   return g_err4;
+}
+
+Fs4Batch* fs4_batch_new() { return new Fs4Batch(); }
+
+void fs4_batch_free(Fs4Batch* b) {
+  if (!b) return;
+  for (auto& p : b->pass) {
+    cudaFree(p.d_params);
+    cudaFree(p.d_axis);
+    cudaFree(p.d_tan);
+    cudaFree(p.d_nblk);
+    cudaFree(p.d_blk);
+  }
+  delete b;
+}
+
+bool fs4_batch_eligible(const GridGeom& g, bool mixed, int tan_mode, bool precond) {
+  return mixed && !precond && !g.zstage && g.fsx_n1 && g.fsy_n1 && g.fsz_n1 &&
+         fs4_batch_size(g.nx) && fs4_batch_size(g.ny) && fs4_batch_size(g.nz) &&
+         (tan_mode == TAN_SVK || tan_mode == TAN_SYM45);
+}
+
+void fs4_batch_record(Fs4Batch* b) { t_rec = b; }
+
+int fs4_batch_cells(const Fs4Batch* b) {
+  if (!b || b->bad) return -1;
+  const size_t c = b->pass[0].axis.size();
+  for (const auto& p : b->pass)
+    if (p.axis.size() != c) return -1;
+  return (int)c;
+}
+
+cudaError_t fs4_batch_upload(Fs4Batch* b) {
+  if (fs4_batch_cells(b) < 0) return cudaErrorInvalidValue;
+  for (auto& p : b->pass) {
+    auto put = [](auto** dst, const auto& v) {
+      cudaFree(*dst);
+      *dst = nullptr;
+      const size_t bytes = v.size() * sizeof(v[0]);
+      if (!bytes) return cudaSuccess;
+      cudaError_t e = cudaMalloc(reinterpret_cast<void**>(dst), bytes);
+      if (e != cudaSuccess) return e;
+      return cudaMemcpy(*dst, v.data(), bytes, cudaMemcpyHostToDevice);
+    };
+    cudaError_t e;
+    if ((e = put(&p.d_params, p.params)) != cudaSuccess) return e;
+    if ((e = put(&p.d_axis, p.axis)) != cudaSuccess) return e;
+    if ((e = put(&p.d_tan, p.tan)) != cudaSuccess) return e;
+    if ((e = put(&p.d_nblk, p.nblk)) != cudaSuccess) return e;
+    if ((e = put(&p.d_blk, p.blk)) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+void fs4_batch_launch(const Fs4Batch* b, cudaStream_t s) {
+  for (int k = 0; k < 5; ++k) {
+    const Fs4Pass& p = b->pass[k];
+    if (p.blk.empty()) continue;
+    const Fs4Tab T{p.d_blk, p.d_axis, p.d_tan, p.d_nblk, p.d_params};
+    const unsigned grid = (unsigned)p.blk.size();
+    switch (k) {
+      case 0: k_fs4_batch_zfwd<<<grid, FFT_THREADS, p.smem, s>>>(T); break;
+      case 1: k_fs4_batch_y<false><<<grid, FFT_THREADS, p.smem, s>>>(T); break;
+      case 2: k_fs4_batch_x<<<grid, FFT_THREADS, p.smem, s>>>(T); break;
+      case 3: k_fs4_batch_y<true><<<grid, FFT_THREADS, p.smem, s>>>(T); break;
+      default: k_fs4_batch_zinv<<<grid, FFT_THREADS, p.smem, s>>>(T); break;
+    }
+  }
 }

@@ -2209,6 +2209,8 @@ struct rve_batch_s {
   bool mixed = false;
   cudaGraphExec_t exec = nullptr;
   std::vector<int> graph_members;  // cells captured in exec
+  Fs4Batch* fs4 = nullptr;         // batched passes of the captured iteration
+  int fs4_cells = 0;               // cells in it (the others are graph branches)
   SolverState** d_states = nullptr;
   int* d_info = nullptr;
   int* h_info = nullptr;
@@ -2235,6 +2237,41 @@ int batch_capture(rve_batch_t b, const std::vector<int>& cells) {
     cudaGraphExecDestroy(b->exec);
     b->exec = nullptr;
   }
+  // float32 CG of cells whose passes all have batched four-step kernels:
+  // their launches are recorded (not run) and become one launch per pass
+  fs4_batch_free(b->fs4);
+  b->fs4 = nullptr;
+  b->fs4_cells = 0;
+  std::vector<int> branch;
+  if constexpr (std::is_same<R, float>::value) {
+    std::vector<int> batched;
+    for (int c : cells) {
+      rve_t h = b->rv[c];
+      if (fs4_batch_eligible(h->g, h->mixed, h->tan, h->precond)) batched.push_back(c);
+      else branch.push_back(c);
+    }
+    if (batched.size() > 1) {
+      b->fs4 = fs4_batch_new();
+      fs4_batch_record(b->fs4);
+      for (int c : batched) {  // recorded, not launched: the cell's count stays
+        const long long l0 = b->rv[c]->launches;
+        enqueue_cg_iteration<R>(b->rv[c], -1);
+        b->rv[c]->launches = l0;
+      }
+      fs4_batch_record(nullptr);
+      const int nb = fs4_batch_cells(b->fs4);
+      if (nb != (int)batched.size() || fs4_batch_upload(b->fs4) != cudaSuccess) {
+        fs4_batch_free(b->fs4);
+        b->fs4 = nullptr;
+        return RVE_ERR_CUDA;
+      }
+      b->fs4_cells = nb;
+    } else {
+      branch.insert(branch.end(), batched.begin(), batched.end());
+    }
+  } else {
+    branch = cells;
+  }
   cudaGraph_t graph;
   cudaEvent_t fork;
   if (cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) != cudaSuccess) return RVE_ERR_CUDA;
@@ -2244,7 +2281,9 @@ int batch_capture(rve_batch_t b, const std::vector<int>& cells) {
     return RVE_ERR_CUDA;
   cudaEventRecord(fork, b->s0);
   std::vector<bool> used(b->streams.size(), false);
-  for (int c : cells) {
+  if (b->fs4)
+    for (int k = 0; k < kGraphIters; ++k) fs4_batch_launch(b->fs4, b->s0);
+  for (int c : branch) {
     rve_t h = b->rv[c];
     const size_t si = (size_t)c % b->streams.size();
     if (!used[si]) {
@@ -2287,13 +2326,25 @@ int batch_cg_phase(rve_batch_t b, const std::vector<int>& active, std::vector<in
   const long long max_launch = (long long)b->rv[active[0]]->opt.max_cg / kGraphIters + 4096;
   while (true) {
     if (cudaGraphLaunch(b->exec, b->s0) != cudaSuccess) return bfail(b, RVE_ERR_CUDA, "graph launch");
-    b->launches += (long long)active.size() * (b->mixed ? 5 : 6) * kGraphIters;
+    b->launches += ((b->fs4 ? 5 : 0) + (long long)(b->graph_members.size() - b->fs4_cells) *
+                                          (b->mixed ? 5 : 6)) * kGraphIters;
     k_gather_cg<<<(nrve + 127) / 128, 128, 0, b->s0>>>(b->d_states, nrve, b->d_info);
     cudaMemcpyAsync(b->h_info, b->d_info, sizeof(int) * 3 * nrve, cudaMemcpyDeviceToHost, b->s0);
     if (cudaStreamSynchronize(b->s0) != cudaSuccess) return bfail(b, RVE_ERR_CUDA, "batched CG");
     bool all = true;
     for (int c : active) all = all && b->h_info[3 * c];
     if (all) break;
+    // a batched launch schedules the blocks of every member cell, finished
+    // or not: once half of the members have finished, capture the rest
+    if (b->fs4) {
+      std::vector<int> running;
+      for (int c : b->graph_members)
+        if (!b->h_info[3 * c]) running.push_back(c);
+      if (2 * running.size() <= b->graph_members.size()) {
+        int rc = batch_capture<R>(b, running);
+        if (rc) return bfail(b, rc, "graph capture of the batched CG iteration failed");
+      }
+    }
     if (++guard > max_launch) return bfail(b, RVE_ERR_TIMEOUT, "batched CG state stopped advancing");
   }
   for (int c : active) {
@@ -2494,6 +2545,7 @@ int rve_batch_create(rve_batch_t* out, int nrve, const int* dims, int model, con
 void rve_batch_destroy(rve_batch_t b) {
   if (!b) return;
   if (b->exec) cudaGraphExecDestroy(b->exec);
+  fs4_batch_free(b->fs4);
   for (rve_t h : b->rv) rve_destroy(h);
   for (auto s : b->streams) {
     cudaStreamSynchronize(s);

@@ -86,3 +86,25 @@ def test_j2_batch_commits_history_like_individual_solves():
         assert r.get_history().reshape(7, -1)[6].max() > 0.0
         r.close()
     b.close()
+
+
+def test_mixed_batch_runs_one_launch_per_pass():
+    """Cells whose axes all have batched four-step kernels run each pass of
+    the float32 CG iteration for the whole batch in one launch: the batch
+    launches far fewer kernels than the same cells solved one by one, with
+    bit-identical results."""
+    cells = _cells(10, seed=5, sizes=(15, 21, 27))
+    batch = RVEBatch([c[0] for c in cells], [c[1] for c in cells], [c[2] for c in cells],
+                     precision="mixed")
+    st = batch.solve(np.stack([c[3] for c in cells]))
+    assert all(s["status"] == 0 for s in st)
+    singles = 0
+    for i, (shape, ph, params, Fbar) in enumerate(cells):
+        r = RVE(shape, phase=ph, phase_params=params, precision="mixed")
+        r.set_macro_F(Fbar)
+        r.solve_increment()
+        singles += r.launch_count()
+        assert np.array_equal(r.get_F(), batch.get_F(i))
+        r.close()
+    assert batch.launch_count() < 0.5 * singles
+    batch.close()
