@@ -264,6 +264,16 @@ RVE_DEV void zfwd_voxel(const ZfwdParams<R>& P, const ZfwdScalars<R>& sc, size_t
 
 RVE_DEV void prefetch_l2(const void* p) { asm volatile("prefetch.global.L2 [%0];" ::"l"(p)); }
 
+// One thread: bulk prefetch into L2 of the 16-byte-aligned span around
+// [p, p + bytes) (the span stays inside the allocation: arrays start 256-byte
+// aligned in one workspace with slack after the last one)
+RVE_DEV void bulk_prefetch_l2(const void* p, size_t bytes) {
+  const uintptr_t a = reinterpret_cast<uintptr_t>(p) & ~(uintptr_t)15;
+  const uintptr_t e = (reinterpret_cast<uintptr_t>(p) + bytes + 15) & ~(uintptr_t)15;
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a), "r"((unsigned)(e - a))
+               : "memory");
+}
+
 // Step length of the fused CG iteration from sum p.(K:p):
 // p.Ap = p.G(K p) = (G p).(K p) = p.(K p) for compatible p (G is an
 // orthogonal projector), so alpha is known before the inverse transforms.

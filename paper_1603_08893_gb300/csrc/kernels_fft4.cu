@@ -262,31 +262,20 @@ __global__ void __launch_bounds__(FFT_THREADS, 2) k_fft_x4_g0(const LineParams<R
 }
 
 // L2 prefetch of the first-pass inputs of a tile (r and F, after the first
-// iteration p and x, the phase bytes): every 128-byte line of each
-// component's range, addresses clamped into the range.
+// iteration p and x, the phase bytes): one bulk prefetch per component's
+// range, issued by one thread.
 template <typename R, int SRC, int TAN>
 RVE_DEV void zfwd_prefetch_tile(const ZfwdParams<R>& P, const ZfwdScalars<R>& sc, size_t v0,
                                 int nvox) {
   if constexpr (SRC == SRC_CGPX && TAN == TAN_SVK) {
     const size_t n = P.g.n;
-    const bool ph = P.tan.mat.phase != nullptr;
     const int nf = sc.first ? 18 : 36;
-    const int narr = nf + (ph ? 1 : 0);
-    const int lpa = (int)(((size_t)nvox * sizeof(R)) / 128) + 2;  // lines per array (bound)
-    for (int j = threadIdx.x; j < narr * lpa; j += FFT_THREADS) {
-      const int a = j / lpa, q = j - a * lpa;
-      const char* lo;
-      size_t len;
-      if (a < nf) {
+    if (threadIdx.x == 0) {
+      for (int a = 0; a < nf; ++a) {
         const R* b = a < 9 ? P.r : a < 18 ? P.tan.Fop : a < 27 ? P.p : P.x;
-        lo = reinterpret_cast<const char*>(b + (size_t)(a % 9) * n + v0);
-        len = (size_t)nvox * sizeof(R);
-      } else {
-        lo = reinterpret_cast<const char*>(P.tan.mat.phase + v0);
-        len = (size_t)nvox;
+        bulk_prefetch_l2(b + (size_t)(a % 9) * n + v0, (size_t)nvox * sizeof(R));
       }
-      const size_t off = (size_t)q * 128 < len ? (size_t)q * 128 : len - 1;
-      prefetch_l2(lo + off);
+      if (P.tan.mat.phase) bulk_prefetch_l2(P.tan.mat.phase + v0, (size_t)nvox);
     }
   }
 }
@@ -543,28 +532,16 @@ __global__ void __launch_bounds__(FFT_THREADS, 3) k_zfwd4p(const ZfwdParams<floa
 
 // L2 prefetch of the last pass's inputs of a tile: the tile's half spectrum
 // (per component nl consecutive rows of hzp values, contiguous) and its r
-// range.
+// range, one bulk prefetch each, issued by one thread.
 template <typename R>
 RVE_DEV void zinv_prefetch_tile(const ZinvParams<R, R>& P, int l0, int nl, size_t v0, int nvox) {
-  const size_t ss = P.g.sstride;
-  const int hzp = P.g.hzp;
-  const size_t slen = (size_t)nl * hzp * sizeof(cplx<R>);
-  const size_t rlen = (size_t)nvox * sizeof(R);
-  const int lps = (int)(slen / 128) + 2, lpr = (int)(rlen / 128) + 2;
-  for (int j = threadIdx.x; j < 9 * (lps + lpr); j += FFT_THREADS) {
-    const int c = j / (lps + lpr), q = j - c * (lps + lpr);
-    const char* lo;
-    size_t len, off;
-    if (q < lps) {
-      lo = reinterpret_cast<const char*>(P.spec + (size_t)c * ss + (size_t)l0 * hzp);
-      len = slen;
-      off = (size_t)q * 128;
-    } else {
-      lo = reinterpret_cast<const char*>(P.r_out + (size_t)c * P.g.n + v0);
-      len = rlen;
-      off = (size_t)(q - lps) * 128;
+  if (threadIdx.x == 0) {
+    const size_t ss = P.g.sstride;
+    const int hzp = P.g.hzp;
+    for (int c = 0; c < 9; ++c) {
+      bulk_prefetch_l2(P.spec + (size_t)c * ss + (size_t)l0 * hzp, (size_t)nl * hzp * sizeof(cplx<R>));
+      bulk_prefetch_l2(P.r_out + (size_t)c * P.g.n + v0, (size_t)nvox * sizeof(R));
     }
-    prefetch_l2(lo + (off < len ? off : len - 1));
   }
 }
 
