@@ -375,10 +375,31 @@ def bench_cube31(args, torch, RVE):
     e1.record(s)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
+    pbar = r.homogenized_P()
+    r.close()
+    gold = json.load(open(os.path.join(ROOT, "tests", "golden", "svk31_cube_schedule.json")))
+    tight = np.array(gold["tight"]["increments"][-1]["Pbar"])
+    # the oracle's whole schedule at the same tolerances on the host cores
+    from oracle import fourier
+    from oracle import solver as osolver
+    old = fourier.get_backend()
+    fourier.set_backend("scipy", workers=host_cores())
+    try:
+        prob = osolver.SVKProblem.from_phase(cfg["phase"], cfg["phase_params"])
+        t0 = time.perf_counter()
+        ocg = 0
+        for Fb in cfg["schedule"]:
+            ocg += sum(prob.increment(Fb, cfg["tol_newton"], cfg["tol_cg"]).cg_iters)
+        t_or = time.perf_counter() - t0
+    finally:
+        fourier.set_backend(old["name"], old["workers"])
     _line("svk31_cube_shear_fp64", "voxel*CG-iterations/s, float64 GPU solver", n * cg / (ms / 1e3),
           UNIT, dtype="f64", increments=len(cfg["schedule"]), cg_iters=cg, newton_iters=newton,
-          solve_ms=ms, pbar_xy=float(r.homogenized_P()[0, 1]))
-    r.close()
+          solve_ms=ms, pbar_xy=float(pbar[0, 1]),
+          pbar_rel_err_vs_tight_oracle=float(np.abs(pbar - tight).max() / np.abs(tight).max()),
+          cpu_oracle={"full_run_s": round(t_or, 2), "cg_iters": ocg, "cores": host_cores(),
+                      "cpu_model": cpu_model(), "value": n * ocg / t_or,
+                      "sample": "the whole 10-increment schedule, scipy.fft backend"})
 
 
 def bench_j2_315(args, torch, RVE):

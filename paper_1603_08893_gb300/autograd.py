@@ -7,7 +7,11 @@ forward solves the cell (Newton-CG through the C ABI) for the macroscopic
 deformation; backward is one adjoint CG solve with the same operator
 followed by the per-voxel sensitivity kernel (rve_adjoint_grad /
 rve_adjoint_grad_params), which gives every gradient from the same adjoint
-field.
+field.  The per-voxel parameters enter at rve_create (host arrays, once per
+forward: the C ABI's creation call copies them in); for CUDA inputs the
+gradients are written by the library straight into CUDA tensors
+(grads_on_device = 1), and only P-bar and dJ/dP-bar (9 values each) cross
+to the host.
 """
 from __future__ import annotations
 
@@ -43,11 +47,13 @@ class HomogenizedStress(torch.autograd.Function):
 
     @staticmethod
     def backward(ctx, grad_P):
-        W = grad_P.detach().cpu().numpy().astype(np.float64)
-        gK, gmu, _ = ctx.rve.adjoint_grad(W, ctx.adjoint_tol)
+        W = grad_P.detach().cpu().numpy().astype(np.float64)  # 9 values
+        dev = ctx.device.type == "cuda"
+        gK, gmu, _ = ctx.rve.adjoint_grad(W, ctx.adjoint_tol, device=dev)
         ctx.rve.close()
-        dK = torch.from_numpy(gK).to(ctx.device) if ctx.K_is_tensor else None
-        return (torch.from_numpy(gmu).to(ctx.device), dK) + (None,) * 7
+        wrap = (lambda g: g) if dev else (lambda g: torch.from_numpy(g))
+        dK = wrap(gK) if ctx.K_is_tensor else None
+        return (wrap(gmu), dK) + (None,) * 7
 
 
 def homogenized_stress(mu, K, Fbar, **kw):
@@ -95,14 +101,15 @@ class J2HomogenizedStress(torch.autograd.Function):
 
     @staticmethod
     def backward(ctx, grad_P):
-        W = grad_P.detach().cpu().numpy().astype(np.float64)
+        W = grad_P.detach().cpu().numpy().astype(np.float64)  # 9 values
+        dev = ctx.device.type == "cuda"
         if ctx.path:
-            g, _ = ctx.rve.adjoint_grad_path(W, ctx.adjoint_tol)
+            g, _ = ctx.rve.adjoint_grad_path(W, ctx.adjoint_tol, device=dev)
         else:
-            g, _ = ctx.rve.adjoint_grad_params(W, ctx.adjoint_tol)
+            g, _ = ctx.rve.adjoint_grad_params(W, ctx.adjoint_tol, device=dev)
         ctx.rve.close()
-        out = [torch.from_numpy(np.ascontiguousarray(g[k])).to(ctx.device) if ctx.is_tensor[k]
-               else None for k in range(4)]
+        wrap = (lambda a: a) if dev else (lambda a: torch.from_numpy(np.ascontiguousarray(a)))
+        out = [wrap(g[k]) if ctx.is_tensor[k] else None for k in range(4)]
         return tuple(out) + (None,) * 6
 
 

@@ -229,28 +229,38 @@ def rve_adjoint_grad_mu(h, W, n, tol_cg=1e-12, out=None):
     return g, its.value
 
 
-def rve_adjoint_grad(h, W, n, tol_cg=1e-12):
+def _grad_buffer(count, device):
+    """(buffer, pointer, on_device): a float64 CUDA tensor written by the
+    library in place (device=True), else a host array."""
+    if device:
+        t = torch.empty(count, dtype=torch.float64, device="cuda")
+        return t, C.c_void_p(t.data_ptr()), 1
+    a = np.empty(count, dtype=np.float64)
+    return a, a.ctypes.data_as(C.c_void_p), 0
+
+
+def rve_adjoint_grad(h, W, n, tol_cg=1e-12, device=False):
     """(dJ/dK, dJ/dmu) per voxel for J = W : P-bar from one adjoint solve;
-    returns (grad_K, grad_mu, cg_iterations)."""
+    returns (grad_K, grad_mu, cg_iterations).  device=True: the gradients
+    are CUDA tensors written by the library directly (no host copy)."""
     Wc = np.ascontiguousarray(W, dtype=np.float64).reshape(9)
     its = C.c_int(0)
-    gK = np.empty(n, dtype=np.float64)
-    gm = np.empty(n, dtype=np.float64)
-    _check(lib.rve_adjoint_grad(h, Wc.ctypes.data_as(C.c_void_p), float(tol_cg),
-                                gK.ctypes.data_as(C.c_void_p), gm.ctypes.data_as(C.c_void_p), 0,
+    gK, pK, dev = _grad_buffer(n, device)
+    gm, pm, _ = _grad_buffer(n, device)
+    _check(lib.rve_adjoint_grad(h, Wc.ctypes.data_as(C.c_void_p), float(tol_cg), pK, pm, dev,
                                 C.byref(its)), h)
     return gK, gm, its.value
 
 
-def rve_adjoint_grad_params(h, W, n, nparam, tol_cg=1e-12):
+def rve_adjoint_grad_params(h, W, n, nparam, tol_cg=1e-12, device=False):
     """dJ/d(parameters) per voxel, [nparam, n], for J = W : P-bar (SVK: K, mu;
     J2: K, mu, tau_y0, H at the history of the last increment's start), and
-    the CG iterations."""
+    the CG iterations (device=True: a CUDA tensor written directly)."""
     Wc = np.ascontiguousarray(W, dtype=np.float64).reshape(9)
     its = C.c_int(0)
-    g = np.empty(nparam * n, dtype=np.float64)
-    _check(lib.rve_adjoint_grad_params(h, Wc.ctypes.data_as(C.c_void_p), float(tol_cg),
-                                       g.ctypes.data_as(C.c_void_p), 0, C.byref(its)), h)
+    g, pg, dev = _grad_buffer(nparam * n, device)
+    _check(lib.rve_adjoint_grad_params(h, Wc.ctypes.data_as(C.c_void_p), float(tol_cg), pg, dev,
+                                       C.byref(its)), h)
     return g.reshape(nparam, n), its.value
 
 
@@ -422,15 +432,17 @@ class RVE:
         g, its = rve_adjoint_grad_mu(self.h, W, self.n, tol_cg)
         return g.reshape(self.shape), its
 
-    def adjoint_grad(self, W, tol_cg=1e-12):
-        """(dJ/dK, dJ/dmu), each [*shape], for J = W : P-bar, and the CG iterations."""
-        gK, gm, its = rve_adjoint_grad(self.h, W, self.n, tol_cg)
+    def adjoint_grad(self, W, tol_cg=1e-12, device=False):
+        """(dJ/dK, dJ/dmu), each [*shape], for J = W : P-bar, and the CG
+        iterations (device=True: CUDA tensors)."""
+        gK, gm, its = rve_adjoint_grad(self.h, W, self.n, tol_cg, device)
         return gK.reshape(self.shape), gm.reshape(self.shape), its
 
-    def adjoint_grad_params(self, W, tol_cg=1e-12):
-        """dJ/d(K, mu[, tau_y0, H]) per voxel, [nparam, *shape], and the CG iterations."""
+    def adjoint_grad_params(self, W, tol_cg=1e-12, device=False):
+        """dJ/d(K, mu[, tau_y0, H]) per voxel, [nparam, *shape], and the CG
+        iterations (device=True: a CUDA tensor)."""
         nparam = 4 if lib.rve_model(self.h) == _MODELS["j2"] else 2
-        g, its = rve_adjoint_grad_params(self.h, W, self.n, nparam, tol_cg)
+        g, its = rve_adjoint_grad_params(self.h, W, self.n, nparam, tol_cg, device)
         return g.reshape((nparam,) + self.shape), its
 
     def tape(self, enable=True):
@@ -440,14 +452,15 @@ class RVE:
     def tape_length(self):
         return int(lib.rve_tape_length(self.h))
 
-    def adjoint_grad_path(self, W, tol_cg=1e-12):
+    def adjoint_grad_path(self, W, tol_cg=1e-12, device=False):
         """J2: dJ/d(K, mu, tau_y0, H) per voxel, [4, *shape], for J = W : P-bar
-        after the taped path (through the history), and the CG iterations."""
+        after the taped path (through the history), and the CG iterations
+        (device=True: a CUDA tensor)."""
         Wc = np.ascontiguousarray(W, dtype=np.float64).reshape(9)
         its = C.c_int(0)
-        g = np.empty(4 * self.n, dtype=np.float64)
+        g, pg, dev = _grad_buffer(4 * self.n, device)
         _check(lib.rve_adjoint_grad_path(self.h, Wc.ctypes.data_as(C.c_void_p), float(tol_cg),
-                                         g.ctypes.data_as(C.c_void_p), 0, C.byref(its)), self.h)
+                                         pg, dev, C.byref(its)), self.h)
         return g.reshape((4,) + self.shape), its.value
 
     def get_history(self):
