@@ -403,8 +403,16 @@ int rve_grid(rve_t h, int dims[3]);
  * the defaults): knobs[0..5] = four-step z pass, blocks per SM of the
  * persistent z passes, four-step y pass, four-step x pass, composite radices
  * in the Stockham plans, TMA-staged first z pass (1 = on); knobs[6] = 1 if
- * they were autotuned.  Returns RVE_OK. */
-int rve_tuning(rve_t h, int knobs[7]);
+ * they were autotuned; knobs[7], knobs[8] = tile height of the four-step x
+ * and y passes (0: the default number of kz values per tile, 1: half of it,
+ * twice the tiles).  Returns RVE_OK. */
+int rve_tuning(rve_t h, int knobs[9]);
+
+/* Sets the kernel variants of a handle explicitly (not in the paper), in the
+ * layout of rve_tuning (knobs[6] is ignored): e.g. a tuning found by the
+ * autotuner in an earlier process.  Values outside 0/1 (1..3 for knobs[1])
+ * give RVE_ERR_INVALID; the handle's later calls use the new variants. */
+int rve_set_tuning(rve_t h, const int knobs[9]);
 
 /* Instrumentation: number of kernels this handle has launched, and optional
  * CUDA-event timing of every launch of one kernel family

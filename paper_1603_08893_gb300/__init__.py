@@ -12,7 +12,7 @@ The compiled library is loaded on first use of a solver name (so that
 """
 _EXPORTS = ("RVE", "RVEBatch", "RVEError", "rve_adjoint_grad", "rve_adjoint_grad_mu", "rve_adjoint_grad_params", "rve_apply_operator", "rve_create", "rve_destroy",
             "rve_get_F", "rve_get_K4", "rve_get_P", "rve_get_history", "rve_homogenized_P",
-            "rve_kernel_time", "rve_kernel_timing", "rve_set_wait_polls", "rve_launch_count", "rve_tuning", "rve_save", "rve_load",
+            "rve_kernel_time", "rve_kernel_timing", "rve_set_wait_polls", "rve_launch_count", "rve_tuning", "rve_set_tuning", "rve_save", "rve_load",
             "rve_project", "rve_project_noalloc", "rve_set_F", "rve_set_macro_F", "rve_solve_increment", "rve_solve_step",
             "rve_solve_mixed", "rve_macro_F",
             "rve_workspace_size", "KERNEL_FAMILIES")

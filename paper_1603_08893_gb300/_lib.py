@@ -96,6 +96,7 @@ _SIGS = {
     "rve_status_string": (C.c_char_p, [C.c_int]),
     "rve_launch_count": (C.c_int, [_H, C.POINTER(C.c_longlong)]),
     "rve_tuning": (C.c_int, [_H, C.POINTER(C.c_int)]),
+    "rve_set_tuning": (C.c_int, [_H, C.POINTER(C.c_int)]),
     "rve_save": (C.c_int, [_H, C.c_char_p]),
     "rve_load": (C.c_int, [C.POINTER(_H), C.c_char_p, C.POINTER(rve_options)]),
     "rve_grid": (C.c_int, [_H, C.POINTER(C.c_int)]),

@@ -74,10 +74,14 @@ constexpr unsigned kDefaultWaitPolls = 1u << 20;
 // Tile shapes of the four-step kernels, compile-time functions of the axis
 // length so that every shared-memory offset of a DFT work item is constant.
 constexpr int fs_y_t() { return 16; }  // kz values per y tile row (128 bytes)
+// The autotuner's alternative tile heights (half the kz values per tile, so
+// twice the tiles, half the shared memory each): y pass 8, x pass fs_x_t / 2.
+constexpr int fs_y_t2() { return 8; }
 constexpr int fs_y_grp(int n) { return 49152 / (8 * n * 16) > 1 ? 49152 / (8 * n * 16) : 1; }
 constexpr int fs_x_t(int n) {
   return 8 * 3 * n * 16 <= 65536 ? 16 : (8 * 3 * n * 8 <= 65536 ? 8 : 4);
 }
+constexpr int fs_x_t2(int n) { return fs_x_t(n) / 2 >= 2 ? fs_x_t(n) / 2 : fs_x_t(n); }
 // first z pass: tiles of about 32 KB (larger tiles measured slower)
 // x pass of the preconditioned iteration: all nine components per tile
 // (the reference-medium operator couples the tensor rows), tiles of at most

@@ -24,10 +24,10 @@ struct Fs4Occ {
 // then A), and the inverse's first phase reads them straight from global
 // memory (N2 = 25 loads per thread in flight), so the transposed
 // intermediate order never leaves shared memory.
-template <typename R, int N1, int N2, bool INV>
+template <typename R, int N1, int N2, bool INV, int T>
 RVE_DEV void fft_y4_tile(const LineParams<R>& P, const int tile) {
   constexpr int N = N1 * N2;
-  constexpr int T = fs_y_t(), GRP = fs_y_grp(N);
+  constexpr int GRP = fs_y_grp(N);
   using LM = FsLayout<T, N * T, 1, T, GRP * T>;
   if (P.done && *P.done) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -75,19 +75,18 @@ RVE_DEV void fft_y4_tile(const LineParams<R>& P, const int tile) {
   }
 }
 
-template <typename R, int N1, int N2, bool INV>
+template <typename R, int N1, int N2, bool INV, int T>
 __global__ void __launch_bounds__(FFT_THREADS, (Fs4Occ<R, N1, N2>::value) + (N1 * N2 <= 125 ? 1 : 0))
     k_fft_y4(const LineParams<R> P) {
-  fft_y4_tile<R, N1, N2, INV>(P, blockIdx.x);
+  fft_y4_tile<R, N1, N2, INV, T>(P, blockIdx.x);
 }
 
 // Forward DFT along x, projection A_ij <- xi_j (sum_l xi_l A_il) / |xi|^2
 // (Eq. G_red) in the transposed order, inverse DFT along x; tile = (tensor
 // row i) x nx x (T kz) for one ky, T compile-time (fs_x_t).
-template <typename R, int N1, int N2>
+template <typename R, int N1, int N2, int T>
 RVE_DEV void fft_x4_tile(const LineParams<R>& P, const int tile) {
   constexpr int N = N1 * N2;
-  constexpr int T = fs_x_t(N);
   using LM = FsLayout<T, N * T, 1, T, 3 * T>;
   if (P.done && *P.done) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -180,10 +179,10 @@ RVE_DEV void fft_x4_tile(const LineParams<R>& P, const int tile) {
   }
 }
 
-template <typename R, int N1, int N2>
+template <typename R, int N1, int N2, int T>
 __global__ void __launch_bounds__(FFT_THREADS, (Fs4Occ<R, N1, N2>::value))
     k_fft_x4(const LineParams<R> P) {
-  fft_x4_tile<R, N1, N2>(P, blockIdx.x);
+  fft_x4_tile<R, N1, N2, T>(P, blockIdx.x);
 }
 
 // x pass of the preconditioned CG iteration: as k_fft_x4, with the
@@ -767,10 +766,15 @@ void launch_fft_y4(const GridGeom& g, bool inverse, cplx<float>* spec, const int
     return;
   }
   switch (g.ny) {
-#define RVE_FS_Y(N, A, B)                                                   \
-  case N:                                                                   \
-    if (inverse) k_fft_y4<float, A, B, true><<<ntiles, FFT_THREADS, sm, s>>>(P); \
-    else k_fft_y4<float, A, B, false><<<ntiles, FFT_THREADS, sm, s>>>(P);   \
+#define RVE_FS_Y(N, A, B)                                                                       \
+  case N:                                                                                       \
+    if (P.t == fs_y_t()) {                                                                      \
+      if (inverse) k_fft_y4<float, A, B, true, fs_y_t()><<<ntiles, FFT_THREADS, sm, s>>>(P);    \
+      else k_fft_y4<float, A, B, false, fs_y_t()><<<ntiles, FFT_THREADS, sm, s>>>(P);           \
+    } else {                                                                                    \
+      if (inverse) k_fft_y4<float, A, B, true, fs_y_t2()><<<ntiles, FFT_THREADS, sm, s>>>(P);   \
+      else k_fft_y4<float, A, B, false, fs_y_t2()><<<ntiles, FFT_THREADS, sm, s>>>(P);          \
+    }                                                                                           \
     break;
     RVE_FS_SIZES(RVE_FS_Y)
 #undef RVE_FS_Y
@@ -817,9 +821,10 @@ void launch_fft_x4(const GridGeom& g, double scale, cplx<float>* spec, const int
     return;
   }
   switch (g.nx) {
-#define RVE_FS_X(N, A, B)                                       \
-  case N:                                                       \
-    k_fft_x4<float, A, B><<<ntiles, FFT_THREADS, sm, s>>>(P);   \
+#define RVE_FS_X(N, A, B)                                                        \
+  case N:                                                                        \
+    if (P.t == fs_x_t(N)) k_fft_x4<float, A, B, fs_x_t(N)><<<ntiles, FFT_THREADS, sm, s>>>(P); \
+    else k_fft_x4<float, A, B, fs_x_t2(N)><<<ntiles, FFT_THREADS, sm, s>>>(P);   \
     break;
     RVE_FS_SIZES(RVE_FS_X)
 #undef RVE_FS_X
@@ -966,9 +971,10 @@ __global__ void __launch_bounds__(FFT_THREADS, 4) k_fs4_batch_y(const Fs4Tab T) 
   const int2 b = T.blk[blockIdx.x];
   const LineParams<float>& P = reinterpret_cast<const LineParams<float>*>(T.params)[b.x];
   switch (T.axis[b.x]) {
-#define RVE_B_Y(N, A, B)                       \
-  case N:                                      \
-    fft_y4_tile<float, A, B, INV>(P, b.y);     \
+#define RVE_B_Y(N, A, B)                                         \
+  case N:                                                        \
+    if (P.t == fs_y_t()) fft_y4_tile<float, A, B, INV, fs_y_t()>(P, b.y);   \
+    else fft_y4_tile<float, A, B, INV, fs_y_t2()>(P, b.y);       \
     break;
     RVE_FS_BATCH_SIZES(RVE_B_Y)
 #undef RVE_B_Y
@@ -981,9 +987,10 @@ __global__ void __launch_bounds__(FFT_THREADS, 4) k_fs4_batch_x(const Fs4Tab T) 
   const int2 b = T.blk[blockIdx.x];
   const LineParams<float>& P = reinterpret_cast<const LineParams<float>*>(T.params)[b.x];
   switch (T.axis[b.x]) {
-#define RVE_B_X(N, A, B)                  \
-  case N:                                 \
-    fft_x4_tile<float, A, B>(P, b.y);     \
+#define RVE_B_X(N, A, B)                                         \
+  case N:                                                        \
+    if (P.t == fs_x_t(N)) fft_x4_tile<float, A, B, fs_x_t(N)>(P, b.y);      \
+    else fft_x4_tile<float, A, B, fs_x_t2(N)>(P, b.y);           \
     break;
     RVE_FS_BATCH_SIZES(RVE_B_X)
 #undef RVE_B_X
@@ -1013,9 +1020,12 @@ __global__ void __launch_bounds__(FFT_THREADS, 3) k_fs4_batch_zinv(const Fs4Tab 
 cudaError_t fft4_kernels_init() {
   g_err4 = cudaSuccess;
 #define RVE_FS_INIT(N, A, B)                                \
-  allow_smem(k_fft_y4<float, A, B, true>);                  \
-  allow_smem(k_fft_y4<float, A, B, false>);                 \
-  allow_smem(k_fft_x4<float, A, B>);                        \
+  allow_smem(k_fft_y4<float, A, B, true, fs_y_t()>);        \
+  allow_smem(k_fft_y4<float, A, B, false, fs_y_t()>);       \
+  allow_smem(k_fft_y4<float, A, B, true, fs_y_t2()>);       \
+  allow_smem(k_fft_y4<float, A, B, false, fs_y_t2()>);      \
+  allow_smem(k_fft_x4<float, A, B, fs_x_t(N)>);             \
+  allow_smem(k_fft_x4<float, A, B, fs_x_t2(N)>);            \
   allow_smem(k_fft_x4_g0<float, A, B>);                     \
   allow_smem(k_zfwd4<float, SRC_CGPX, TAN_FULL81, A, B>);   \
   allow_smem(k_zfwd4<float, SRC_CGPX, TAN_SVK, A, B>);      \

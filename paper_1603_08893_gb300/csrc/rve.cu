@@ -204,7 +204,7 @@ struct rve_s {
   Twiddles<dfl> twdf{};
   bool floatfloat = false;  // mixed: float64-accuracy transforms in float-float
   bool precond = false;     // reference-medium preconditioned float32 CG
-  int knobs[7] = {1, 3, 1, 1, 1, 0, 0};  // kernel variants (rve_tuning)
+  int knobs[9] = {1, 3, 1, 1, 1, 0, 0, 0, 0};  // kernel variants (rve_tuning)
   double Fbar[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
   double Fbar_committed[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};  // F-bar of the last committed state
   double* adj_b = nullptr;  // adjoint right-hand side [9][n] (SVK)
@@ -686,10 +686,13 @@ struct TuneKey {
     return std::tie(nx, ny, nz, dev, tan) < std::tie(o.nx, o.ny, o.nz, o.dev, o.tan);
   }
 };
+// autotuner knobs: the six of rve_tuning knobs[0..5], then the x and y tile
+// heights (0 default, 1 half)
+typedef std::array<int, 8> Knobs;
 std::mutex g_tune_mu;
-std::map<TuneKey, std::array<int, 6>> g_tune_cache;
+std::map<TuneKey, Knobs> g_tune_cache;
 
-void apply_knobs(rve_t h, const std::array<int, 6>& k) {
+void apply_knobs(rve_t h, const Knobs& k) {
   GridGeom& g = h->g;
   GridGeom base;
   make_geom(g.nx, g.ny, g.nz, &base);
@@ -701,7 +704,16 @@ void apply_knobs(rve_t h, const std::array<int, 6>& k) {
   g.py = k[4] ? base.py : base.pys;
   g.pz = k[4] ? base.pz : base.pzs;
   g.zstage = k[5];
+  // tile heights of the four-step x and y passes: the default or half
+  g.fsx_t = k[6] ? fs_x_t2(g.nx) : fs_x_t(g.nx);
+  g.fsy_t = k[7] ? fs_y_t2() : fs_y_t();
+  g.f_fsy_ntk = make_fastdiv((unsigned)((g.hz + g.fsy_t - 1) / g.fsy_t));
+  g.f_fsx_ntk = make_fastdiv((unsigned)((g.hz + g.fsx_t - 1) / g.fsx_t));
+  g.f_fsy_L = make_fastdiv((unsigned)(g.fsy_grp * g.fsy_t));
+  g.f_fsx_L = make_fastdiv((unsigned)(3 * g.fsx_t));
   for (int i = 0; i < 6; ++i) h->knobs[i] = k[i];
+  h->knobs[7] = k[6];
+  h->knobs[8] = k[7];
 }
 
 // Milliseconds per float32 CG iteration with the current knobs; < 0 if the
@@ -744,15 +756,16 @@ int autotune(rve_t h) {
       return RVE_OK;
     }
   }
-  std::array<int, 6> best = {1, 3, 1, 1, 1, 0};
+  Knobs best = {1, 3, 1, 1, 1, 0, 0, 0};
   apply_knobs(h, best);
   double tbest = time_cg_iteration(h);
   if (tbest < 0) return fail(h, RVE_ERR_CUDA, "autotune: CG timing run failed");
-  const std::vector<int> choices[6] = {{1, 0}, {3, 2, 1}, {1, 0}, {1, 0}, {1, 0}, {0, 1}};
-  for (int knob = 0; knob < 6; ++knob)
+  const std::vector<int> choices[8] = {{1, 0}, {3, 2, 1}, {1, 0}, {1, 0}, {1, 0}, {0, 1},
+                                       {0, 1}, {0, 1}};
+  for (int knob = 0; knob < 8; ++knob)
     for (int v : choices[knob]) {
       if (v == best[knob]) continue;
-      std::array<int, 6> cand = best;
+      Knobs cand = best;
       cand[knob] = v;
       apply_knobs(h, cand);
       const double t = time_cg_iteration(h);
@@ -1066,7 +1079,7 @@ struct CkptHeader {
   int version, nx, ny, nz, model, nparam, use_phase, precision, tangent, residual;
   int max_newton, max_cg, mixed_refine;
   double cg_tol_floor, cg_atol;
-  int knobs[7];
+  int knobs[9];
   int precond;
   double Fbar[9], Fbar_committed[9];
 };
@@ -1105,7 +1118,7 @@ int rve_save(rve_t h, const char* path) {
   CkptHeader hd;
   std::memset(&hd, 0, sizeof(hd));
   std::memcpy(hd.magic, "RVECKPT1", 8);
-  hd.version = 2;
+  hd.version = 3;
   hd.nx = h->g.nx;
   hd.ny = h->g.ny;
   hd.nz = h->g.nz;
@@ -1152,7 +1165,7 @@ int rve_load(rve_t* out, const char* path, const rve_options* opt) {
   if (!f) return RVE_ERR_INVALID;
   CkptHeader hd;
   if (std::fread(&hd, sizeof(hd), 1, f) != 1 || std::memcmp(hd.magic, "RVECKPT1", 8) != 0 ||
-      hd.version != 2) {
+      hd.version != 3) {
     std::fclose(f);
     return RVE_ERR_INVALID;
   }
@@ -1232,8 +1245,10 @@ int rve_load(rve_t* out, const char* path, const rve_options* opt) {
   }
   std::memcpy(h->Fbar, hd.Fbar, sizeof(hd.Fbar));
   std::memcpy(h->Fbar_committed, hd.Fbar_committed, sizeof(hd.Fbar_committed));
-  std::array<int, 6> k;
+  Knobs k;
   for (int i = 0; i < 6; ++i) k[i] = hd.knobs[i];
+  k[6] = hd.knobs[7];
+  k[7] = hd.knobs[8];
   apply_knobs(h, k);
   h->knobs[6] = hd.knobs[6];
   *out = h;
@@ -1250,9 +1265,24 @@ int rve_grid(rve_t h, int dims[3]) {
   return RVE_OK;
 }
 
-int rve_tuning(rve_t h, int knobs[7]) {
+int rve_set_tuning(rve_t h, const int knobs[9]) {
   if (!h || !knobs) return RVE_ERR_INVALID;
-  for (int i = 0; i < 7; ++i) knobs[i] = h->knobs[i];
+  for (int i : {0, 2, 3, 4, 5, 7, 8})
+    if (knobs[i] != 0 && knobs[i] != 1) return fail(h, RVE_ERR_INVALID, "tuning knobs are 0 or 1");
+  if (knobs[1] < 1 || knobs[1] > 3) return fail(h, RVE_ERR_INVALID, "z blocks per SM in 1..3");
+  CK(cudaStreamSynchronize(h->s));
+  Knobs k;
+  for (int i = 0; i < 6; ++i) k[i] = knobs[i];
+  k[6] = knobs[7];
+  k[7] = knobs[8];
+  apply_knobs(h, k);
+  h->knobs[6] = 0;
+  return RVE_OK;
+}
+
+int rve_tuning(rve_t h, int knobs[9]) {
+  if (!h || !knobs) return RVE_ERR_INVALID;
+  for (int i = 0; i < 9; ++i) knobs[i] = h->knobs[i];
   return RVE_OK;
 }
 

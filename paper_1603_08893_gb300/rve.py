@@ -342,14 +342,23 @@ def rve_load(path, stream=None):
 
 
 TUNING_KNOBS = ("four_step_z", "z_blocks_per_sm", "four_step_y", "four_step_x",
-                "composite_radices", "staged_z", "autotuned")
+                "composite_radices", "staged_z", "autotuned", "x_tile_half", "y_tile_half")
 
 
 def rve_tuning(h):
     """Kernel variants in use (set by the autotuner or the defaults)."""
-    k = (C.c_int * 7)()
+    k = (C.c_int * 9)()
     _check(lib.rve_tuning(h, k), h)
     return dict(zip(TUNING_KNOBS, (int(v) for v in k)))
+
+
+def rve_set_tuning(h, **knobs):
+    """Sets kernel variants by name (TUNING_KNOBS; the others keep their
+    current values)."""
+    cur = rve_tuning(h)
+    cur.update(knobs)
+    k = (C.c_int * 9)(*[int(cur[name]) for name in TUNING_KNOBS])
+    _check(lib.rve_set_tuning(h, k), h)
 
 
 def rve_kernel_timing(h, family, enable=True):
@@ -481,6 +490,9 @@ class RVE:
 
     def tuning(self):
         return rve_tuning(self.h)
+
+    def set_tuning(self, **knobs):
+        rve_set_tuning(self.h, **knobs)
 
     def save(self, path):
         rve_save(self.h, path)

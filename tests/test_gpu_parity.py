@@ -405,3 +405,48 @@ def test_autotuned_handle_matches_oracle():
         assert maxrel(r.homogenized_P(), prob.homogenized_P()) < 1e-8
         assert rel(r.get_F(), prob.F) < 1e-7
         r.close()
+
+
+@pytest.mark.parametrize("shape", [(45, 63, 125), (243, 15, 21), (15, 315, 27)])
+@pytest.mark.parametrize("halves", [(1, 0), (0, 1), (1, 1)])
+def test_operator_tile_variants_match_oracle(shape, halves):
+    """The autotuner's alternative tile heights of the four-step x and y
+    passes (half the kz values per tile), set explicitly with
+    rve_set_tuning: one float32 operator application against the oracle."""
+    r, F, K, mu, rng = _random_problem(shape, 6, "mixed", "recompute")
+    r.set_tuning(x_tile_half=halves[0], y_tile_half=halves[1])
+    t = r.tuning()
+    assert (t["x_tile_half"], t["y_tile_half"]) == halves and t["autotuned"] == 0
+    _, K4 = svk.constitutive(F, K, mu)
+    dF = rng.standard_normal((3, 3) + shape)
+    got = r.apply_operator(dF)
+    ref = fourier.G(svk.tangent_apply(K4, dF))
+    assert rel(got, ref) < 5e-6
+    r.close()
+
+
+def test_mixed_solve_with_half_tiles_matches_tight_oracle():
+    shape = (27, 33, 45)
+    rng = np.random.default_rng(17)
+    phase = (rng.uniform(size=shape) < 0.3).astype(np.uint8)
+    params = synth.two_phase_params(10.0)
+    Fbar = synth.simple_shear(0.03)
+    prob = solver.SVKProblem.from_phase(phase, params)
+    prob.increment(Fbar, tol_newton=1e-10, tol_cg=1e-12, cg_atol=1e-13)
+    r = RVE(shape, phase=phase, phase_params=params, precision="mixed")
+    r.set_tuning(x_tile_half=1, y_tile_half=1)
+    r.set_macro_F(Fbar)
+    r.solve_increment(1e-5, 1e-8)
+    assert maxrel(r.homogenized_P(), prob.homogenized_P()) < 1e-8
+    assert rel(r.get_F(), prob.F) < 1e-7
+    r.close()
+
+
+def test_set_tuning_rejects_bad_values():
+    r = RVE((9, 9, 9), phase=np.zeros((9, 9, 9), np.uint8), phase_params=[[1.0, 0.5]],
+            precision="mixed")
+    with pytest.raises(RVEError):
+        r.set_tuning(z_blocks_per_sm=4)
+    with pytest.raises(RVEError):
+        r.set_tuning(x_tile_half=2)
+    r.close()
