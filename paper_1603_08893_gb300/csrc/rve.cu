@@ -2222,6 +2222,11 @@ int rve_kernel_time(rve_t h, double* total_ms, long long* launches) {
 namespace {
 constexpr int kBatchStreams = 64;
 constexpr int kGraphIters = 2;
+// once few cells are left (the long CG runs of hard cells), more iterations
+// per graph launch: fewer host round trips; iterations enqueued after a
+// cell's CG has finished return at once
+constexpr int kGraphItersFew = 8;
+constexpr size_t kFewCells = 8;
 
 __global__ void k_gather_cg(SolverState* const* st, int nrve, int* out) {
   for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nrve; b += gridDim.x * blockDim.x) {
@@ -2239,6 +2244,7 @@ struct rve_batch_s {
   bool mixed = false;
   cudaGraphExec_t exec = nullptr;
   std::vector<int> graph_members;  // cells captured in exec
+  int graph_iters = kGraphIters;   // CG iterations per graph launch
   Fs4Batch* fs4 = nullptr;         // batched passes of the captured iteration
   int fs4_cells = 0;               // cells in it (the others are graph branches)
   SolverState** d_states = nullptr;
@@ -2267,6 +2273,8 @@ int batch_capture(rve_batch_t b, const std::vector<int>& cells) {
     cudaGraphExecDestroy(b->exec);
     b->exec = nullptr;
   }
+  const int iters = cells.size() <= kFewCells ? kGraphItersFew : kGraphIters;
+  b->graph_iters = iters;
   // float32 CG of cells whose passes all have batched four-step kernels:
   // their launches are recorded (not run) and become one launch per pass
   fs4_batch_free(b->fs4);
@@ -2312,7 +2320,7 @@ int batch_capture(rve_batch_t b, const std::vector<int>& cells) {
   cudaEventRecord(fork, b->s0);
   std::vector<bool> used(b->streams.size(), false);
   if (b->fs4)
-    for (int k = 0; k < kGraphIters; ++k) fs4_batch_launch(b->fs4, b->s0);
+    for (int k = 0; k < iters; ++k) fs4_batch_launch(b->fs4, b->s0);
   for (int c : branch) {
     rve_t h = b->rv[c];
     const size_t si = (size_t)c % b->streams.size();
@@ -2320,7 +2328,7 @@ int batch_capture(rve_batch_t b, const std::vector<int>& cells) {
       cudaStreamWaitEvent(b->streams[si], fork, 0);
       used[si] = true;
     }
-    for (int k = 0; k < kGraphIters; ++k) enqueue_cg_iteration<R>(h, -1);
+    for (int k = 0; k < iters; ++k) enqueue_cg_iteration<R>(h, -1);
   }
   for (size_t si = 0; si < b->streams.size(); ++si)
     if (used[si]) {
@@ -2357,7 +2365,7 @@ int batch_cg_phase(rve_batch_t b, const std::vector<int>& active, std::vector<in
   while (true) {
     if (cudaGraphLaunch(b->exec, b->s0) != cudaSuccess) return bfail(b, RVE_ERR_CUDA, "graph launch");
     b->launches += ((b->fs4 ? 5 : 0) + (long long)(b->graph_members.size() - b->fs4_cells) *
-                                          (b->mixed ? 5 : 6)) * kGraphIters;
+                                          (b->mixed ? 5 : 6)) * b->graph_iters;
     k_gather_cg<<<(nrve + 127) / 128, 128, 0, b->s0>>>(b->d_states, nrve, b->d_info);
     cudaMemcpyAsync(b->h_info, b->d_info, sizeof(int) * 3 * nrve, cudaMemcpyDeviceToHost, b->s0);
     if (cudaStreamSynchronize(b->s0) != cudaSuccess) return bfail(b, RVE_ERR_CUDA, "batched CG");
