@@ -61,10 +61,13 @@ def test_batch_cell_matches_oracle():
 
 def test_j2_batch_commits_history_like_individual_solves():
     """J2 cells: the batch commits each cell's history as a single cell does
-    (two increments, the second starting from the first's plastic state)."""
+    (two increments, the second starting from the first's plastic state),
+    bit for bit, in the batched passes and in the graph branches."""
     params = np.array([[1 / 1.2, 1 / 2.6, 0.003, 0.01], [1 / 1.2, 1 / 2.6, 0.006, 0.01]])
     cells = []
-    for n, seed in ((9, 1), (15, 2), (9, 3)):
+    # 15^3 and 21^3 cells run the batched passes (stored SYM45 tangent),
+    # the 9^3 cells are graph branches
+    for n, seed in ((9, 1), (15, 2), (9, 3), (21, 4), (15, 5)):
         ph, _ = synth.voronoi(n, 6, np.random.default_rng(seed))
         cells.append(((n, n, n), ph))
     b = RVEBatch([c[0] for c in cells], [c[1] for c in cells], [params] * len(cells),
