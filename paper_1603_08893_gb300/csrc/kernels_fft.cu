@@ -119,6 +119,20 @@ __global__ void FFT_BOUNDS(R) k_fft_y(const LineParams<R> P) {
 // A_ij <- xi_j (sum_l xi_l A_il) / |xi|^2 (Eq. G_red) couples only the three
 // components of one tensor row i, so a tile is (row i) x nx x (T kz) for one
 // ky.
+// 1/a: float reciprocal, or for float64 the Newton-Raphson iteration
+// x <- x (2 - a x) from the float reciprocal (about 24 correct bits, doubled
+// by each step; two steps, written with FMAs as e = 1 - a x, x <- x + x e),
+// which avoids a float64 division per element on a part whose float64
+// rate is 1/64 of its float32 rate.
+RVE_DEV float recip(float a) { return 1.0f / a; }
+RVE_DEV double recip(double a) {
+  double x = (double)__frcp_rn((float)a);
+  double e = fma(-a, x, 1.0);
+  x = fma(x, e, x);
+  e = fma(-a, x, 1.0);
+  return fma(x, e, x);
+}
+
 template <typename R>
 __global__ void FFT_BOUNDS(R) k_fft_x_proj(const LineParams<R> P) {
   if (P.done && *P.done) return;
@@ -156,31 +170,49 @@ __global__ void FFT_BOUNDS(R) k_fft_x_proj(const LineParams<R> P) {
   const RQ sc_ = (RQ)P.scale;
   // Nyquist frequencies of even axes: G-hat = 0 there (Appendix C)
   const bool nyq_y = (ny % 2 == 0) && (2 * y == ny);
+  // blockDim.x is a multiple of T: each thread keeps one t (one kz), so its
+  // xi_z and z-Nyquist test once
+  const int t0 = (int)(threadIdx.x & (T - 1));
+  const RQ qz_ = (RQ)(k0 + t0) / (RQ)P.g.nz;
+  const bool nyq_z = (P.g.nz % 2 == 0) && (2 * (k0 + t0) == P.g.nz);
+  const RQ inv_nx = RQ(1) / (RQ)nx;
   for (int i = threadIdx.x; i < nx * T; i += blockDim.x) {
-    const int t = i & (T - 1);
     const int x = i >> ts;
     // frequencies and 1/|xi|^2 in R (float-float: in float64, then split)
-    const RQ qx_ = signed_freq<RQ>(x, nx) / (RQ)nx;
-    const RQ qz_ = (RQ)(k0 + t) / (RQ)P.g.nz;
+    const RQ qx_ = signed_freq<RQ>(x, nx) * inv_nx;
     const RQ q2 = qx_ * qx_ + qy_ * qy_ + qz_ * qz_;
-    const bool nyq = nyq_y || ((nx % 2 == 0) && (2 * x == nx)) ||
-                     ((P.g.nz % 2 == 0) && (2 * (k0 + t) == P.g.nz));
-    const R f = R((q2 > RQ(0) && !nyq) ? sc_ / q2 : RQ(0));
+    const bool nyq = nyq_y || nyq_z || ((nx % 2 == 0) && (2 * x == nx));
+    const R f = R((q2 > RQ(0) && !nyq) ? sc_ * recip(q2) : RQ(0));
     const R qx = R(qx_), qy = R(qy_), qz = R(qz_);
     const cplx<R> A0 = X[i], A1 = X[nx * T + i], A2 = X[2 * nx * T + i];
     const R sx = f * (qx * A0.x + qy * A1.x + qz * A2.x);
     const R sy = f * (qx * A0.y + qy * A1.y + qz * A2.y);
     X[i] = {sx * qx, sy * qx};
-    X[nx * T + i] = {sx * qy, sy * qy};
-    X[2 * nx * T + i] = {sx * qz, sy * qz};
+    X[nx * T + i] = {sx, sy};
   }
   __syncthreads();
-  const cplx<R>* res = fft_lines_call<R, true>(X, Y, lm, 3 * T, fL, &plan, tw);
+  // row j of the projected spectrum is s xi_j and xi_y, xi_z are constant
+  // along an x line: components 1 and 2 are xi_y and xi_z times the inverse
+  // transform of s -- two inverse transforms per tensor row instead of three
+  FastDiv f2L;  // lines of two components: 2T, a power of two
+  f2L.d = 2u * (unsigned)T;
+  f2L.m = (1ull << 40) / f2L.d;
+  const cplx<R>* res = fft_lines_call<R, true>(X, Y, lm, 2 * T, f2L, &plan, tw);
   const int tc = min(T, hz - k0);
   const int tot = 3 * nx * T;
+  const R qy = R(qy_), qz = R(qz_);
   for (int i = threadIdx.x; i < tot; i += blockDim.x) {
     const int t = i & (T - 1);
-    if (t < tc) gbase[(size_t)(i >> ts) * rs + t] = res[i];
+    if (t >= tc) continue;
+    const int row = i >> ts;  // component c of the row, times nx, plus x
+    if (row < nx) {
+      gbase[(size_t)row * rs + t] = res[i];
+    } else {
+      const int c2 = row >= 2 * nx;
+      const cplx<R> u = res[i - c2 * nx * T];
+      const R fq = c2 ? qz : qy;
+      gbase[(size_t)row * rs + t] = {fq * u.x, fq * u.y};
+    }
   }
 }
 
