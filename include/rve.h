@@ -161,8 +161,10 @@ int rve_workspace_size(int nx, int ny, int nz, int model, const rve_options* opt
  *  phase_params : [nphase][nparam] float64 (host), nparam = 2 (SVK: K, mu)
  *                 or 4 (J2: K, mu, tau_y0, H); K is the bulk modulus
  *                 (lambda = K - 2 mu / 3, Eq. elas:C)
- *  voxel_params : [nparam][n] float64 (host) per-voxel parameters, used
- *                 when phase is NULL
+ *  voxel_params : [nparam][n] float64 per-voxel parameters, used when phase
+ *                 is NULL; host memory, or device memory of the current
+ *                 device (detected; converted on the device without a
+ *                 copy through the host)
  *  opt          : may be NULL (defaults)
  * Errors: RVE_ERR_INVALID (non-positive sizes, bad model, phase index
  * >= nphase, missing parameters), RVE_ERR_NOMEM, RVE_ERR_CUDA. */

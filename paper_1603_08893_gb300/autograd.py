@@ -7,11 +7,10 @@ forward solves the cell (Newton-CG through the C ABI) for the macroscopic
 deformation; backward is one adjoint CG solve with the same operator
 followed by the per-voxel sensitivity kernel (rve_adjoint_grad /
 rve_adjoint_grad_params), which gives every gradient from the same adjoint
-field.  The per-voxel parameters enter at rve_create (host arrays, once per
-forward: the C ABI's creation call copies them in); for CUDA inputs the
-gradients are written by the library straight into CUDA tensors
-(grads_on_device = 1), and only P-bar and dJ/dP-bar (9 values each) cross
-to the host.
+field.  For CUDA inputs the per-voxel parameters go to rve_create as a
+device array (converted on the device) and the gradients are written by the
+library straight into CUDA tensors (grads_on_device = 1): only P-bar and
+dJ/dP-bar (9 values each) cross to the host.
 """
 from __future__ import annotations
 
@@ -28,12 +27,19 @@ class HomogenizedStress(torch.autograd.Function):
     @staticmethod
     def forward(ctx, mu, K, Fbar, increments=1, tol_newton=1e-5, tol_cg=1e-8,
                 precision="fp64", adjoint_tol=1e-10, cg_atol=0.0):
-        mu_np = mu.detach().cpu().numpy().astype(np.float64)
-        K_np = (K.detach().cpu().numpy() if isinstance(K, torch.Tensor)
-                else np.broadcast_to(np.asarray(K, np.float64), mu_np.shape))
-        shape = mu_np.shape
-        r = RVE(shape, voxel_params=np.stack([np.broadcast_to(K_np, shape), mu_np]),
-                precision=precision, cg_atol=cg_atol)
+        shape = tuple(mu.shape)
+        if mu.is_cuda:
+            # parameters stay on the device: the library converts them there
+            m = mu.detach().to(torch.float64)
+            k = (K.detach().to(device=mu.device, dtype=torch.float64) if isinstance(K, torch.Tensor)
+                 else torch.as_tensor(np.asarray(K, np.float64), device=mu.device))
+            vp = torch.stack([k.expand(shape), m]).contiguous()
+        else:
+            mu_np = mu.detach().numpy().astype(np.float64)
+            K_np = (K.detach().numpy() if isinstance(K, torch.Tensor)
+                    else np.asarray(K, np.float64))
+            vp = np.stack([np.broadcast_to(K_np, shape), mu_np])
+        r = RVE(shape, voxel_params=vp, precision=precision, cg_atol=cg_atol)
         Fbar = np.asarray(Fbar, dtype=np.float64)
         eye = np.eye(3)
         for k in range(1, increments + 1):
@@ -80,12 +86,16 @@ class J2HomogenizedStress(torch.autograd.Function):
                 adjoint_tol=1e-10, cg_atol=0.0):
         ref = next(t for t in (K, mu, ty0, H) if isinstance(t, torch.Tensor) and t.dim() == 3)
         shape = tuple(ref.shape)
-        vals = []
-        for t in (K, mu, ty0, H):
-            a = t.detach().cpu().numpy() if isinstance(t, torch.Tensor) else np.asarray(t)
-            vals.append(np.broadcast_to(a.astype(np.float64), shape))
-        r = RVE(shape, model="j2", voxel_params=np.stack(vals), precision=precision,
-                cg_atol=cg_atol)
+        if ref.is_cuda:
+            vals = [(t.detach().to(device=ref.device, dtype=torch.float64) if isinstance(t, torch.Tensor)
+                     else torch.as_tensor(np.asarray(t, np.float64), device=ref.device)).expand(shape)
+                    for t in (K, mu, ty0, H)]
+            vp = torch.stack(vals).contiguous()
+        else:
+            vp = np.stack([np.broadcast_to((t.detach().numpy() if isinstance(t, torch.Tensor)
+                                            else np.asarray(t)).astype(np.float64), shape)
+                           for t in (K, mu, ty0, H)])
+        r = RVE(shape, model="j2", voxel_params=vp, precision=precision, cg_atol=cg_atol)
         ramp = np.asarray(Fbar, dtype=np.float64).reshape(-1, 3, 3)
         ctx.path = len(ramp) > 1
         if ctx.path:

@@ -190,6 +190,9 @@ void launch_fft_y4(const GridGeom& g, bool inverse, cplx<float>* spec, const int
                    const cplx<float>* tw, cudaStream_t s);
 void launch_fft_x4(const GridGeom& g, double scale, cplx<float>* spec, const int* done,
                    const cplx<float>* tw, cudaStream_t s, bool gamma0 = false);
+// per-voxel parameters in device memory to the internal form (kernels_mat.cu)
+void launch_voxel_params(const double* vp, size_t n, int nparam, double* v64, float* v32,
+                         double* sums, double* partials, unsigned int* counter, cudaStream_t s);
 cudaError_t fft4_kernels_init();
 
 // Batched passes of the fused float32 CG iteration (kernels_fft4.cu) for

@@ -361,6 +361,45 @@ static unsigned int grid_for(size_t work) {
   return (unsigned int)b;
 }
 
+// Per-voxel parameters [nparam][n] (K, mu, ...) already in device memory to
+// the internal form (lambda = K - 2 mu / 3, mu, ...) in float64 and, if
+// v32, float32; sums[0..1] = the sums of lambda and mu over the voxels
+// (deterministic last-block reduction), for the preconditioner's reference
+// medium.
+__global__ void __launch_bounds__(VEC_THREADS) k_voxel_params(const double* __restrict__ vp, size_t n,
+                                                              int nparam, double* __restrict__ v64,
+                                                              float* __restrict__ v32, double* sums,
+                                                              double* partials, unsigned int* counter) {
+  double a[2] = {0.0, 0.0}, tot[2];
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+    const double K = vp[v], mu = vp[n + v];
+    const double lam = K - 2.0 * mu / 3.0;
+    v64[v] = lam;
+    v64[n + v] = mu;
+    if (v32) {
+      v32[v] = (float)lam;
+      v32[n + v] = (float)mu;
+    }
+    for (int q = 2; q < nparam; ++q) {
+      const double x = vp[(size_t)q * n + v];
+      v64[(size_t)q * n + v] = x;
+      if (v32) v32[(size_t)q * n + v] = (float)x;
+    }
+    a[0] += lam;
+    a[1] += mu;
+  }
+  if (last_block_sum<2>(a, partials, counter, tot) && threadIdx.x == 0) {
+    sums[0] = tot[0];
+    sums[1] = tot[1];
+  }
+}
+
+void launch_voxel_params(const double* vp, size_t n, int nparam, double* v64, float* v32,
+                         double* sums, double* partials, unsigned int* counter, cudaStream_t s) {
+  k_voxel_params<<<grid_for(n), VEC_THREADS, 0, s>>>(vp, n, nparam, v64, v32, sums, partials, counter);
+}
+
 template <typename R>
 void launch_cg_update(size_t n9, R* x, R* r, const R* p, const R* Ap, SolverState* st,
                       double* partials, cudaStream_t s) {

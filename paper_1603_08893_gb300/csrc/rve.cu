@@ -977,6 +977,14 @@ int rve_create(rve_t* out, int nx, int ny, int nz, int model, int nphase, const 
     ok &= ck(cudaStreamSynchronize(h->s));
   }
   // materials: (lambda, mu) with lambda = K - 2 mu / 3 (Eq. elas:C)
+  bool vp_on_device = false;
+  double vp_sums[2] = {0.0, 0.0};
+  if (!phase && voxel_params) {
+    cudaPointerAttributes pa{};
+    if (cudaPointerGetAttributes(&pa, voxel_params) == cudaSuccess)
+      vp_on_device = pa.type == cudaMemoryTypeDevice || pa.type == cudaMemoryTypeManaged;
+    cudaGetLastError();  // a plain host pointer may leave an error on older drivers
+  }
   if (phase) {
     std::vector<double> t64(256 * 4, 0.0);
     std::vector<float> t32(256 * 4, 0.0f);
@@ -990,6 +998,16 @@ int rve_create(rve_t* out, int nx, int ny, int nz, int model, int nphase, const 
     ok &= ck(cudaMemcpyAsync(h->table64, t64.data(), t64.size() * 8, cudaMemcpyHostToDevice, h->s));
     ok &= ck(cudaMemcpyAsync(h->table32, t32.data(), t32.size() * 4, cudaMemcpyHostToDevice, h->s));
     ok &= ck(cudaMemcpyAsync(h->phase, phase, h->n, cudaMemcpyHostToDevice, h->s));
+    ok &= ck(cudaStreamSynchronize(h->s));
+  } else if (vp_on_device) {
+    // device parameters: converted and averaged by a kernel, only the two
+    // sums of the reference medium come back to the host
+    unsigned int* cnt = &h->st->counter[SLOT_MISC];
+    ok &= ck(cudaMemsetAsync(cnt, 0, sizeof(unsigned int), h->s));
+    launch_voxel_params(voxel_params, h->n, h->nparam, h->vox64, h->vox32, h->tmp64, h->partials, cnt,
+                        h->s);
+    ok &= ck(cudaGetLastError());
+    ok &= ck(cudaMemcpyAsync(vp_sums, h->tmp64, sizeof(vp_sums), cudaMemcpyDeviceToHost, h->s));
     ok &= ck(cudaStreamSynchronize(h->s));
   } else {
     std::vector<double> v64((size_t)h->nparam * h->n);
@@ -1021,6 +1039,9 @@ int rve_create(rve_t* out, int nx, int ny, int nz, int model, int nphase, const 
         lam0 += (double)cnt[k] * (K - 2.0 * mu / 3.0);
         mu0 += (double)cnt[k] * mu;
       }
+    } else if (vp_on_device) {
+      lam0 = vp_sums[0];
+      mu0 = vp_sums[1];
     } else {
       for (size_t v = 0; v < h->n; ++v) {
         lam0 += voxel_params[v] - 2.0 * voxel_params[h->n + v] / 3.0;

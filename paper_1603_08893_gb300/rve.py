@@ -107,12 +107,21 @@ def rve_create(shape, model="svk", phase=None, phase_params=None,
         pp = np.ascontiguousarray(phase_params, dtype=np.float64)
         nphase = pp.shape[0]
         keep += [ph, pp]
-    if voxel_params is not None:
+    vptr = None
+    if voxel_params is not None and _is_torch_cuda(voxel_params):
+        # device tensor: the library converts it on the device
+        t = voxel_params.detach().to(torch.float64).contiguous()
+        if t.numel() != (4 if model == "j2" else 2) * nx * ny * nz:
+            raise ValueError("voxel_params must hold nparam * n values")
+        keep.append(t)
+        vptr = C.c_void_p(t.data_ptr())
+    elif voxel_params is not None:
         vp = np.ascontiguousarray(voxel_params, dtype=np.float64)
         keep.append(vp)
+        vptr = vp.ctypes.data_as(C.c_void_p)
     ptr = (lambda a: a.ctypes.data_as(C.c_void_p) if a is not None else None)
     code = lib.rve_create(C.byref(h), nx, ny, nz, _MODELS[model], nphase,
-                          ptr(ph), ptr(pp), ptr(vp), C.byref(o))
+                          ptr(ph), ptr(pp), vptr, C.byref(o))
     _check(code, what="rve_create failed")
     return h, keep
 
