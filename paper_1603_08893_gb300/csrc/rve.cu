@@ -2242,11 +2242,11 @@ int rve_kernel_time(rve_t h, double* total_ms, long long* launches) {
 // ===========================================================================
 namespace {
 constexpr int kBatchStreams = 64;
-constexpr int kGraphIters = 2;
+constexpr int kGraphIters = 4;
 // once few cells are left (the long CG runs of hard cells), more iterations
 // per graph launch: fewer host round trips; iterations enqueued after a
 // cell's CG has finished return at once
-constexpr int kGraphItersFew = 8;
+constexpr int kGraphItersFew = 16;
 constexpr size_t kFewCells = 8;
 
 __global__ void k_gather_cg(SolverState* const* st, int nrve, int* out) {
