@@ -111,3 +111,25 @@ def test_mixed_batch_runs_one_launch_per_pass():
         r.close()
     assert batch.launch_count() < 0.5 * singles
     batch.close()
+
+
+def test_autotuned_mixed_batch_matches_oracle():
+    """An autotuned mixed batch (each cell's kernel variants timed and chosen,
+    tile heights included; cells on the four-step lengths run the batched
+    passes whatever tile heights they chose) reaches the oracle's converged
+    state for every cell: P-bar 1e-8, F 1e-7 (tight oracle, float32 CG inside
+    the float64 Newton refinement)."""
+    cells = _cells(4, seed=9, sizes=(15, 21))
+    batch = RVEBatch([c[0] for c in cells], [c[1] for c in cells], [c[2] for c in cells],
+                     precision="mixed", autotune=True)
+    st = batch.solve(np.stack([c[3] for c in cells]), tol_newton=1e-10, tol_cg=1e-8)
+    assert all(s["status"] == 0 for s in st)
+    Pb = batch.homogenized_P()
+    for i, (shape, ph, params, Fbar) in enumerate(cells):
+        prob = solver.SVKProblem.from_phase(ph, params)
+        prob.increment(Fbar, tol_newton=1e-10, tol_cg=1e-12, cg_atol=1e-13)
+        ref = prob.homogenized_P()
+        assert np.abs(Pb[i] - ref).max() < 1e-8 * np.abs(ref).max(), i
+        F = batch.get_F(i)
+        assert np.linalg.norm(F - prob.F) / np.linalg.norm(prob.F) < 1e-7, i
+    batch.close()
