@@ -6,8 +6,10 @@
 
 #define RVE_DEV __device__ __forceinline__
 
+// aligned to its size, so that a complex value moves in one vector load or
+// store (8 bytes float, 16 bytes double and float-float)
 template <typename R>
-struct cplx {
+struct alignas(2 * sizeof(R)) cplx {
   R x, y;
 };
 
@@ -103,6 +105,24 @@ RVE_DEV void cg_after_rr(SolverState* st, double rr_new) {
   if (rr_new < 0.81 * st->rr_min) {
     st->rr_min = rr_new;
     st->it_min = st->it;
+  }
+}
+
+// CG start once b.b of the right-hand side b = r (x = 0) is known (one
+// thread): stopping threshold max(tol^2 b.b, atol^2), counters reset.
+RVE_DEV void cg_after_bb(SolverState* st, double bb) {
+  st->bb = bb;
+  st->rr = bb;
+  st->rr_min = bb;
+  st->it_min = 0;
+  st->it = 0;
+  st->beta = 0.0;
+  st->status = 0;
+  st->tol2 = fmax(st->cg_tol * st->cg_tol * bb, st->cg_atol * st->cg_atol);
+  st->done = (bb == 0.0) ? 1 : 0;
+  if (!isfinite(bb)) {
+    st->status = RVE_DEV_ERR_NONFINITE;
+    st->done = 1;
   }
 }
 

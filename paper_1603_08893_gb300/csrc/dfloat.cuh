@@ -65,6 +65,47 @@ RVE_DEV dfl operator*(dfl a, dfl b) {
 }
 
 RVE_DEV dfl fma(dfl a, dfl b, dfl c) { return a * b + c; }
+
+// float64 <-> float-float by integer operations on the bit patterns (the
+// float64 arithmetic and conversion units run at a small fraction of the
+// float32 rate on this hardware).  Split: hi is the float64 significand
+// truncated to 24 bits, which a float holds exactly, lo the remaining 29
+// bits truncated to 24 (one leading-zero count), so hi + lo is within
+// 2^-47 of d relative; then renormalised.  |d| < 2^-126 gives zero (hi
+// would be subnormal), the part of lo below 2^-126 is dropped, and |d| at
+// or beyond 2^128 comes out as inf (nan stays nan if its payload has high
+// bits) -- outside the range a float-float represents.
+RVE_DEV dfl dfl_from_bits(double d) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+  const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+  const int e = (int)(b >> 52) & 0x7ff;
+  const unsigned mh = (unsigned)(b >> 29) & 0x7fffffu;
+  const int eh = e - 896;  // exponent field of hi (float bias 127, float64 bias 1023)
+  if (eh <= 0) return dfl(0.0f, 0.0f);
+  if (eh >= 255) return dfl(__uint_as_float(sign | 0x7f800000u | mh), 0.0f);
+  const float hi = __uint_as_float(sign | ((unsigned)eh << 23) | mh);
+  const unsigned r = (unsigned)b & 0x1fffffffu;  // lo = r 2^(e - 1075)
+  if (r == 0) return dfl(hi, 0.0f);
+  const int z = __clz(r);  // r's leading one moves to bit 31
+  const int el = e - 917 - z;
+  if (el <= 0) return dfl(hi, 0.0f);
+  const float lo = __uint_as_float(sign | ((unsigned)el << 23) | (((r << z) >> 8) & 0x7fffffu));
+  return fast_two_sum(hi, lo);
+}
+
+// a float as a float64, exactly, from its bits (zero, subnormal, inf and nan
+// take the conversion instruction)
+RVE_DEV double f2d_bits(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned ef = (u >> 23) & 0xffu;
+  if (ef == 0u || ef == 255u) return (double)f;
+  return __longlong_as_double((long long)(((unsigned long long)(u & 0x80000000u) << 32) |
+                                          ((unsigned long long)(ef + 896u) << 52) |
+                                          ((unsigned long long)(u & 0x7fffffu) << 29)));
+}
+
+// hi + lo rounded to float64: one float64 addition of the two exact parts
+RVE_DEV double dfl_to_double(dfl a) { return f2d_bits(a.hi) + f2d_bits(a.lo); }
 RVE_DEV dfl& operator+=(dfl& a, dfl b) { return a = a + b; }
 RVE_DEV dfl& operator-=(dfl& a, dfl b) { return a = a - b; }
 RVE_DEV dfl& operator*=(dfl& a, dfl b) { return a = a * b; }

@@ -25,6 +25,9 @@ enum { SRC_FIELD = 0, SRC_CGP = 1, SRC_UNIFORM = 2, SRC_CGPX = 3 };
 // outputs of the inverse z pass
 // OUT_CGR: fused CG iteration end: r -= alpha Ap in place, r.r, CG control
 enum { OUT_PLAIN = 0, OUT_CGAP = 1, OUT_RESID = 2, OUT_CGR = 3 };
+// OUT_PLAIN plus the component means of the result into st->meanX (the
+// float-float projection of dF on the four-step z kernels)
+enum { OUT_PLAIN_MEANX = 4 };
 
 struct GridGeom {
   int nx, ny, nz;
@@ -190,6 +193,19 @@ void launch_fft_y4(const GridGeom& g, bool inverse, cplx<float>* spec, const int
                    const cplx<float>* tw, cudaStream_t s);
 void launch_fft_x4(const GridGeom& g, double scale, cplx<float>* spec, const int* done,
                    const cplx<float>* tw, cudaStream_t s, bool gamma0 = false);
+// the y and x passes of G in float-float arithmetic on the four-step
+// kernels; false (nothing launched) when the axis has no four-step split
+bool launch_fft_y4_df(const GridGeom& g, bool inverse, cplx<dfl>* spec, const cplx<dfl>* tw,
+                      cudaStream_t s);
+bool launch_fft_x4_df(const GridGeom& g, double scale, cplx<dfl>* spec, const cplx<dfl>* tw,
+                      cudaStream_t s);
+// the z passes of G in float-float on the four-step kernels (float64 field
+// in; OUT_PLAIN: float64 out, OUT_RESID: float32 r, x = 0, CG start)
+bool launch_zfwd4_df(const GridGeom& g, const double* in, cplx<dfl>* spec, const cplx<dfl>* tw,
+                     cudaStream_t s);
+bool launch_zinv4_df(const GridGeom& g, int out_mode, const cplx<dfl>* spec, double* out64,
+                     float* r_out, float* x_out, SolverState* st, double* partials,
+                     const cplx<dfl>* tw, cudaStream_t s);
 // per-voxel parameters in device memory to the internal form (kernels_mat.cu)
 void launch_voxel_params(const double* vp, size_t n, int nparam, double* v64, float* v32,
                          double* sums, double* partials, unsigned int* counter, cudaStream_t s);
@@ -215,8 +231,11 @@ void fs4_batch_launch(const Fs4Batch* b, cudaStream_t s);
 
 // G : in in float-float arithmetic on the float32 pipe (float64 in and out):
 // out_mode OUT_PLAIN writes out64 = scale * G:in; OUT_RESID writes
-// r_out = scale * G:in (float32), x_out = 0 and initialises the CG state.
-void launch_G_df(const GridGeom& g, const double* in, double scale, int out_mode, double* out64,
+// r_out = scale * G:in (float32), x_out = 0 and initialises the CG state;
+// OUT_PLAIN_MEANX is OUT_PLAIN that also stores the component means of the
+// result in st->meanX where the z axis has four-step kernels.  Returns
+// whether the means were stored.
+bool launch_G_df(const GridGeom& g, const double* in, double scale, int out_mode, double* out64,
                  float* r_out, float* x_out, SolverState* st, double* partials, cplx<dfl>* spec,
                  const Twiddles<dfl>& tw, cudaStream_t s);
 

@@ -351,20 +351,7 @@ __global__ void FFT_BOUNDS(R) k_zinv(const ZinvParams<R, RC> P) {
         st->alpha = st->rr / pap;
       }
     } else {
-      const double bb = tot[0];
-      st->bb = bb;
-      st->rr = bb;
-      st->rr_min = bb;
-      st->it_min = 0;
-      st->it = 0;
-      st->beta = 0.0;
-      st->status = 0;
-      st->tol2 = fmax(st->cg_tol * st->cg_tol * bb, st->cg_atol * st->cg_atol);
-      st->done = (bb == 0.0) ? 1 : 0;
-      if (!isfinite(bb)) {
-        st->status = RVE_DEV_ERR_NONFINITE;
-        st->done = 1;
-      }
+      cg_after_bb(st, tot[0]);
     }
   }
 }
@@ -540,14 +527,16 @@ static void init_r() {
   allow_big_smem(k_fft_x_proj<R>);
 }
 
-void launch_G_df(const GridGeom& g, const double* in, double scale, int out_mode, double* out64,
+bool launch_G_df(const GridGeom& g, const double* in, double scale, int out_mode, double* out64,
                  float* r_out, float* x_out, SolverState* st, double* partials, cplx<dfl>* spec,
                  const Twiddles<dfl>& tw, cudaStream_t s) {
   const int nlines = g.nx * g.ny;
   const int lz = g.lz_d;
   const dim3 grid((nlines + lz - 1) / lz);
   const size_t smz = sizeof(cplx<dfl>) * ((size_t)((g.nz + 1) & ~1) + 10 * (size_t)lz * g.nz);
-  {
+  // four-step kernels where the axis length has a compiled split, the
+  // Stockham engine otherwise
+  if (!launch_zfwd4_df(g, in, spec, tw.z, s)) {
     ZfwdParams<dfl> P{};
     P.g = g;
     P.lz = lz;
@@ -558,10 +547,12 @@ void launch_G_df(const GridGeom& g, const double* in, double scale, int out_mode
     P.tw = tw.z;
     k_zfwd<dfl, SRC_FIELD, 0><<<grid, FFT_THREADS, smz, s>>>(P);
   }
-  launch_fft_y<dfl>(g, false, spec, nullptr, tw, s);
-  launch_fft_x_proj<dfl>(g, scale, spec, nullptr, tw, s);
-  launch_fft_y<dfl>(g, true, spec, nullptr, tw, s);
-  if (out_mode == OUT_PLAIN) {
+  if (!launch_fft_y4_df(g, false, spec, tw.y, s)) launch_fft_y<dfl>(g, false, spec, nullptr, tw, s);
+  if (!launch_fft_x4_df(g, scale, spec, tw.x, s)) launch_fft_x_proj<dfl>(g, scale, spec, nullptr, tw, s);
+  if (!launch_fft_y4_df(g, true, spec, tw.y, s)) launch_fft_y<dfl>(g, true, spec, nullptr, tw, s);
+  if (launch_zinv4_df(g, out_mode, spec, out64, r_out, x_out, st, partials, tw.z, s))
+    return out_mode == OUT_PLAIN_MEANX;
+  if (out_mode != OUT_RESID) {
     ZinvParams<dfl, double> P{};
     P.g = g;
     P.lz = lz;
@@ -583,6 +574,7 @@ void launch_G_df(const GridGeom& g, const double* in, double scale, int out_mode
     P.tw = tw.z;
     k_zinv<dfl, float, OUT_RESID><<<grid, FFT_THREADS, smz, s>>>(P);
   }
+  return false;
 }
 
 cudaError_t fft_kernels_init() {

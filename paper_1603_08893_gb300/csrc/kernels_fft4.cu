@@ -36,7 +36,8 @@ RVE_DEV void fft_y4_tile(const LineParams<R>& P, const int tile) {
   const int hz = P.g.hz, hzp = P.g.hzp;  // kz extent (z axis), not this axis
   const int ngroups = 9 * P.g.nx;
   const int ntk = (hz + T - 1) / T;
-  const int tg = (int)P.g.f_fsy_ntk.div((unsigned)tile);
+  // the float-float tiles have their own height: plain division there
+  const int tg = is_dfl<R>::value ? tile / ntk : (int)P.g.f_fsy_ntk.div((unsigned)tile);
   const int k0 = (tile - tg * ntk) * T, g0 = tg * GRP;
   const int ng = min(GRP, ngroups - g0);
   cplx<R>* gbase = P.spec + (size_t)g0 * N * hzp + k0;
@@ -81,6 +82,39 @@ __global__ void __launch_bounds__(FFT_THREADS, (Fs4Occ<R, N1, N2>::value) + (N1 
   fft_y4_tile<R, N1, N2, INV, T>(P, blockIdx.x);
 }
 
+// k / n in the pass's arithmetic.  Float: the rounded quotient.
+// Float-float: the rounded quotient h plus the rounded quotient of the
+// remainder k - h n, which one fma gives exactly (the remainder of a
+// correctly rounded division is representable).
+template <typename R>
+RVE_DEV R fs_ratio(int k, int n);
+template <>
+RVE_DEV float fs_ratio<float>(int k, int n) {
+  return (float)k / (float)n;
+}
+template <>
+RVE_DEV dfl fs_ratio<dfl>(int k, int n) {
+  const float kf = (float)k, nf = (float)n;
+  const float h = __fdiv_rn(kf, nf);
+  return fast_two_sum(h, __fdiv_rn(fmaf(-h, nf, kf), nf));
+}
+
+RVE_DEV bool fs_positive(float a) { return a > 0.0f; }
+RVE_DEV bool fs_positive(dfl a) { return a.hi > 0.0f; }
+
+// 1 / a.  Float: the correctly rounded reciprocal.  Float-float: one Newton
+// step from it, r = r0 + r0 e with e = 1 - a r0 formed from the exact
+// product a.hi r0 = p + pe (fma) -- 1 - p is exact since p is within an
+// ulp of 1 -- so the relative error is of order e^2 ~ 2^-48.
+RVE_DEV float fs_rcp(float a) { return __frcp_rn(a); }
+RVE_DEV dfl fs_rcp(dfl a) {
+  const float r0 = __frcp_rn(a.hi);
+  const float p = a.hi * r0;
+  const float pe = fmaf(a.hi, r0, -p);
+  const float e = ((1.0f - p) - pe) - a.lo * r0;
+  return fast_two_sum(r0, r0 * e);
+}
+
 // Forward DFT along x, projection A_ij <- xi_j (sum_l xi_l A_il) / |xi|^2
 // (Eq. G_red) in the transposed order, inverse DFT along x; tile = (tensor
 // row i) x nx x (T kz) for one ky, T compile-time (fs_x_t).
@@ -96,7 +130,7 @@ RVE_DEV void fft_x4_tile(const LineParams<R>& P, const int tile) {
   const int hz = P.g.hz, hzp = P.g.hzp;
   const int ntk = (hz + T - 1) / T;
   const size_t rs = (size_t)ny * hzp;  // stride of spectrum rows (c*nx + x)
-  const int q = (int)P.g.f_fsx_ntk.div((unsigned)tile);
+  const int q = is_dfl<R>::value ? tile / ntk : (int)P.g.f_fsx_ntk.div((unsigned)tile);
   const int k0 = (tile - q * ntk) * T;
   const int irow = (int)P.g.f_ny.div((unsigned)q);
   const int y = q - irow * ny;
@@ -111,14 +145,14 @@ RVE_DEV void fft_x4_tile(const LineParams<R>& P, const int tile) {
   fs_phase_a_g2s<R, N1, N2, LM, decltype(gl), false>(buf, tw2, gl);
   __syncthreads();
   fs_phase_b<R, N1, N2, false, LM, false>(buf);
-  const R qy = signed_freq<R>(y, ny) / (R)ny;
+  const R qy = fs_ratio<R>(signed_freq<int>(y, ny), ny);
   const R sc = (R)P.scale;
   // xi_x of each transposed position and xi_z of each kz of the tile
   R* qxs = reinterpret_cast<R*>(buf + 3 * N * T);  // [N]
   R* qzs = qxs + N;                                // [T]
   for (int i = threadIdx.x; i < N + T; i += FFT_THREADS) {
-    if (i < N) qxs[i] = signed_freq<R>(fs_freq<N1, N2>(i), N) / (R)N;
-    else qzs[i - N] = (R)(k0 + i - N) / (R)P.g.nz;
+    if (i < N) qxs[i] = fs_ratio<R>(signed_freq<int>(fs_freq<N1, N2>(i), N), N);
+    else qzs[i - N] = fs_ratio<R>(k0 + i - N, P.g.nz);
   }
   __syncthreads();
   // Nyquist frequencies of even y / z axes: G-hat = 0 there (Appendix C;
@@ -130,7 +164,7 @@ RVE_DEV void fft_x4_tile(const LineParams<R>& P, const int tile) {
     const R qz = qzs[i % T];
     const R q2 = qx * qx + qy * qy + qz * qz;
     const bool nyq = nyq_y || (k0 + i % T == kz_nyq);
-    const R f = (q2 > R(0) && !nyq) ? sc * __frcp_rn(q2) : R(0);
+    const R f = (fs_positive(q2) && !nyq) ? sc * fs_rcp(q2) : R(0);
     const cplx<R> A0 = buf[i], A1 = buf[N * T + i], A2 = buf[2 * N * T + i];
     const R sx = f * (qx * A0.x + qy * A1.x + qz * A2.x);
     const R sy = f * (qx * A0.y + qy * A1.y + qz * A2.y);
@@ -183,6 +217,401 @@ template <typename R, int N1, int N2, int T>
 __global__ void __launch_bounds__(FFT_THREADS, (Fs4Occ<R, N1, N2>::value))
     k_fft_x4(const LineParams<R> P) {
   fft_x4_tile<R, N1, N2, T>(P, blockIdx.x);
+}
+
+// The y and x passes of G in float-float arithmetic (the float64-accurate
+// residual and projection of the mixed solver): the same tiles with 16-byte
+// complex values, two blocks per SM for the registers that the N2-point
+// float-float DFTs hold.  T = 16 kz per tile where the tile fits 100 KB
+// (x pass: 8 or 4 beyond), so that the N2-point DFTs of the second phase
+// still give most of the 256 threads a line (tile lines x N1 items).
+constexpr int fs_y_t_df() { return 16; }
+constexpr int fs_x_t_df(int n) {
+  return 16 * 2 * n * 16 <= 102400 ? 16 : (16 * 2 * n * 8 <= 102400 ? 8 : 4);
+}
+// z lines per tile of the float-float z passes: the most whose five packed
+// lines fit 104 KB (two blocks per SM)
+constexpr int fs_zd_lz(int n) {
+  int best = 1;
+  for (int lz = 1; lz <= 64; ++lz)
+    if (16 * ((size_t)((n + 1) & ~1) + (size_t)n * ((5 * lz) | 1)) <= 104 * 1024) best = lz;
+  return best;
+}
+
+template <int N1, int N2, bool INV>
+__global__ void __launch_bounds__(FFT_THREADS, 2) k_fft_y4_df(const LineParams<dfl> P) {
+  fft_y4_tile<dfl, N1, N2, INV, fs_y_t_df()>(P, blockIdx.x);
+}
+
+// Phase B of the float-float x pass with its N2-point DFTs split once more
+// where N2 is composite, N2 = Na Nb (Na its smallest factor), through the
+// shared buffer: sub-phase 1 runs Na-point DFTs on stride Nb within each
+// N2 block, times w_N2^(b ka) (twb[m] = w_N2^m), sub-phase 2 Nb-point DFTs on
+// its contiguous runs, leaving frequency ka + Na kb of the block at position
+// Nb ka + kb (fs_freq_df).  A float-float N2-point DFT is long, and the x
+// tile's 2T lines give only 2T N1 of them (160 for 256 threads at 125);
+// the sub-phases give 2T N1 Nb and 2T N1 Na short ones.  The inverse runs
+// the conjugate steps in reverse order.
+template <int N1, int N2>
+RVE_DEV int fs_freq_df(int p) {
+  constexpr int Na = smallest_factor(N2), Nb = N2 / Na;
+  if constexpr (Na == N2) {
+    return fs_freq<N1, N2>(p);
+  } else {
+    const int s = p % N2;
+    return p / N2 + N1 * (s / Nb + Na * (s % Nb));
+  }
+}
+
+template <int N1, int N2, bool INV, typename LM>
+RVE_DEV void df_phase_b(cplx<dfl>* buf, const cplx<dfl>* twb) {
+  using R = dfl;
+  constexpr int Na = smallest_factor(N2), Nb = N2 / Na;
+  if constexpr (Na == N2) {
+    fs_phase_b<R, N1, N2, INV, LM>(buf);
+  } else {
+    constexpr int tot1 = LM::L * N1 * Nb, tot2 = LM::L * N1 * Na;
+    auto sub1 = [&]() {  // items (line, k1, b): positions Nb a + b of the block
+      for (int i = threadIdx.x; i < tot1; i += FFT_THREADS) {
+        const int l = i % LM::L, r = i / LM::L;
+        const int b = r % Nb, k1 = r / Nb;
+        cplx<R>* line = buf + LM::base(l) + (N2 * k1 + b) * LM::ES;
+        cplx<R> t[Na];
+#pragma unroll
+        for (int a = 0; a < Na; ++a) t[a] = line[Nb * a * LM::ES];
+        if (INV && b != 0) {
+#pragma unroll
+          for (int ka = 1; ka < Na; ++ka) t[ka] = c_mulc(t[ka], twb[b * ka]);
+        }
+        dft_reg<R, Na, INV>(t);
+        if (!INV && b != 0) {
+#pragma unroll
+          for (int ka = 1; ka < Na; ++ka) t[ka] = c_mul(t[ka], twb[b * ka]);
+        }
+#pragma unroll
+        for (int a = 0; a < Na; ++a) line[Nb * a * LM::ES] = t[a];
+      }
+    };
+    auto sub2 = [&]() {  // items (line, k1, ka): positions Nb ka + kb of the block
+      for (int i = threadIdx.x; i < tot2; i += FFT_THREADS) {
+        const int l = i % LM::L, r = i / LM::L;
+        const int ka = r % Na, k1 = r / Na;
+        cplx<R>* line = buf + LM::base(l) + (N2 * k1 + Nb * ka) * LM::ES;
+        cplx<R> u[Nb];
+#pragma unroll
+        for (int b = 0; b < Nb; ++b) u[b] = line[b * LM::ES];
+        dft_reg<R, Nb, INV>(u);
+#pragma unroll
+        for (int b = 0; b < Nb; ++b) line[b * LM::ES] = u[b];
+      }
+    };
+    if (!INV) {
+      sub1();
+      __syncthreads();
+      sub2();
+    } else {
+      sub2();
+      __syncthreads();
+      sub1();
+    }
+  }
+}
+
+// x pass of G in float-float.  xi_y and xi_z are constant along an x line,
+// so the sum over l of xi_l A^_il needs only two forward transforms per
+// tensor row: A_i0 and B_i = xi_y A_i1 + xi_z A_i2, formed while the tile
+// is loaded (xi . A^_i = xi_x A^_i0 + B^_i); with the two inverse
+// transforms of the projection, four line DFTs per row instead of five --
+// the DFTs being most of this pass's float-float arithmetic.
+template <int N1, int N2, int T>
+RVE_DEV void fft_x4_df_tile(const LineParams<dfl>& P, const int tile) {
+  using R = dfl;
+  constexpr int N = N1 * N2;
+  using LM = FsLayout<T, N * T, 1, T, 2 * T>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cplx<R>* tw2 = reinterpret_cast<cplx<R>*>(smem_raw);
+  cplx<R>* buf = tw2 + ((N + 1) & ~1);
+  R* qxs = reinterpret_cast<R*>(buf + 2 * N * T);  // [N]
+  R* qzs = qxs + N;                                // [T]
+  // w_N2^m, after qzs rounded to 16 bytes
+  cplx<R>* twb = reinterpret_cast<cplx<R>*>(qzs + T + ((N + T) & 1));
+  const int ny = P.g.ny;
+  const int hz = P.g.hz, hzp = P.g.hzp;
+  const int ntk = (hz + T - 1) / T;
+  const size_t rs = (size_t)ny * hzp;  // stride of spectrum rows (c*nx + x)
+  const int q = tile / ntk;
+  const int k0 = (tile - q * ntk) * T;
+  const int irow = (int)P.g.f_ny.div((unsigned)q);
+  const int y = q - irow * ny;
+  cplx<R>* gbase = P.spec + (size_t)(3 * irow) * N * rs + (size_t)y * hzp + k0;
+  const R qy = fs_ratio<R>(signed_freq<int>(y, ny), ny);
+  fs_twiddles<R, N1, N2>(tw2, P.tw);
+  for (int i = threadIdx.x; i < N + T + N2; i += FFT_THREADS) {
+    if (i < N) qxs[i] = fs_ratio<R>(signed_freq<int>(fs_freq_df<N1, N2>(i), N), N);
+    else if (i < N + T) qzs[i - N] = fs_ratio<R>(k0 + i - N, P.g.nz);
+    else twb[i - N - T] = P.tw[N1 * (i - N - T)];
+  }
+  __syncthreads();
+  // forward phase A from global: line l < T is A_i0 at kz k0 + l, line
+  // T + t is B_i at kz k0 + t
+  constexpr int totA = 2 * T * N2;
+  for (int i = threadIdx.x; i < totA; i += FFT_THREADS) {
+    const int n2 = i / (2 * T);
+    const int l = i - n2 * (2 * T);
+    const int t = l % T;
+    const bool ok = k0 + t < hz;
+    cplx<R> v[N1];
+    if (l < T) {
+#pragma unroll
+      for (int m = 0; m < N1; ++m)
+        v[m] = ok ? gbase[(size_t)(N2 * m + n2) * rs + t] : cplx<R>{R(0.0f, 0.0f), R(0.0f, 0.0f)};
+    } else {
+      const R qz = qzs[t];
+#pragma unroll
+      for (int m = 0; m < N1; ++m) {
+        if (ok) {
+          const size_t o = (size_t)(N2 * m + n2) * rs + t;
+          const cplx<R> a1 = gbase[(size_t)N * rs + o], a2 = gbase[(size_t)(2 * N) * rs + o];
+          v[m] = {qy * a1.x + qz * a2.x, qy * a1.y + qz * a2.y};
+        } else {
+          v[m] = {R(0.0f, 0.0f), R(0.0f, 0.0f)};
+        }
+      }
+    }
+    dft_reg<R, N1, false>(v);
+    if (n2 != 0) {
+      const cplx<R>* w = tw2 + n2 * N1;
+#pragma unroll
+      for (int k1 = 1; k1 < N1; ++k1) v[k1] = c_mul(v[k1], w[k1]);
+    }
+    cplx<R>* line = buf + LM::base(l) + n2 * LM::ES;
+#pragma unroll
+    for (int m = 0; m < N1; ++m) line[m * N2 * LM::ES] = v[m];
+  }
+  __syncthreads();
+  df_phase_b<N1, N2, false, LM>(buf, twb);
+  __syncthreads();
+  const R sc = (R)P.scale;
+  const bool nyq_y = (ny % 2 == 0) && (2 * y == ny);
+  const int kz_nyq = (P.g.nz % 2 == 0) ? P.g.nz / 2 : -1;
+  for (int i = threadIdx.x; i < N * T; i += FFT_THREADS) {
+    const R qx = qxs[i / T];
+    const R qz = qzs[i % T];
+    const R q2 = qx * qx + qy * qy + qz * qz;
+    const bool nyq = nyq_y || (k0 + i % T == kz_nyq);
+    const R f = (fs_positive(q2) && !nyq) ? sc * fs_rcp(q2) : R(0.0f, 0.0f);
+    const cplx<R> A0 = buf[i], B = buf[N * T + i];
+    const R sx = f * (qx * A0.x + B.x);
+    const R sy = f * (qx * A0.y + B.y);
+    buf[i] = {sx * qx, sy * qx};
+    buf[N * T + i] = {sx, sy};
+  }
+  __syncthreads();
+  // inverse: row j of the projected tensor is s xi_j; components 1 and 2
+  // are xi_y and xi_z times the inverse transform of s
+  df_phase_b<N1, N2, true, LM>(buf, twb);
+  __syncthreads();
+  constexpr int total = 2 * T * N2;
+  for (int i = threadIdx.x; i < total; i += FFT_THREADS) {
+    const int n2 = i / (2 * T);
+    const int l = i - n2 * (2 * T);
+    const cplx<R>* line = buf + LM::base(l) + n2 * LM::ES;
+    cplx<R> v[N1];
+#pragma unroll
+    for (int k1 = 0; k1 < N1; ++k1) v[k1] = line[k1 * N2 * LM::ES];
+    if (n2 != 0) {
+      const cplx<R>* w = tw2 + n2 * N1;
+#pragma unroll
+      for (int k1 = 1; k1 < N1; ++k1) v[k1] = c_mulc(v[k1], w[k1]);
+    }
+    dft_reg<R, N1, true>(v);
+    const int t = l % T;
+    if (k0 + t < hz) {
+      if (l < T) {
+        cplx<R>* g = gbase + t;
+#pragma unroll
+        for (int m = 0; m < N1; ++m) g[(size_t)(N2 * m + n2) * rs] = v[m];
+      } else {
+        const R qz = qzs[t];
+        cplx<R>* g1 = gbase + (size_t)N * rs + t;
+        cplx<R>* g2 = gbase + (size_t)(2 * N) * rs + t;
+#pragma unroll
+        for (int m = 0; m < N1; ++m) {
+          g1[(size_t)(N2 * m + n2) * rs] = {qy * v[m].x, qy * v[m].y};
+          g2[(size_t)(N2 * m + n2) * rs] = {qz * v[m].x, qz * v[m].y};
+        }
+      }
+    }
+  }
+}
+
+template <int N1, int N2>
+__global__ void __launch_bounds__(FFT_THREADS, 2) k_fft_x4_df(const LineParams<dfl> P) {
+  fft_x4_df_tile<N1, N2, fs_x_t_df(N1 * N2)>(P, blockIdx.x);
+}
+
+RVE_DEV dfl dfl_half(dfl a) { return {0.5f * a.hi, 0.5f * a.lo}; }  // exact
+
+// First z pass of G in float-float, persistent: each block walks tiles of
+// lz z-lines (stride gridDim.x) -- the float64 field split into hi + lo
+// pairs (integer operations, dfl_from_bits), components 2k and 2k+1 packed as the real and imaginary parts of
+// complex line k (five per voxel line), in-place four-step DFT, half
+// spectrum out (the two real spectra separated by the Hermitian symmetry).
+template <int N1, int N2>
+__global__ void __launch_bounds__(FFT_THREADS, 2) k_zfwd4_df(const ZfwdParams<dfl> P) {
+  using R = dfl;
+  constexpr int N = N1 * N2;
+  constexpr int lz = fs_zd_lz(N), LP = (5 * lz) | 1, hz = N / 2 + 1;
+  using LM = FsLayout<5 * lz, 0, 1, LP, 5 * lz>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cplx<R>* tw2 = reinterpret_cast<cplx<R>*>(smem_raw);
+  cplx<R>* buf = tw2 + ((N + 1) & ~1);
+  fs_twiddles<R, N1, N2>(tw2, P.tw);
+  const size_t n = P.g.n;
+  const int nlines = P.g.nx * P.g.ny;
+  const int ntiles = (nlines + lz - 1) / lz;
+  const int hzp = P.g.hzp;
+  const size_t ss = P.g.sstride;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int l0 = tile * lz;
+    const int nl = min(lz, nlines - l0);
+    const int nvox = nl * N;
+    const size_t v0 = (size_t)l0 * N;
+    for (int i = threadIdx.x; i < lz * N; i += FFT_THREADS) {
+      R out[9];
+      if (i < nvox) {
+        double d[9];
+#pragma unroll
+        for (int c = 0; c < 9; ++c) d[c] = P.field64[(size_t)c * n + v0 + i];
+#pragma unroll
+        for (int c = 0; c < 9; ++c) out[c] = dfl_from_bits(d[c]);
+      } else {
+#pragma unroll
+        for (int c = 0; c < 9; ++c) out[c] = R(0.0f, 0.0f);
+      }
+      const int li = i / N;
+      cplx<R>* e = buf + (i - li * N) * LP + li;
+#pragma unroll
+      for (int k = 0; k < 5; ++k)
+        e[k * lz] = {out[2 * k], (2 * k + 1 < 9) ? out[2 * k + 1] : R(0.0f, 0.0f)};
+    }
+    __syncthreads();
+    fs_lines<R, N1, N2, false, LM>(buf, tw2);
+    // spectrum k of line z = a + i b: A = (Z_k + conj Z_-k) / 2,
+    // B = (Z_k - conj Z_-k) / (2i)
+    for (int i = threadIdx.x; i < 5 * lz * hz; i += FFT_THREADS) {
+      const int rest = i / hz;
+      const int kz = i - rest * hz;
+      const int k = rest / lz;
+      const int li = rest - k * lz;
+      if (li >= nl) continue;
+      const int l = k * lz + li;
+      const cplx<R> z1 = buf[fs_pos<N1, N2>(kz) * LP + l];
+      const cplx<R> z2 = buf[fs_pos<N1, N2>(kz ? N - kz : 0) * LP + l];
+      const size_t o = (size_t)(l0 + li) * hzp + kz;
+      P.spec[(size_t)(2 * k) * ss + o] = {dfl_half(z1.x + z2.x), dfl_half(z1.y - z2.y)};
+      if (2 * k + 1 < 9)
+        P.spec[(size_t)(2 * k + 1) * ss + o] = {dfl_half(z1.y + z2.y), dfl_half(z2.x - z1.x)};
+    }
+    __syncthreads();  // the buffer is refilled by the next tile
+  }
+}
+
+// Last z pass of G in float-float, persistent: the full z spectrum of each
+// packed line rebuilt from the two half spectra (Z_k = A_k + i B_k, Z_-k =
+// conj A_k + i conj B_k), in-place inverse four-step DFT, then OUT_PLAIN:
+// the float64 result (OUT_PLAIN_MEANX: and its component means, summed in
+// float-float per thread, in float64 across threads and blocks, into
+// st->meanX); OUT_RESID: r = result (float32), x = 0, and the CG start
+// from b.b.
+template <int N1, int N2, typename RC, int OUT>
+__global__ void __launch_bounds__(FFT_THREADS, 2) k_zinv4_df(const ZinvParams<dfl, RC> P) {
+  using R = dfl;
+  constexpr int N = N1 * N2;
+  constexpr int lz = fs_zd_lz(N), LP = (5 * lz) | 1, hz = N / 2 + 1;
+  using LM = FsLayout<5 * lz, 0, 1, LP, 5 * lz>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cplx<R>* tw2 = reinterpret_cast<cplx<R>*>(smem_raw);
+  cplx<R>* buf = tw2 + ((N + 1) & ~1);
+  fs_twiddles<R, N1, N2>(tw2, P.tw);
+  const size_t n = P.g.n;
+  const int nlines = P.g.nx * P.g.ny;
+  const int ntiles = (nlines + lz - 1) / lz;
+  const int hzp = P.g.hzp;
+  const size_t ss = P.g.sstride;
+  double acc = 0.0;
+  dfl msum[9];
+#pragma unroll
+  for (int c = 0; c < 9; ++c) msum[c] = dfl(0.0f, 0.0f);
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int l0 = tile * lz;
+    const int nl = min(lz, nlines - l0);
+    const int nvox = nl * N;
+    const size_t v0 = (size_t)l0 * N;
+    for (int i = threadIdx.x; i < 5 * lz * hz; i += FFT_THREADS) {
+      const int rest = i / hz;
+      const int kz = i - rest * hz;
+      const int k = rest / lz;
+      const int li = rest - k * lz;
+      const int l = k * lz + li;
+      const R zero(0.0f, 0.0f);
+      cplx<R> A = {zero, zero}, B = {zero, zero};
+      if (li < nl) {
+        const size_t o = (size_t)(l0 + li) * hzp + kz;
+        A = P.spec[(size_t)(2 * k) * ss + o];
+        if (2 * k + 1 < 9) B = P.spec[(size_t)(2 * k + 1) * ss + o];
+      }
+      buf[fs_pos<N1, N2>(kz) * LP + l] = {A.x - B.y, A.y + B.x};
+      if (kz > 0) buf[fs_pos<N1, N2>(N - kz) * LP + l] = {A.x + B.y, B.x - A.y};
+    }
+    __syncthreads();
+    fs_lines<R, N1, N2, true, LM>(buf, tw2);
+    for (int i = threadIdx.x; i < nvox; i += FFT_THREADS) {
+      const int li = i / N;
+      const cplx<R>* e = buf + (i - li * N) * LP + li;
+      R out[9];
+#pragma unroll
+      for (int k = 0; k < 5; ++k) {
+        const cplx<R> z = e[k * lz];
+        out[2 * k] = z.x;
+        if (2 * k + 1 < 9) out[2 * k + 1] = z.y;
+      }
+      const size_t v = v0 + i;
+      if constexpr (OUT == OUT_PLAIN || OUT == OUT_PLAIN_MEANX) {
+#pragma unroll
+        for (int c = 0; c < 9; ++c) P.dst64[(size_t)c * n + v] = (double)out[c];
+        if constexpr (OUT == OUT_PLAIN_MEANX) {
+#pragma unroll
+          for (int c = 0; c < 9; ++c) msum[c] = msum[c] + out[c];
+        }
+      } else {
+        R s(0.0f, 0.0f);
+#pragma unroll
+        for (int c = 0; c < 9; ++c) {
+          P.r_out[(size_t)c * n + v] = (RC)out[c];
+          P.x_out[(size_t)c * n + v] = (RC)0;
+          s = fma(out[c], out[c], s);
+        }
+        acc += (double)s;
+      }
+    }
+    __syncthreads();  // the buffer is refilled by the next tile
+  }
+  if constexpr (OUT == OUT_RESID) {
+    double v1[1] = {acc}, tot[1];
+    if (last_block_sum_of<1>(v1, P.partials, &P.st->counter[SLOT_BB], tot, blockIdx.x, gridDim.x) &&
+        threadIdx.x == 0)
+      cg_after_bb(P.st, tot[0]);
+  } else if constexpr (OUT == OUT_PLAIN_MEANX) {
+    double v9[9], tot[9];
+#pragma unroll
+    for (int c = 0; c < 9; ++c) v9[c] = (double)msum[c];
+    if (last_block_sum_of<9>(v9, P.partials, &P.st->counter[SLOT_MEAN], tot, blockIdx.x,
+                             gridDim.x) &&
+        threadIdx.x == 0) {
+      for (int c = 0; c < 9; ++c) P.st->meanX[c] = tot[c] / (double)n;
+    }
+  }
 }
 
 // x pass of the preconditioned CG iteration: as k_fft_x4, with the
@@ -833,6 +1262,130 @@ void launch_fft_x4(const GridGeom& g, double scale, cplx<float>* spec, const int
   }
 }
 
+bool launch_fft_y4_df(const GridGeom& g, bool inverse, cplx<dfl>* spec, const cplx<dfl>* tw,
+                      cudaStream_t s) {
+  LineParams<dfl> P;
+  P.g = g;
+  P.t = fs_y_t_df();
+  P.scale = 1.0;
+  P.spec = spec;
+  P.done = nullptr;
+  P.tw = tw;
+  constexpr int T = fs_y_t_df();
+  switch (g.ny) {
+#define RVE_FS_YD(N, A, B)                                                                       \
+  case N: {                                                                                      \
+    constexpr int GRP = fs_y_grp(N);                                                             \
+    P.grp = GRP;                                                                                 \
+    const int ntiles = ((g.hz + T - 1) / T) * ((9 * g.nx + GRP - 1) / GRP);                      \
+    const size_t sm = sizeof(cplx<dfl>) * ((size_t)((N + 1) & ~1) + (size_t)GRP * N * T);         \
+    if (inverse) k_fft_y4_df<A, B, true><<<ntiles, FFT_THREADS, sm, s>>>(P);                     \
+    else k_fft_y4_df<A, B, false><<<ntiles, FFT_THREADS, sm, s>>>(P);                            \
+    return true;                                                                                 \
+  }
+    RVE_FS_SIZES(RVE_FS_YD)
+#undef RVE_FS_YD
+    default:
+      return false;
+  }
+}
+
+static int sm_count();
+
+bool launch_zfwd4_df(const GridGeom& g, const double* in, cplx<dfl>* spec, const cplx<dfl>* tw,
+                     cudaStream_t s) {
+  ZfwdParams<dfl> P{};
+  P.g = g;
+  P.src = SRC_FIELD;
+  P.field64 = in;
+  P.spec = spec;
+  P.tw = tw;
+  const int nlines = g.nx * g.ny;
+  switch (g.nz) {
+#define RVE_FS_ZFD(N, A, B)                                                                      \
+  case N: {                                                                                      \
+    constexpr int lz = fs_zd_lz(N);                                                              \
+    const int nblk = std::min((nlines + lz - 1) / lz, 2 * sm_count());                           \
+    const size_t sm = sizeof(cplx<dfl>) * ((size_t)((N + 1) & ~1) + (size_t)N * ((5 * lz) | 1)); \
+    k_zfwd4_df<A, B><<<nblk, FFT_THREADS, sm, s>>>(P);                                           \
+    return true;                                                                                 \
+  }
+    RVE_FS_SIZES(RVE_FS_ZFD)
+#undef RVE_FS_ZFD
+    default:
+      return false;
+  }
+}
+
+bool launch_zinv4_df(const GridGeom& g, int out_mode, const cplx<dfl>* spec, double* out64,
+                     float* r_out, float* x_out, SolverState* st, double* partials,
+                     const cplx<dfl>* tw, cudaStream_t s) {
+  const int nlines = g.nx * g.ny;
+  switch (g.nz) {
+#define RVE_FS_ZID(N, A, B)                                                                      \
+  case N: {                                                                                      \
+    constexpr int lz = fs_zd_lz(N);                                                              \
+    const int nblk = std::min((nlines + lz - 1) / lz, 2 * sm_count());                           \
+    const size_t sm = sizeof(cplx<dfl>) * ((size_t)((N + 1) & ~1) + (size_t)N * ((5 * lz) | 1)); \
+    if (out_mode != OUT_RESID) {                                                                 \
+      ZinvParams<dfl, double> P{};                                                               \
+      P.g = g;                                                                                   \
+      P.spec = spec;                                                                             \
+      P.dst64 = out64;                                                                           \
+      P.st = st;                                                                                 \
+      P.partials = partials;                                                                     \
+      P.tw = tw;                                                                                 \
+      if (out_mode == OUT_PLAIN_MEANX)                                                           \
+        k_zinv4_df<A, B, double, OUT_PLAIN_MEANX><<<nblk, FFT_THREADS, sm, s>>>(P);              \
+      else                                                                                       \
+        k_zinv4_df<A, B, double, OUT_PLAIN><<<nblk, FFT_THREADS, sm, s>>>(P);                    \
+    } else {                                                                                     \
+      ZinvParams<dfl, float> P{};                                                                \
+      P.g = g;                                                                                   \
+      P.spec = spec;                                                                             \
+      P.r_out = r_out;                                                                           \
+      P.x_out = x_out;                                                                           \
+      P.st = st;                                                                                 \
+      P.partials = partials;                                                                     \
+      P.tw = tw;                                                                                 \
+      k_zinv4_df<A, B, float, OUT_RESID><<<nblk, FFT_THREADS, sm, s>>>(P);                       \
+    }                                                                                            \
+    return true;                                                                                 \
+  }
+    RVE_FS_SIZES(RVE_FS_ZID)
+#undef RVE_FS_ZID
+    default:
+      return false;
+  }
+}
+
+bool launch_fft_x4_df(const GridGeom& g, double scale, cplx<dfl>* spec, const cplx<dfl>* tw,
+                      cudaStream_t s) {
+  LineParams<dfl> P;
+  P.g = g;
+  P.grp = 1;
+  P.scale = scale;
+  P.spec = spec;
+  P.done = nullptr;
+  P.tw = tw;
+  switch (g.nx) {
+#define RVE_FS_XD(N, A, B)                                                                       \
+  case N: {                                                                                      \
+    constexpr int T = fs_x_t_df(N);                                                              \
+    P.t = T;                                                                                     \
+    const int ntiles = 3 * g.ny * ((g.hz + T - 1) / T);                                          \
+    const size_t sm = sizeof(cplx<dfl>) * ((size_t)((N + 1) & ~1) + 2 * (size_t)N * T + B) +      \
+                      sizeof(dfl) * ((size_t)N + T + 1);                                         \
+    k_fft_x4_df<A, B><<<ntiles, FFT_THREADS, sm, s>>>(P);                                        \
+    return true;                                                                                 \
+  }
+    RVE_FS_SIZES(RVE_FS_XD)
+#undef RVE_FS_XD
+    default:
+      return false;
+  }
+}
+
 // SMs of the current device (persistent grids: three blocks per SM)
 static int sm_count() {
   static int cache[64] = {0};
@@ -1031,7 +1584,14 @@ cudaError_t fft4_kernels_init() {
   allow_smem(k_zfwd4<float, SRC_CGPX, TAN_SVK, A, B>);      \
   allow_smem(k_zfwd4<float, SRC_CGPX, TAN_SYM45, A, B>);    \
   allow_smem(k_zinv4_cgr<float, A, B>);                     \
-  allow_smem(k_zfwd4p<A, B>);
+  allow_smem(k_zfwd4p<A, B>);                               \
+  allow_smem(k_fft_y4_df<A, B, true>);                      \
+  allow_smem(k_fft_y4_df<A, B, false>);                     \
+  allow_smem(k_fft_x4_df<A, B>);                            \
+  allow_smem(k_zfwd4_df<A, B>);                             \
+  allow_smem(k_zinv4_df<A, B, double, OUT_PLAIN>);          \
+  allow_smem(k_zinv4_df<A, B, double, OUT_PLAIN_MEANX>);    \
+  allow_smem(k_zinv4_df<A, B, float, OUT_RESID>);
   RVE_FS_SIZES(RVE_FS_INIT)
 #undef RVE_FS_INIT
   allow_smem(k_fs4_batch_zfwd);

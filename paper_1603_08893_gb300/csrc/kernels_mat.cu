@@ -227,6 +227,79 @@ __global__ void __launch_bounds__(VEC_THREADS) k_svk(const double* __restrict__ 
   if (flags) atomicOr(&st->err_flags, flags);
 }
 
+// The same update for the mixed solver with the tangent recomputed from F
+// in the CG (Fop = F in float32, no stored K4 or S) in float-float
+// arithmetic, written in the displacement gradient H = F - I (exact in
+// float64 for the diagonal, F_aa in [1/2, 2]): E = (H + H^T + H^T H) / 2
+// and P = S + H S, so that the cancellation in F^T F - I costs nothing
+// and P is accurate to about 2^-46 relative, the accuracy of the
+// float-float residual G:P it feeds.  F, H and the parameters are split and
+// P assembled from the float64 bits by integer operations (dfloat.cuh), so
+// the float64 units, a small fraction of the float32 rate on this
+// hardware, only form the three diagonal entries of H and add the two
+// parts of each P entry.  det F (the failure test) is taken in float32
+// from the high parts of F.
+__global__ void __launch_bounds__(VEC_THREADS) k_svk_df(const double* __restrict__ F, size_t n,
+                                                        MatView<double> mat,
+                                                        double* __restrict__ P,
+                                                        float* __restrict__ Fop,
+                                                        SolverState* st) {
+  int flags = 0;
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (size_t v = (size_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += stride) {
+    double fd[9];
+#pragma unroll
+    for (int c = 0; c < 9; ++c) fd[c] = F[(size_t)c * n + v];
+    const double lamd = mat.get(v, 0), mud = mat.get(v, 1);
+    dfl hm[9];
+    float fh[9];
+#pragma unroll
+    for (int c = 0; c < 9; ++c) {
+      fh[c] = dfl_from_bits(fd[c]).hi;
+      hm[c] = dfl_from_bits(c % 4 == 0 ? fd[c] - 1.0 : fd[c]);
+    }
+    const dfl lam = dfl_from_bits(lamd), mu = dfl_from_bits(mud);
+    dfl E[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = a; b < 3; ++b) {
+        const dfl e = (hm[3 * a + b] + hm[3 * b + a]) +
+                      (hm[a] * hm[b] + hm[3 + a] * hm[3 + b] + hm[6 + a] * hm[6 + b]);
+        E[a][b] = E[b][a] = dfl(0.5f * e.hi, 0.5f * e.lo);
+      }
+    const dfl ltr = lam * (E[0][0] + E[1][1] + E[2][2]);
+    const dfl mu2(2.0f * mu.hi, 2.0f * mu.lo);
+    dfl S[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = a; b < 3; ++b) {
+        dfl sv = mu2 * E[a][b];
+        if (a == b) sv = sv + ltr;
+        S[a][b] = S[b][a] = sv;
+      }
+    float pmax = 0.0f;
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        const dfl pv =
+            S[a][b] + (hm[3 * a] * S[0][b] + hm[3 * a + 1] * S[1][b] + hm[3 * a + 2] * S[2][b]);
+        P[(size_t)(3 * a + b) * n + v] = (double)pv;
+        pmax = fmaxf(pmax, fabsf(pv.hi));
+      }
+    const float det = fh[0] * (fh[4] * fh[8] - fh[5] * fh[7]) -
+                      fh[1] * (fh[3] * fh[8] - fh[5] * fh[6]) +
+                      fh[2] * (fh[3] * fh[7] - fh[4] * fh[6]);
+    if (!(det > 0.0f)) flags |= 1;
+    if (!isfinite(pmax) || !isfinite(det)) flags |= 2;
+#pragma unroll
+    for (int c = 0; c < 9; ++c) Fop[(size_t)c * n + v] = fh[c];
+  }
+  if (flags) atomicOr(&st->err_flags, flags);
+}
+
 // FP64 K4 of a voxel range [v0, v0+count) into dst[81][count].
 __global__ void __launch_bounds__(VEC_THREADS) k_svk_k4(const double* __restrict__ F, size_t v0,
                                                         size_t count, size_t n,
@@ -280,22 +353,8 @@ __global__ void __launch_bounds__(VEC_THREADS) k_cg_init(size_t n9, const double
     acc += ri * ri;
   }
   double a[1] = {acc}, tot[1];
-  if (last_block_sum<1>(a, partials, &st->counter[SLOT_BB], tot) && threadIdx.x == 0) {
-    const double bb = tot[0];
-    st->bb = bb;
-    st->rr = bb;
-    st->rr_min = bb;
-    st->it_min = 0;
-    st->it = 0;
-    st->beta = 0.0;
-    st->status = 0;
-    st->tol2 = fmax(st->cg_tol * st->cg_tol * bb, st->cg_atol * st->cg_atol);
-    st->done = (bb == 0.0) ? 1 : 0;
-    if (!isfinite(bb)) {
-      st->status = RVE_DEV_ERR_NONFINITE;
-      st->done = 1;
-    }
-  }
+  if (last_block_sum<1>(a, partials, &st->counter[SLOT_BB], tot) && threadIdx.x == 0)
+    cg_after_bb(st, tot[0]);
 }
 
 // y += (double) x
@@ -432,6 +491,12 @@ template <typename RO>
 void launch_svk_constitutive(const double* F, size_t n, MatView<double> mat, double* P,
                              int tan_mode, RO* K4, RO* Fop, RO* Sop, SolverState* st,
                              cudaStream_t s) {
+  if constexpr (std::is_same<RO, float>::value) {
+    if (tan_mode == TAN_SVK && Fop && !Sop) {
+      k_svk_df<<<grid_for(n), VEC_THREADS, 0, s>>>(F, n, mat, P, Fop, st);
+      return;
+    }
+  }
   k_svk<RO><<<grid_for(n), VEC_THREADS, 0, s>>>(F, n, mat, P, tan_mode, K4, Fop, Sop, st);
 }
 

@@ -430,13 +430,17 @@ void enqueue_residual(rve_t h) {
 // buf <- G : buf in float64 (Eq. weak:discr:FFT-intermediate), in place;
 // in float-float arithmetic for mixed handles unless hardware float64 is
 // asked for.
-void enqueue_project_fp64(rve_t h, double* buf, bool allow_floatfloat = true) {
+// With mean_x, also the component means of the result into st->meanX
+// where the float-float passes can fuse them; returns whether they did.
+bool enqueue_project_fp64(rve_t h, double* buf, bool allow_floatfloat = true,
+                          bool mean_x = false) {
   const GridGeom& g = h->g;
   if (h->floatfloat && allow_floatfloat) {
-    launch_G_df(g, buf, 1.0 / (double)h->n, OUT_PLAIN, buf, nullptr, nullptr, h->st, h->partials,
-                reinterpret_cast<cplx<dfl>*>(h->spec64), h->twdf, h->s);
+    const bool m = launch_G_df(g, buf, 1.0 / (double)h->n, mean_x ? (int)OUT_PLAIN_MEANX : (int)OUT_PLAIN,
+                               buf, nullptr, nullptr, h->st, h->partials,
+                               reinterpret_cast<cplx<dfl>*>(h->spec64), h->twdf, h->s);
     h->launches += 5;
-    return;
+    return m;
   }
   TangentView<double> plain{};
   plain.mode = 0;
@@ -448,6 +452,24 @@ void enqueue_project_fp64(rve_t h, double* buf, bool allow_floatfloat = true) {
   launch_zinv<double, double>(g, OUT_PLAIN, h->spec64, buf, nullptr, nullptr, nullptr, h->st,
                               h->partials, nullptr, h->twd, h->s);
   h->launches += 5;
+  return false;
+}
+
+// Newton update of a mixed handle from its float32 CG solution x: dF = x in
+// float64, projected onto the compatible fields (float32 CG leaves dF
+// compatible only up to float32 round-off amplified by the cancellation in
+// the CG sum; Sec. 2.3), its mean (zero up to round-off, Eq. mean:zero)
+// removed, F += dF (+ dF-bar on the first iteration of an increment).
+template <typename R>
+void enqueue_mixed_update(rve_t h, bool first) {
+  launch_convert<R, double>(as<R>(h->x), h->tmp64, 9 * h->n, h->s);
+  if (!enqueue_project_fp64(h, h->tmp64, true, true)) {
+    launch_mean9<double>(h->tmp64, h->n, nullptr, h->partials, &h->st->counter[SLOT_MEAN],
+                         MEAN_X, h->st, h->s);
+    h->launches += 1;
+  }
+  launch_newton_update<double>(h->F, h->tmp64, h->n, h->st, h->partials, first, h->s);
+  h->launches += 2;
 }
 
 // Float64 view of the SVK tangent at the current F (mixed handles keep only
@@ -1422,12 +1444,7 @@ static int solve_increment_t(rve_t h, double tol_newton, double tol_cg, rve_stat
       // float32 CG leaves dF compatible only up to float32 round-off
       // amplified by the cancellation in the CG sum; project it onto the
       // compatible fields in float64 so that F stays compatible (Sec. 2.3)
-      launch_convert<R, double>(as<R>(h->x), h->tmp64, n9, h->s);
-      enqueue_project_fp64(h, h->tmp64);
-      launch_mean9<double>(h->tmp64, h->n, nullptr, h->partials, &h->st->counter[SLOT_MEAN],
-                           MEAN_X, h->st, h->s);
-      launch_newton_update<double>(h->F, h->tmp64, h->n, h->st, h->partials, i == 0, h->s);
-      h->launches += 3;
+      enqueue_mixed_update<R>(h, i == 0);
     } else {
       launch_mean9<R>(as<R>(h->x), h->n, nullptr, h->partials, &h->st->counter[SLOT_MEAN], MEAN_X,
                       h->st, h->s);
@@ -1436,7 +1453,6 @@ static int solve_increment_t(rve_t h, double tol_newton, double tol_cg, rve_stat
     }
     enqueue_constitutive(h);
     enqueue_residual<R>(h);
-    h->launches += 2;
     rc = sync_state(h);
     if (rc) {
       result = rc;
@@ -2460,21 +2476,16 @@ int batch_solve_t(rve_batch_t b, const double* Fbar, double tol_newton, double t
         result[c] = status[c];
         continue;
       }
-      const size_t n9 = 9 * h->n;
       if (h->mixed) {
-        launch_convert<R, double>(as<R>(h->x), h->tmp64, n9, h->s);
-        enqueue_project_fp64(h, h->tmp64);
-        launch_mean9<double>(h->tmp64, h->n, nullptr, h->partials, &h->st->counter[SLOT_MEAN],
-                             MEAN_X, h->st, h->s);
-        launch_newton_update<double>(h->F, h->tmp64, h->n, h->st, h->partials, i == 0, h->s);
+        enqueue_mixed_update<R>(h, i == 0);
       } else {
         launch_mean9<R>(as<R>(h->x), h->n, nullptr, h->partials, &h->st->counter[SLOT_MEAN],
                         MEAN_X, h->st, h->s);
         launch_newton_update<R>(h->F, as<R>(h->x), h->n, h->st, h->partials, i == 0, h->s);
+        h->launches += 2;
       }
       enqueue_constitutive(h);
       enqueue_residual<R>(h);
-      h->launches += 4;
       still.push_back(c);
     }
     active.clear();

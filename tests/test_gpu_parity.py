@@ -69,7 +69,13 @@ def test_projection_matches_oracle(shape):
     r.close()
 
 
-@pytest.mark.parametrize("shape", SHAPES)
+# x and y lengths with four-step float-float passes (several tiles, ragged
+# last kz tile, even z lengths for the Nyquist planes)
+FF_FOURSTEP_SHAPES = [(125, 125, 6), (125, 15, 125), (243, 243, 3), (315, 21, 4),
+                      (15, 315, 2), (63, 45, 9), (33, 27, 20)]
+
+
+@pytest.mark.parametrize("shape", SHAPES + FF_FOURSTEP_SHAPES)
 def test_floatfloat_projection_matches_oracle(shape):
     """G:A in the float-float arithmetic of the mixed path (hi + lo float
     pairs, rounding ~2^-47 relative to the operands per operation): the
@@ -123,6 +129,23 @@ def test_constitutive_matches_oracle(shape):
     P_ref, K4_ref = svk.constitutive(F, K, mu)
     assert maxrel(r.get_P(), P_ref) < 1e-13
     assert maxrel(r.get_K4(), K4_ref) < 1e-13
+    assert np.array_equal(r.get_F(), F)
+    r.close()
+
+
+@pytest.mark.parametrize("amp", [3e-3, 0.15])
+@pytest.mark.parametrize("shape", [(15, 15, 15), (33, 21, 27)])
+def test_constitutive_mixed_matches_oracle(shape, amp):
+    """P of a mixed handle with the recomputed tangent (float-float update
+    written in H = F - I), Eq. elas:S-P, against the oracle's stress
+    evaluated in extended precision (in float64 its F^T F - I cancels about
+    log10(1/|E|) digits at small strains).  At strains of 3e-3 an update
+    formed from F itself (2^-47 of |F^T F| ~ 1) would be off by about 2e-12
+    of the largest stress; the H form stays near 1e-14."""
+    r, F, K, mu, rng = _random_problem(shape, 6, "mixed", "recompute", amp=amp)
+    ld = np.longdouble
+    P_ref = svk.stress(F.astype(ld), K.astype(ld), mu.astype(ld))
+    assert maxrel(r.get_P(), P_ref) < 1e-13
     assert np.array_equal(r.get_F(), F)
     r.close()
 
