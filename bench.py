@@ -545,6 +545,45 @@ def bench_tangent125(args, torch, RVE):
                                        "full81": 253.3 - 37 + 324})
 
 
+def bench_project125(args, torch, RVE):
+    """The float64-accuracy projection G:A of the mixed solver (the residual
+    G:P and the projection of dF take the same passes) on the 125^3 and
+    243^3 grids: float-float arithmetic on the float32 pipe (the default of
+    mixed handles) against hardware float64 (residual="fp64"), device
+    buffers, the two device copies of rve_project (A in, result out)
+    included; the largest difference of the two results."""
+    out = {}
+    for nn in (125, 243):
+        shape = (nn, nn, nn)
+        rng = np.random.default_rng(7)
+        A = rng.standard_normal((3, 3) + shape)
+        At = torch.from_numpy(A).cuda()
+        o = torch.empty_like(At)
+        row = {}
+        got = {}
+        for res in ("floatfloat", "fp64"):
+            r = RVE(shape, phase=np.zeros(shape, np.uint8), phase_params=[[1.0, 0.5]],
+                    precision="mixed", residual=res)
+            for _ in range(3):
+                r.project(At, o)
+            torch.cuda.synchronize()
+            reps = 20 if nn == 125 else 5
+            t0 = time.perf_counter()
+            for _ in range(reps):
+                r.project(At, o)
+            torch.cuda.synchronize()
+            row[res + "_ms"] = (time.perf_counter() - t0) / reps * 1e3
+            got[res] = o.clone()
+            r.close()
+        d = (got["floatfloat"] - got["fp64"]).abs().max() / got["fp64"].abs().max()
+        row["maxrel_floatfloat_vs_fp64"] = float(d)
+        row["copy_bytes"] = 2 * A.nbytes
+        del got
+        out[str(nn)] = row
+    _line("project125_floatfloat", "ms per G application (two 9-component device copies included)",
+          out["125"]["floatfloat_ms"], "ms", dtype="float-float (f32 pairs) / f64", grids=out)
+
+
 def bench_mixed125(args, torch, RVE):
     """Mixed macroscopic control on the 125^3 spheres, mixed precision:
     uniaxial stress along x (F11 = 1.01 prescribed, the lateral and shear
@@ -678,7 +717,7 @@ def main():
                     help="increments of the pure-shear ramp of --workload contrast63")
     ap.add_argument("--workload", default="svk125",
                     choices=["svk125", "cube31", "j2_315", "batch256", "adjoint243", "tangent125",
-                             "mixed125", "precond125", "contrast63"],
+                             "mixed125", "precond125", "contrast63", "project125"],
                     help="svk125 (default) is the headline; the others print one line each")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -693,7 +732,8 @@ def main():
               "tangent125": lambda: bench_tangent125(args, torch, RVE),
               "mixed125": lambda: bench_mixed125(args, torch, RVE),
               "precond125": lambda: bench_precond125(args, torch, RVE),
-              "contrast63": lambda: bench_contrast63(args, torch, RVE)}[args.workload]
+              "contrast63": lambda: bench_contrast63(args, torch, RVE),
+              "project125": lambda: bench_project125(args, torch, RVE)}[args.workload]
         fn()
         return None
 
