@@ -107,8 +107,9 @@ typedef struct {
                            first passes (further refinement with the float64 residual);
                            default 0 */
   int residual;         /* MIXED only: arithmetic of the float64-accuracy transforms (the
-                           residual G:P and the projection of dF): RVE_RES_FLOATFLOAT
-                           (default) or RVE_RES_FP64 */
+                           residual G:P and the projection of dF) and of the SVK
+                           constitutive update with the recomputed tangent:
+                           RVE_RES_FLOATFLOAT (default) or RVE_RES_FP64 */
   int autotune;         /* MIXED only: 1 = time the float32 CG iteration's kernel
                            variants (DFT engine per axis, z-pass grid and staging) at
                            rve_create on this grid and keep the fastest; the choice

@@ -266,6 +266,10 @@ template <typename RO>
 void launch_svk_constitutive(const double* F, size_t n, MatView<double> mat, double* P,
                              int tan_mode, RO* K4, RO* Fop, RO* Sop, SolverState* st,
                              cudaStream_t s);
+// the SVK update of mixed handles with the recomputed tangent in float-float
+// arithmetic (P float64, Fop = F in float32; no K4, no S)
+void launch_svk_constitutive_df(const double* F, size_t n, MatView<double> mat, double* P,
+                                float* Fop, SolverState* st, cudaStream_t s);
 void launch_svk_k4_full(const double* F, size_t v0, size_t count, size_t n,
                         MatView<double> mat, double* dst, cudaStream_t s);
 template <typename Ti, typename To>

@@ -491,13 +491,12 @@ template <typename RO>
 void launch_svk_constitutive(const double* F, size_t n, MatView<double> mat, double* P,
                              int tan_mode, RO* K4, RO* Fop, RO* Sop, SolverState* st,
                              cudaStream_t s) {
-  if constexpr (std::is_same<RO, float>::value) {
-    if (tan_mode == TAN_SVK && Fop && !Sop) {
-      k_svk_df<<<grid_for(n), VEC_THREADS, 0, s>>>(F, n, mat, P, Fop, st);
-      return;
-    }
-  }
   k_svk<RO><<<grid_for(n), VEC_THREADS, 0, s>>>(F, n, mat, P, tan_mode, K4, Fop, Sop, st);
+}
+
+void launch_svk_constitutive_df(const double* F, size_t n, MatView<double> mat, double* P,
+                                float* Fop, SolverState* st, cudaStream_t s) {
+  k_svk_df<<<grid_for(n), VEC_THREADS, 0, s>>>(F, n, mat, P, Fop, st);
 }
 
 void launch_svk_k4_full(const double* F, size_t v0, size_t count, size_t n,

@@ -542,7 +542,9 @@ int enqueue_constitutive(rve_t h) {
     h->launches += 1;
     return RVE_OK;
   }
-  if (h->mixed)
+  if (h->mixed && h->floatfloat && h->tan == TAN_SVK)
+    launch_svk_constitutive_df(h->F, h->n, m, h->P, as<float>(h->Fop), h->st, h->s);
+  else if (h->mixed)
     launch_svk_constitutive<float>(h->F, h->n, m, h->P, h->tan, as<float>(h->K4),
                                    as<float>(h->Fop), nullptr, h->st, h->s);
   else

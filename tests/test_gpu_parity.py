@@ -150,6 +150,22 @@ def test_constitutive_mixed_matches_oracle(shape, amp):
     r.close()
 
 
+def test_constitutive_mixed_float64_residual_matches_oracle():
+    """residual="fp64" keeps the float64 SVK kernel for mixed handles: its P
+    follows the float64 oracle as the float64 path does."""
+    shape = (15, 15, 15)
+    rng = np.random.default_rng(6)
+    phase = (rng.uniform(size=shape) < 0.35).astype(np.uint8)
+    params = synth.two_phase_params(7.0)
+    r = RVE(shape, phase=phase, phase_params=params, precision="mixed", tangent="recompute",
+            residual="fp64")
+    F = synth.random_F(shape, rng, 3e-3)
+    r.set_F(F)
+    P_ref, _ = svk.constitutive(F, params[phase, 0], params[phase, 1])
+    assert maxrel(r.get_P(), P_ref) < 1e-13
+    r.close()
+
+
 @pytest.fixture(scope="module")
 def cube31_oracle():
     cfg = synth.config_cube31()
