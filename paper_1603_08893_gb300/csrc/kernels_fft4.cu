@@ -130,7 +130,7 @@ RVE_DEV void fft_x4_tile(const LineParams<R>& P, const int tile) {
   const int hz = P.g.hz, hzp = P.g.hzp;
   const int ntk = (hz + T - 1) / T;
   const size_t rs = (size_t)ny * hzp;  // stride of spectrum rows (c*nx + x)
-  const int q = is_dfl<R>::value ? tile / ntk : (int)P.g.f_fsx_ntk.div((unsigned)tile);
+  const int q = (int)P.g.f_fsx_ntk.div((unsigned)tile);
   const int k0 = (tile - q * ntk) * T;
   const int irow = (int)P.g.f_ny.div((unsigned)q);
   const int y = q - irow * ny;
