@@ -3,8 +3,9 @@
 // ~ 2^-47 per operation, relative to the operands).  Built on the error-free transformations
 // of Knuth (two-sum), Dekker (fast two-sum, |a| >= |b|) and the FMA
 // two-product.  GB300 issues float32 at 64x its float64 rate, so the
-// float64-accuracy transforms of the mixed path (residual G:P and the
-// projection of dF) run on the float32 pipe in this representation.
+// float64-accuracy parts of the mixed path (the residual G:P, the
+// projection of dF, the SVK update) run on the float32 pipe in this
+// representation.
 #pragma once
 #include <type_traits>
 
@@ -66,9 +67,9 @@ RVE_DEV dfl operator*(dfl a, dfl b) {
 
 RVE_DEV dfl fma(dfl a, dfl b, dfl c) { return a * b + c; }
 
-// float64 <-> float-float by integer operations on the bit patterns (the
+// float64 -> float-float by integer operations on the bit pattern (the
 // float64 arithmetic and conversion units run at a small fraction of the
-// float32 rate on this hardware).  Split: hi is the float64 significand
+// float32 rate on this hardware): hi is the float64 significand
 // truncated to 24 bits, which a float holds exactly, lo the remaining 29
 // bits truncated to 24 (one leading-zero count), so hi + lo is within
 // 2^-47 of d relative; then renormalised.  |d| < 2^-126 gives zero (hi
@@ -93,19 +94,6 @@ RVE_DEV dfl dfl_from_bits(double d) {
   return fast_two_sum(hi, lo);
 }
 
-// a float as a float64, exactly, from its bits (zero, subnormal, inf and nan
-// take the conversion instruction)
-RVE_DEV double f2d_bits(float f) {
-  const unsigned u = __float_as_uint(f);
-  const unsigned ef = (u >> 23) & 0xffu;
-  if (ef == 0u || ef == 255u) return (double)f;
-  return __longlong_as_double((long long)(((unsigned long long)(u & 0x80000000u) << 32) |
-                                          ((unsigned long long)(ef + 896u) << 52) |
-                                          ((unsigned long long)(u & 0x7fffffu) << 29)));
-}
-
-// hi + lo rounded to float64: one float64 addition of the two exact parts
-RVE_DEV double dfl_to_double(dfl a) { return f2d_bits(a.hi) + f2d_bits(a.lo); }
 RVE_DEV dfl& operator+=(dfl& a, dfl b) { return a = a + b; }
 RVE_DEV dfl& operator-=(dfl& a, dfl b) { return a = a - b; }
 RVE_DEV dfl& operator*=(dfl& a, dfl b) { return a = a * b; }
